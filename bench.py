@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 QED step: particle-steps/s and QED events/s.
+
+Default workload: the rotating-field cascade (1e5 electrons at rest in a
+0.1-wavelength ball, E = a0 (cos t, sin t, 0) with a0 = 1000, dt = T/100,
+3 periods = 300 steps, Compton + Breit-Wheeler, leveling cap 5e7 per
+species).  One bench "step" is one PIC step of the whole ensemble through the
+library (push with sub-stepping, avalanche passes, dead-photon removal,
+leveling).  W warm-up steps (0..W-1) run untimed, then K steps are timed with
+CUDA events on the library's stream, with L2 flushed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2409_17299_gb300 import workloads as W  # noqa: E402  (no CUDA, no method arithmetic)
+
+# algorithmic bytes per particle-step of the lepton pass (read x,y,z,px,py,pz,w + id;
+# write x,y,z,px,py,pz) and per emission (nevents update + photon record + birth clock)
+LEPTON_BYTES = {"fp32": 7 * 4 + 8 + 6 * 4, "fp64": 7 * 8 + 8 + 6 * 8}
+EMIT_BYTES = {"fp32": 8 + 7 * 4 + 8 + 4 + 8, "fp64": 8 + 7 * 8 + 8 + 4 + 8}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="rotating_e_cascade",
+                    choices=["rotating_e_cascade", "uniform_b_emission", "standing_wave_cascade"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--compare-fp64", type=int, default=1, help="also time the FP64 mode (extra key)")
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--e2e", type=int, default=1)
+    ap.add_argument("--scale", type=float, default=1.0, help="scale the seed count (tests only)")
+    return ap.parse_args()
+
+
+def make_workload(name, scale=1.0, rank=0):
+    if name == "rotating_e_cascade":
+        w = W.rotating_e_cascade(n=int(100000 * scale), seed=1 + 1000 * rank,
+                                 thin_cap=int(50_000_000 * scale))
+    elif name == "standing_wave_cascade":
+        w = W.standing_wave_cascade(n=int(1_000_000 * scale), seed=4 + 1000 * rank,
+                                    thin_cap=int(200_000_000 * scale))
+    else:
+        w = W.uniform_b_emission(n=int(16384 * scale), seed=1000 * rank)
+    return w
+
+
+def default_steps(w):
+    return 3, w.nsteps - 3
+
+
+def capacities(w):
+    n0 = sum(len(s["id"]) for s in w.species)
+    if w.thin_cap:
+        c = int(1.6 * w.thin_cap) + 4 * n0
+        return [c // 3 + n0, c // 3, c]
+    return [n0, 16, int(n0 * (1 + 0.2 * w.nsteps)) + 1024]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (spawned processes; never touch CUDA)
+# ---------------------------------------------------------------------------
+def _oracle_shard(args):
+    name, scale_seed, lo, hi, warm, steps = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    w = make_workload(name, 1.0)
+    total = len(w.species[0]["id"])
+    frac = (hi - lo) / total
+    ws = W.subset(w, 0, slice(lo, hi))
+    tabs = oracle.build_tables()
+    cap = [max(1024, int(c * frac * 1.2)) for c in capacities(w)]
+    ens = oracle.Ensemble.from_arrays(ws.species, cap)
+    cfg = oracle.make_cfg(seed=w.seed, push_photons=w.push_photons, thin_cap=int(w.thin_cap * frac),
+                          field_kind=w.field_kind, field_prm=w.field_prm)
+    if warm:
+        oracle.push_and_generate(ens, tabs, cfg, w.dt, warm, 0)
+    t0 = time.perf_counter()
+    st = oracle.push_and_generate(ens, tabs, cfg, w.dt, steps, warm)
+    dt = time.perf_counter() - t0
+    return st["particle_steps"], st["emit_events"] + st["pair_events"], dt
+
+
+def oracle_run(name, warm, steps, target_s=15.0, procs=None):
+    """Time the oracle on disjoint seed subsets of the workload, one process
+    per host core.  Returns particle-steps/s, events/s, cores, sample text."""
+    import multiprocessing as mp
+    procs = procs or min(16, os.cpu_count() or 1)
+    w = make_workload(name, 1.0)
+    total = len(w.species[0]["id"])
+    # seeds per shard sized from a nominal oracle rate of ~3e6 particle-steps/s
+    if name == "rotating_e_cascade":
+        per = 250
+    elif name == "standing_wave_cascade":
+        per = 60
+    else:
+        per = 2000
+    per = max(1, min(per, total // procs))
+    jobs = [(name, 0, k * per, (k + 1) * per, warm, steps) for k in range(procs)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_shard, jobs)
+    wall = time.perf_counter() - t0
+    ps = sum(r[0] for r in res)
+    ev = sum(r[1] for r in res)
+    tmax = max(r[2] for r in res)
+    sample = ("%d disjoint subsets of %d seed electrons each (%d of %d) of %s, steps %d..%d, "
+              "FP64 oracle, one process per core" % (procs, per, procs * per, total, name, warm, warm + steps - 1))
+    return ps / tmax, ev / tmax, procs, sample, wall
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, index=0):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.index = index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_run(args, w, precision, warm, steps, timed=True, profile=True):
+    import torch
+    import paper_2409_17299_gb300 as q
+    prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
+    # capacities are sized for the whole run, so no per-call overflow snapshot
+    cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
+                        profile=int(profile), restore_on_overflow=0)
+    gen = q.Generator(cfg)
+    ens = q.DeviceEnsemble.from_host(w.species, capacities(w), prec)
+    field = q.make_field(w.field_kind, w.field_prm)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for s in range(warm):
+        gen.push(ens, field, w.dt, 1, s, auto_grow=False)
+    torch.cuda.synchronize()
+    evs = []
+    tot = {"particle_steps": 0, "emit_events": 0, "pair_events": 0, "lepton_steps": 0, "photon_steps": 0,
+           "launches": 0, "kernel_ms": [0.0, 0.0], "passes": 0, "thinned": 0}
+    lepton_launches = 0
+    t0 = time.perf_counter()
+    for s in range(warm, warm + steps):
+        flush.fill_(float(s))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = gen.push(ens, field, w.dt, 1, s, auto_grow=False)
+        b.record(stream)
+        evs.append((a, b))
+        for k in ("particle_steps", "emit_events", "pair_events", "lepton_steps", "photon_steps", "launches",
+                  "passes", "thinned"):
+            tot[k] += st[k]
+        tot["kernel_ms"][0] += st["kernel_ms"][0]
+        tot["kernel_ms"][1] += st["kernel_ms"][1]
+        lepton_launches += 1 + st["passes"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    counts = list(ens.count)
+    gen.close()
+    del ens, flush
+    torch.cuda.empty_cache()
+    tot["lepton_launches"] = lepton_launches
+    return ms, wall, tot, counts
+
+
+def e2e_run(w, precision, warm, steps):
+    """Same steps through the C ABI with the ensemble in pinned host memory:
+    every step copies it to the device, pushes one step, and copies it back."""
+    import numpy as np
+    import torch
+    import paper_2409_17299_gb300 as q
+    prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
+    cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
+                        restore_on_overflow=0)
+    gen = q.Generator(cfg)
+    caps = capacities(w)
+    dev = q.DeviceEnsemble(caps, prec)
+    fd = dev.fdtype
+    host = []
+    for s in range(3):
+        d = {f: torch.zeros(caps[s], dtype=fd).pin_memory() for f in ("x", "y", "z", "px", "py", "pz", "w")}
+        d["id"] = torch.zeros(caps[s], dtype=torch.int64).pin_memory()
+        d["nevents"] = torch.zeros(caps[s], dtype=torch.int32).pin_memory()
+        sp = w.species[s]
+        n = len(sp["id"])
+        for f in ("x", "y", "z", "px", "py", "pz", "w"):
+            d[f][:n].copy_(torch.from_numpy(np.asarray(sp[f], dtype=np.float64)).to(fd))
+        d["id"][:n].copy_(torch.from_numpy(np.asarray(sp["id"], dtype=np.uint64).view(np.int64)))
+        host.append(d)
+    count = [len(sp["id"]) for sp in w.species]
+    field = q.make_field(w.field_kind, w.field_prm)
+    stream = torch.cuda.current_stream()
+
+    def one_step(s, nb):
+        for k in range(3):
+            n = count[k]
+            for f in host[k]:
+                dev.arr[k][f][:n].copy_(host[k][f][:n], non_blocking=True)
+                nb[0] += n * host[k][f].element_size()
+        dev.count = list(count)
+        gen.push(dev, field, w.dt, 1, s, auto_grow=False)
+        for k in range(3):
+            n = dev.count[k]
+            for f in host[k]:
+                host[k][f][:n].copy_(dev.arr[k][f][:n], non_blocking=True)
+                nb[1] += n * host[k][f].element_size()
+            count[k] = n
+        stream.synchronize()
+
+    nbw = [0, 0]
+    for s in range(warm):
+        one_step(s, nbw)
+    torch.cuda.synchronize()
+    nb = [0, 0]
+    ps = 0
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    t0 = time.perf_counter()
+    for s in range(warm, warm + steps):
+        before = q.qed_get_stats(gen.ctx)["particle_steps"]
+        one_step(s, nb)
+        ps += q.qed_get_stats(gen.ctx)["particle_steps"] - before
+    b.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    gen.close()
+    return ps, a.elapsed_time(b), wall, nb
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w0 = make_workload(args.workload, args.scale)
+    dw, ds = default_steps(w0)
+    warm = args.warmup if args.warmup is not None else dw
+    steps = args.steps if args.steps is not None else ds
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ps_rate, ev_rate, cores, sample, wall = oracle_run(args.workload, warm, steps)
+        line = {"impl": "reference", "metric": "particle-steps/s", "value": ps_rate, "unit": "particle-steps/s",
+                "n_gpus": args.gpus, "steps": steps, "warmup": warm, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "precision": "fp64", "l2": "n/a (CPU)"},
+                "events_per_s": ev_rate,
+                "cpu_baseline": {"value": ps_rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": ps_rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    # CPU baseline first: its process pool is spawned before CUDA is initialised
+    cpu = None
+    if args.cpu_baseline and rank == 0 and world == 1:
+        cpu = oracle_run(args.workload, warm, steps)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("gloo")
+    from paper_2409_17299_gb300 import build
+    build.build()
+    import paper_2409_17299_gb300 as q  # noqa: F401
+
+    w = make_workload(args.workload, args.scale, rank)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms, wall, tot, counts = gpu_run(args, w, args.precision, warm, steps)
+    torch.cuda.synchronize()
+    secs = ms / 1e3
+    work = torch.tensor([float(tot["particle_steps"]), float(tot["emit_events"] + tot["pair_events"]), secs])
+    if world > 1:
+        t = torch.tensor([secs])
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s = work[:2].clone()
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        work = torch.cat([s, t])
+    ps_total, ev_total, tmax = float(work[0]), float(work[1]), float(work[2])
+
+    fp64 = None
+    if args.compare_fp64 and args.precision == "fp32" and world == 1:
+        ms64, wall64, tot64, _ = gpu_run(args, w, "fp64", warm, steps)
+        fp64 = {"value": tot64["particle_steps"] / (ms64 / 1e3), "events_per_s":
+                (tot64["emit_events"] + tot64["pair_events"]) / (ms64 / 1e3), "ms_per_step": ms64 / steps}
+
+    e2e = None
+    if args.e2e:
+        ps_e, ms_e, wall_e, nb = e2e_run(w, args.precision, warm, steps)
+        e2e = {"value": ps_e / (ms_e / 1e3) * world, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": nb[0] // max(1, steps), "d2h_bytes_per_step": nb[1] // max(1, steps)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    prec = args.precision
+    lep_bytes = LEPTON_BYTES[prec] * tot["lepton_steps"] + EMIT_BYTES[prec] * tot["emit_events"]
+    lep_ms = tot["kernel_ms"][0]
+    achieved = lep_bytes / (lep_ms / 1e3) / 1e9 if lep_ms > 0 else None
+    line = {
+        "metric": "particle-steps/s", "value": ps_total / tmax, "unit": "particle-steps/s",
+        "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": tmax * 1e3 / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "precision": prec + ("+fp64-chi-clock" if prec == "fp32" else ""),
+                   "seed_electrons": len(w.species[0]["id"]), "thin_cap": w.thin_cap,
+                   "steps_total": w.nsteps, "dt": "T/%d" % round(2 * math.pi / w.dt),
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "events_per_s": ev_total / tmax,
+        "final_counts": counts,
+        "gpu_launches": tot["launches"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                     "kernel": "k_lepton_pass<%s>" % ("float" if prec == "fp32" else "double"),
+                     "peak_source": peak_src + " hbm_gbs",
+                     "bytes_per_particle_step": LEPTON_BYTES[prec], "bytes_per_emission": EMIT_BYTES[prec],
+                     "lepton_kernel_ms": lep_ms, "photon_kernel_ms": tot["kernel_ms"][1],
+                     "lepton_launches": tot["lepton_launches"]},
+        "clocks": clk.summary(),
+    }
+    if fp64:
+        line["fp64"] = fp64
+        line["fp32_speedup_over_fp64"] = line["value"] / fp64["value"]
+    if e2e:
+        line["e2e"] = e2e
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": "particle-steps/s", "cores": cpu[2], "kind": "oracle",
+                                "sample": cpu[3], "events_per_s": cpu[1]}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * sfqed.h -- C ABI of the GB300 strong-field QED event generator.
+ *
+ * The library implements the per-macroparticle QED step of the optimized
+ * event generator of arXiv:2409.17299 (Sec. 3, Algorithms 1 and 2): chi from
+ * the local fields and momentum, the Compton and Breit-Wheeler rates from an
+ * approximation of precomputed rates, an exponential event clock sub-stepped
+ * inside each PIC step, inverse-CDF energy sampling, and the append of the
+ * new particles to the ensemble (Sec. 4.1-4.2), plus compaction and global
+ * leveling (Sec. 4.2, Sec. 5.1).  All work runs in CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every call
+ *  - Units: time 1/omega, length c/omega, momentum m c, energy m c^2, fields
+ *    m c omega / e, wavelength 0.8 um.  One laser period is 2 pi.
+ *  - Pointers named *_dev are device pointers; everything else is host memory.
+ *  - Particle memory (qed_species) is owned by the caller and is never freed,
+ *    reallocated or resized by the library.  The context owns its tables,
+ *    work buffers and statistics.
+ *  - Every call returns a qed_status; nothing is thrown across the ABI and no
+ *    kernel traps.  qed_strerror() names a status.
+ *  - All device work is issued on the stream given to qed_init_tables().
+ *    Calls that return host-side values (counts, statistics) synchronise
+ *    that stream before returning.
+ *  - Randomness is counter-based (Philox4x32-10, key = seed, counter =
+ *    (id low, id high, step, k)), so results do not depend on thread
+ *    scheduling or append order, and any call can be replayed exactly.
+ */
+#ifndef SFQED_H
+#define SFQED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qed_ctx qed_ctx;   /* opaque; owns tables, work buffers, statistics */
+
+typedef enum {
+    QED_OK = 0,
+    QED_ERR_INVALID = 1,    /* bad argument: null pointer, unknown kind, misaligned buffer, ... */
+    QED_ERR_CAPACITY = 2,   /* a species ran out of capacity; see qed_stats.needed_capacity */
+    QED_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    QED_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
+    QED_ERR_NOMEM = 5,      /* the context could not allocate its own work memory */
+    QED_ERR_STATE = 6       /* call not valid in the context's current state */
+} qed_status;
+
+enum { QED_FP64 = 0,        /* all arithmetic and storage in FP64 */
+       QED_FP32 = 1 };      /* FP32 storage, push, rates and sampling; chi and the
+                               event clock in FP64 */
+enum { QED_SAMPLER_TABLE = 0, QED_SAMPLER_MLP = 1 };
+enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 };
+
+/* Analytic field descriptors (the device cannot call a host field_fn).
+ *  QED_FIELD_UNIFORM     params[0..2] = E, params[3..5] = B (constant)
+ *  QED_FIELD_ROTATING_E  params[0] = a0:  E = a0 (cos t, sin t, 0), B = 0
+ *  QED_FIELD_STANDING_CP params[0] = a0:  standing circularly polarised wave
+ *                        E = a0 cos x (0, cos t, sin t), B = a0 sin x (0, cos t, sin t)
+ *                        (electric antinode at x = 0; Sec. 5.1 test problem) */
+enum { QED_FIELD_UNIFORM = 0, QED_FIELD_ROTATING_E = 1, QED_FIELD_STANDING_CP = 2 };
+
+typedef struct {
+    int precision;            /* QED_FP64 or QED_FP32 */
+    int sampler;              /* QED_SAMPLER_TABLE (QED_SAMPLER_MLP once trained) */
+    uint64_t seed;            /* Philox key */
+    int push_photons;         /* 1: photons are pushed and may create pairs;
+                                 0: emitted photons are recorded, not pushed */
+    int soft_photon_filter;   /* 1: emitted photons below 2 m c^2 are dropped (Sec. 4.2) */
+    int64_t thin_cap;         /* global leveling cap per species; 0 = off (Sec. 5.1) */
+    int restore_on_overflow;  /* 1: on QED_ERR_CAPACITY the particle buffers are put
+                                 back to their state at the start of the call */
+    int block_threads;        /* threads per block of the push kernels; 0 = default */
+    int blocks_per_sm;        /* resident blocks per SM of the push kernels; 0 = default */
+    int profile;              /* 1: time the push kernels with CUDA events on the context's
+                                 stream (qed_stats.kernel_ms) */
+    int reserved[5];
+} qed_config;
+
+/* One species: structure of arrays (Sec. 4.1), one array set per particle
+ * type.  x..w are double (QED_FP64) or float (QED_FP32) device arrays of
+ * `capacity` elements, each 16-byte aligned; id and nevents likewise.
+ * `count` is read on entry and updated on return. */
+typedef struct {
+    void *x, *y, *z, *px, *py, *pz, *w;
+    uint64_t *id;             /* unique 64-bit particle id (keys the random streams) */
+    uint32_t *nevents;        /* cumulative number of QED events of this particle */
+    int64_t count, capacity;
+} qed_species;
+
+typedef struct { qed_species s[3]; } qed_particles;  /* e-, e+, photon */
+
+typedef struct { int kind; double params[16]; } qed_field_desc;
+
+typedef struct {
+    int64_t particle_steps;   /* sum over steps of particles pushed (newborns included) */
+    int64_t emit_events;      /* photon emissions (nonlinear Compton) */
+    int64_t pair_events;      /* pair creations (nonlinear Breit-Wheeler) */
+    int64_t needed_capacity[3];
+    int64_t max_subevents;    /* largest number of events of one particle in one step */
+    int64_t overflow;         /* 1 if a species ran out of capacity */
+    int64_t passes;           /* newborn passes run (Algorithm 2 sweeps) */
+    int64_t thinned;          /* particles removed by leveling */
+    int64_t lepton_steps;     /* particle-steps done by the lepton kernel */
+    int64_t photon_steps;     /* particle-steps done by the photon kernel */
+    int64_t launches;         /* kernels launched by the call */
+    double kernel_ms[2];      /* with cfg.profile: summed device time of the lepton and
+                                 photon push kernels (CUDA events) */
+} qed_stats;
+
+/* Create a context and build its rate approximant and inverse-CDF tables on
+ * the device (Sec. 3: "polynomial approximations" of precomputed rates and
+ * 2-D inverse-CDF tables over chi and energy).
+ *  ctx          out: new context (host pointer to opaque handle)
+ *  cfg          in: configuration (copied)
+ *  cuda_stream  in: cudaStream_t for all work of this context (NULL = default stream)
+ * Tables: rate = Chebyshev interpolant of degree 10 per decade of log10 chi
+ * (emission F/chi on [1e-3,1e3], pair ln F + 8/(3 chi) on [1e-2,1e3]);
+ * inverse CDF bilinear in (log10 chi, logit u) on 121 x 257 (emission,
+ * stores ln y, y = 2 delta/(3 chi (1-delta))) and 101 x 129 (pair, u <= 1/2,
+ * stores ln delta) nodes, each node the root of the exact LCFA CDF. */
+qed_status qed_init_tables(qed_ctx **ctx, const qed_config *cfg, void *cuda_stream);
+
+/* Push every particle through `nsteps` PIC steps of length dt, starting at
+ * step index step0 (time t = step * dt), generating photons and pairs
+ * (Sec. 3, Algorithm 1 per particle, Algorithm 2 for the avalanche: every
+ * particle born inside a step is pushed to the end of that step).  Dead
+ * photons are removed and, with thin_cap > 0, each species is leveled after
+ * every step.  Counts in *p are updated.  On QED_ERR_CAPACITY the demand is in
+ * out->needed_capacity and, with restore_on_overflow, *p is as on entry; grow
+ * the buffers and call again to obtain the identical result.
+ *  out may be NULL. */
+qed_status qed_push_and_generate(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field,
+                                 double dt, int nsteps, int64_t step0, qed_stats *out);
+
+/* Remove dead particles (weight 0) from every species, then, with thin_cap > 0,
+ * apply global leveling at step index `step` (Sec. 4.2 merge step, Sec. 5.1).
+ * Leveling: threshold w* with sum_i min(1, w_i/w*) = cap; particle i kept with
+ * probability min(1, w_i/w*) (Philox counter word 3 = 0xFFFFFFFF); kept
+ * particles below w* get weight w*.  Counts in *p are updated. */
+qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step);
+
+/* Statistics accumulated since the context was created or last reset. */
+qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset);
+
+const char *qed_strerror(qed_status s);
+void qed_destroy(qed_ctx *ctx);
+
+/* ---- component entry points, used by the parity tests ---------------- */
+
+/* Philox4x32-10 on the device: out_dev[4i..4i+3] = Philox(ctr_dev[4i..4i+3], key)
+ * with key words (key low, key high).  n counters; both arrays 4n uint32. */
+qed_status qed_philox(const uint32_t *ctr_dev, int64_t n, uint64_t key, uint32_t *out_dev,
+                      void *cuda_stream);
+
+/* Copy the context's FP64 tables to host arrays of 66, 55, 121*257 and
+ * 101*129 doubles (any pointer may be NULL). */
+qed_status qed_get_tables(qed_ctx *ctx, double *cheb_em, double *cheb_pair,
+                          double *icdf_em, double *icdf_pair);
+
+/* Rate approximant F(chi) at n points, in the context's precision
+ * (chi_dev, F_dev: n doubles on the device).  is_photon selects the pair rate. */
+qed_status qed_eval_rate(qed_ctx *ctx, int is_photon, const double *chi_dev, int64_t n, double *F_dev);
+
+/* Energy fraction delta (and 1 - delta) drawn by inverse CDF at (chi, u), in
+ * the context's precision: emission (photon fraction) or pair (electron
+ * fraction).  All arrays n doubles on the device. */
+qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const double *u_dev,
+                      int64_t n, double *delta_dev, double *one_minus_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFQED_H */

@@ -1,0 +1,322 @@
+"""GB300 strong-field QED event generator (arXiv:2409.17299 method).
+
+Thin Python binding of the C ABI declared in ``include/sfqed.h``.  Every
+function with a ``qed_`` name marshals its arguments and calls the function
+of the same name in ``libsfqed.so``; all computation runs in the library's
+CUDA kernels.  PyTorch only provides device memory and streams
+(``DeviceEnsemble``).  There is no CPU fallback: importing the binding
+without the compiled library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB, up_to_date  # noqa: F401
+
+QED_OK, QED_ERR_INVALID, QED_ERR_CAPACITY, QED_ERR_CUDA, QED_ERR_TIMEOUT, QED_ERR_NOMEM, QED_ERR_STATE = range(7)
+QED_FP64, QED_FP32 = 0, 1
+QED_SAMPLER_TABLE, QED_SAMPLER_MLP = 0, 1
+QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
+QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP = 0, 1, 2
+
+EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_compact", "qed_get_stats", "qed_strerror",
+            "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample")
+
+
+class QedConfig(C.Structure):
+    _fields_ = [("precision", C.c_int), ("sampler", C.c_int), ("seed", C.c_uint64),
+                ("push_photons", C.c_int), ("soft_photon_filter", C.c_int), ("thin_cap", C.c_int64),
+                ("restore_on_overflow", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
+                ("profile", C.c_int), ("reserved", C.c_int * 5)]
+
+
+class QedSpecies(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("px", C.c_void_p),
+                ("py", C.c_void_p), ("pz", C.c_void_p), ("w", C.c_void_p), ("id", C.c_void_p),
+                ("nevents", C.c_void_p), ("count", C.c_int64), ("capacity", C.c_int64)]
+
+
+class QedParticles(C.Structure):
+    _fields_ = [("s", QedSpecies * 3)]
+
+
+class QedFieldDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("params", C.c_double * 16)]
+
+
+class QedStats(C.Structure):
+    _fields_ = [("particle_steps", C.c_int64), ("emit_events", C.c_int64), ("pair_events", C.c_int64),
+                ("needed_capacity", C.c_int64 * 3), ("max_subevents", C.c_int64), ("overflow", C.c_int64),
+                ("passes", C.c_int64), ("thinned", C.c_int64), ("lepton_steps", C.c_int64),
+                ("photon_steps", C.c_int64), ("launches", C.c_int64), ("kernel_ms", C.c_double * 2)]
+
+    def as_dict(self):
+        return {"particle_steps": self.particle_steps, "emit_events": self.emit_events,
+                "pair_events": self.pair_events, "needed_capacity": list(self.needed_capacity),
+                "max_subevents": self.max_subevents, "overflow": self.overflow,
+                "passes": self.passes, "thinned": self.thinned, "lepton_steps": self.lepton_steps,
+                "photon_steps": self.photon_steps, "launches": self.launches,
+                "kernel_ms": list(self.kernel_ms)}
+
+
+class QedError(RuntimeError):
+    def __init__(self, status, where, stats=None):
+        super().__init__("%s: %s (status %d)" % (where, qed_strerror(status), status))
+        self.status = status
+        self.stats = stats
+
+
+_lib = None
+
+
+def lib():
+    """Load libsfqed.so from the package tree; raise if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError("libsfqed.so is not built; run paper_2409_17299_gb300.build.build() "
+                          "(the CUDA library is required: there is no CPU path)")
+    L = C.CDLL(LIB)
+    p, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    sig = {
+        "qed_init_tables": (i32, [C.POINTER(p), C.POINTER(QedConfig), p]),
+        "qed_push_and_generate": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedFieldDesc), C.c_double, i32, i64,
+                                        C.POINTER(QedStats)]),
+        "qed_compact": (i32, [p, C.POINTER(QedParticles), i64]),
+        "qed_get_stats": (i32, [p, C.POINTER(QedStats), i32]),
+        "qed_strerror": (C.c_char_p, [i32]),
+        "qed_destroy": (None, [p]),
+        "qed_philox": (i32, [p, i64, C.c_uint64, p, p]),
+        "qed_get_tables": (i32, [p, p, p, p, p]),
+        "qed_eval_rate": (i32, [p, i32, p, i64, p]),
+        "qed_sample": (i32, [p, i32, p, p, i64, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+# --------------------------------------------------------------------------
+# one Python function per C entry point (argument marshalling only)
+# --------------------------------------------------------------------------
+def qed_strerror(status: int) -> str:
+    return lib().qed_strerror(int(status)).decode()
+
+
+def qed_init_tables(cfg: QedConfig, cuda_stream: int | None = None) -> C.c_void_p:
+    ctx = C.c_void_p()
+    st = lib().qed_init_tables(C.byref(ctx), C.byref(cfg), C.c_void_p(cuda_stream or 0))
+    if st != QED_OK:
+        raise QedError(st, "qed_init_tables")
+    return ctx
+
+
+def qed_push_and_generate(ctx, particles: QedParticles, field: QedFieldDesc, dt: float, nsteps: int,
+                          step0: int = 0):
+    """Returns (status, stats dict); QED_ERR_CAPACITY is returned, not raised."""
+    st = QedStats()
+    rc = lib().qed_push_and_generate(ctx, C.byref(particles), C.byref(field), float(dt), int(nsteps),
+                                     int(step0), C.byref(st))
+    if rc not in (QED_OK, QED_ERR_CAPACITY):
+        raise QedError(rc, "qed_push_and_generate")
+    return rc, st.as_dict()
+
+
+def qed_compact(ctx, particles: QedParticles, step: int) -> int:
+    rc = lib().qed_compact(ctx, C.byref(particles), int(step))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_compact")
+    return rc
+
+
+def qed_get_stats(ctx, reset: bool = False) -> dict:
+    st = QedStats()
+    rc = lib().qed_get_stats(ctx, C.byref(st), int(reset))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_get_stats")
+    return st.as_dict()
+
+
+def qed_destroy(ctx) -> None:
+    lib().qed_destroy(ctx)
+
+
+def qed_philox(ctr_dev_ptr: int, n: int, key: int, out_dev_ptr: int, cuda_stream: int | None = None) -> None:
+    rc = lib().qed_philox(C.c_void_p(ctr_dev_ptr), int(n), C.c_uint64(key), C.c_void_p(out_dev_ptr),
+                          C.c_void_p(cuda_stream or 0))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_philox")
+
+
+def qed_get_tables(ctx, cheb_em_ptr=None, cheb_pair_ptr=None, icdf_em_ptr=None, icdf_pair_ptr=None) -> None:
+    rc = lib().qed_get_tables(ctx, C.c_void_p(cheb_em_ptr or 0), C.c_void_p(cheb_pair_ptr or 0),
+                              C.c_void_p(icdf_em_ptr or 0), C.c_void_p(icdf_pair_ptr or 0))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_get_tables")
+
+
+def qed_eval_rate(ctx, is_photon: bool, chi_dev_ptr: int, n: int, F_dev_ptr: int) -> None:
+    rc = lib().qed_eval_rate(ctx, int(is_photon), C.c_void_p(chi_dev_ptr), int(n), C.c_void_p(F_dev_ptr))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_eval_rate")
+
+
+def qed_sample(ctx, is_photon: bool, chi_dev_ptr: int, u_dev_ptr: int, n: int, delta_dev_ptr: int,
+               one_minus_dev_ptr: int | None = None) -> None:
+    rc = lib().qed_sample(ctx, int(is_photon), C.c_void_p(chi_dev_ptr), C.c_void_p(u_dev_ptr), int(n),
+                          C.c_void_p(delta_dev_ptr), C.c_void_p(one_minus_dev_ptr or 0))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_sample")
+
+
+# --------------------------------------------------------------------------
+# small helpers around the ABI structs (no computation)
+# --------------------------------------------------------------------------
+def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0, thin_cap=0,
+                restore_on_overflow=1, block_threads=0, blocks_per_sm=0, profile=0) -> QedConfig:
+    c = QedConfig()
+    c.precision = int(precision)
+    c.sampler = QED_SAMPLER_TABLE
+    c.seed = int(seed)
+    c.push_photons = int(push_photons)
+    c.soft_photon_filter = int(soft_photon_filter)
+    c.thin_cap = int(thin_cap)
+    c.restore_on_overflow = int(restore_on_overflow)
+    c.block_threads = int(block_threads)
+    c.blocks_per_sm = int(blocks_per_sm)
+    c.profile = int(profile)
+    return c
+
+
+def make_field(kind: int, params) -> QedFieldDesc:
+    f = QedFieldDesc()
+    f.kind = int(kind)
+    for i, v in enumerate(params):
+        f.params[i] = float(v)
+    return f
+
+
+_FIELDS = ("x", "y", "z", "px", "py", "pz", "w")
+
+
+class DeviceEnsemble:
+    """Three species of structure-of-arrays particle buffers in torch device
+    memory (caller-owned memory in the sense of the ABI)."""
+
+    def __init__(self, capacity, precision=QED_FP64, device="cuda"):
+        import torch
+        self.torch = torch
+        self.precision = precision
+        self.device = device
+        self.fdtype = torch.float32 if precision == QED_FP32 else torch.float64
+        self.capacity = [int(c) for c in capacity]
+        self.count = [0, 0, 0]
+        self.arr = []
+        for cap in self.capacity:
+            c = max(cap, 1)
+            d = {f: torch.zeros(c, dtype=self.fdtype, device=device) for f in _FIELDS}
+            d["id"] = torch.zeros(c, dtype=torch.int64, device=device)
+            d["nevents"] = torch.zeros(c, dtype=torch.int32, device=device)
+            self.arr.append(d)
+
+    @classmethod
+    def from_host(cls, species, capacity, precision=QED_FP64, device="cuda"):
+        """species: 3 dicts of numpy arrays (x..w float64, id uint64[, nevents])."""
+        import numpy as np
+        e = cls(capacity, precision, device)
+        for s, sp in enumerate(species):
+            n = len(sp["id"])
+            if n > e.capacity[s]:
+                raise ValueError("capacity %d < count %d for species %d" % (e.capacity[s], n, s))
+            if n == 0:
+                continue
+            for f in _FIELDS:
+                e.arr[s][f][:n].copy_(e.torch.from_numpy(np.asarray(sp[f], dtype=np.float64)).to(e.fdtype))
+            e.arr[s]["id"][:n].copy_(e.torch.from_numpy(np.asarray(sp["id"], dtype=np.uint64).view(np.int64)))
+            if "nevents" in sp:
+                e.arr[s]["nevents"][:n].copy_(e.torch.from_numpy(np.asarray(sp["nevents"], dtype=np.uint32).view(np.int32)))
+            e.count[s] = n
+        return e
+
+    def struct(self) -> QedParticles:
+        P = QedParticles()
+        for s in range(3):
+            d = self.arr[s]
+            S = P.s[s]
+            for f in _FIELDS:
+                setattr(S, f, d[f].data_ptr())
+            S.id = d["id"].data_ptr()
+            S.nevents = d["nevents"].data_ptr()
+            S.count = self.count[s]
+            S.capacity = self.capacity[s]
+        return P
+
+    def pull_counts(self, P: QedParticles):
+        for s in range(3):
+            self.count[s] = int(P.s[s].count)
+
+    def to_host(self, s):
+        import numpy as np
+        n = self.count[s]
+        d = self.arr[s]
+        out = {f: d[f][:n].double().cpu().numpy() for f in _FIELDS}
+        out["id"] = d["id"][:n].cpu().numpy().view(np.uint64)
+        out["nevents"] = d["nevents"][:n].cpu().numpy().view(np.uint32)
+        return out
+
+    def grow(self, capacity):
+        torch = self.torch
+        for s in range(3):
+            cap = max(int(capacity[s]), self.capacity[s])
+            if cap == self.capacity[s]:
+                continue
+            d = self.arr[s]
+            for f in list(d.keys()):
+                a = torch.zeros(cap, dtype=d[f].dtype, device=self.device)
+                a[: self.count[s]].copy_(d[f][: self.count[s]])
+                d[f] = a
+            self.capacity[s] = cap
+
+
+class Generator:
+    """Context + ensemble convenience wrapper used by the tests and benchmark."""
+
+    def __init__(self, cfg: QedConfig, stream=None):
+        import torch
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = qed_init_tables(cfg, self.stream.cuda_stream)
+
+    def push(self, ens: DeviceEnsemble, field: QedFieldDesc, dt: float, nsteps: int, step0: int = 0,
+             auto_grow: bool = True):
+        while True:
+            P = ens.struct()
+            rc, st = qed_push_and_generate(self.ctx, P, field, dt, nsteps, step0)
+            ens.pull_counts(P)
+            if rc == QED_OK:
+                return st
+            if not auto_grow:
+                raise QedError(rc, "qed_push_and_generate", st)
+            need = [max(2 * ens.capacity[s], 2 * st["needed_capacity"][s]) for s in range(3)]
+            ens.grow(need)
+
+    def compact(self, ens: DeviceEnsemble, step: int):
+        P = ens.struct()
+        qed_compact(self.ctx, P, step)
+        ens.pull_counts(P)
+
+    def close(self):
+        if self.ctx:
+            qed_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,143 @@
+// C-ABI entry points (declared and documented in include/sfqed.h).
+#include <stdlib.h>
+#include <string.h>
+
+#include "sfqed_internal.h"
+
+using namespace sfq;
+
+static void free_ctx(qed_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    void *dev[] = {c->coef64, c->coef32, c->icdf_em64, c->icdf_pair64, c->icdf_em32, c->icdf_pair32, c->gl,
+                   c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    if (c->ev_ready)
+        for (int k = 0; k < 2; ++k)
+            for (int i = 0; i < qed_ctx::EVN; ++i)
+                for (int j = 0; j < 2; ++j) cudaEventDestroy(c->ev[k][i][j]);
+    free(c);
+}
+
+extern "C" qed_status qed_init_tables(qed_ctx **out, const qed_config *cfg, void *cuda_stream) {
+    if (!out || !cfg) return QED_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->precision != QED_FP64 && cfg->precision != QED_FP32) return QED_ERR_INVALID;
+    if (cfg->sampler != QED_SAMPLER_TABLE) return QED_ERR_INVALID;
+    if (cfg->thin_cap < 0 || cfg->block_threads < 0 || cfg->block_threads > 1024 || cfg->block_threads % 32 ||
+        cfg->blocks_per_sm < 0)
+        return QED_ERR_INVALID;
+    qed_ctx *c = static_cast<qed_ctx *>(calloc(1, sizeof(qed_ctx)));
+    if (!c) return QED_ERR_NOMEM;
+    c->cfg = *cfg;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        free(c);
+        return QED_ERR_CUDA;
+    }
+    bool ok = cudaMalloc(&c->coef64, sizeof(double) * NCOEF) == cudaSuccess &&
+              cudaMalloc(&c->coef32, sizeof(float) * NCOEF) == cudaSuccess &&
+              cudaMalloc(&c->icdf_em64, sizeof(double) * EM_NCHI * EM_NS) == cudaSuccess &&
+              cudaMalloc(&c->icdf_pair64, sizeof(double) * PAIR_NCHI * PAIR_NS) == cudaSuccess &&
+              cudaMalloc(&c->icdf_em32, sizeof(float) * EM_NCHI * EM_NS) == cudaSuccess &&
+              cudaMalloc(&c->icdf_pair32, sizeof(float) * PAIR_NCHI * PAIR_NS) == cudaSuccess &&
+              cudaMalloc(&c->gl, sizeof(double) * 64) == cudaSuccess &&
+              cudaMalloc(&c->ctl, sizeof(DevCtl)) == cudaSuccess &&
+              cudaHostAlloc(&c->ctl_host, sizeof(DevCtl), cudaHostAllocDefault) == cudaSuccess;
+    if (!ok) {
+        free_ctx(c);
+        return QED_ERR_NOMEM;
+    }
+    if (cudaMemsetAsync(c->ctl, 0, sizeof(DevCtl), c->stream) != cudaSuccess) {
+        free_ctx(c);
+        return QED_ERR_CUDA;
+    }
+    qed_status e = sfq_build_tables(c);
+    if (e != QED_OK) {
+        free_ctx(c);
+        return e;
+    }
+    *out = c;
+    return QED_OK;
+}
+
+extern "C" void qed_destroy(qed_ctx *ctx) { free_ctx(ctx); }
+
+extern "C" qed_status qed_push_and_generate(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field,
+                                            double dt, int nsteps, int64_t step0, qed_stats *out) {
+    return sfq_push(ctx, p, field, dt, nsteps, step0, out);
+}
+
+extern "C" qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step) {
+    if (!ctx || !p || step < 0 || step > 0xFFFFFFFFll) return QED_ERR_INVALID;
+    DevCtl h{};
+    for (int s = 0; s < 3; ++s) {
+        if (p->s[s].count < 0 || p->s[s].count > p->s[s].capacity) return QED_ERR_INVALID;
+        h.count[s] = (unsigned long long)p->s[s].count;
+        h.capacity[s] = (unsigned long long)p->s[s].capacity;
+    }
+    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl, &h, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
+    for (int s = 0; s < 3; ++s) {
+        qed_status e = sfq_compact_species(ctx, &p->s[s], s);
+        if (e != QED_OK) return e;
+        e = sfq_level_species(ctx, &p->s[s], s, step);   // also reads back the count
+        if (e != QED_OK) return e;
+    }
+    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)ctx->ctl_host->count[s];
+    ctx->acc.thinned += (int64_t)ctx->ctl_host->thinned;
+    return QED_OK;
+}
+
+extern "C" qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset) {
+    if (!ctx || !out) return QED_ERR_INVALID;
+    *out = ctx->acc;
+    if (reset) memset(&ctx->acc, 0, sizeof(ctx->acc));
+    return QED_OK;
+}
+
+extern "C" const char *qed_strerror(qed_status s) {
+    switch (s) {
+    case QED_OK: return "ok";
+    case QED_ERR_INVALID: return "invalid argument";
+    case QED_ERR_CAPACITY: return "particle buffer capacity exceeded";
+    case QED_ERR_CUDA: return "CUDA runtime error";
+    case QED_ERR_TIMEOUT: return "bounded device wait gave up";
+    case QED_ERR_NOMEM: return "out of device memory";
+    case QED_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+extern "C" qed_status qed_philox(const uint32_t *ctr_dev, int64_t n, uint64_t key, uint32_t *out_dev,
+                                 void *cuda_stream) {
+    return sfq_philox(ctr_dev, n, key, out_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" qed_status qed_get_tables(qed_ctx *ctx, double *cheb_em, double *cheb_pair, double *icdf_em,
+                                     double *icdf_pair) {
+    if (!ctx) return QED_ERR_INVALID;
+    cudaStream_t st = ctx->stream;
+    if (cheb_em) SFQ_CUDA(cudaMemcpyAsync(cheb_em, ctx->coef64, sizeof(double) * EM_NDEC * CHEB_N, cudaMemcpyDeviceToHost, st));
+    if (cheb_pair)
+        SFQ_CUDA(cudaMemcpyAsync(cheb_pair, ctx->coef64 + EM_NDEC * CHEB_N, sizeof(double) * PAIR_NDEC * CHEB_N,
+                                 cudaMemcpyDeviceToHost, st));
+    if (icdf_em) SFQ_CUDA(cudaMemcpyAsync(icdf_em, ctx->icdf_em64, sizeof(double) * EM_NCHI * EM_NS, cudaMemcpyDeviceToHost, st));
+    if (icdf_pair)
+        SFQ_CUDA(cudaMemcpyAsync(icdf_pair, ctx->icdf_pair64, sizeof(double) * PAIR_NCHI * PAIR_NS, cudaMemcpyDeviceToHost, st));
+    SFQ_CUDA(cudaStreamSynchronize(st));
+    return QED_OK;
+}
+
+extern "C" qed_status qed_eval_rate(qed_ctx *ctx, int is_photon, const double *chi_dev, int64_t n, double *F_dev) {
+    return sfq_eval_rate(ctx, is_photon, chi_dev, n, F_dev);
+}
+
+extern "C" qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const double *u_dev, int64_t n,
+                                 double *delta_dev, double *one_minus_dev) {
+    return sfq_sample(ctx, is_photon, chi_dev, u_dev, n, delta_dev, one_minus_dev);
+}

@@ -1,0 +1,257 @@
+// Device building blocks of the QED step (arXiv:2409.17299, Sec. 3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sfqed_internal.h"
+
+namespace sfq {
+
+// CODATA 2018, wavelength 0.8 um: R = m c^2 / (hbar omega).
+constexpr double ALPHA = 7.2973525693e-3;
+constexpr double RS = 329718.75885517005;
+constexpr double PAIR_CHI_MIN = 0.01;   // pair rate taken as zero below
+constexpr uint64_t CHILD_KEY_XOR = 0xC0FFEEull;
+
+// ---------------------------------------------------------------------------
+// Precision-generic math (T = double: FP64 mode; T = float: FP32 mode).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double m_exp(double a) { return exp(a); }
+__device__ __forceinline__ float m_exp(float a) { return expf(a); }
+__device__ __forceinline__ double m_log(double a) { return log(a); }
+__device__ __forceinline__ float m_log(float a) { return logf(a); }
+__device__ __forceinline__ double m_log1p(double a) { return log1p(a); }
+__device__ __forceinline__ float m_log1p(float a) { return log1pf(a); }
+__device__ __forceinline__ double m_log10(double a) { return log10(a); }
+__device__ __forceinline__ float m_log10(float a) { return log10f(a); }
+__device__ __forceinline__ double m_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float m_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double m_floor(double a) { return floor(a); }
+__device__ __forceinline__ float m_floor(float a) { return floorf(a); }
+__device__ __forceinline__ double m_cbrt2(double a) { double c = cbrt(a); return c * c; }  // a^(2/3)
+__device__ __forceinline__ float m_cbrt2(float a) { float c = cbrtf(a); return c * c; }
+__device__ __forceinline__ void m_sincos(double a, double *s, double *c) { sincos(a, s, c); }
+__device__ __forceinline__ void m_sincos(float a, float *s, float *c) { sincosf(a, s, c); }
+
+// particle arrays are read and written by the same kernels: plain loads
+template <class T> __device__ __forceinline__ T ld(const void *p, size_t i) {
+    return reinterpret_cast<const T *>(p)[i];
+}
+template <class T> __device__ __forceinline__ void st(void *p, size_t i, T v) {
+    reinterpret_cast<T *>(p)[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): counter (c0..c3), key (k0, k1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 event_draw(uint64_t seed, uint64_t id, unsigned step, unsigned k) {
+    return philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, k),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Uniform in (0,1): FP64 mode uses 52 bits, (m + 1/2) 2^-52; FP32 mode uses
+// 23 bits, (m + 1/2) 2^-23, built from the exponent trick without any FP64 op.
+template <class T> struct Uniform;
+template <> struct Uniform<double> {
+    static __device__ __forceinline__ double from(uint32_t a, uint32_t b) {
+        const uint64_t m = ((uint64_t)a << 20) | (uint64_t)(b >> 12);
+        return ((double)m + 0.5) * 0x1p-52;
+    }
+};
+template <> struct Uniform<float> {
+    static __device__ __forceinline__ float from(uint32_t a, uint32_t) {
+        const float f = __uint_as_float(0x3F800000u | (a >> 9)) - 1.0f;   // m 2^-23, exact
+        return f + 0x1p-24f;                                                // (m + 1/2) 2^-23, exact
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Fields (analytic descriptors).  FP64 mode: phase t = t_n + tau, as given.
+// FP32 mode: phase from t_n reduced modulo 2 pi plus tau.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void eval_field(const PassArgs &a, T x, double tau, T E[3], T B[3]) {
+    if (a.field_kind == QED_FIELD_UNIFORM) {
+        E[0] = (T)a.prm[0]; E[1] = (T)a.prm[1]; E[2] = (T)a.prm[2];
+        B[0] = (T)a.prm[3]; B[1] = (T)a.prm[4]; B[2] = (T)a.prm[5];
+        return;
+    }
+    T ph;
+    if (sizeof(T) == 8) ph = (T)(a.t_n + tau);
+    else ph = (T)a.t_n_red + (T)tau;
+    T s, c;
+    m_sincos(ph, &s, &c);
+    const T a0 = (T)a.prm[0];
+    if (a.field_kind == QED_FIELD_ROTATING_E) {
+        E[0] = a0 * c; E[1] = a0 * s; E[2] = 0;
+        B[0] = 0; B[1] = 0; B[2] = 0;
+    } else {   // standing circularly polarised wave, E antinode at x = 0
+        T sx, cx;
+        m_sincos(x, &sx, &cx);
+        const T e = a0 * cx, b = a0 * sx;
+        E[0] = 0; E[1] = e * c; E[2] = e * s;
+        B[0] = 0; B[1] = b * c; B[2] = b * s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// chi = sqrt((e0 E + p x B)^2 - (p.E)^2) / R, always in FP64 (the difference
+// cancels for particles moving with a wave).  e0 = gamma (lepton) or k0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double chi_fp64(double e0, double px, double py, double pz,
+                                           double Ex, double Ey, double Ez,
+                                           double Bx, double By, double Bz) {
+    const double ux = fma(e0, Ex, fma(py, Bz, -pz * By));
+    const double uy = fma(e0, Ey, fma(pz, Bx, -px * Bz));
+    const double uz = fma(e0, Ez, fma(px, By, -py * Bx));
+    const double pe = fma(px, Ex, fma(py, Ey, pz * Ez));
+    double q = fma(ux, ux, fma(uy, uy, uz * uz)) - pe * pe;
+    q = q > 0.0 ? q : 0.0;
+    return sqrt(q) * (1.0 / RS);
+}
+
+// ---------------------------------------------------------------------------
+// Boris push: half electric kick, magnetic rotation, half kick, then
+// x += p/gamma h with the new momentum.  q = -1 (e-) or +1 (e+).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void boris(T x[3], T p[3], T q, const T E[3], const T B[3], T h) {
+    const T qh2 = (T)0.5 * q * h;
+    T m0 = p[0] + qh2 * E[0], m1 = p[1] + qh2 * E[1], m2 = p[2] + qh2 * E[2];
+    const T ig = (T)1 / m_sqrt((T)1 + m0 * m0 + m1 * m1 + m2 * m2);
+    const T t0 = qh2 * B[0] * ig, t1 = qh2 * B[1] * ig, t2 = qh2 * B[2] * ig;
+    const T f = (T)2 / ((T)1 + t0 * t0 + t1 * t1 + t2 * t2);
+    const T s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    const T a0 = m0 + (m1 * t2 - m2 * t1);
+    const T a1 = m1 + (m2 * t0 - m0 * t2);
+    const T a2 = m2 + (m0 * t1 - m1 * t0);
+    m0 += a1 * s2 - a2 * s1;
+    m1 += a2 * s0 - a0 * s2;
+    m2 += a0 * s1 - a1 * s0;
+    p[0] = m0 + qh2 * E[0];
+    p[1] = m1 + qh2 * E[1];
+    p[2] = m2 + qh2 * E[2];
+    const T vh = h / m_sqrt((T)1 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    x[0] += p[0] * vh;
+    x[1] += p[1] * vh;
+    x[2] += p[2] * vh;
+}
+
+// ---------------------------------------------------------------------------
+// Rate approximant (Sec. 3, Sec. 4.3: polynomial approximation with a fixed
+// operation count).  Coefficient layout: 6 emission decades [-3..3] then 5
+// pair decades [-2..3], 11 Chebyshev coefficients each (first term halved).
+// ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T clenshaw(const T *c, T x) {
+    T b1 = 0, b2 = 0;
+    const T x2 = x + x;
+#pragma unroll
+    for (int j = CHEB_N - 1; j >= 1; --j) {
+        const T b0 = c[j] + x2 * b1 - b2;
+        b2 = b1;
+        b1 = b0;
+    }
+    return (T)0.5 * c[0] + x * b1 - b2;
+}
+
+// F_gamma(chi)
+template <class T> __device__ __forceinline__ T rate_em(const T *coef, T chi) {
+    if (!(chi > (T)0)) return (T)0;
+    const T s = m_log10(chi);
+    if (s < (T)-3) return chi * clenshaw(coef, (T)-1);
+    if (s > (T)3) return (T)1e3 * clenshaw(coef + 5 * CHEB_N, (T)1) * m_cbrt2(chi * (T)1e-3);
+    int d = (int)m_floor(s + (T)3);
+    d = d > 5 ? 5 : d;
+    const T x = (T)2 * (s - (T)(d - 3)) - (T)1;
+    return chi * clenshaw(coef + d * CHEB_N, x);
+}
+
+// F_pair(chi)
+template <class T> __device__ __forceinline__ T rate_pair(const T *coef, T chi) {
+    if (!(chi >= (T)PAIR_CHI_MIN)) return (T)0;
+    const T *c = coef + EM_NDEC * CHEB_N;
+    const T s = m_log10(chi);
+    if (s > (T)3) return m_exp(clenshaw(c + 4 * CHEB_N, (T)1) - (T)(8.0 / 3e3)) * m_cbrt2(chi * (T)1e-3);
+    int d = (int)m_floor(s + (T)2);
+    d = d > 4 ? 4 : (d < 0 ? 0 : d);
+    const T x = (T)2 * (s - (T)(d - 2)) - (T)1;
+    return m_exp(clenshaw(c + d * CHEB_N, x) - (T)(8.0 / 3.0) / chi);
+}
+
+// ---------------------------------------------------------------------------
+// Inverse-CDF sampling (Sec. 3).  Bilinear in (log10 chi, logit u); chi is
+// clamped to the table, logit u extrapolated linearly from the end cells.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T bilinear(const T *tab, int nchi, int ns, T c, T t) {
+    c = c < (T)0 ? (T)0 : (c > (T)(nchi - 1) ? (T)(nchi - 1) : c);
+    int i0 = (int)m_floor(c);
+    i0 = i0 > nchi - 2 ? nchi - 2 : i0;
+    const T fc = c - (T)i0;
+    int j0 = (int)m_floor(t);
+    j0 = j0 < 0 ? 0 : (j0 > ns - 2 ? ns - 2 : j0);
+    const T ft = t - (T)j0;
+    const T *r0 = tab + (size_t)i0 * ns + j0;
+    const T *r1 = r0 + ns;
+    const T a = __ldg(r0), b = __ldg(r0 + 1), cc = __ldg(r1), d = __ldg(r1 + 1);
+    const T lo = a + ft * (b - a), hi = cc + ft * (d - cc);
+    return lo + fc * (hi - lo);
+}
+
+// photon energy fraction delta (returned) and 1 - delta
+template <class T>
+__device__ __forceinline__ T sample_emission(const T *tab, T chi, T u, T *one_minus) {
+    const T s = m_log(u) - m_log1p(-u);
+    const T c = (m_log10(chi) + (T)3) * (T)20;
+    const T t = (s + (T)16) * (T)8;
+    const T zeta = bilinear(tab, EM_NCHI, EM_NS, c, t);
+    const T a = (T)3 * chi * m_exp(zeta);
+    *one_minus = (T)2 / ((T)2 + a);
+    return a / ((T)2 + a);
+}
+
+// electron energy fraction delta (returned) and 1 - delta (positron fraction)
+template <class T>
+__device__ __forceinline__ T sample_pair(const T *tab, T chi, T u, T *one_minus) {
+    const bool flip = u > (T)0.5;
+    const T uu = flip ? (T)1 - u : u;
+    const T s = m_log(uu) - m_log1p(-uu);
+    const T c = (m_log10(chi) + (T)2) * (T)20;
+    const T t = (s + (T)16) * (T)8;
+    const T d = m_exp(bilinear(tab, PAIR_NCHI, PAIR_NS, c, t));
+    if (flip) { *one_minus = d; return (T)1 - d; }
+    *one_minus = (T)1 - d;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-aggregated append: the lanes that want a slot get consecutive slots
+// from one atomicAdd per converged group.  Returns the slot (may be beyond
+// capacity; the caller checks).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long *counter, unsigned n_each) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)(__popc(mask) * n_each));
+    base = __shfl_sync(mask, base, leader);
+    const unsigned below = __popc(mask & ((1u << lane) - 1u));
+    return base + (unsigned long long)below * n_each;
+}
+
+}  // namespace sfq

@@ -1,0 +1,127 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfqed.h"
+
+namespace sfq {
+
+// Table grids (the header of the public ABI states their meaning).
+constexpr int EM_NCHI = 121;     // log10 chi in [-3, 3], 20 per decade
+constexpr int PAIR_NCHI = 101;   // log10 chi in [-2, 3], 20 per decade
+constexpr int EM_NS = 257;       // logit u in [-16, 16]
+constexpr int PAIR_NS = 129;     // logit u in [-16, 0]
+constexpr int CHEB_N = 11;       // degree-10 Chebyshev interpolant per decade
+constexpr int EM_NDEC = 6;
+constexpr int PAIR_NDEC = 5;
+constexpr int NCOEF = (EM_NDEC + PAIR_NDEC) * CHEB_N;   // 121 coefficients
+
+// Device-resident control block: counts, pass ranges and statistics.  Every
+// counter is 64-bit so that appends can count demand beyond capacity.
+struct DevCtl {
+    unsigned long long count[3];        // append cursor (may exceed capacity on overflow)
+    unsigned long long capacity[3];
+    unsigned long long begin[3];        // range of the current pass
+    unsigned long long end[3];
+    unsigned long long particle_steps;
+    unsigned long long lepton_steps;
+    unsigned long long photon_steps;
+    unsigned long long emit_events;
+    unsigned long long pair_events;
+    unsigned long long max_subevents;
+    unsigned long long overflow;
+    unsigned long long needed[3];
+    unsigned long long more;            // the last pass setup found work
+    unsigned long long passes;
+    unsigned long long thinned;
+    unsigned long long alive[3];        // compaction: alive entries per species
+    unsigned long long wmax_bits[3];    // leveling: largest weight (as ordered bits)
+    double wstar[3];                    // leveling threshold per species
+    unsigned long long pad[8];
+};
+
+struct SpeciesDev {
+    void *x, *y, *z, *px, *py, *pz, *w;
+    unsigned long long *id;
+    unsigned *nev;
+    double *tau;            // birth clock of newborns (context work buffer)
+};
+
+struct PassArgs {
+    SpeciesDev sp[3];
+    DevCtl *ctl;
+    const void *coef;       // NCOEF coefficients (T)
+    const void *icdf_em;    // EM_NCHI * EM_NS (T)
+    const void *icdf_pair;  // PAIR_NCHI * PAIR_NS (T)
+    int field_kind;
+    double prm[6];
+    double dt;
+    double t_n;             // step * dt
+    double t_n_red;         // (step * dt) reduced modulo 2 pi (FP32 phase)
+    unsigned step;
+    unsigned long long seed;
+    int pass;               // 0: particles present at the step start (tau = 0)
+    int soft_filter;
+    int record_newborn_tau; // newborns get their birth clock stored (cascades)
+};
+
+}  // namespace sfq
+
+struct qed_ctx {
+    qed_config cfg;
+    cudaStream_t stream;
+    int device;
+    int sm_count;
+    // tables
+    double *coef64;          // NCOEF
+    float *coef32;
+    double *icdf_em64, *icdf_pair64;
+    float *icdf_em32, *icdf_pair32;
+    double *gl;              // Gauss-Legendre nodes and weights (work)
+    // control
+    sfq::DevCtl *ctl;
+    sfq::DevCtl *ctl_host;   // pinned mirror
+    // newborn birth clocks
+    double *tau[3];
+    int64_t tau_cap[3];
+    // compaction / leveling work buffers
+    unsigned long long *blk;      // per-block counts
+    int64_t blk_cap;
+    unsigned long long *slots;    // hole indices
+    int64_t slots_cap;
+    // overflow snapshot
+    void *snap;
+    int64_t snap_bytes;
+    qed_stats acc;           // accumulated statistics (host)
+    // profiling: CUDA event pairs around the push kernels
+    static constexpr int EVN = 512;
+    cudaEvent_t ev[2][EVN][2];   // [lepton|photon][pair][start|stop]
+    int ev_used[2];
+    bool ev_ready;
+    double kernel_ms[2];
+    int64_t launches;            // kernels launched since the last reset
+};
+
+// Implemented in sfqed_tables.cu
+qed_status sfq_build_tables(qed_ctx *ctx);
+// Implemented in sfqed_push.cu
+qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt,
+                    int nsteps, int64_t step0, qed_stats *out);
+qed_status sfq_eval_rate(qed_ctx *ctx, int is_photon, const double *chi, int64_t n, double *F);
+qed_status sfq_sample(qed_ctx *ctx, int is_photon, const double *chi, const double *u, int64_t n,
+                      double *delta, double *one_minus);
+qed_status sfq_philox(const uint32_t *ctr, int64_t n, uint64_t key, uint32_t *out, cudaStream_t s);
+// Implemented in sfqed_compact.cu
+qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);
+qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step);
+qed_status sfq_ensure_work(qed_ctx *ctx, int64_t n_blocks, int64_t n_slots);
+
+#define SFQ_LAUNCHED(ctx, n) ((ctx)->launches += (n))
+
+#define SFQ_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return QED_ERR_CUDA;                     \
+    } while (0)

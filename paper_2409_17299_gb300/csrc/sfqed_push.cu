@@ -1,0 +1,591 @@
+// K2 / K3: the per-particle QED step (arXiv:2409.17299 Sec. 3, Algorithms 1-2).
+//
+// One pass kernel per particle kind.  Each thread takes one particle of the
+// pass range (grid-stride), runs Algorithm 1 for it to the end of the step
+// (rate -> waiting time -> Boris push -> event), and appends every particle
+// it creates with a warp-aggregated atomic.  Newborns carry their birth
+// clock and are pushed by the next pass (Algorithm 2): leptons and photons
+// are swept alternately until a pass creates nothing.
+#include <math.h>
+
+#include "sfqed_device.cuh"
+#include "sfqed_internal.h"
+
+namespace sfq {
+namespace {
+
+template <class T> __device__ __forceinline__ T t_inf();
+template <> __device__ __forceinline__ double t_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+template <> __device__ __forceinline__ float t_inf<float>() { return __int_as_float(0x7f800000); }
+
+__device__ __forceinline__ void flush_stats(DevCtl *ctl, unsigned long long steps, unsigned long long ev,
+                                            unsigned mx, bool pair) {
+    // called by every lane of the warp after the grid-stride loop
+    for (int o = 16; o > 0; o >>= 1) {
+        steps += __shfl_down_sync(0xffffffffu, steps, o);
+        ev += __shfl_down_sync(0xffffffffu, ev, o);
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (steps) {
+            atomicAdd(&ctl->particle_steps, steps);
+            atomicAdd(pair ? &ctl->photon_steps : &ctl->lepton_steps, steps);
+        }
+        if (ev) atomicAdd(pair ? &ctl->pair_events : &ctl->emit_events, ev);
+        if (mx) atomicMax(&ctl->max_subevents, (unsigned long long)mx);
+    }
+}
+
+__device__ __forceinline__ void note_overflow(DevCtl *ctl, int s, unsigned long long slot) {
+    atomicMax(&ctl->needed[s], slot + 1);
+    atomicExch(&ctl->overflow, 1ull);
+}
+
+// Algorithm 1 for electrons and positrons (both species of one pass).
+template <class T>
+__global__ void __launch_bounds__(256) k_lepton_pass(PassArgs a) {
+    __shared__ T s_coef[NCOEF];
+    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    __syncthreads();
+    DevCtl *ctl = a.ctl;
+    const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
+    const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
+    const unsigned long long n = n0 + n1;
+    const unsigned long long cap_ph = ctl->capacity[2];
+    const T *icdf = reinterpret_cast<const T *>(a.icdf_em);
+    const T alpha_r = (T)(ALPHA * RS);
+    unsigned long long my_steps = 0, my_ev = 0;
+    unsigned my_max = 0;
+
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const int s = j < n0 ? 0 : 1;
+        const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
+        const SpeciesDev &S = a.sp[s];
+        const T w = ld<T>(S.w, i);
+        if (!(w > (T)0)) continue;
+        T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
+        T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
+        const unsigned long long id = __ldg(S.id + i);
+        double tau = a.pass ? S.tau[i] : 0.0;
+        const T q = s == 0 ? (T)-1 : (T)1;
+        unsigned k = 0;
+        while (tau < a.dt) {
+            T E[3], B[3];
+            eval_field<T>(a, x[0], tau, E, B);
+            double pd0 = p[0], pd1 = p[1], pd2 = p[2];
+            double p2 = pd0 * pd0 + pd1 * pd1 + pd2 * pd2;
+            double gd = sqrt(1.0 + p2);
+            double chi = chi_fp64(gd, pd0, pd1, pd2, E[0], E[1], E[2], B[0], B[1], B[2]);
+            const T lam = p2 > 0.0 ? alpha_r / (T)gd * rate_em<T>(s_coef, (T)chi) : (T)0;
+            uint4 r = make_uint4(0, 0, 0, 0);
+            T dth = t_inf<T>();
+            if (lam > (T)0) {
+                r = event_draw(a.seed, id, a.step, k);
+                dth = -m_log(Uniform<T>::from(r.x, r.y)) / lam;
+            }
+            if (tau + (double)dth > a.dt) {           // no event before the step ends
+                boris<T>(x, p, q, E, B, (T)(a.dt - tau));
+                tau = a.dt;
+                break;
+            }
+            boris<T>(x, p, q, E, B, dth);
+            tau += (double)dth;
+            // event: chi at the emission point, energy from the inverse CDF
+            eval_field<T>(a, x[0], tau, E, B);
+            pd0 = p[0]; pd1 = p[1]; pd2 = p[2];
+            p2 = pd0 * pd0 + pd1 * pd1 + pd2 * pd2;
+            gd = sqrt(1.0 + p2);
+            chi = chi_fp64(gd, pd0, pd1, pd2, E[0], E[1], E[2], B[0], B[1], B[2]);
+            T om;
+            const T delta = sample_emission<T>(icdf, (T)chi, Uniform<T>::from(r.z, r.w), &om);
+            const T g = (T)gd;
+            T g_after = om * g, k0 = delta * g;
+            if (g_after < (T)1) { g_after = (T)1; k0 = g - (T)1; }
+            const T inv = (T)1 / (T)sqrt(p2);
+            const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
+            const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
+            if (!(a.soft_filter && k0 < (T)2)) {
+                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, k);
+                const unsigned long long slot = warp_append(&ctl->count[2], 1);
+                if (slot < cap_ph) {
+                    const SpeciesDev &P = a.sp[2];
+                    st<T>(P.x, slot, x[0]); st<T>(P.y, slot, x[1]); st<T>(P.z, slot, x[2]);
+                    st<T>(P.px, slot, k0 * nx); st<T>(P.py, slot, k0 * ny); st<T>(P.pz, slot, k0 * nz);
+                    st<T>(P.w, slot, w);
+                    P.id[slot] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
+                    P.nev[slot] = 0u;
+                    if (a.record_newborn_tau) P.tau[slot] = tau;
+                } else {
+                    note_overflow(ctl, 2, slot);
+                }
+            }
+            p[0] = pa * nx; p[1] = pa * ny; p[2] = pa * nz;
+            ++k;
+        }
+        st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
+        st<T>(S.px, i, p[0]); st<T>(S.py, i, p[1]); st<T>(S.pz, i, p[2]);
+        if (k) S.nev[i] += k;
+        ++my_steps;
+        my_ev += k;
+        my_max = max(my_max, k);
+    }
+    __syncwarp();
+    flush_stats(ctl, my_steps, my_ev, my_max, false);
+}
+
+// Photon push: straight flight, pair creation at the event, the photon is
+// removed (weight 0) and the pair appended.
+template <class T>
+__global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
+    __shared__ T s_coef[NCOEF];
+    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    __syncthreads();
+    DevCtl *ctl = a.ctl;
+    const unsigned long long b = ctl->begin[2], n = ctl->end[2] - b;
+    const unsigned long long cap_e = ctl->capacity[0], cap_p = ctl->capacity[1];
+    const T *icdf = reinterpret_cast<const T *>(a.icdf_pair);
+    const T alpha_r = (T)(ALPHA * RS);
+    const SpeciesDev &S = a.sp[2];
+    unsigned long long my_steps = 0, my_ev = 0;
+    unsigned my_max = 0;
+
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = b + j;
+        T w = ld<T>(S.w, i);
+        if (!(w > (T)0)) continue;
+        T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
+        const T kx = ld<T>(S.px, i), ky = ld<T>(S.py, i), kz = ld<T>(S.pz, i);
+        const unsigned long long id = __ldg(S.id + i);
+        double tau = a.pass ? S.tau[i] : 0.0;
+        const double kd0 = kx, kd1 = ky, kd2 = kz;
+        const double k0d = sqrt(kd0 * kd0 + kd1 * kd1 + kd2 * kd2);
+        unsigned k = 0;
+        if (k0d > 0.0) {
+            const T k0 = (T)k0d;
+            const T inv = (T)1 / k0;
+            const T nx = kx * inv, ny = ky * inv, nz = kz * inv;
+            while (tau < a.dt) {
+                T E[3], B[3];
+                eval_field<T>(a, x[0], tau, E, B);
+                double chi = chi_fp64(k0d, kd0, kd1, kd2, E[0], E[1], E[2], B[0], B[1], B[2]);
+                const T lam = alpha_r / k0 * rate_pair<T>(s_coef, (T)chi);
+                uint4 r = make_uint4(0, 0, 0, 0);
+                T dth = t_inf<T>();
+                if (lam > (T)0) {
+                    r = event_draw(a.seed, id, a.step, k);
+                    dth = -m_log(Uniform<T>::from(r.x, r.y)) / lam;
+                }
+                if (tau + (double)dth > a.dt) {
+                    const T h = (T)(a.dt - tau);
+                    x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
+                    tau = a.dt;
+                    break;
+                }
+                x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
+                tau += (double)dth;
+                eval_field<T>(a, x[0], tau, E, B);
+                chi = chi_fp64(k0d, kd0, kd1, kd2, E[0], E[1], E[2], B[0], B[1], B[2]);
+                T om;
+                const T delta = sample_pair<T>(icdf, (T)chi, Uniform<T>::from(r.z, r.w), &om);
+                T em = delta * k0, ep = om * k0;
+                em = em < (T)1 ? (T)1 : em;
+                ep = ep < (T)1 ? (T)1 : ep;
+                const T pm = m_sqrt((em - (T)1) * (em + (T)1)), pp = m_sqrt((ep - (T)1) * (ep + (T)1));
+                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, k);
+                const unsigned long long se = warp_append(&ctl->count[0], 1);
+                const unsigned long long sp = warp_append(&ctl->count[1], 1);
+                if (se < cap_e) {
+                    const SpeciesDev &P = a.sp[0];
+                    st<T>(P.x, se, x[0]); st<T>(P.y, se, x[1]); st<T>(P.z, se, x[2]);
+                    st<T>(P.px, se, pm * nx); st<T>(P.py, se, pm * ny); st<T>(P.pz, se, pm * nz);
+                    st<T>(P.w, se, w);
+                    P.id[se] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
+                    P.nev[se] = 0u;
+                    P.tau[se] = tau;
+                } else {
+                    note_overflow(ctl, 0, se);
+                }
+                if (sp < cap_p) {
+                    const SpeciesDev &P = a.sp[1];
+                    st<T>(P.x, sp, x[0]); st<T>(P.y, sp, x[1]); st<T>(P.z, sp, x[2]);
+                    st<T>(P.px, sp, pp * nx); st<T>(P.py, sp, pp * ny); st<T>(P.pz, sp, pp * nz);
+                    st<T>(P.w, sp, w);
+                    P.id[sp] = (unsigned long long)rid.z | ((unsigned long long)rid.w << 32);
+                    P.nev[sp] = 0u;
+                    P.tau[sp] = tau;
+                } else {
+                    note_overflow(ctl, 1, sp);
+                }
+                w = (T)0;       // the photon is eliminated
+                k = 1;
+                break;
+            }
+        }
+        st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
+        if (k) { st<T>(S.w, i, w); S.nev[i] += k; }
+        ++my_steps;
+        my_ev += k;
+        my_max = max(my_max, k);
+    }
+    __syncwarp();
+    flush_stats(ctl, my_steps, my_ev, my_max, true);
+}
+
+// Pass ranges: at the step start every particle present; afterwards the
+// particles appended since the previous pass.
+__global__ void k_step_begin(DevCtl *ctl) {
+    for (int s = 0; s < 3; ++s) {
+        ctl->begin[s] = 0;
+        ctl->end[s] = min(ctl->count[s], ctl->capacity[s]);
+    }
+}
+
+__global__ void k_pass_setup(DevCtl *ctl) {
+    unsigned long long more = 0;
+    for (int s = 0; s < 3; ++s) {
+        const unsigned long long e = min(ctl->count[s], ctl->capacity[s]);
+        ctl->begin[s] = ctl->end[s];
+        ctl->end[s] = e;
+        if (e > ctl->begin[s]) more = 1;
+    }
+    ctl->more = more;
+    ctl->passes += more;
+}
+
+// ---- component kernels for the parity tests ----
+__global__ void k_philox(const uint4 *ctr, long long n, uint2 key, uint4 *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], key);
+}
+
+template <class T>
+__global__ void k_eval_rate(const T *coef, int is_photon, const double *chi, long long n, double *F) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T c = (T)chi[i];
+    F[i] = (double)(is_photon ? rate_pair<T>(coef, c) : rate_em<T>(coef, c));
+}
+
+template <class T>
+__global__ void k_sample(const T *tab, int is_photon, const double *chi, const double *u, long long n,
+                         double *delta, double *om) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T o;
+    const T d = is_photon ? sample_pair<T>(tab, (T)chi[i], (T)u[i], &o) : sample_emission<T>(tab, (T)chi[i], (T)u[i], &o);
+    delta[i] = (double)d;
+    if (om) om[i] = (double)o;
+}
+
+}  // namespace
+}  // namespace sfq
+
+using namespace sfq;
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static qed_status check_species(const qed_species &s) {
+    const void *ptrs[] = {s.x, s.y, s.z, s.px, s.py, s.pz, s.w, s.id, s.nevents};
+    if (s.capacity < 0 || s.count < 0 || s.count > s.capacity) return QED_ERR_INVALID;
+    if (s.capacity == 0) return QED_OK;
+    for (const void *q : ptrs)
+        if (!q || !aligned16(q)) return QED_ERR_INVALID;
+    return QED_OK;
+}
+
+static qed_status ensure_tau(qed_ctx *ctx, int s, int64_t cap) {
+    if (ctx->tau_cap[s] >= cap) return QED_OK;
+    if (ctx->tau[s]) SFQ_CUDA(cudaFreeAsync(ctx->tau[s], ctx->stream));
+    ctx->tau[s] = nullptr;
+    ctx->tau_cap[s] = 0;
+    if (cudaMallocAsync(&ctx->tau[s], sizeof(double) * (size_t)(cap > 0 ? cap : 1), ctx->stream) != cudaSuccess)
+        return QED_ERR_NOMEM;
+    ctx->tau_cap[s] = cap;
+    return QED_OK;
+}
+
+static size_t elem_bytes(const qed_ctx *ctx) { return ctx->cfg.precision == QED_FP32 ? 4 : 8; }
+
+// Save / restore the particle state at the start of a call (overflow replay).
+static qed_status snapshot(qed_ctx *ctx, qed_particles *p, bool restore) {
+    const size_t eb = elem_bytes(ctx);
+    size_t need = 0;
+    for (int s = 0; s < 3; ++s) need += (size_t)p->s[s].count * (7 * eb + 8 + 4);
+    if (!restore && (int64_t)need > ctx->snap_bytes) {
+        if (ctx->snap) SFQ_CUDA(cudaFreeAsync(ctx->snap, ctx->stream));
+        ctx->snap = nullptr;
+        ctx->snap_bytes = 0;
+        if (cudaMallocAsync(&ctx->snap, need + 16, ctx->stream) != cudaSuccess) return QED_ERR_NOMEM;
+        ctx->snap_bytes = (int64_t)need;
+    }
+    char *b = static_cast<char *>(ctx->snap);
+    for (int s = 0; s < 3; ++s) {
+        const qed_species &S = p->s[s];
+        const size_t n = (size_t)S.count;
+        if (!n) continue;
+        void *arr[] = {S.x, S.y, S.z, S.px, S.py, S.pz, S.w};
+        for (void *q : arr) {
+            if (restore) SFQ_CUDA(cudaMemcpyAsync(q, b, n * eb, cudaMemcpyDeviceToDevice, ctx->stream));
+            else SFQ_CUDA(cudaMemcpyAsync(b, q, n * eb, cudaMemcpyDeviceToDevice, ctx->stream));
+            b += n * eb;
+        }
+        if (restore) SFQ_CUDA(cudaMemcpyAsync(S.id, b, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        else SFQ_CUDA(cudaMemcpyAsync(b, S.id, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        b += n * 8;
+        if (restore) SFQ_CUDA(cudaMemcpyAsync(S.nevents, b, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        else SFQ_CUDA(cudaMemcpyAsync(b, S.nevents, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        b += n * 4;
+    }
+    return QED_OK;
+}
+
+static qed_status read_ctl(qed_ctx *ctx) {
+    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}
+
+// Profiling: event pairs around the push kernels, drained into kernel_ms.
+static qed_status drain_events(qed_ctx *ctx) {
+    for (int k = 0; k < 2; ++k) {
+        for (int i = 0; i < ctx->ev_used[k]; ++i) {
+            float ms = 0.f;
+            SFQ_CUDA(cudaEventSynchronize(ctx->ev[k][i][1]));
+            SFQ_CUDA(cudaEventElapsedTime(&ms, ctx->ev[k][i][0], ctx->ev[k][i][1]));
+            ctx->kernel_ms[k] += ms;
+        }
+        ctx->ev_used[k] = 0;
+    }
+    return QED_OK;
+}
+
+static qed_status ensure_events(qed_ctx *ctx) {
+    if (ctx->ev_ready) return QED_OK;
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < qed_ctx::EVN; ++i)
+            for (int j = 0; j < 2; ++j) SFQ_CUDA(cudaEventCreate(&ctx->ev[k][i][j]));
+    ctx->ev_ready = true;
+    return QED_OK;
+}
+
+template <class K>
+static qed_status timed_launch(qed_ctx *ctx, int which, K launch) {
+    if (!ctx->cfg.profile) {
+        launch();
+        return QED_OK;
+    }
+    if (ctx->ev_used[which] == qed_ctx::EVN) {
+        qed_status e = drain_events(ctx);
+        if (e != QED_OK) return e;
+    }
+    const int i = ctx->ev_used[which]++;
+    SFQ_CUDA(cudaEventRecord(ctx->ev[which][i][0], ctx->stream));
+    launch();
+    SFQ_CUDA(cudaEventRecord(ctx->ev[which][i][1], ctx->stream));
+    return QED_OK;
+}
+
+template <class T>
+static qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons) {
+    const int threads = ctx->cfg.block_threads > 0 ? ctx->cfg.block_threads : 256;
+    const int per_sm = ctx->cfg.blocks_per_sm > 0 ? ctx->cfg.blocks_per_sm : 4;
+    const int blocks = ctx->sm_count * per_sm;
+    cudaStream_t st = ctx->stream;
+    qed_status e = timed_launch(ctx, 0, [&] { k_lepton_pass<T><<<blocks, threads, 0, st>>>(a); });
+    if (e != QED_OK) return e;
+    SFQ_LAUNCHED(ctx, 1);
+    if (photons) {
+        e = timed_launch(ctx, 1, [&] { k_photon_pass<T><<<blocks, threads, 0, st>>>(a); });
+        if (e != QED_OK) return e;
+        SFQ_LAUNCHED(ctx, 1);
+    }
+    SFQ_CUDA(cudaGetLastError());
+    return QED_OK;
+}
+
+template <class T>
+static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
+                            int64_t step0, qed_stats *out) {
+    const bool cascade = ctx->cfg.push_photons != 0;
+    ctx->launches = 0;
+    ctx->kernel_ms[0] = ctx->kernel_ms[1] = 0.0;
+    if (ctx->cfg.profile) {
+        qed_status e = ensure_events(ctx);
+        if (e != QED_OK) return e;
+    }
+    int64_t count0[3];
+    for (int s = 0; s < 3; ++s) count0[s] = p->s[s].count;
+    DevCtl h{};
+    for (int s = 0; s < 3; ++s) {
+        h.count[s] = (unsigned long long)p->s[s].count;
+        h.capacity[s] = (unsigned long long)p->s[s].capacity;
+    }
+    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl, &h, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
+    for (int s = 0; s < 3; ++s) {
+        qed_status e = ensure_tau(ctx, s, p->s[s].capacity);
+        if (e != QED_OK) return e;
+    }
+    if (ctx->cfg.restore_on_overflow) {
+        qed_status e = snapshot(ctx, p, false);
+        if (e != QED_OK) return e;
+    }
+    PassArgs a{};
+    for (int s = 0; s < 3; ++s) {
+        const qed_species &S = p->s[s];
+        a.sp[s] = SpeciesDev{S.x, S.y, S.z, S.px, S.py, S.pz, S.w,
+                             reinterpret_cast<unsigned long long *>(S.id), S.nevents, ctx->tau[s]};
+    }
+    a.ctl = ctx->ctl;
+    const bool f32 = sizeof(T) == 4;
+    a.coef = f32 ? (const void *)ctx->coef32 : (const void *)ctx->coef64;
+    a.icdf_em = f32 ? (const void *)ctx->icdf_em32 : (const void *)ctx->icdf_em64;
+    a.icdf_pair = f32 ? (const void *)ctx->icdf_pair32 : (const void *)ctx->icdf_pair64;
+    a.field_kind = field->kind;
+    for (int i = 0; i < 6; ++i) a.prm[i] = field->params[i];
+    a.dt = dt;
+    a.seed = ctx->cfg.seed;
+    a.soft_filter = ctx->cfg.soft_photon_filter;
+    a.record_newborn_tau = cascade ? 1 : 0;
+
+    qed_status rc = QED_OK;
+    for (int it = 0; it < nsteps; ++it) {
+        const int64_t step = step0 + it;
+        a.step = (unsigned)step;
+        a.t_n = (double)step * dt;
+        a.t_n_red = fmod(a.t_n, 2.0 * 3.14159265358979323846);
+        a.pass = 0;
+        k_step_begin<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
+        SFQ_LAUNCHED(ctx, 1);
+        qed_status e = launch_pass<T>(ctx, a, cascade);
+        if (e != QED_OK) return e;
+        if (cascade) {
+            // Algorithm 2: sweep the newborns until a pass creates nothing.
+            for (int pass = 1; pass < 100000; ++pass) {
+                k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
+                SFQ_LAUNCHED(ctx, 1);
+                e = read_ctl(ctx);
+                if (e != QED_OK) return e;
+                if (ctx->ctl_host->overflow || !ctx->ctl_host->more) break;
+                a.pass = pass;
+                e = launch_pass<T>(ctx, a, true);
+                if (e != QED_OK) return e;
+            }
+        }
+        if (cascade || ctx->cfg.thin_cap > 0) {
+            // merge step (Sec. 4.2): drop dead photons, then level
+            if (!cascade) {
+                e = read_ctl(ctx);
+                if (e != QED_OK) return e;
+            }
+            if (ctx->ctl_host->overflow) { rc = QED_ERR_CAPACITY; break; }
+            for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)ctx->ctl_host->count[s];
+            if (cascade) {
+                e = sfq_compact_species(ctx, &p->s[2], 2);
+                if (e != QED_OK) return e;
+            }
+            if (ctx->cfg.thin_cap > 0) {
+                for (int s = 0; s < 3; ++s) {
+                    e = sfq_level_species(ctx, &p->s[s], s, step);
+                    if (e != QED_OK) return e;
+                }
+            }
+        }
+    }
+    qed_status e = read_ctl(ctx);
+    if (e != QED_OK) return e;
+    DevCtl &c = *ctx->ctl_host;
+    if (c.overflow) rc = QED_ERR_CAPACITY;
+    qed_stats st{};
+    st.particle_steps = (int64_t)c.particle_steps;
+    st.emit_events = (int64_t)c.emit_events;
+    st.pair_events = (int64_t)c.pair_events;
+    for (int s = 0; s < 3; ++s) st.needed_capacity[s] = (int64_t)c.needed[s];
+    st.max_subevents = (int64_t)c.max_subevents;
+    st.overflow = (int64_t)c.overflow;
+    st.passes = (int64_t)c.passes;
+    st.thinned = (int64_t)c.thinned;
+    st.lepton_steps = (int64_t)c.lepton_steps;
+    st.photon_steps = (int64_t)c.photon_steps;
+    if (ctx->cfg.profile) {
+        e = drain_events(ctx);
+        if (e != QED_OK) return e;
+    }
+    st.kernel_ms[0] = ctx->kernel_ms[0];
+    st.kernel_ms[1] = ctx->kernel_ms[1];
+    st.launches = ctx->launches;
+    if (rc == QED_ERR_CAPACITY && ctx->cfg.restore_on_overflow) {
+        for (int s = 0; s < 3; ++s) p->s[s].count = count0[s];
+        e = snapshot(ctx, p, true);
+        if (e != QED_OK) return e;
+        SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    } else {
+        for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)min(c.count[s], c.capacity[s]);
+    }
+    if (out) *out = st;
+    ctx->acc.particle_steps += st.particle_steps;
+    ctx->acc.emit_events += st.emit_events;
+    ctx->acc.pair_events += st.pair_events;
+    ctx->acc.passes += st.passes;
+    ctx->acc.thinned += st.thinned;
+    ctx->acc.lepton_steps += st.lepton_steps;
+    ctx->acc.photon_steps += st.photon_steps;
+    ctx->acc.launches += st.launches;
+    ctx->acc.kernel_ms[0] += st.kernel_ms[0];
+    ctx->acc.kernel_ms[1] += st.kernel_ms[1];
+    if (st.max_subevents > ctx->acc.max_subevents) ctx->acc.max_subevents = st.max_subevents;
+    return rc;
+}
+
+qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
+                    int64_t step0, qed_stats *out) {
+    if (!ctx || !p || !field || nsteps < 0 || !(dt > 0.0) || step0 < 0 || step0 + nsteps > 0xFFFFFFFFll)
+        return QED_ERR_INVALID;
+    if (field->kind < QED_FIELD_UNIFORM || field->kind > QED_FIELD_STANDING_CP) return QED_ERR_INVALID;
+    for (int s = 0; s < 3; ++s) {
+        qed_status e = check_species(p->s[s]);
+        if (e != QED_OK) return e;
+    }
+    if (ctx->cfg.precision == QED_FP32) return push_impl<float>(ctx, p, field, dt, nsteps, step0, out);
+    return push_impl<double>(ctx, p, field, dt, nsteps, step0, out);
+}
+
+qed_status sfq_philox(const uint32_t *ctr, int64_t n, uint64_t key, uint32_t *out, cudaStream_t s) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return QED_ERR_INVALID;
+    if (!aligned16(ctr) || !aligned16(out)) return QED_ERR_INVALID;
+    if (n == 0) return QED_OK;
+    k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(reinterpret_cast<const uint4 *>(ctr), n,
+                                                         make_uint2((uint32_t)key, (uint32_t)(key >> 32)),
+                                                         reinterpret_cast<uint4 *>(out));
+    SFQ_CUDA(cudaGetLastError());
+    SFQ_CUDA(cudaStreamSynchronize(s));
+    return QED_OK;
+}
+
+qed_status sfq_eval_rate(qed_ctx *ctx, int is_photon, const double *chi, int64_t n, double *F) {
+    if (!ctx || n < 0 || (n > 0 && (!chi || !F))) return QED_ERR_INVALID;
+    if (n == 0) return QED_OK;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (ctx->cfg.precision == QED_FP32) k_eval_rate<float><<<g, 256, 0, ctx->stream>>>(ctx->coef32, is_photon, chi, n, F);
+    else k_eval_rate<double><<<g, 256, 0, ctx->stream>>>(ctx->coef64, is_photon, chi, n, F);
+    SFQ_CUDA(cudaGetLastError());
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}
+
+qed_status sfq_sample(qed_ctx *ctx, int is_photon, const double *chi, const double *u, int64_t n, double *delta,
+                      double *one_minus) {
+    if (!ctx || n < 0 || (n > 0 && (!chi || !u || !delta))) return QED_ERR_INVALID;
+    if (n == 0) return QED_OK;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (ctx->cfg.precision == QED_FP32)
+        k_sample<float><<<g, 256, 0, ctx->stream>>>(is_photon ? ctx->icdf_pair32 : ctx->icdf_em32, is_photon, chi, u,
+                                                    n, delta, one_minus);
+    else
+        k_sample<double><<<g, 256, 0, ctx->stream>>>(is_photon ? ctx->icdf_pair64 : ctx->icdf_em64, is_photon, chi,
+                                                     u, n, delta, one_minus);
+    SFQ_CUDA(cudaGetLastError());
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}

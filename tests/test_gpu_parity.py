@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars (written in each test): Philox and per-particle event counts bit-exact;
+FP64 momenta within 1e-5 relative (observed ~1e-12); FP32 (+FP64 chi/clock)
+within 1e-3 relative on particles whose event sequence matches, with the
+fraction of mismatching particles bounded; spectra by two-sample KS.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_17299_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2409_17299_gb300 as q  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gen64():
+    from paper_2409_17299_gb300 import build
+    build.build()
+    g = q.Generator(q.make_config(precision=q.QED_FP64, seed=0))
+    yield g
+    g.close()
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device="cuda").contiguous()
+
+
+# ---------------------------------------------------------------------------
+# components
+# ---------------------------------------------------------------------------
+def test_philox_bit_exact():
+    rng = np.random.default_rng(0)
+    n = 1 << 20
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [0, 0, 0xFFFFFFFF, 0xFFFFFFFF]]
+    for key in (0, 0xC0FFEE, 0xFFFFFFFFFFFFFFFF, 0x0123456789ABCDEF):
+        dctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+        dout = torch.empty_like(dctr)
+        q.qed_philox(dctr.data_ptr(), n, key, dout.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        got = dout.cpu().numpy().view(np.uint32).reshape(n, 4)
+        want = oracle.philox(ctr, [key & 0xFFFFFFFF, key >> 32])
+        assert np.array_equal(got, want)
+
+
+def test_philox_empty_and_misaligned():
+    q.qed_philox(0, 0, 0, 0)
+    buf = torch.zeros(64, dtype=torch.int32, device="cuda")
+    with pytest.raises(q.QedError):
+        q.qed_philox(buf.data_ptr() + 4, 1, 0, buf.data_ptr())
+
+
+def test_tables_match_oracle(gen64, otables):
+    ce, cp = np.zeros(66), np.zeros(55)
+    ie, ip = np.zeros(121 * 257), np.zeros(101 * 129)
+    q.qed_get_tables(gen64.ctx, ce.ctypes.data, cp.ctypes.data, ie.ctypes.data, ip.ctypes.data)
+    # both sides build the same mathematical objects with independent quadrature
+    assert np.allclose(ce, otables.cheb_em, rtol=0, atol=1e-11 * np.abs(otables.cheb_em).max())
+    assert np.allclose(cp, otables.cheb_pair, rtol=0, atol=1e-10 * np.abs(otables.cheb_pair).max())
+    assert np.max(np.abs(ie - otables.icdf_em)) < 1e-9
+    assert np.max(np.abs(ip - otables.icdf_pair)) < 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [(q.QED_FP64, 1e-11), (q.QED_FP32, 3e-5)])
+def test_rate_approximant(prec, tol, otables):
+    g = q.Generator(q.make_config(precision=prec))
+    chi = np.concatenate([np.logspace(-5, 5, 4001), [0.0, 1e-3, 1e3, 0.01, 0.0099]])
+    dchi = _dev(chi)
+    F = torch.empty_like(dchi)
+    for is_ph in (0, 1):
+        q.qed_eval_rate(g.ctx, is_ph, dchi.data_ptr(), len(chi), F.data_ptr())
+        got = F.cpu().numpy()
+        want = np.array([otables.rate_F(is_ph, c) for c in chi])
+        nz = want > 1e-30
+        assert np.all((got == 0) == (want == 0)), "zero pattern"
+        assert np.max(np.abs(got[nz] / want[nz] - 1)) < tol
+    g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(q.QED_FP64, 1e-10), (q.QED_FP32, 1e-4)])
+def test_inverse_cdf_sampler(prec, tol, otables):
+    g = q.Generator(q.make_config(precision=prec))
+    rng = np.random.default_rng(5)
+    n = 20000
+    chi = 10 ** rng.uniform(-4, 4, n)
+    u = rng.random(n)
+    u[:4] = [2.0 ** -30, 0.5, 1 - 2.0 ** -20, 0.25]
+    dchi, du = _dev(chi), _dev(u)
+    d, om = torch.empty_like(dchi), torch.empty_like(dchi)
+    for is_ph in (0, 1):
+        q.qed_sample(g.ctx, is_ph, dchi.data_ptr(), du.data_ptr(), n, d.data_ptr(), om.data_ptr())
+        gd, gom = d.cpu().numpy(), om.cpu().numpy()
+        ref = [otables.sample_pair(c, x) if is_ph else otables.sample_emission(c, x) for c, x in zip(chi, u)]
+        wd = np.array([r[0] for r in ref])
+        wom = np.array([r[1] for r in ref])
+        assert np.all((gd > 0) & (gd < 1))
+        assert np.max(np.abs(gd / wd - 1)) < tol * 10
+        assert np.max(np.abs(gom / wom - 1)) < tol * 10
+        assert np.median(np.abs(gd / wd - 1)) < tol
+    g.close()
+
+
+# ---------------------------------------------------------------------------
+# full steps
+# ---------------------------------------------------------------------------
+def run_gpu(w, prec, nsteps=None, capacity=None, thin_cap=None, gen=None, step0=0):
+    cap = capacity or [max(64, 4 * len(s["id"])) for s in w.species]
+    g = gen or q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons,
+                                         thin_cap=w.thin_cap if thin_cap is None else thin_cap))
+    ens = q.DeviceEnsemble.from_host(w.species, cap, prec)
+    st = g.push(ens, q.make_field(w.field_kind, w.field_prm), w.dt, w.nsteps if nsteps is None else nsteps, step0)
+    torch.cuda.synchronize()
+    out = [ens.to_host(s) for s in range(3)]
+    if gen is None:
+        g.close()
+    return out, st
+
+
+def run_oracle(w, otables, nsteps=None, capacity=None, thin_cap=None, step0=0):
+    cap = capacity or [max(64, 4 * len(s["id"])) for s in w.species]
+    ens = oracle.Ensemble.from_arrays(w.species, cap)
+    cfg = oracle.make_cfg(seed=w.seed, push_photons=w.push_photons,
+                          thin_cap=w.thin_cap if thin_cap is None else thin_cap,
+                          field_kind=w.field_kind, field_prm=w.field_prm)
+    st = oracle.push_and_generate(ens, otables, cfg, w.dt, w.nsteps if nsteps is None else nsteps, step0)
+    return [ens.view(s) for s in range(3)], st
+
+
+def by_id(d):
+    o = np.argsort(d["id"])
+    return {k: v[o] for k, v in d.items()}
+
+
+def assert_same_fp64(g, o, rtol=1e-5, what=""):
+    assert len(g["id"]) == len(o["id"]), (what, len(g["id"]), len(o["id"]))
+    g, o = by_id(g), by_id(o)
+    assert np.array_equal(g["id"], o["id"]), what
+    assert np.array_equal(g["nevents"], o["nevents"]), what
+    for f in ("x", "y", "z", "px", "py", "pz"):
+        scale = np.maximum(np.abs(o[f]), 1e-3 * max(1.0, np.abs(o[f]).max()))
+        err = np.abs(g[f] - o[f]) / scale
+        assert err.max() < rtol, (what, f, err.max())
+    assert np.allclose(g["w"], o["w"], rtol=1e-12, atol=0), what
+
+
+@pytest.mark.parametrize("n,nsteps", [(1, 3), (33, 20), (1025, 10)])
+def test_emission_fp64_ragged_sizes(n, nsteps, otables):
+    w = W.uniform_b_emission(n=n, seed=3, nsteps=nsteps)
+    g, gs = run_gpu(w, q.QED_FP64)
+    o, os_ = run_oracle(w, otables)
+    assert gs["emit_events"] == os_["emit_events"]
+    assert gs["particle_steps"] == os_["particle_steps"] == n * nsteps
+    for s in range(3):
+        assert_same_fp64(g[s], o[s], what="species %d" % s)
+
+
+def test_empty_ensemble(otables):
+    w = W.uniform_b_emission(n=1, seed=0, nsteps=2)
+    w.species[0] = W._empty()
+    g, gs = run_gpu(w, q.QED_FP64, capacity=[8, 8, 8])
+    assert gs["particle_steps"] == 0 and gs["emit_events"] == 0
+    assert all(len(x["id"]) == 0 for x in g)
+
+
+def test_emission_full_size_fp64(otables):
+    """The uniform-B emission workload at full size: 16384 electrons, 200 steps,
+    chi0 = 1, photons recorded (bit-exact event counts, momenta 1e-5)."""
+    w = W.uniform_b_emission(n=16384, seed=0)
+    g, gs = run_gpu(w, q.QED_FP64, capacity=[16384, 8, 400000])
+    o, os_ = run_oracle(w, otables, capacity=[16384, 8, 400000])
+    assert gs["emit_events"] == os_["emit_events"]
+    assert gs["particle_steps"] == os_["particle_steps"]
+    assert_same_fp64(g[0], o[0], what="electrons")
+    assert_same_fp64(g[2], o[2], what="photons")
+
+
+def test_cascade_fp64_rotating_field(otables):
+    w = W.rotating_e_cascade(n=600, seed=1, periods=1)
+    g, gs = run_gpu(w, q.QED_FP64, nsteps=60, capacity=[20000, 20000, 60000])
+    o, os_ = run_oracle(w, otables, nsteps=60, capacity=[20000, 20000, 60000])
+    assert os_["pair_events"] > 0
+    assert (gs["emit_events"], gs["pair_events"], gs["particle_steps"]) == \
+        (os_["emit_events"], os_["pair_events"], os_["particle_steps"])
+    for s in range(3):
+        assert_same_fp64(g[s], o[s], what="species %d" % s)
+
+
+def test_cascade_fp64_standing_wave(otables):
+    w = W.standing_wave_cascade(n=400, seed=4, periods=1)
+    g, gs = run_gpu(w, q.QED_FP64, nsteps=40, capacity=[20000, 20000, 60000])
+    o, os_ = run_oracle(w, otables, nsteps=40, capacity=[20000, 20000, 60000])
+    assert (gs["emit_events"], gs["pair_events"]) == (os_["emit_events"], os_["pair_events"])
+    for s in range(3):
+        assert_same_fp64(g[s], o[s], what="species %d" % s)
+
+
+def test_overflow_restores_and_replays(otables):
+    w = W.rotating_e_cascade(n=300, seed=1, periods=1)
+    big, _ = run_gpu(w, q.QED_FP64, nsteps=30, capacity=[20000, 20000, 60000])
+    # raw ABI: too small a photon buffer -> QED_ERR_CAPACITY with the state put back
+    gen = q.Generator(q.make_config(precision=q.QED_FP64, seed=w.seed, push_photons=1))
+    ens = q.DeviceEnsemble.from_host(w.species, [20000, 20000, 16], q.QED_FP64)
+    before = ens.to_host(0)
+    P = ens.struct()
+    rc, st = q.qed_push_and_generate(gen.ctx, P, q.make_field(w.field_kind, w.field_prm), w.dt, 30, 0)
+    assert rc == q.QED_ERR_CAPACITY and st["overflow"] == 1 and st["needed_capacity"][2] > 16
+    ens.pull_counts(P)
+    after = ens.to_host(0)
+    assert ens.count == [300, 0, 0]
+    for f in before:
+        assert np.array_equal(before[f], after[f])
+    # grow and replay: identical to the large-capacity run
+    gen.push(ens, q.make_field(w.field_kind, w.field_prm), w.dt, 30, 0)
+    for s in range(3):
+        a, b = by_id(big[s]), by_id(ens.to_host(s))
+        for f in a:
+            assert np.array_equal(a[f], b[f]), (s, f)
+    gen.close()
+
+
+def test_thinning_fp64_matches_oracle(otables):
+    w = W.rotating_e_cascade(n=500, seed=1, periods=1)
+    cap = 700
+    g, gs = run_gpu(w, q.QED_FP64, nsteps=50, capacity=[20000, 20000, 60000], thin_cap=cap)
+    o, os_ = run_oracle(w, otables, nsteps=50, capacity=[20000, 20000, 60000], thin_cap=cap)
+    assert any(len(x["id"]) > 0.8 * cap for x in o)
+    for s in range(3):
+        assert len(g[s]["id"]) <= cap * 1.2 + 100
+        assert_same_fp64(g[s], o[s], what="species %d" % s)
+
+
+def test_fp32_against_fp64_oracle(otables):
+    """FP32 storage/push/rates/sampling with FP64 chi and clock: momenta within
+    1e-3 of the FP64 oracle for particles whose event count matches; at most
+    1% of particles may take a different event sequence after 20 steps."""
+    w = W.uniform_b_emission(n=16384, seed=0, nsteps=20)
+    g, gs = run_gpu(w, q.QED_FP32, capacity=[16384, 8, 100000])
+    o, os_ = run_oracle(w, otables, capacity=[16384, 8, 100000])
+    a, b = by_id(g[0]), by_id(o[0])
+    assert np.array_equal(a["id"], b["id"])
+    same = a["nevents"] == b["nevents"]
+    assert same.mean() > 0.99, same.mean()
+    for f in ("px", "py", "pz"):
+        scale = np.maximum(np.abs(b[f][same]), 1e-3 * np.abs(b[f]).max())
+        assert np.max(np.abs(a[f][same] - b[f][same]) / scale) < 1e-3
+    assert abs(gs["emit_events"] - os_["emit_events"]) < 5 * math.sqrt(os_["emit_events"])
+    # photon spectrum: two-sample KS between GPU FP32 and the oracle
+    from scipy.stats import ks_2samp
+    ka = np.sqrt(g[2]["px"] ** 2 + g[2]["py"] ** 2 + g[2]["pz"] ** 2)
+    kb = np.sqrt(o[2]["px"] ** 2 + o[2]["py"] ** 2 + o[2]["pz"] ** 2)
+    assert ks_2samp(ka, kb).pvalue > 0.01
+
+
+def test_fp32_cascade_statistics(otables):
+    w = W.rotating_e_cascade(n=3000, seed=1, periods=1)
+    g, gs = run_gpu(w, q.QED_FP32, nsteps=60, capacity=[100000, 100000, 300000])
+    o, os_ = run_oracle(w, otables, nsteps=60, capacity=[100000, 100000, 300000])
+    for key in ("emit_events", "pair_events"):
+        assert abs(gs[key] - os_[key]) < 6 * math.sqrt(os_[key]) + 5, key
+    from scipy.stats import ks_2samp
+    for s in range(3):
+        ea = np.sqrt(g[s]["px"] ** 2 + g[s]["py"] ** 2 + g[s]["pz"] ** 2)
+        eb = np.sqrt(o[s]["px"] ** 2 + o[s]["py"] ** 2 + o[s]["pz"] ** 2)
+        assert ks_2samp(ea, eb).pvalue > 0.01, s
