@@ -88,6 +88,7 @@ extern "C" qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step) 
     }
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
     SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ctl_host->bad_index) return QED_ERR_STATE;
     for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)ctx->ctl_host->count[s];
     ctx->acc.thinned += (int64_t)ctx->ctl_host->thinned;
     return QED_OK;

@@ -108,25 +108,35 @@ __global__ void k_scan_blocks(unsigned long long *blk, long long nb, DevCtl *ctl
         if (threadIdx.x == 0) carry += sw[(blockDim.x >> 5) - 1];
         __syncthreads();
     }
-    if (threadIdx.x == 0) ctl->alive[s] = carry;
+    if (threadIdx.x == 0) {
+        ctl->alive[s] = carry;
+        ctl->holes[s] = 0;
+    }
 }
 
-// dead slots below A record their rank
+// dead slots below A record their rank (= number of dead entries before them)
+// and are counted (H, the number of holes)
 template <class T>
-__global__ void __launch_bounds__(CT) k_mark_holes(const void *w, const DevCtl *ctl, int s,
+__global__ void __launch_bounds__(CT) k_mark_holes(const void *w, DevCtl *ctl, int s,
                                                    const unsigned long long *blk, unsigned long long *slots) {
     __shared__ unsigned sw[32];
     const unsigned long long n = ctl->count[s], A = ctl->alive[s];
     const unsigned long long base = (unsigned long long)blockIdx.x * CTILE;
     unsigned long long run = blk[blockIdx.x];
+    unsigned my_holes = 0;
     for (int r = 0; r < CITEMS; ++r) {
         const unsigned long long i = base + r * CT + threadIdx.x;
         const bool al = i < n && alive_at<T>(w, i);
         unsigned tot;
         const unsigned before = block_scan(al ? 1u : 0u, sw, &tot);
-        if (i < A && !al) slots[i - (run + before)] = i;
+        if (i < A && !al) {
+            slots[i - (run + before)] = i;     // rank < A <= n (slots holds n entries)
+            ++my_holes;
+        }
         run += tot;
     }
+    for (int o = 16; o > 0; o >>= 1) my_holes += __shfl_down_sync(0xffffffffu, my_holes, o);
+    if ((threadIdx.x & 31) == 0 && my_holes) atomicAdd(&ctl->holes[s], (unsigned long long)my_holes);
 }
 
 template <class T> __device__ __forceinline__ void move_entry(const SpeciesDev &S, unsigned long long d,
@@ -138,12 +148,14 @@ template <class T> __device__ __forceinline__ void move_entry(const SpeciesDev &
     S.nev[d] = S.nev[i];
 }
 
-// alive entries at or above A move into the holes, in rank order
+// alive entries at or above A move into the holes, in rank order: the mover
+// rank is the number of alive entries in [A, i) = alive_before(i) - (A - H)
 template <class T>
 __global__ void __launch_bounds__(CT) k_fill_holes(SpeciesDev S, DevCtl *ctl, int s, const unsigned long long *blk,
                                                    const unsigned long long *slots) {
     __shared__ unsigned sw[32];
-    const unsigned long long n = ctl->count[s], A = ctl->alive[s];
+    const unsigned long long n = ctl->count[s], A = ctl->alive[s], H = ctl->holes[s];
+    const unsigned long long alive_below_A = A - H;
     const unsigned long long base = (unsigned long long)blockIdx.x * CTILE;
     if (base + CTILE <= A) return;                 // whole tile below A: nothing moves
     unsigned long long run = blk[blockIdx.x];
@@ -152,7 +164,17 @@ __global__ void __launch_bounds__(CT) k_fill_holes(SpeciesDev S, DevCtl *ctl, in
         const bool al = i < n && alive_at<T>(S.w, i);
         unsigned tot;
         const unsigned before = block_scan(al ? 1u : 0u, sw, &tot);
-        if (al && i >= A) move_entry<T>(S, slots[run + before - A], i);
+        if (al && i >= A) {
+            const unsigned long long ab = run + before;     // alive entries before i
+            const unsigned long long rank = ab - alive_below_A;
+            if (ab >= alive_below_A && rank < H) {
+                const unsigned long long d = slots[rank];
+                if (d < A) move_entry<T>(S, d, i);
+                else atomicExch(&ctl->bad_index, i + 1);
+            } else {
+                atomicExch(&ctl->bad_index, i + 1);
+            }
+        }
         run += tot;
     }
 }

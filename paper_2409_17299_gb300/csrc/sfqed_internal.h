@@ -37,8 +37,8 @@ struct DevCtl {
     unsigned long long passes;
     unsigned long long thinned;
     unsigned long long alive[3];        // compaction: alive entries per species
-    unsigned long long wmax_bits[3];    // leveling: largest weight (as ordered bits)
-    double wstar[3];                    // leveling threshold per species
+    unsigned long long holes[3];        // compaction: dead entries below alive[s]
+    unsigned long long bad_index;       // a bounds check failed (index recorded, access skipped)
     unsigned long long pad[8];
 };
 

@@ -497,6 +497,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     if (e != QED_OK) return e;
     DevCtl &c = *ctx->ctl_host;
     if (c.overflow) rc = QED_ERR_CAPACITY;
+    if (c.bad_index) return QED_ERR_STATE;
     qed_stats st{};
     st.particle_steps = (int64_t)c.particle_steps;
     st.emit_events = (int64_t)c.emit_events;
