@@ -907,8 +907,18 @@ double or_level_threshold(const double *w, int64_t n, int64_t cap)
     for (int it = 0; it < 200; ++it) {
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        double s = 0.0;
-        for (int64_t i = 0; i < n; ++i) if (w[i] > 0.0) s += (w[i] < mid) ? w[i] / mid : 1.0;
+        /* Neumaier compensated sum, so that the computed sum is accurate to
+         * working precision and the root is that of the defining equation */
+        double s = 0.0, comp = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(w[i] > 0.0)) continue;
+            double term = (w[i] < mid) ? w[i] / mid : 1.0;
+            double t = s + term;
+            if (fabs(s) >= fabs(term)) comp += (s - t) + term;
+            else comp += (term - t) + s;
+            s = t;
+        }
+        s += comp;
         if (s > (double)cap) lo = mid; else hi = mid;
     }
     return hi;
