@@ -65,12 +65,14 @@ def default_steps(w):
     return 3, w.nsteps - 3
 
 
-def capacities(w):
+def capacities(w, nsteps=None):
+    """Buffer sizes for a run of nsteps steps (cascades: bounded by the cap)."""
+    nsteps = w.nsteps if nsteps is None else nsteps
     n0 = sum(len(s["id"]) for s in w.species)
     if w.thin_cap:
         c = int(1.6 * w.thin_cap) + 4 * n0
         return [c // 3 + n0, c // 3, c]
-    return [n0, 16, int(n0 * (1 + 0.2 * w.nsteps)) + 1024]
+    return [n0, 16, int(n0 * (1 + 0.15 * nsteps)) + 1024]
 
 
 # ---------------------------------------------------------------------------
@@ -190,7 +192,7 @@ def gpu_run(args, w, precision, warm, steps, timed=True, profile=True):
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
                         profile=int(profile), restore_on_overflow=0)
     gen = q.Generator(cfg)
-    ens = q.DeviceEnsemble.from_host(w.species, capacities(w), prec)
+    ens = q.DeviceEnsemble.from_host(w.species, capacities(w, warm + steps), prec)
     field = q.make_field(w.field_kind, w.field_prm)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -237,7 +239,7 @@ def e2e_run(w, precision, warm, steps):
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
                         restore_on_overflow=0)
     gen = q.Generator(cfg)
-    caps = capacities(w)
+    caps = capacities(w, warm + steps)
     dev = q.DeviceEnsemble(caps, prec)
     fd = dev.fdtype
     host = []

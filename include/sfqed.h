@@ -104,6 +104,8 @@ typedef struct {
     int64_t lepton_steps;     /* particle-steps done by the lepton kernel */
     int64_t photon_steps;     /* particle-steps done by the photon kernel */
     int64_t launches;         /* kernels launched by the call */
+    int64_t chi_fp64;         /* FP32 mode: chi evaluations whose cancellation test sent
+                                 them to the FP64 form */
     double kernel_ms[2];      /* with cfg.profile: summed device time of the lepton and
                                  photon push kernels (CUDA events) */
 } qed_stats;
@@ -161,6 +163,16 @@ qed_status qed_get_tables(qed_ctx *ctx, double *cheb_em, double *cheb_pair,
 /* Rate approximant F(chi) at n points, in the context's precision
  * (chi_dev, F_dev: n doubles on the device).  is_photon selects the pair rate. */
 qed_status qed_eval_rate(qed_ctx *ctx, int is_photon, const double *chi_dev, int64_t n, double *F_dev);
+
+/* Quantum parameter chi = sqrt((e0 E + p x B)^2 - (p.E)^2) / R (Algorithm 1,
+ * Calculate chi) of n particles, in the context's precision: FP64 mode the
+ * direct form in FP64; FP32 mode the inputs rounded to FP32 and the
+ * cancellation-free split S + T (Lagrange's identity) in FP32, with the direct
+ * FP64 form where the cancellation test fails.  e0 = sqrt(1 + p^2) (lepton) or
+ * |k| (photon).  p_dev, E_dev, B_dev: n x 3 doubles on the device; chi_dev: n
+ * doubles on the device; *n_fp64 (host, may be NULL): how many took the FP64 form. */
+qed_status qed_eval_chi(qed_ctx *ctx, int is_photon, const double *p_dev, const double *E_dev,
+                        const double *B_dev, int64_t n, double *chi_dev, int64_t *n_fp64);
 
 /* Energy fraction delta (and 1 - delta) drawn by inverse CDF at (chi, u), in
  * the context's precision: emission (photon fraction) or pair (electron

@@ -21,7 +21,7 @@ QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
 QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP = 0, 1, 2
 
 EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_compact", "qed_get_stats", "qed_strerror",
-            "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample")
+            "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi")
 
 
 class QedConfig(C.Structure):
@@ -49,14 +49,15 @@ class QedStats(C.Structure):
     _fields_ = [("particle_steps", C.c_int64), ("emit_events", C.c_int64), ("pair_events", C.c_int64),
                 ("needed_capacity", C.c_int64 * 3), ("max_subevents", C.c_int64), ("overflow", C.c_int64),
                 ("passes", C.c_int64), ("thinned", C.c_int64), ("lepton_steps", C.c_int64),
-                ("photon_steps", C.c_int64), ("launches", C.c_int64), ("kernel_ms", C.c_double * 2)]
+                ("photon_steps", C.c_int64), ("launches", C.c_int64), ("chi_fp64", C.c_int64),
+                ("kernel_ms", C.c_double * 2)]
 
     def as_dict(self):
         return {"particle_steps": self.particle_steps, "emit_events": self.emit_events,
                 "pair_events": self.pair_events, "needed_capacity": list(self.needed_capacity),
                 "max_subevents": self.max_subevents, "overflow": self.overflow,
                 "passes": self.passes, "thinned": self.thinned, "lepton_steps": self.lepton_steps,
-                "photon_steps": self.photon_steps, "launches": self.launches,
+                "photon_steps": self.photon_steps, "launches": self.launches, "chi_fp64": self.chi_fp64,
                 "kernel_ms": list(self.kernel_ms)}
 
 
@@ -92,6 +93,7 @@ def lib():
         "qed_get_tables": (i32, [p, p, p, p, p]),
         "qed_eval_rate": (i32, [p, i32, p, i64, p]),
         "qed_sample": (i32, [p, i32, p, p, i64, p, p]),
+        "qed_eval_chi": (i32, [p, i32, p, p, p, i64, p, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -164,6 +166,17 @@ def qed_eval_rate(ctx, is_photon: bool, chi_dev_ptr: int, n: int, F_dev_ptr: int
     rc = lib().qed_eval_rate(ctx, int(is_photon), C.c_void_p(chi_dev_ptr), int(n), C.c_void_p(F_dev_ptr))
     if rc != QED_OK:
         raise QedError(rc, "qed_eval_rate")
+
+
+def qed_eval_chi(ctx, is_photon: bool, p_dev_ptr: int, E_dev_ptr: int, B_dev_ptr: int, n: int,
+                 chi_dev_ptr: int) -> int:
+    """Returns how many evaluations took the FP64 form."""
+    n64 = C.c_int64(0)
+    rc = lib().qed_eval_chi(ctx, int(is_photon), C.c_void_p(p_dev_ptr), C.c_void_p(E_dev_ptr),
+                            C.c_void_p(B_dev_ptr), int(n), C.c_void_p(chi_dev_ptr), C.byref(n64))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_eval_chi")
+    return n64.value
 
 
 def qed_sample(ctx, is_photon: bool, chi_dev_ptr: int, u_dev_ptr: int, n: int, delta_dev_ptr: int,

@@ -10,7 +10,7 @@ static void free_ctx(qed_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     void *dev[] = {c->coef64, c->coef32, c->icdf_em64, c->icdf_pair64, c->icdf_em32, c->icdf_pair32, c->gl,
-                   c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap};
+                   c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap, c->lev};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
@@ -46,6 +46,7 @@ extern "C" qed_status qed_init_tables(qed_ctx **out, const qed_config *cfg, void
               cudaMalloc(&c->icdf_pair32, sizeof(float) * PAIR_NCHI * PAIR_NS) == cudaSuccess &&
               cudaMalloc(&c->gl, sizeof(double) * 64) == cudaSuccess &&
               cudaMalloc(&c->ctl, sizeof(DevCtl)) == cudaSuccess &&
+              cudaMalloc(&c->lev, sizeof(LevelWork)) == cudaSuccess &&
               cudaHostAlloc(&c->ctl_host, sizeof(DevCtl), cudaHostAllocDefault) == cudaSuccess;
     if (!ok) {
         free_ctx(c);
@@ -136,6 +137,11 @@ extern "C" qed_status qed_get_tables(qed_ctx *ctx, double *cheb_em, double *cheb
 
 extern "C" qed_status qed_eval_rate(qed_ctx *ctx, int is_photon, const double *chi_dev, int64_t n, double *F_dev) {
     return sfq_eval_rate(ctx, is_photon, chi_dev, n, F_dev);
+}
+
+extern "C" qed_status qed_eval_chi(qed_ctx *ctx, int is_photon, const double *p_dev, const double *E_dev,
+                                   const double *B_dev, int64_t n, double *chi_dev, int64_t *n_fp64) {
+    return sfq_eval_chi(ctx, is_photon, p_dev, E_dev, B_dev, n, chi_dev, n_fp64);
 }
 
 extern "C" qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const double *u_dev, int64_t n,

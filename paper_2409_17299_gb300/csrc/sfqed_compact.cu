@@ -262,8 +262,146 @@ __global__ void k_level_apply(SpeciesDev S, DevCtl *ctl, int s, double wstar, ui
         const double v = (double)ld<T>(S.w, i);
         if (!(v > 0.0) || v >= wstar) continue;
         const uint4 r = event_draw(seed, S.id[i], step, 0xFFFFFFFFu);
-        const double u = Uniform<double>::from(r.x, r.y);
+        double u, v_unused;
+        Uniform<double>::draw(r.x, r.y, u, v_unused);
         if (u < v / wstar) st<T>(S.w, i, (T)wstar);
+        else { st<T>(S.w, i, (T)0); ++removed; }
+    }
+    for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
+    if ((threadIdx.x & 31) == 0 && removed) atomicAdd(&ctl->thinned, removed);
+}
+
+// ---- leveling by weight classes (one pass, no host round trip) ----
+__device__ __forceinline__ void class_flush(LevelWork *lw, int s, unsigned long long b, unsigned long long c) {
+    if (!c) return;
+    unsigned j = (unsigned)((b >> 20) ^ (b >> 40)) & (LEVEL_K - 1);
+    for (int probe = 0; probe < LEVEL_K; ++probe, j = (j + 1) & (LEVEL_K - 1)) {
+        const unsigned long long prev = atomicCAS(&lw->bits[s][j], 0ull, b);
+        if (prev == 0ull || prev == b) {
+            atomicAdd(&lw->cnt[s][j], c);
+            return;
+        }
+    }
+    atomicExch(&lw->overflow[s], 1ull);
+}
+
+// distinct alive weights and their counts; a 4-entry register cache per
+// thread keeps the table atomics rare when few weight values exist
+template <class T>
+__global__ void k_level_classes(const void *w, const DevCtl *ctl, int s, LevelWork *lw, long long cap) {
+    const unsigned long long n = ctl->count[s];
+    if (n <= (unsigned long long)cap) return;
+    unsigned long long cb[4] = {0, 0, 0, 0}, cc[4] = {0, 0, 0, 0};
+    unsigned victim = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const double v = (double)ld<T>(w, i);
+        if (!(v > 0.0)) continue;
+        const unsigned long long b = dbits(v);
+        int hit = -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (cc[q] && cb[q] == b) hit = q;
+        if (hit < 0) {
+#pragma unroll
+            for (int q = 3; q >= 0; --q)
+                if (!cc[q]) hit = q;
+        }
+        if (hit < 0) {
+            hit = (int)(victim++ & 3u);
+            class_flush(lw, s, cb[hit], cc[hit]);
+            cc[hit] = 0;
+        }
+        cb[hit] = b;
+        ++cc[hit];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) class_flush(lw, s, cb[q], cc[q]);
+}
+
+// one warp: sort the classes, solve sum_c n_c min(1, v_c / w*) = cap on the
+// piece (v_j, v_{j+1}] where it changes sign (there S = A_j / w + C_j), and
+// set per class the integer keep threshold: u = (m + 1/2) 2^-52 < v_c / w*
+// exactly when m < ceil(2^52 v_c / w* - 1/2)
+__global__ void k_level_solve(DevCtl *ctl, int s, LevelWork *lw, long long cap) {
+    if (threadIdx.x != 0) return;
+    const unsigned long long n = ctl->count[s];
+    lw->wstar[s] = 0.0;
+    lw->ncls[s] = 0;
+    ctl->need_hist[s] = 0;
+    if (n <= (unsigned long long)cap) return;
+    if (lw->overflow[s]) { ctl->need_hist[s] = 1; return; }
+    double v[LEVEL_K];
+    unsigned long long c[LEVEL_K], bb[LEVEL_K];
+    int k = 0;
+    for (int j = 0; j < LEVEL_K; ++j)
+        if (lw->bits[s][j]) {
+            bb[k] = lw->bits[s][j];
+            v[k] = __longlong_as_double((long long)bb[k]);
+            c[k] = lw->cnt[s][j];
+            ++k;
+        }
+    for (int i = 1; i < k; ++i) {          // insertion sort, ascending weight
+        const double vv = v[i];
+        const unsigned long long cv = c[i], bv = bb[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > vv) { v[j + 1] = v[j]; c[j + 1] = c[j]; bb[j + 1] = bb[j]; --j; }
+        v[j + 1] = vv; c[j + 1] = cv; bb[j + 1] = bv;
+    }
+    double wstar = 0.0, A = 0.0;
+    unsigned long long C = 0;
+    for (int j = 0; j < k; ++j) C += c[j];
+    for (int j = 0; j < k; ++j) {
+        A += (double)c[j] * v[j];
+        C -= c[j];
+        const double hi = j + 1 < k ? v[j + 1] : INFINITY;
+        // S(hi) = A / hi + C: the solution lies in (v_j, hi] once S(hi) <= cap
+        const double S_hi = j + 1 < k ? A / hi + (double)C : 0.0;
+        if (S_hi <= (double)cap) {
+            wstar = A / ((double)cap - (double)C);
+            if (!(wstar > v[j])) wstar = __longlong_as_double(__double_as_longlong(v[j]) + 1);  // next double up
+            if (wstar > hi) wstar = hi;
+            break;
+        }
+    }
+    for (int j = 0; j < k; ++j) {
+        lw->cls_bits[s][j] = bb[j];
+        unsigned long long thr = 1ull << 52;          // kept, weight unchanged
+        if (v[j] < wstar) {
+            const double P = (v[j] / wstar) * 0x1p52;  // exact scaling of the keep probability
+            thr = (unsigned long long)ceil(P - 0.5);
+        }
+        lw->cls_thr[s][j] = thr;
+    }
+    lw->ncls[s] = (unsigned long long)k;
+    lw->wstar[s] = wstar;
+}
+
+template <class T>
+__global__ void k_level_apply_classes(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw, uint64_t seed,
+                                      unsigned step) {
+    __shared__ unsigned long long sb[LEVEL_K], sthr[LEVEL_K];
+    __shared__ int sk;
+    __shared__ double sw;
+    if (threadIdx.x == 0) { sk = (int)lw->ncls[s]; sw = lw->wstar[s]; }
+    if (threadIdx.x < LEVEL_K) { sb[threadIdx.x] = lw->cls_bits[s][threadIdx.x]; sthr[threadIdx.x] = lw->cls_thr[s][threadIdx.x]; }
+    __syncthreads();
+    const double wstar = sw;
+    if (!(wstar > 0.0)) return;
+    const int k = sk;
+    const unsigned long long n = ctl->count[s];
+    unsigned long long removed = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const double v = (double)ld<T>(S.w, i);
+        if (!(v > 0.0) || v >= wstar) continue;
+        const unsigned long long b = dbits(v);
+        unsigned long long thr = 0;
+        for (int j = 0; j < k; ++j)
+            if (sb[j] == b) thr = sthr[j];
+        const uint4 r = event_draw(seed, S.id[i], step, 0xFFFFFFFFu);
+        const unsigned long long m = ((unsigned long long)r.x << 20) | (unsigned long long)(r.y >> 12);
+        if (m < thr) st<T>(S.w, i, (T)wstar);
         else { st<T>(S.w, i, (T)0); ++removed; }
     }
     for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
@@ -290,18 +428,12 @@ qed_status compact_impl(qed_ctx *ctx, qed_species *sp, int s) {
     return QED_OK;
 }
 
+// Histogram path, for species with more than LEVEL_K distinct weights.
 template <class T>
-qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
+qed_status level_hist(qed_ctx *ctx, qed_species *sp, int s, int64_t step, int64_t n) {
     const int64_t cap = ctx->cfg.thin_cap;
     cudaStream_t st = ctx->stream;
-    // alive count after compaction
-    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
-    SFQ_CUDA(cudaStreamSynchronize(st));
-    const int64_t n = (int64_t)ctx->ctl_host->count[s];
-    sp->count = n;
-    if (cap <= 0 || n <= cap) return QED_OK;
     const int blocks = ctx->sm_count * 4;
-    // scratch: 2 range words, candidates, histogram
     struct Work { unsigned long long range[2]; double cand[NCAND]; Hist h; };
     Work *dw = nullptr;
     SFQ_CUDA(cudaMallocAsync(&dw, sizeof(Work), st));
@@ -316,50 +448,44 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     double wmin, wmax;
     memcpy(&wmin, &hw.range[0], 8);
     memcpy(&wmax, &hw.range[1], 8);
-    double wstar;
-    if (wmin == wmax) {
-        wstar = wmax * (double)n / (double)cap;
-    } else {
-        double lo = wmin, hi = wmax * (double)n / (double)cap;
-        wstar = hi;
-        for (int it = 0; it < 24; ++it) {
-            for (int m = 0; m < NCAND; ++m) hw.cand[m] = lo + (hi - lo) * m / (NCAND - 1);
-            hw.cand[NCAND - 1] = hi;
-            memset(&hw.h, 0, sizeof(Hist));
-            SFQ_CUDA(cudaMemcpyAsync(dw->cand, hw.cand, sizeof(hw.cand) + sizeof(Hist), cudaMemcpyHostToDevice, st));
-            k_weight_hist<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, dw->cand, &dw->h);
-            SFQ_LAUNCHED(ctx, 1);
-            SFQ_CUDA(cudaMemcpyAsync(&hw.h, &dw->h, sizeof(Hist), cudaMemcpyDeviceToHost, st));
-            SFQ_CUDA(cudaStreamSynchronize(st));
-            // S(c_m) = (sum of weights below c_m) / c_m + (count at or above c_m)
-            double below = 0.0;
-            unsigned long long above = 0;
-            for (int b = 0; b < NBIN; ++b) above += hw.h.cnt[b];
-            int m_hit = -1;
-            double A = 0.0;
-            unsigned long long C = 0;
-            for (int m = 0; m < NCAND; ++m) {
-                below += hw.h.sum[m];        // bins 0..m hold weights below c_m
-                above -= hw.h.cnt[m];
-                const double S = below / hw.cand[m] + (double)above;
-                if (S <= (double)cap) { m_hit = m; A = below; C = above; break; }
-            }
-            if (m_hit <= 0) { wstar = hi; break; }
-            // bracket (c_{m-1}, c_m]; weights inside it live in bin m
-            const double clo = hw.cand[m_hit - 1], chi_ = hw.cand[m_hit];
-            double bmax;
-            memcpy(&bmax, &hw.h.maxbits[m_hit], 8);
-            if (hw.h.cnt[m_hit] == 0 || bmax <= clo) {
-                // for w in (c_{m-1}, c_m]: S(w) = A / w + C with A over weights < c_m
-                wstar = A / ((double)cap - (double)C);
-                if (!(wstar > clo && wstar <= chi_)) wstar = chi_;
-                break;
-            }
-            lo = clo;
-            hi = chi_;
-            wstar = hi;
-            if (hi - lo <= 4.0 * (nextafter(hi, INFINITY) - hi)) break;
+    double lo = wmin, hi = wmax * (double)n / (double)cap;
+    double wstar = hi;
+    for (int it = 0; it < 24; ++it) {
+        for (int m = 0; m < NCAND; ++m) hw.cand[m] = lo + (hi - lo) * m / (NCAND - 1);
+        hw.cand[NCAND - 1] = hi;
+        memset(&hw.h, 0, sizeof(Hist));
+        SFQ_CUDA(cudaMemcpyAsync(dw->cand, hw.cand, sizeof(hw.cand) + sizeof(Hist), cudaMemcpyHostToDevice, st));
+        k_weight_hist<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, dw->cand, &dw->h);
+        SFQ_LAUNCHED(ctx, 1);
+        SFQ_CUDA(cudaMemcpyAsync(&hw.h, &dw->h, sizeof(Hist), cudaMemcpyDeviceToHost, st));
+        SFQ_CUDA(cudaStreamSynchronize(st));
+        // S(c_m) = (sum of weights below c_m) / c_m + (count at or above c_m)
+        double below = 0.0;
+        unsigned long long above = 0;
+        for (int bi = 0; bi < NBIN; ++bi) above += hw.h.cnt[bi];
+        int m_hit = -1;
+        double A = 0.0;
+        unsigned long long C = 0;
+        for (int m = 0; m < NCAND; ++m) {
+            below += hw.h.sum[m];        // bins 0..m hold weights below c_m
+            above -= hw.h.cnt[m];
+            const double S = below / hw.cand[m] + (double)above;
+            if (S <= (double)cap) { m_hit = m; A = below; C = above; break; }
         }
+        if (m_hit <= 0) { wstar = hi; break; }
+        const double clo = hw.cand[m_hit - 1], chi_ = hw.cand[m_hit];
+        double bmax;
+        memcpy(&bmax, &hw.h.maxbits[m_hit], 8);
+        if (hw.h.cnt[m_hit] == 0 || bmax <= clo) {
+            // for w in (c_{m-1}, c_m]: S(w) = A / w + C with A over weights < c_m
+            wstar = A / ((double)cap - (double)C);
+            if (!(wstar > clo && wstar <= chi_)) wstar = chi_;
+            break;
+        }
+        lo = clo;
+        hi = chi_;
+        wstar = hi;
+        if (hi - lo <= 4.0 * (nextafter(hi, INFINITY) - hi)) break;
     }
     SFQ_CUDA(cudaFreeAsync(dw, st));
     SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
@@ -367,10 +493,41 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     k_level_apply<T><<<blocks, 256, 0, st>>>(S, ctx->ctl, s, wstar, ctx->cfg.seed, (unsigned)step);
     SFQ_LAUNCHED(ctx, 1);
     SFQ_CUDA(cudaGetLastError());
+    return compact_impl<T>(ctx, sp, s);
+}
+
+// Leveling of one species at `step`: weight classes, device-side solve,
+// keep/drop, compaction.  No host round trip unless the species has more
+// than LEVEL_K distinct weights (then the histogram path runs).  sp->count
+// must bound the device count from above; it is refreshed on return when
+// `sync` is set.
+template <class T>
+qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step, bool sync) {
+    const int64_t cap = ctx->cfg.thin_cap;
+    cudaStream_t st = ctx->stream;
+    if (cap <= 0 || sp->count <= cap) return QED_OK;
+    const int blocks = ctx->sm_count * 4;
+    SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
+                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
+    SFQ_CUDA(cudaMemsetAsync(ctx->lev->bits[s], 0, sizeof(ctx->lev->bits[s]), st));
+    SFQ_CUDA(cudaMemsetAsync(ctx->lev->cnt[s], 0, sizeof(ctx->lev->cnt[s]), st));
+    SFQ_CUDA(cudaMemsetAsync(&ctx->lev->overflow[s], 0, sizeof(unsigned long long), st));
+    k_level_classes<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
+    k_level_solve<<<1, 32, 0, st>>>(ctx->ctl, s, ctx->lev, (long long)cap);
+    k_level_apply_classes<T><<<blocks, 256, 0, st>>>(S, ctx->ctl, s, ctx->lev, ctx->cfg.seed, (unsigned)step);
+    SFQ_LAUNCHED(ctx, 3);
+    SFQ_CUDA(cudaGetLastError());
     qed_status e = compact_impl<T>(ctx, sp, s);
     if (e != QED_OK) return e;
+    if (!sync) return QED_OK;
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
     SFQ_CUDA(cudaStreamSynchronize(st));
+    if (ctx->ctl_host->need_hist[s]) {
+        e = level_hist<T>(ctx, sp, s, step, (int64_t)ctx->ctl_host->count[s]);
+        if (e != QED_OK) return e;
+        SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+        SFQ_CUDA(cudaStreamSynchronize(st));
+    }
     sp->count = (int64_t)ctx->ctl_host->count[s];
     return QED_OK;
 }
@@ -406,6 +563,7 @@ qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s) {
 }
 
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
-    if (ctx->cfg.precision == QED_FP32) return level_impl<float>(ctx, sp, s, step);
-    return level_impl<double>(ctx, sp, s, step);
+    if (ctx->cfg.precision == QED_FP32) return level_impl<float>(ctx, sp, s, step, true);
+    return level_impl<double>(ctx, sp, s, step, true);
 }
+

@@ -63,20 +63,28 @@ __device__ __forceinline__ uint4 event_draw(uint64_t seed, uint64_t id, unsigned
                          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
-// Uniform in (0,1): FP64 mode uses 52 bits, (m + 1/2) 2^-52; FP32 mode uses
-// 23 bits, (m + 1/2) 2^-23, built from the exponent trick without any FP64 op.
+// Uniform draws from two Philox words (a, b): u = (m + 1/2) 2^-52 with
+// m = a 2^20 + (b >> 12), in (0, 1) and never 0 or 1.  FP64 mode uses u
+// itself and v = 1 - u (exact in double).  FP32 mode builds u and 1 - u
+// separately from the bits, (m + 1/2) 2^-52 and (m' + 1/2) 2^-52 with
+// m' = ~a 2^20 + (~b >> 12) = 2^52 - 1 - m, each to FP32 relative precision,
+// so that log u and log(1 - u) stay accurate at both ends without FP64.
 template <class T> struct Uniform;
 template <> struct Uniform<double> {
-    static __device__ __forceinline__ double from(uint32_t a, uint32_t b) {
+    static __device__ __forceinline__ void draw(uint32_t a, uint32_t b, double &u, double &v) {
         const uint64_t m = ((uint64_t)a << 20) | (uint64_t)(b >> 12);
-        return ((double)m + 0.5) * 0x1p-52;
+        u = ((double)m + 0.5) * 0x1p-52;
+        v = 1.0 - u;
     }
+    static __device__ __forceinline__ double neglog(double u, double) { return -log(u); }
 };
 template <> struct Uniform<float> {
-    static __device__ __forceinline__ float from(uint32_t a, uint32_t) {
-        const float f = __uint_as_float(0x3F800000u | (a >> 9)) - 1.0f;   // m 2^-23, exact
-        return f + 0x1p-24f;                                                // (m + 1/2) 2^-23, exact
+    static __device__ __forceinline__ void draw(uint32_t a, uint32_t b, float &u, float &v) {
+        u = fmaf(__uint2float_rn(a), 0x1p-32f, fmaf(__uint2float_rn(b >> 12), 0x1p-52f, 0x1p-53f));
+        v = fmaf(__uint2float_rn(~a), 0x1p-32f, fmaf(__uint2float_rn((~b) >> 12), 0x1p-52f, 0x1p-53f));
     }
+    // -ln u, from v = 1 - u when u is near 1
+    static __device__ __forceinline__ float neglog(float u, float v) { return u < 0.5f ? -logf(u) : -log1pf(-v); }
 };
 
 // ---------------------------------------------------------------------------
@@ -122,6 +130,46 @@ __device__ __forceinline__ double chi_fp64(double e0, double px, double py, doub
     double q = fma(ux, ux, fma(uy, uy, uz * uz)) - pe * pe;
     q = q > 0.0 ? q : 0.0;
     return sqrt(q) * (1.0 / RS);
+}
+
+// ---------------------------------------------------------------------------
+// FP32-mode chi, FP64-accurate where it matters.  With e0^2 = 1 + p^2
+// (lepton) or k^2 (photon), Lagrange's identity turns the cancelling form into
+//   chi^2 R^2 = S + T,  S = [E^2] + |p x E|^2 + |p x B|^2  (>= 0, no cancellation),
+//                       T = 2 e0 E.(p x B)
+// so only T can cancel S.  Cross products use Kahan's difference of products
+// (error about one ulp of the result).  When the magnitude of the terms,
+// S + 2 e0 sum|E_i (p x B)_i|, exceeds four times S + T the cancellation is
+// real and the direct form is evaluated in FP64 instead.  Returns chi.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    // a*b - c*d
+    const float w = c * d;
+    const float e = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+template <bool LEPTON>
+__device__ __forceinline__ float chi_guarded(float e0, const float p[3], const float E[3], const float B[3],
+                                             unsigned *fp64_used) {
+    const float ax = diff_of_products(p[1], E[2], p[2], E[1]);
+    const float ay = diff_of_products(p[2], E[0], p[0], E[2]);
+    const float az = diff_of_products(p[0], E[1], p[1], E[0]);
+    const float bx = diff_of_products(p[1], B[2], p[2], B[1]);
+    const float by = diff_of_products(p[2], B[0], p[0], B[2]);
+    const float bz = diff_of_products(p[0], B[1], p[1], B[0]);
+    float S = ax * ax + ay * ay + az * az + bx * bx + by * by + bz * bz;
+    if (LEPTON) S += E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
+    const float te = 2.0f * e0;
+    const float T = te * (E[0] * bx + E[1] * by + E[2] * bz);
+    const float M = S + te * (fabsf(E[0] * bx) + fabsf(E[1] * by) + fabsf(E[2] * bz));
+    const float r = S + T;
+    if (M <= 4.0f * r) return sqrtf(r) * (float)(1.0 / RS);
+    ++*fp64_used;
+    const double pd0 = p[0], pd1 = p[1], pd2 = p[2];
+    const double e0d = LEPTON ? sqrt(1.0 + (pd0 * pd0 + pd1 * pd1 + pd2 * pd2)) : sqrt(pd0 * pd0 + pd1 * pd1 + pd2 * pd2);
+    return (float)chi_fp64(e0d, pd0, pd1, pd2, E[0], E[1], E[2], B[0], B[1], B[2]);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,10 +260,14 @@ __device__ __forceinline__ T bilinear(const T *tab, int nchi, int ns, T c, T t) 
     return lo + fc * (hi - lo);
 }
 
+// logit u = ln u - ln(1 - u) from (u, v = 1 - u)
+__device__ __forceinline__ double logit(double u, double) { return log(u) - log1p(-u); }
+__device__ __forceinline__ float logit(float u, float v) { return logf(u) - logf(v); }
+
 // photon energy fraction delta (returned) and 1 - delta
 template <class T>
-__device__ __forceinline__ T sample_emission(const T *tab, T chi, T u, T *one_minus) {
-    const T s = m_log(u) - m_log1p(-u);
+__device__ __forceinline__ T sample_emission(const T *tab, T chi, T u, T v, T *one_minus) {
+    const T s = logit(u, v);
     const T c = (m_log10(chi) + (T)3) * (T)20;
     const T t = (s + (T)16) * (T)8;
     const T zeta = bilinear(tab, EM_NCHI, EM_NS, c, t);
@@ -226,10 +278,9 @@ __device__ __forceinline__ T sample_emission(const T *tab, T chi, T u, T *one_mi
 
 // electron energy fraction delta (returned) and 1 - delta (positron fraction)
 template <class T>
-__device__ __forceinline__ T sample_pair(const T *tab, T chi, T u, T *one_minus) {
+__device__ __forceinline__ T sample_pair(const T *tab, T chi, T u, T v, T *one_minus) {
     const bool flip = u > (T)0.5;
-    const T uu = flip ? (T)1 - u : u;
-    const T s = m_log(uu) - m_log1p(-uu);
+    const T s = flip ? logit(v, u) : logit(u, v);   // logit of min(u, 1 - u)
     const T c = (m_log10(chi) + (T)2) * (T)20;
     const T t = (s + (T)16) * (T)8;
     const T d = m_exp(bilinear(tab, PAIR_NCHI, PAIR_NS, c, t));

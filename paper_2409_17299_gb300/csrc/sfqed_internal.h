@@ -39,7 +39,22 @@ struct DevCtl {
     unsigned long long alive[3];        // compaction: alive entries per species
     unsigned long long holes[3];        // compaction: dead entries below alive[s]
     unsigned long long bad_index;       // a bounds check failed (index recorded, access skipped)
-    unsigned long long pad[8];
+    unsigned long long chi_fp64;        // FP32 mode: chi evaluations that fell back to FP64
+    unsigned long long need_hist[3];    // leveling: too many weight classes, use the histogram path
+    unsigned long long pad[4];
+};
+
+// Leveling by weight classes: the distinct alive weights of a species (at
+// most LEVEL_K), their counts, and per class the integer keep threshold.
+constexpr int LEVEL_K = 32;
+struct LevelWork {
+    unsigned long long bits[3][LEVEL_K];   // hash table: weight as double bits (0 = empty)
+    unsigned long long cnt[3][LEVEL_K];
+    unsigned long long overflow[3];
+    unsigned long long ncls[3];            // compacted classes, ascending weight
+    unsigned long long cls_bits[3][LEVEL_K];
+    unsigned long long cls_thr[3][LEVEL_K]; // keep iff m < thr (m: 52-bit draw); 2^52: always kept, unchanged
+    double wstar[3];                       // 0: no leveling this step
 };
 
 struct SpeciesDev {
@@ -58,6 +73,8 @@ struct PassArgs {
     int field_kind;
     double prm[6];
     double dt;
+    float dt_f;             // (float)dt
+    float dt_f_gt;          // smallest float above dt (FP32 first-iteration event test)
     double t_n;             // step * dt
     double t_n_red;         // (step * dt) reduced modulo 2 pi (FP32 phase)
     unsigned step;
@@ -91,6 +108,7 @@ struct qed_ctx {
     int64_t blk_cap;
     unsigned long long *slots;    // hole indices
     int64_t slots_cap;
+    sfq::LevelWork *lev;          // leveling work (device)
     // overflow snapshot
     void *snap;
     int64_t snap_bytes;
@@ -112,6 +130,8 @@ qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field,
 qed_status sfq_eval_rate(qed_ctx *ctx, int is_photon, const double *chi, int64_t n, double *F);
 qed_status sfq_sample(qed_ctx *ctx, int is_photon, const double *chi, const double *u, int64_t n,
                       double *delta, double *one_minus);
+qed_status sfq_eval_chi(qed_ctx *ctx, int is_photon, const double *p, const double *E, const double *B, int64_t n,
+                        double *chi, int64_t *n_fp64);
 qed_status sfq_philox(const uint32_t *ctr, int64_t n, uint64_t key, uint32_t *out, cudaStream_t s);
 // Implemented in sfqed_compact.cu
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);

@@ -19,14 +19,16 @@ template <> __device__ __forceinline__ double t_inf<double>() { return __longlon
 template <> __device__ __forceinline__ float t_inf<float>() { return __int_as_float(0x7f800000); }
 
 __device__ __forceinline__ void flush_stats(DevCtl *ctl, unsigned long long steps, unsigned long long ev,
-                                            unsigned mx, bool pair) {
+                                            unsigned mx, bool pair, unsigned n64) {
     // called by every lane of the warp after the grid-stride loop
     for (int o = 16; o > 0; o >>= 1) {
         steps += __shfl_down_sync(0xffffffffu, steps, o);
         ev += __shfl_down_sync(0xffffffffu, ev, o);
         mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        n64 += __shfl_down_sync(0xffffffffu, n64, o);
     }
     if ((threadIdx.x & 31) == 0) {
+        if (n64) atomicAdd(&ctl->chi_fp64, (unsigned long long)n64);
         if (steps) {
             atomicAdd(&ctl->particle_steps, steps);
             atomicAdd(pair ? &ctl->photon_steps : &ctl->lepton_steps, steps);
@@ -34,6 +36,46 @@ __device__ __forceinline__ void flush_stats(DevCtl *ctl, unsigned long long step
         if (ev) atomicAdd(pair ? &ctl->pair_events : &ctl->emit_events, ev);
         if (mx) atomicMax(&ctl->max_subevents, (unsigned long long)mx);
     }
+}
+
+// chi and energy of a lepton / photon in the mode's precision: FP64 mode uses
+// the direct FP64 form; FP32 mode the guarded form with FP64 fallback.
+template <class T>
+__device__ __forceinline__ void lepton_chi(const T p[3], const T E[3], const T B[3], T &gam, T &chi, T &p2,
+                                           unsigned &n64) {
+    if constexpr (sizeof(T) == 8) {
+        p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        gam = sqrt(1.0 + p2);
+        chi = chi_fp64(gam, p[0], p[1], p[2], E[0], E[1], E[2], B[0], B[1], B[2]);
+    } else {
+        p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        gam = sqrtf(1.0f + p2);
+        chi = chi_guarded<true>(gam, p, E, B, &n64);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T photon_chi(T k0, const T k[3], const T E[3], const T B[3], unsigned &n64) {
+    if constexpr (sizeof(T) == 8) return chi_fp64(k0, k[0], k[1], k[2], E[0], E[1], E[2], B[0], B[1], B[2]);
+    else return chi_guarded<false>(k0, k, E, B, &n64);
+}
+
+// Event test "tau + dt_hat > dt" and the remaining push length.  In FP32 mode
+// the first iteration (tau = 0) uses FP32 only: the smallest float above dt
+// gives the same decision, and (float)dt the same length.
+template <class T>
+__device__ __forceinline__ bool no_event_before_end(const PassArgs &a, double tau, T dth) {
+    if constexpr (sizeof(T) == 4) {
+        if (tau == 0.0) return dth >= a.dt_f_gt;
+    }
+    return tau + (double)dth > a.dt;
+}
+
+template <class T> __device__ __forceinline__ T remaining(const PassArgs &a, double tau) {
+    if constexpr (sizeof(T) == 4) {
+        if (tau == 0.0) return a.dt_f;
+    }
+    return (T)(a.dt - tau);
 }
 
 __device__ __forceinline__ void note_overflow(DevCtl *ctl, int s, unsigned long long slot) {
@@ -55,7 +97,7 @@ __global__ void __launch_bounds__(256) k_lepton_pass(PassArgs a) {
     const T *icdf = reinterpret_cast<const T *>(a.icdf_em);
     const T alpha_r = (T)(ALPHA * RS);
     unsigned long long my_steps = 0, my_ev = 0;
-    unsigned my_max = 0;
+    unsigned my_max = 0, n64 = 0;
 
     for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
@@ -73,19 +115,19 @@ __global__ void __launch_bounds__(256) k_lepton_pass(PassArgs a) {
         while (tau < a.dt) {
             T E[3], B[3];
             eval_field<T>(a, x[0], tau, E, B);
-            double pd0 = p[0], pd1 = p[1], pd2 = p[2];
-            double p2 = pd0 * pd0 + pd1 * pd1 + pd2 * pd2;
-            double gd = sqrt(1.0 + p2);
-            double chi = chi_fp64(gd, pd0, pd1, pd2, E[0], E[1], E[2], B[0], B[1], B[2]);
-            const T lam = p2 > 0.0 ? alpha_r / (T)gd * rate_em<T>(s_coef, (T)chi) : (T)0;
+            T gam, chi, p2;
+            lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+            const T lam = p2 > (T)0 ? alpha_r / gam * rate_em<T>(s_coef, chi) : (T)0;
             uint4 r = make_uint4(0, 0, 0, 0);
             T dth = t_inf<T>();
             if (lam > (T)0) {
                 r = event_draw(a.seed, id, a.step, k);
-                dth = -m_log(Uniform<T>::from(r.x, r.y)) / lam;
+                T uw, vw;
+                Uniform<T>::draw(r.x, r.y, uw, vw);
+                dth = Uniform<T>::neglog(uw, vw) / lam;
             }
-            if (tau + (double)dth > a.dt) {           // no event before the step ends
-                boris<T>(x, p, q, E, B, (T)(a.dt - tau));
+            if (no_event_before_end<T>(a, tau, dth)) {      // push to the end of the step
+                boris<T>(x, p, q, E, B, remaining<T>(a, tau));
                 tau = a.dt;
                 break;
             }
@@ -93,16 +135,14 @@ __global__ void __launch_bounds__(256) k_lepton_pass(PassArgs a) {
             tau += (double)dth;
             // event: chi at the emission point, energy from the inverse CDF
             eval_field<T>(a, x[0], tau, E, B);
-            pd0 = p[0]; pd1 = p[1]; pd2 = p[2];
-            p2 = pd0 * pd0 + pd1 * pd1 + pd2 * pd2;
-            gd = sqrt(1.0 + p2);
-            chi = chi_fp64(gd, pd0, pd1, pd2, E[0], E[1], E[2], B[0], B[1], B[2]);
-            T om;
-            const T delta = sample_emission<T>(icdf, (T)chi, Uniform<T>::from(r.z, r.w), &om);
-            const T g = (T)gd;
+            lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+            T om, ue, ve;
+            Uniform<T>::draw(r.z, r.w, ue, ve);
+            const T delta = sample_emission<T>(icdf, chi, ue, ve, &om);
+            const T g = gam;
             T g_after = om * g, k0 = delta * g;
             if (g_after < (T)1) { g_after = (T)1; k0 = g - (T)1; }
-            const T inv = (T)1 / (T)sqrt(p2);
+            const T inv = (T)1 / m_sqrt(p2);
             const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
             const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
             if (!(a.soft_filter && k0 < (T)2)) {
@@ -131,7 +171,7 @@ __global__ void __launch_bounds__(256) k_lepton_pass(PassArgs a) {
         my_max = max(my_max, k);
     }
     __syncwarp();
-    flush_stats(ctl, my_steps, my_ev, my_max, false);
+    flush_stats(ctl, my_steps, my_ev, my_max, false, n64);
 }
 
 // Photon push: straight flight, pair creation at the event, the photon is
@@ -148,7 +188,7 @@ __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
     const T alpha_r = (T)(ALPHA * RS);
     const SpeciesDev &S = a.sp[2];
     unsigned long long my_steps = 0, my_ev = 0;
-    unsigned my_max = 0;
+    unsigned my_max = 0, n64 = 0;
 
     for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
@@ -159,26 +199,27 @@ __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
         const T kx = ld<T>(S.px, i), ky = ld<T>(S.py, i), kz = ld<T>(S.pz, i);
         const unsigned long long id = __ldg(S.id + i);
         double tau = a.pass ? S.tau[i] : 0.0;
-        const double kd0 = kx, kd1 = ky, kd2 = kz;
-        const double k0d = sqrt(kd0 * kd0 + kd1 * kd1 + kd2 * kd2);
+        const T kv[3] = {kx, ky, kz};
+        const T k0 = m_sqrt(kx * kx + ky * ky + kz * kz);
         unsigned k = 0;
-        if (k0d > 0.0) {
-            const T k0 = (T)k0d;
+        if (k0 > (T)0) {
             const T inv = (T)1 / k0;
             const T nx = kx * inv, ny = ky * inv, nz = kz * inv;
             while (tau < a.dt) {
                 T E[3], B[3];
                 eval_field<T>(a, x[0], tau, E, B);
-                double chi = chi_fp64(k0d, kd0, kd1, kd2, E[0], E[1], E[2], B[0], B[1], B[2]);
-                const T lam = alpha_r / k0 * rate_pair<T>(s_coef, (T)chi);
+                T chi = photon_chi<T>(k0, kv, E, B, n64);
+                const T lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);
                 uint4 r = make_uint4(0, 0, 0, 0);
                 T dth = t_inf<T>();
                 if (lam > (T)0) {
                     r = event_draw(a.seed, id, a.step, k);
-                    dth = -m_log(Uniform<T>::from(r.x, r.y)) / lam;
+                    T uw, vw;
+                    Uniform<T>::draw(r.x, r.y, uw, vw);
+                    dth = Uniform<T>::neglog(uw, vw) / lam;
                 }
-                if (tau + (double)dth > a.dt) {
-                    const T h = (T)(a.dt - tau);
+                if (no_event_before_end<T>(a, tau, dth)) {
+                    const T h = remaining<T>(a, tau);
                     x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
                     tau = a.dt;
                     break;
@@ -186,9 +227,10 @@ __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
                 x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
                 tau += (double)dth;
                 eval_field<T>(a, x[0], tau, E, B);
-                chi = chi_fp64(k0d, kd0, kd1, kd2, E[0], E[1], E[2], B[0], B[1], B[2]);
-                T om;
-                const T delta = sample_pair<T>(icdf, (T)chi, Uniform<T>::from(r.z, r.w), &om);
+                chi = photon_chi<T>(k0, kv, E, B, n64);
+                T om, ue, ve;
+                Uniform<T>::draw(r.z, r.w, ue, ve);
+                const T delta = sample_pair<T>(icdf, chi, ue, ve, &om);
                 T em = delta * k0, ep = om * k0;
                 em = em < (T)1 ? (T)1 : em;
                 ep = ep < (T)1 ? (T)1 : ep;
@@ -230,7 +272,7 @@ __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
         my_max = max(my_max, k);
     }
     __syncwarp();
-    flush_stats(ctl, my_steps, my_ev, my_max, true);
+    flush_stats(ctl, my_steps, my_ev, my_max, true, n64);
 }
 
 // Pass ranges: at the step start every particle present; afterwards the
@@ -268,13 +310,36 @@ __global__ void k_eval_rate(const T *coef, int is_photon, const double *chi, lon
     F[i] = (double)(is_photon ? rate_pair<T>(coef, c) : rate_em<T>(coef, c));
 }
 
+// chi of n particles (p, E, B as n x 3 doubles) in the mode's precision
+template <class T>
+__global__ void k_eval_chi(int is_photon, const double *p, const double *E, const double *B, long long n,
+                           double *chi, unsigned long long *n64_out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T pv[3] = {(T)p[3 * i], (T)p[3 * i + 1], (T)p[3 * i + 2]};
+    const T Ev[3] = {(T)E[3 * i], (T)E[3 * i + 1], (T)E[3 * i + 2]};
+    const T Bv[3] = {(T)B[3 * i], (T)B[3 * i + 1], (T)B[3 * i + 2]};
+    unsigned n64 = 0;
+    T c;
+    if (is_photon) {
+        const T k0 = m_sqrt(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
+        c = photon_chi<T>(k0, pv, Ev, Bv, n64);
+    } else {
+        T gam, p2;
+        lepton_chi<T>(pv, Ev, Bv, gam, c, p2, n64);
+    }
+    chi[i] = (double)c;
+    if (n64) atomicAdd(n64_out, (unsigned long long)n64);
+}
+
 template <class T>
 __global__ void k_sample(const T *tab, int is_photon, const double *chi, const double *u, long long n,
                          double *delta, double *om) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T o;
-    const T d = is_photon ? sample_pair<T>(tab, (T)chi[i], (T)u[i], &o) : sample_emission<T>(tab, (T)chi[i], (T)u[i], &o);
+    const T uu = (T)u[i], vv = (T)(1.0 - u[i]);
+    const T d = is_photon ? sample_pair<T>(tab, (T)chi[i], uu, vv, &o) : sample_emission<T>(tab, (T)chi[i], uu, vv, &o);
     delta[i] = (double)d;
     if (om) om[i] = (double)o;
 }
@@ -445,6 +510,8 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.field_kind = field->kind;
     for (int i = 0; i < 6; ++i) a.prm[i] = field->params[i];
     a.dt = dt;
+    a.dt_f = (float)dt;
+    a.dt_f_gt = (double)a.dt_f > dt ? a.dt_f : nextafterf(a.dt_f, INFINITY);
     a.seed = ctx->cfg.seed;
     a.soft_filter = ctx->cfg.soft_photon_filter;
     a.record_newborn_tau = cascade ? 1 : 0;
@@ -508,6 +575,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     st.passes = (int64_t)c.passes;
     st.thinned = (int64_t)c.thinned;
     st.lepton_steps = (int64_t)c.lepton_steps;
+    st.chi_fp64 = (int64_t)c.chi_fp64;
     st.photon_steps = (int64_t)c.photon_steps;
     if (ctx->cfg.profile) {
         e = drain_events(ctx);
@@ -531,6 +599,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     ctx->acc.passes += st.passes;
     ctx->acc.thinned += st.thinned;
     ctx->acc.lepton_steps += st.lepton_steps;
+    ctx->acc.chi_fp64 += st.chi_fp64;
     ctx->acc.photon_steps += st.photon_steps;
     ctx->acc.launches += st.launches;
     ctx->acc.kernel_ms[0] += st.kernel_ms[0];
@@ -572,6 +641,24 @@ qed_status sfq_eval_rate(qed_ctx *ctx, int is_photon, const double *chi, int64_t
     else k_eval_rate<double><<<g, 256, 0, ctx->stream>>>(ctx->coef64, is_photon, chi, n, F);
     SFQ_CUDA(cudaGetLastError());
     SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}
+
+qed_status sfq_eval_chi(qed_ctx *ctx, int is_photon, const double *p, const double *E, const double *B, int64_t n,
+                        double *chi, int64_t *n_fp64) {
+    if (!ctx || n < 0 || (n > 0 && (!p || !E || !B || !chi))) return QED_ERR_INVALID;
+    if (n_fp64) *n_fp64 = 0;
+    if (n == 0) return QED_OK;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    unsigned long long *cnt = &ctx->ctl->chi_fp64;
+    SFQ_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream));
+    if (ctx->cfg.precision == QED_FP32) k_eval_chi<float><<<g, 256, 0, ctx->stream>>>(is_photon, p, E, B, n, chi, cnt);
+    else k_eval_chi<double><<<g, 256, 0, ctx->stream>>>(is_photon, p, E, B, n, chi, cnt);
+    SFQ_CUDA(cudaGetLastError());
+    unsigned long long h = 0;
+    SFQ_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (n_fp64) *n_fp64 = (int64_t)h;
     return QED_OK;
 }
 

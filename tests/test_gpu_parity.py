@@ -278,3 +278,111 @@ def test_fp32_cascade_statistics(otables):
         ea = np.sqrt(g[s]["px"] ** 2 + g[s]["py"] ** 2 + g[s]["pz"] ** 2)
         eb = np.sqrt(o[s]["px"] ** 2 + o[s]["py"] ** 2 + o[s]["pz"] ** 2)
         assert ks_2samp(ea, eb).pvalue > 0.01, s
+
+
+def _chi_cases(rng, n):
+    """Random momenta and fields, plus cancelling geometries: a lepton or
+    photon co-moving with a plane wave (E = a y, B = a z, p along x), and E
+    parallel to B (standing circularly polarised wave)."""
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    p = d * 10 ** rng.uniform(-2, 4, (n, 1))
+    E = rng.normal(size=(n, 3)) * 10 ** rng.uniform(0, 3.5, (n, 1))
+    B = rng.normal(size=(n, 3)) * 10 ** rng.uniform(0, 3.5, (n, 1))
+    m = n // 8
+    a = 10 ** rng.uniform(1, 3.5, m)
+    P = 10 ** rng.uniform(0, 3.5, m)
+    p[:m] = np.stack([P, 1e-3 * rng.normal(size=m), np.zeros(m)], 1)
+    E[:m] = np.stack([np.zeros(m), a, np.zeros(m)], 1)
+    B[:m] = np.stack([np.zeros(m), np.zeros(m), a], 1)
+    u = rng.normal(size=(m, 3))
+    E[m:2 * m] = u * a[:, None]
+    B[m:2 * m] = u * (0.7 * a)[:, None]
+    return p, E, B
+
+
+def _chi_exact(p, E, B, photon):
+    """50-digit decimal evaluation of the direct form on the given doubles."""
+    from decimal import Decimal as D, getcontext
+    getcontext().prec = 50
+    R = D(W.R_SCHWINGER)
+    out, cf = [], []
+    for pi, Ei, Bi in zip(p, E, B):
+        pv = [D(float(v)) for v in pi]
+        Ev = [D(float(v)) for v in Ei]
+        Bv = [D(float(v)) for v in Bi]
+        p2 = sum(v * v for v in pv)
+        e0 = p2.sqrt() if photon else (1 + p2).sqrt()
+        cx = [pv[1] * Bv[2] - pv[2] * Bv[1], pv[2] * Bv[0] - pv[0] * Bv[2], pv[0] * Bv[1] - pv[1] * Bv[0]]
+        u = [e0 * Ev[i] + cx[i] for i in range(3)]
+        s = sum(pv[i] * Ev[i] for i in range(3))
+        uu = sum(v * v for v in u)
+        qq = uu - s * s
+        out.append(float(max(qq, D(0)).sqrt() / R))
+        # condition number of the direct form: magnitudes of all terms over the result
+        mag = [abs(e0 * Ev[0]) + abs(pv[1] * Bv[2]) + abs(pv[2] * Bv[1]),
+               abs(e0 * Ev[1]) + abs(pv[2] * Bv[0]) + abs(pv[0] * Bv[2]),
+               abs(e0 * Ev[2]) + abs(pv[0] * Bv[1]) + abs(pv[1] * Bv[0])]
+        sm = sum(abs(pv[i] * Ev[i]) for i in range(3))
+        cf.append(float((sum(m * m for m in mag) + sm * sm) / qq) if qq > 0 else float("inf"))
+    return np.array(out), np.array(cf)
+
+
+@pytest.mark.parametrize("prec", [q.QED_FP64, q.QED_FP32])
+@pytest.mark.parametrize("photon", [False, True])
+def test_chi_against_exact(prec, photon):
+    """chi in FP64 mode and in FP32 mode (FP32 split S + T with FP64 fallback)
+    against a 50-digit evaluation on the same (rounded) inputs.  Bound: the
+    mode's rounding plus the FP64 cancellation loss ~2^-52 c of the direct form,
+    c = (sum_i (sum of |terms of u_i|)^2 + (sum |p_i E_i|)^2) / chi^2 R^2."""
+    rng = np.random.default_rng(17 + photon)
+    n = 4000
+    p, E, B = _chi_cases(rng, n)
+    if prec == q.QED_FP32:
+        p, E, B = (a.astype(np.float32).astype(np.float64) for a in (p, E, B))
+    g = q.Generator(q.make_config(precision=prec))
+    dp, dE, dB = _dev(p.ravel()), _dev(E.ravel()), _dev(B.ravel())
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    n64 = q.qed_eval_chi(g.ctx, photon, dp.data_ptr(), dE.data_ptr(), dB.data_ptr(), n, out.data_ptr())
+    got = out.cpu().numpy()
+    want, cf = _chi_exact(p, E, B, photon)
+    base = 1e-13 if prec == q.QED_FP64 else 6e-6
+    ok = want > 0
+    rel = np.abs(got[ok] - want[ok]) / want[ok]
+    bound = base + 4e-16 * cf[ok]
+    assert np.all(rel <= bound), (rel / bound).max()
+    assert np.all(np.abs(got[~ok]) <= 1e-7 * np.linalg.norm(E[~ok], axis=1))
+    if prec == q.QED_FP32:
+        assert n64 >= (n // 8) * 0.9          # the co-moving cases fell back to FP64
+        assert n64 <= n // 4                  # the rest stayed in FP32
+    g.close()
+
+
+@pytest.mark.parametrize("weights", ["classes", "lognormal"])
+def test_leveling_matches_oracle(weights):
+    """qed_compact with a cap: the survivor set and the new weights equal the
+    oracle's.  "classes" has 5 distinct weights (class path); "lognormal"
+    has ~1e5 distinct weights (histogram path)."""
+    rng = np.random.default_rng(9)
+    n, cap = 100000, 30000
+    if weights == "classes":
+        w = rng.choice([0.5, 1.0, 1.25, 2.0, 7.0], size=n)
+    else:
+        w = np.exp(rng.normal(size=n))
+    w[::11] = 0.0                                    # a few dead entries as well
+    sp = {"x": rng.normal(size=n), "y": rng.normal(size=n), "z": rng.normal(size=n),
+          "px": rng.normal(size=n), "py": rng.normal(size=n), "pz": rng.normal(size=n), "w": w,
+          "id": rng.permutation(10 * n)[:n].astype(np.uint64)}
+    g = q.Generator(q.make_config(precision=q.QED_FP64, seed=9, thin_cap=cap))
+    e = q.DeviceEnsemble.from_host([sp, W._empty(), W._empty()], [n, 1, 1], q.QED_FP64)
+    g.compact(e, 17)
+    got = by_id(e.to_host(0))
+    oe = oracle.Ensemble.from_arrays([sp, None, None], [n, 1, 1])
+    oracle.compact(oe, 0)
+    oracle.level(oe, 0, cap, seed=9, step=17)
+    want = by_id(oe.view(0))
+    assert np.array_equal(got["id"], want["id"])
+    assert np.allclose(got["w"], want["w"], rtol=1e-14, atol=0)
+    for f in ("x", "px", "nevents"):
+        assert np.array_equal(got[f], want[f])
+    g.close()
