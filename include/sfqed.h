@@ -180,6 +180,37 @@ qed_status qed_eval_chi(qed_ctx *ctx, int is_photon, const double *p_dev, const 
 qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const double *u_dev,
                       int64_t n, double *delta_dev, double *one_minus_dev);
 
+/* ---- compaction for callers that cannot allocate --------------------- */
+
+/* Largest species count qed_compact_species_noalloc() accepts. */
+#define QED_NOALLOC_MAX_ENTRIES (1 << 20)
+
+/* Remove dead entries (weight 0) from one species without allocating any
+ * memory.  The paper has no counterpart: this exists for callers that cannot
+ * call cudaMalloc, such as a host code whose device memory belongs entirely
+ * to its own pool allocator, or a time loop that cannot accept the
+ * device-wide synchronisation cudaMalloc / cudaFree may cause.
+ *  sp           in/out: caller-owned device arrays (16-byte aligned); count is
+ *               read and updated (alive entries end up in [0, count))
+ *  precision    QED_FP64 (double arrays) or QED_FP32 (float arrays)
+ *  cuda_stream  stream for the work (NULL = default stream); synchronised
+ *               before returning
+ * Same result as the compaction inside qed_compact(): the r-th dead slot
+ * below the new count receives the r-th alive entry at or above it.
+ * Scratch: one file-scope device array of about 8 MB holding control words,
+ * per-block counts and hole ranks, kept by every GPU that loads the library
+ * until the process exits.  No context is needed and nothing is allocated:
+ * no cudaMalloc, cudaFree or allocating library routine.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call
+ * resets the words it needs), so calls that overlap on the GPU -- from
+ * several threads or streams at once -- race and corrupt each other.
+ * Errors: QED_ERR_INVALID for a null or misaligned array, an unknown
+ * precision, count < 0 or > capacity, or count > QED_NOALLOC_MAX_ENTRIES;
+ * QED_ERR_STATE if a bounds check inside the kernels failed; QED_ERR_CUDA. */
+qed_status qed_compact_species_noalloc(qed_species *sp, int precision, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,9 @@ QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
 QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP = 0, 1, 2
 
 EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_compact", "qed_get_stats", "qed_strerror",
-            "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi")
+            "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
+            "qed_compact_species_noalloc")
+QED_NOALLOC_MAX_ENTRIES = 1 << 20
 
 
 class QedConfig(C.Structure):
@@ -93,6 +95,7 @@ def lib():
         "qed_get_tables": (i32, [p, p, p, p, p]),
         "qed_eval_rate": (i32, [p, i32, p, i64, p]),
         "qed_sample": (i32, [p, i32, p, p, i64, p, p]),
+        "qed_compact_species_noalloc": (i32, [C.POINTER(QedSpecies), i32, p]),
         "qed_eval_chi": (i32, [p, i32, p, p, p, i64, p, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
@@ -185,6 +188,16 @@ def qed_sample(ctx, is_photon: bool, chi_dev_ptr: int, u_dev_ptr: int, n: int, d
                           C.c_void_p(delta_dev_ptr), C.c_void_p(one_minus_dev_ptr or 0))
     if rc != QED_OK:
         raise QedError(rc, "qed_sample")
+
+
+def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream: int | None = None) -> int:
+    """Compaction of one species that allocates no device memory (for callers
+    whose device memory is owned by another allocator); species.count is
+    updated in place.  Overlapping calls on the GPU race (shared scratch)."""
+    rc = lib().qed_compact_species_noalloc(C.byref(species), int(precision), C.c_void_p(cuda_stream or 0))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_compact_species_noalloc")
+    return rc
 
 
 # --------------------------------------------------------------------------

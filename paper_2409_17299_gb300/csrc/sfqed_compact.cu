@@ -567,3 +567,85 @@ qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step)
     return level_impl<double>(ctx, sp, s, step, true);
 }
 
+// ---------------------------------------------------------------------------
+// Compaction that allocates nothing.  Some callers cannot call cudaMalloc:
+// their device memory is owned entirely by another allocator (a host code's
+// memory pool), or they cannot accept the device-wide synchronisation that
+// cudaMalloc / cudaFree may cause inside their time loop.  This variant keeps
+// its scratch (control words, per-block counts, hole ranks) in one
+// file-scope device array of fixed size, which every GPU that loads the
+// library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace sfq {
+namespace {
+constexpr long long NA_MAX_ENTRIES = 1ll << 20;                       // largest species count accepted
+constexpr long long NA_CTL_WORDS = ((long long)sizeof(DevCtl) + 255) / 256 * 32;
+constexpr long long NA_BLK_WORDS = (NA_MAX_ENTRIES / CTILE + 2 + 31) / 32 * 32;
+constexpr long long NA_WORDS = NA_CTL_WORDS + NA_BLK_WORDS + NA_MAX_ENTRIES;
+
+__global__ void k_noalloc_begin(DevCtl *ctl, unsigned long long count) {
+    // the array keeps the previous call's contents: reset what must start at zero
+    ctl->count[0] = count;
+    ctl->capacity[0] = count;
+    ctl->alive[0] = 0;
+    ctl->holes[0] = 0;
+    ctl->bad_index = 0;
+}
+}  // namespace
+}  // namespace sfq
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[sfq::NA_WORDS];
+
+namespace {
+constexpr int NA_MAX_DEVICES = 64;
+unsigned long long *g_noalloc_addr[NA_MAX_DEVICES];   // device address of the array, per device
+}
+
+template <class T>
+static qed_status noalloc_compact(qed_species *sp, cudaStream_t st, unsigned long long *base) {
+    using namespace sfq;
+    DevCtl *ctl = reinterpret_cast<DevCtl *>(base);
+    unsigned long long *blk = base + NA_CTL_WORDS;
+    unsigned long long *slots = blk + NA_BLK_WORDS;
+    const long long n = sp->count;
+    const long long nb = (n + CTILE - 1) / CTILE;
+    SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
+                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
+    k_noalloc_begin<<<1, 1, 0, st>>>(ctl, (unsigned long long)n);
+    k_count_alive<T><<<(unsigned)nb, CT, 0, st>>>(sp->w, ctl, 0, blk);
+    k_scan_blocks<<<1, 1024, 0, st>>>(blk, nb, ctl, 0);
+    k_mark_holes<T><<<(unsigned)nb, CT, 0, st>>>(sp->w, ctl, 0, blk, slots);
+    k_fill_holes<T><<<(unsigned)nb, CT, 0, st>>>(S, ctl, 0, blk, slots);
+    SFQ_CUDA(cudaGetLastError());
+    unsigned long long res[2];   // alive, bad index
+    SFQ_CUDA(cudaMemcpyAsync(&res[0], &ctl->alive[0], sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    SFQ_CUDA(cudaMemcpyAsync(&res[1], &ctl->bad_index, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    SFQ_CUDA(cudaStreamSynchronize(st));
+    if (res[1]) return QED_ERR_STATE;
+    sp->count = (int64_t)res[0];
+    return QED_OK;
+}
+
+extern "C" qed_status qed_compact_species_noalloc(qed_species *sp, int precision, void *cuda_stream) {
+    using namespace sfq;
+    if (!sp || (precision != QED_FP64 && precision != QED_FP32)) return QED_ERR_INVALID;
+    if (sp->count < 0 || sp->count > sp->capacity) return QED_ERR_INVALID;
+    if (sp->count > NA_MAX_ENTRIES) return QED_ERR_INVALID;
+    if (sp->count == 0) return QED_OK;
+    const void *ptrs[] = {sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w, sp->id, sp->nevents};
+    for (const void *q : ptrs)
+        if (!q || (reinterpret_cast<uintptr_t>(q) & 15u)) return QED_ERR_INVALID;
+    int dev = 0;
+    SFQ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return QED_ERR_INVALID;
+    if (!g_noalloc_addr[dev]) {
+        // once per device, with that device current: the host-side name of the
+        // array is not a device address, so ask the runtime for it
+        void *p = nullptr;
+        SFQ_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = static_cast<unsigned long long *>(p);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == QED_FP32) return noalloc_compact<float>(sp, st, g_noalloc_addr[dev]);
+    return noalloc_compact<double>(sp, st, g_noalloc_addr[dev]);
+}
