@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rotating_e_cascade",
-                    choices=["rotating_e_cascade", "uniform_b_emission", "standing_wave_cascade"])
+                    choices=["rotating_e_cascade", "uniform_b_emission", "standing_wave_cascade",
+                             "batched_uniform_b"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time the FP64 mode (extra key)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
@@ -56,12 +57,16 @@ def make_workload(name, scale=1.0, rank=0):
     elif name == "standing_wave_cascade":
         w = W.standing_wave_cascade(n=int(1_000_000 * scale), seed=4 + 1000 * rank,
                                     thin_cap=int(200_000_000 * scale))
+    elif name == "batched_uniform_b":
+        w = W.batched_uniform_b(seed=2 + 1000 * rank, size_scale=scale)
     else:
         w = W.uniform_b_emission(n=int(16384 * scale), seed=1000 * rank)
     return w
 
 
 def default_steps(w):
+    if isinstance(w, list):
+        return 3, w[0].nsteps
     return 3, w.nsteps - 3
 
 
@@ -83,6 +88,10 @@ def _oracle_shard(args):
     sys.path.insert(0, ROOT)
     import oracle
     w = make_workload(name, 1.0)
+    if isinstance(w, list):                       # batched: shard k samples ensemble k
+        w = w[scale_seed % len(w)]
+        hi = lo + min(hi - lo, len(w.species[0]["id"]))
+        lo, hi = 0, hi - lo
     total = len(w.species[0]["id"])
     frac = (hi - lo) / total
     ws = W.subset(w, 0, slice(lo, hi))
@@ -105,16 +114,21 @@ def oracle_run(name, warm, steps, target_s=15.0, procs=None):
     import multiprocessing as mp
     procs = procs or min(16, os.cpu_count() or 1)
     w = make_workload(name, 1.0)
-    total = len(w.species[0]["id"])
+    total = sum(len(x.species[0]["id"]) for x in w) if isinstance(w, list) else len(w.species[0]["id"])
     # seeds per shard sized from a nominal oracle rate of ~3e6 particle-steps/s
     if name == "rotating_e_cascade":
         per = 250
     elif name == "standing_wave_cascade":
         per = 60
+    elif name == "batched_uniform_b":
+        per = 400
     else:
         per = 2000
     per = max(1, min(per, total // procs))
-    jobs = [(name, 0, k * per, (k + 1) * per, warm, steps) for k in range(procs)]
+    if isinstance(w, list):
+        jobs = [(name, k, 0, per, warm, steps) for k in range(procs)]
+    else:
+        jobs = [(name, 0, k * per, (k + 1) * per, warm, steps) for k in range(procs)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(procs) as pool:
@@ -201,7 +215,8 @@ def gpu_run(args, w, precision, warm, steps, timed=True, profile=True):
     torch.cuda.synchronize()
     evs = []
     tot = {"particle_steps": 0, "emit_events": 0, "pair_events": 0, "lepton_steps": 0, "photon_steps": 0,
-           "launches": 0, "kernel_ms": [0.0, 0.0], "passes": 0, "thinned": 0}
+           "launches": 0, "kernel_ms": [0.0, 0.0, 0.0, 0.0], "passes": 0, "thinned": 0, "sync_ms": 0.0,
+           "call_ms": 0.0, "chi_fp64": 0}
     lepton_launches = 0
     t0 = time.perf_counter()
     for s in range(warm, warm + steps):
@@ -213,10 +228,10 @@ def gpu_run(args, w, precision, warm, steps, timed=True, profile=True):
         b.record(stream)
         evs.append((a, b))
         for k in ("particle_steps", "emit_events", "pair_events", "lepton_steps", "photon_steps", "launches",
-                  "passes", "thinned"):
+                  "passes", "thinned", "sync_ms", "call_ms", "chi_fp64"):
             tot[k] += st[k]
-        tot["kernel_ms"][0] += st["kernel_ms"][0]
-        tot["kernel_ms"][1] += st["kernel_ms"][1]
+        for k in range(4):
+            tot["kernel_ms"][k] += st["kernel_ms"][k]
         lepton_launches += 1 + st["passes"]
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -227,6 +242,65 @@ def gpu_run(args, w, precision, warm, steps, timed=True, profile=True):
     torch.cuda.empty_cache()
     tot["lepton_launches"] = lepton_launches
     return ms, wall, tot, counts
+
+
+def batch_run(ws, precision, warm, steps, tune=True):
+    """64 ensembles through qed_batch_push: one persistent launch per call.
+    A sizing pass on copies fixes the photon buffers; W warm-up steps run as
+    one call, then the K timed steps as one call."""
+    import torch
+    import paper_2409_17299_gb300 as q
+    prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
+    cfg = q.make_config(precision=prec, seed=ws[0].seed, push_photons=0, profile=1)
+    gen = q.Generator(cfg)
+    fields = (q.QedFieldDesc * len(ws))()
+    for k, w in enumerate(ws):
+        fields[k] = q.make_field(w.field_kind, w.field_prm)
+
+    def fresh(ph_caps):
+        ens = [q.DeviceEnsemble.from_host(w.species, [len(w.species[0]["id"]), 1, int(c)], prec)
+               for w, c in zip(ws, ph_caps)]
+        arr = (q.QedParticles * len(ens))()
+        for k, e in enumerate(ens):
+            arr[k] = e.struct()
+        return ens, arr
+
+    # sizing pass: photon demand of the whole run, ensemble by ensemble
+    caps = [len(w.species[0]["id"]) * 2 + 1024 for w in ws]
+    while True:
+        ens, arr = fresh(caps)
+        rc, st = q.qed_batch_push(gen.ctx, arr, fields, ws[0].dt, warm + steps, 0)
+        if rc == q.QED_OK:
+            need = [int(arr[k].s[2].count) for k in range(len(ws))]
+            break
+        caps = [c * 4 for c in caps]
+        del ens, arr
+        torch.cuda.empty_cache()
+    del ens, arr
+    torch.cuda.empty_cache()
+    caps = [int(n * 1.05) + 1024 for n in need]
+    tuned = None
+    if tune:
+        ens, arr = fresh(caps)
+        tuned = q.qed_autotune_batch(gen.ctx, arr, fields, ws[0].dt, 2)
+        del ens, arr
+    ens, arr = fresh(caps)
+    if warm:
+        q.qed_batch_push(gen.ctx, arr, fields, ws[0].dt, warm, 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush.fill_(1.0)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rc, st = q.qed_batch_push(gen.ctx, arr, fields, ws[0].dt, steps, warm)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    counts = [[int(arr[k].s[s].count) for s in range(3)] for k in range(len(ws))]
+    gen.close()
+    return ms, st, counts, tuned
 
 
 def e2e_run(w, precision, warm, steps):
@@ -334,6 +408,8 @@ def main():
     import paper_2409_17299_gb300 as q  # noqa: F401
 
     w = make_workload(args.workload, args.scale, rank)
+    if args.workload == "batched_uniform_b":
+        return batched_main(args, w, warm, steps, rank, world, cpu)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -399,6 +475,11 @@ def main():
                      "bytes_per_particle_step": LEPTON_BYTES[prec], "bytes_per_emission": EMIT_BYTES[prec],
                      "lepton_kernel_ms": lep_ms, "photon_kernel_ms": tot["kernel_ms"][1],
                      "lepton_launches": tot["lepton_launches"]},
+        "breakdown_ms": {"lepton": tot["kernel_ms"][0], "photon": tot["kernel_ms"][1],
+                         "compaction": tot["kernel_ms"][2], "leveling": tot["kernel_ms"][3],
+                         "host_sync_wait": tot["sync_ms"], "host_call_wall": tot["call_ms"],
+                         "device_total": ms},
+        "chi_fp64_fallbacks": tot["chi_fp64"],
         "clocks": clk.summary(),
     }
     if fp64:
@@ -412,6 +493,43 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_main(args, ws, warm, steps, rank, world, cpu):
+    import torch
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms, st, counts, tuned = batch_run(ws, args.precision, warm, steps)
+    secs = ms / 1e3
+    ps = float(st["particle_steps"])
+    ev = float(st["emit_events"])
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([secs])
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s = torch.tensor([ps, ev])
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        secs, ps, ev = float(t[0]), float(s[0]), float(s[1])
+    if rank != 0:
+        return
+    n_lep = sum(len(w.species[0]["id"]) for w in ws)
+    line = {
+        "metric": "particle-steps/s", "value": ps / secs, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "batched_uniform_b", "ensembles": len(ws), "leptons": n_lep,
+                   "precision": args.precision, "launch": "one persistent kernel per call (CUDA graph)",
+                   "l2": "inputs larger than L2 (%d MB of leptons)" % (n_lep * 40 // 2 ** 20)},
+        "events_per_s": ev / secs,
+        "gpu_launches": st["launches"],
+        "autotune": {"chosen_threads": tuned[0], "ms_128_256_512": tuned[1]} if tuned else None,
+        "roofline": {"bound": "alu", "note": "step-fused: leptons stay in registers across steps",
+                     "kernel": "k_emission_fused", "kernel_ms": st["kernel_ms"][0]},
+        "clocks": clk.summary(),
+    }
+    if cpu:
+        line["cpu_baseline"] = {"value": cpu[0], "unit": "particle-steps/s", "cores": cpu[2], "kind": "oracle",
+                                "sample": cpu[3], "events_per_s": cpu[1]}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -106,8 +106,11 @@ typedef struct {
     int64_t launches;         /* kernels launched by the call */
     int64_t chi_fp64;         /* FP32 mode: chi evaluations whose cancellation test sent
                                  them to the FP64 form */
-    double kernel_ms[2];      /* with cfg.profile: summed device time of the lepton and
-                                 photon push kernels (CUDA events) */
+    double kernel_ms[4];      /* with cfg.profile: summed device time (CUDA events on the
+                                 context's stream) of the lepton push kernels, the photon
+                                 push kernels, the dead-photon compaction, and leveling */
+    double sync_ms;           /* host time spent waiting in stream synchronisation */
+    double call_ms;           /* host wall time of the call */
 } qed_stats;
 
 /* Create a context and build its rate approximant and inverse-CDF tables on
@@ -141,6 +144,31 @@ qed_status qed_push_and_generate(qed_ctx *ctx, qed_particles *p, const qed_field
  * probability min(1, w_i/w*) (Philox counter word 3 = 0xFFFFFFFF); kept
  * particles below w* get weight w*.  Counts in *p are updated. */
 qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step);
+
+/* Push n_ens independent ensembles (ens[k] in the field fields[k]) through
+ * nsteps steps in one persistent launch (replayed from a CUDA graph): the
+ * emission step of Sec. 3 / Algorithm 1 for every lepton, photons recorded
+ * and not pushed.  With photons not pushed and no leveling nothing couples
+ * particles across steps, so each lepton is carried through all steps in
+ * registers (read and written once); tiles of all ensembles are scheduled
+ * by a device work counter.  Results equal nsteps calls of
+ * qed_push_and_generate.  Requires cfg.push_photons == 0 and thin_cap == 0
+ * (else QED_ERR_INVALID).  ens: n_ens host structs of caller-owned device
+ * arrays; photon counts are updated; on QED_ERR_CAPACITY (a photon buffer
+ * too small) out->needed_capacity[2] holds the largest demand and the
+ * lepton arrays have been advanced (not restored): replay from a copy.
+ * Block shape: cfg.block_threads if 128, 256 or 512, else the autotuner's
+ * choice (qed_autotune_batch), else 256. */
+qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens,
+                          double dt, int nsteps, int64_t step0, qed_stats *out);
+
+/* Autotuner of qed_batch_push: times block shapes of 128, 256 and 512
+ * threads (one tile of particles per block) for nsteps steps on scratch
+ * copies of up to 2^20 leptons sampled from ens (the caller's buffers are
+ * not modified) and keeps the fastest for this context.  *chosen_threads and
+ * ms3[3] (device ms per candidate) may be NULL. */
+qed_status qed_autotune_batch(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields,
+                              int n_ens, double dt, int nsteps, int *chosen_threads, double *ms3);
 
 /* Statistics accumulated since the context was created or last reset. */
 qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset);

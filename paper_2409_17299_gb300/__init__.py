@@ -20,7 +20,7 @@ QED_SAMPLER_TABLE, QED_SAMPLER_MLP = 0, 1
 QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
 QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP = 0, 1, 2
 
-EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_compact", "qed_get_stats", "qed_strerror",
+EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_batch_push", "qed_autotune_batch", "qed_compact", "qed_get_stats", "qed_strerror",
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
             "qed_compact_species_noalloc")
 QED_NOALLOC_MAX_ENTRIES = 1 << 20
@@ -52,7 +52,7 @@ class QedStats(C.Structure):
                 ("needed_capacity", C.c_int64 * 3), ("max_subevents", C.c_int64), ("overflow", C.c_int64),
                 ("passes", C.c_int64), ("thinned", C.c_int64), ("lepton_steps", C.c_int64),
                 ("photon_steps", C.c_int64), ("launches", C.c_int64), ("chi_fp64", C.c_int64),
-                ("kernel_ms", C.c_double * 2)]
+                ("kernel_ms", C.c_double * 4), ("sync_ms", C.c_double), ("call_ms", C.c_double)]
 
     def as_dict(self):
         return {"particle_steps": self.particle_steps, "emit_events": self.emit_events,
@@ -60,7 +60,7 @@ class QedStats(C.Structure):
                 "max_subevents": self.max_subevents, "overflow": self.overflow,
                 "passes": self.passes, "thinned": self.thinned, "lepton_steps": self.lepton_steps,
                 "photon_steps": self.photon_steps, "launches": self.launches, "chi_fp64": self.chi_fp64,
-                "kernel_ms": list(self.kernel_ms)}
+                "kernel_ms": list(self.kernel_ms), "sync_ms": self.sync_ms, "call_ms": self.call_ms}
 
 
 class QedError(RuntimeError):
@@ -88,6 +88,10 @@ def lib():
         "qed_push_and_generate": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedFieldDesc), C.c_double, i32, i64,
                                         C.POINTER(QedStats)]),
         "qed_compact": (i32, [p, C.POINTER(QedParticles), i64]),
+        "qed_batch_push": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedFieldDesc), i32, C.c_double, i32, i64,
+                                 C.POINTER(QedStats)]),
+        "qed_autotune_batch": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedFieldDesc), i32, C.c_double, i32,
+                                     C.POINTER(i32), C.POINTER(C.c_double)]),
         "qed_get_stats": (i32, [p, C.POINTER(QedStats), i32]),
         "qed_strerror": (C.c_char_p, [i32]),
         "qed_destroy": (None, [p]),
@@ -130,6 +134,28 @@ def qed_push_and_generate(ctx, particles: QedParticles, field: QedFieldDesc, dt:
     if rc not in (QED_OK, QED_ERR_CAPACITY):
         raise QedError(rc, "qed_push_and_generate")
     return rc, st.as_dict()
+
+
+def qed_batch_push(ctx, ensembles, fields, dt: float, nsteps: int, step0: int = 0):
+    """ensembles: ctypes array of QedParticles; fields: ctypes array of
+    QedFieldDesc (same length).  Returns (status, stats dict)."""
+    st = QedStats()
+    rc = lib().qed_batch_push(ctx, ensembles, fields, len(ensembles), float(dt), int(nsteps), int(step0),
+                              C.byref(st))
+    if rc not in (QED_OK, QED_ERR_CAPACITY):
+        raise QedError(rc, "qed_batch_push")
+    return rc, st.as_dict()
+
+
+def qed_autotune_batch(ctx, ensembles, fields, dt: float, nsteps: int):
+    """Returns (chosen threads per block, [ms for 128, 256, 512])."""
+    chosen = C.c_int(0)
+    ms = (C.c_double * 3)()
+    rc = lib().qed_autotune_batch(ctx, ensembles, fields, len(ensembles), float(dt), int(nsteps),
+                                  C.byref(chosen), ms)
+    if rc != QED_OK:
+        raise QedError(rc, "qed_autotune_batch")
+    return chosen.value, list(ms)
 
 
 def qed_compact(ctx, particles: QedParticles, step: int) -> int:

@@ -9,13 +9,16 @@ using namespace sfq;
 static void free_ctx(qed_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    sfq_batch_free(c);
     void *dev[] = {c->coef64, c->coef32, c->icdf_em64, c->icdf_pair64, c->icdf_em32, c->icdf_pair32, c->gl,
                    c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap, c->lev};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    if (c->pin) cudaFreeHost(c->pin);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_ready)
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 4; ++k)
             for (int i = 0; i < qed_ctx::EVN; ++i)
                 for (int j = 0; j < 2; ++j) cudaEventDestroy(c->ev[k][i][j]);
     free(c);
@@ -47,7 +50,9 @@ extern "C" qed_status qed_init_tables(qed_ctx **out, const qed_config *cfg, void
               cudaMalloc(&c->gl, sizeof(double) * 64) == cudaSuccess &&
               cudaMalloc(&c->ctl, sizeof(DevCtl)) == cudaSuccess &&
               cudaMalloc(&c->lev, sizeof(LevelWork)) == cudaSuccess &&
-              cudaHostAlloc(&c->ctl_host, sizeof(DevCtl), cudaHostAllocDefault) == cudaSuccess;
+              cudaHostAlloc(&c->ctl_host, sizeof(DevCtl), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(&c->pin, 64, cudaHostAllocDefault) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         free_ctx(c);
         return QED_ERR_NOMEM;
@@ -72,19 +77,32 @@ extern "C" qed_status qed_push_and_generate(qed_ctx *ctx, qed_particles *p, cons
     return sfq_push(ctx, p, field, dt, nsteps, step0, out);
 }
 
+extern "C" qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens,
+                                     double dt, int nsteps, int64_t step0, qed_stats *out) {
+    return sfq_batch_push(ctx, ens, fields, n_ens, dt, nsteps, step0, out, 0);
+}
+
+extern "C" qed_status qed_autotune_batch(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields,
+                                         int n_ens, double dt, int nsteps, int *chosen_threads, double *ms3) {
+    return sfq_batch_autotune(ctx, ens, fields, n_ens, dt, nsteps, chosen_threads, ms3);
+}
+
 extern "C" qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step) {
     if (!ctx || !p || step < 0 || step > 0xFFFFFFFFll) return QED_ERR_INVALID;
-    DevCtl h{};
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < 3; ++s)
         if (p->s[s].count < 0 || p->s[s].count > p->s[s].capacity) return QED_ERR_INVALID;
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    DevCtl &h = *ctx->ctl_host;                 // pinned staging
+    memset(&h, 0, sizeof(DevCtl));
+    for (int s = 0; s < 3; ++s) {
         h.count[s] = (unsigned long long)p->s[s].count;
         h.capacity[s] = (unsigned long long)p->s[s].capacity;
     }
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl, &h, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
     for (int s = 0; s < 3; ++s) {
-        qed_status e = sfq_compact_species(ctx, &p->s[s], s);
-        if (e != QED_OK) return e;
-        e = sfq_level_species(ctx, &p->s[s], s, step);   // also reads back the count
+        // leveling skips dead entries and compacts; otherwise compaction only
+        const bool level = ctx->cfg.thin_cap > 0 && p->s[s].count > ctx->cfg.thin_cap;
+        qed_status e = level ? sfq_level_species(ctx, &p->s[s], s, step) : sfq_compact_species(ctx, &p->s[s], s);
         if (e != QED_OK) return e;
     }
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));

@@ -6,12 +6,14 @@
 // [0, N), the r-th dead slot below A receives the r-th alive entry at or
 // above A (ranks from block scans), so no entry is read after it is written.
 //
-// Leveling: the threshold w* solves sum_i min(1, w_i / w*) = cap.  A weight
-// histogram over 32 candidate values brackets w*; inside a bracket with no
-// weights the sum is A / w + C, solved in closed form.  Particle i is kept
-// with probability min(1, w_i / w*) from Philox(seed; id, step, 0xFFFFFFFF),
-// and kept particles below w* get weight w*.
+// Leveling: the threshold w* solves sum_i min(1, w_i / w*) = cap (solved on
+// the device, see k_lev_next).  Particle i is kept with probability
+// min(1, w_i / w*) from Philox(seed; id, step, 0xFFFFFFFF), and kept
+// particles below w* get weight w*.
 #include <math.h>
+#include <string.h>
+
+#include <chrono>
 
 #include "sfqed_device.cuh"
 #include "sfqed_internal.h"
@@ -22,8 +24,6 @@ namespace {
 constexpr int CT = 256;            // threads per compaction block
 constexpr int CITEMS = 4;          // items per thread
 constexpr int CTILE = CT * CITEMS; // entries per block
-constexpr int NCAND = 33;          // candidate thresholds (32 brackets)
-constexpr int NBIN = NCAND + 1;
 
 template <class T> __device__ __forceinline__ bool alive_at(const void *w, unsigned long long i) {
     return ld<T>(w, i) > (T)0;
@@ -185,224 +185,198 @@ __global__ void k_set_count(DevCtl *ctl, int s) {
     ctl->begin[s] = ctl->alive[s];
 }
 
-// ---- leveling ----
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 
-template <class T>
-__global__ void k_weight_range(const void *w, DevCtl *ctl, int s, unsigned long long *out /* min bits, max bits */) {
-    const unsigned long long n = ctl->count[s];
-    unsigned long long lo = ~0ull, hi = 0ull;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const double v = (double)ld<T>(w, i);
-        if (v > 0.0) {   // positive doubles order like their bit patterns
-            lo = min(lo, dbits(v));
-            hi = max(hi, dbits(v));
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, __shfl_down_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_down_sync(0xffffffffu, hi, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(out, lo);
-        atomicMax(out + 1, hi);
-    }
+// ---- leveling: device-resident piecewise-exact Newton iteration ----
+// S(w) = sum_i min(1, w_i / w) = A(w) / w + C(w) with A = sum of weights below
+// w and C = count at or above w.  On the piece of w containing the root,
+// S = A/w + C, whose root is A / (cap - C): evaluating (A, C) at w and jumping
+// to A / (cap - C) lands on the root once the piece is right, otherwise it
+// moves toward it; a bisection bracket keeps every step inside [lo, hi].
+// Block partial sums are reduced in a fixed order (deterministic result).
+constexpr int LEVEL_ITERS = 40;
+
+// smallest float >= a positive double (v < d <=> v < ceil_f(d) for floats v)
+__device__ __forceinline__ float ceil_f(double d) {
+    float f = __double2float_ru(d);
+    return f;
 }
 
-// per-bracket count, weight sum and largest weight; bin 0 below cand[0],
-// bin m+1 for cand[m] <= w < cand[m+1], bin NCAND at or above cand[NCAND-1]
-struct Hist {
-    unsigned long long cnt[NBIN];
-    double sum[NBIN];
-    unsigned long long maxbits[NBIN];
+__global__ void k_lev_begin(LevelWork *lw, int s) {
+    LevelIter &it = lw->it[s];
+    it.lo = 0.0;
+    it.hi = __longlong_as_double(0x7ff0000000000000ll);
+    it.w = it.hi;
+    it.w_up = __int_as_float(0x7f800000);
+    it.wstar = 0.0;
+    it.done = 0;
+    it.iters = 0;
+    it.alive = 0;
+}
+
+// error-free float-float accumulation (TwoSum), accurate to ~2^-48 relative
+struct FF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float b) {
+        const float t = hi + b;
+        const float bp = t - hi;
+        const float e = (hi - (t - bp)) + (b - bp);
+        hi = t;
+        lo += e;
+    }
 };
 
 template <class T>
-__global__ void k_weight_hist(const void *w, const DevCtl *ctl, int s, const double *cand, Hist *h) {
-    __shared__ double c[NCAND];
-    __shared__ unsigned long long sc[NBIN], smax[NBIN];
-    __shared__ double ss[NBIN];
-    if (threadIdx.x < NCAND) c[threadIdx.x] = cand[threadIdx.x];
-    if (threadIdx.x < NBIN) { sc[threadIdx.x] = 0; ss[threadIdx.x] = 0.0; smax[threadIdx.x] = 0; }
-    __syncthreads();
+__global__ void __launch_bounds__(256) k_lev_eval(const void *w, const DevCtl *ctl, int s, LevelWork *lw) {
+    const LevelIter &it = lw->it[s];
+    if (it.done) return;
     const unsigned long long n = ctl->count[s];
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const double v = (double)ld<T>(w, i);
-        if (!(v > 0.0)) continue;
-        int b;
-        if (v < c[0]) b = 0;
-        else {
-            int lo = 0, hi = NCAND - 1;                // largest m with c[m] <= v
-            while (lo < hi) {
-                const int m = (lo + hi + 1) >> 1;
-                if (c[m] <= v) lo = m; else hi = m - 1;
+    double A;
+    unsigned long long C = 0, N = 0, M = 0;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 weights: exact float comparisons and float-float sums, no FP64 per element
+        const float wc = it.w_up;
+        FF acc;
+        unsigned mb = 0;
+        for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (unsigned long long)gridDim.x * blockDim.x) {
+            const float v = reinterpret_cast<const float *>(w)[i];
+            if (!(v > 0.f)) continue;
+            ++N;
+            mb = max(mb, __float_as_uint(v));
+            if (v < wc) acc.add(v);
+            else ++C;
+        }
+        A = (double)acc.hi + (double)acc.lo;
+        M = N ? dbits((double)__uint_as_float(mb)) : 0ull;
+    } else {
+        const double wc = it.w;
+        double comp = 0.0;           // Kahan
+        A = 0.0;
+        for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (unsigned long long)gridDim.x * blockDim.x) {
+            const double v = (double)ld<T>(w, i);
+            if (!(v > 0.0)) continue;
+            ++N;
+            M = max(M, dbits(v));
+            if (v < wc) {
+                const double y = v - comp;
+                const double t = A + y;
+                comp = (t - A) - y;
+                A = t;
+            } else {
+                ++C;
             }
-            b = lo + 1;
         }
-        atomicAdd(&sc[b], 1ull);
-        atomicAdd(&ss[b], v);
-        atomicMax(&smax[b], dbits(v));
     }
+    __shared__ double sA[8];
+    __shared__ unsigned long long sC[8], sN[8], sM[8];
+    for (int o = 16; o > 0; o >>= 1) {
+        A += __shfl_down_sync(0xffffffffu, A, o);
+        C += __shfl_down_sync(0xffffffffu, C, o);
+        N += __shfl_down_sync(0xffffffffu, N, o);
+        M = max(M, __shfl_down_sync(0xffffffffu, M, o));
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sA[wid] = A; sC[wid] = C; sN[wid] = N; sM[wid] = M; }
     __syncthreads();
-    if (threadIdx.x < NBIN && sc[threadIdx.x]) {
-        atomicAdd(&h->cnt[threadIdx.x], sc[threadIdx.x]);
-        atomicAdd(&h->sum[threadIdx.x], ss[threadIdx.x]);
-        atomicMax(&h->maxbits[threadIdx.x], smax[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        unsigned long long c = 0, nn = 0, m = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sA[k]; c += sC[k]; nn += sN[k]; m = max(m, sM[k]); }
+        lw->partA[blockIdx.x] = a;
+        lw->partC[blockIdx.x] = c;
+        lw->partN[blockIdx.x] = nn;
+        lw->partM[blockIdx.x] = m;
     }
 }
 
-template <class T>
-__global__ void k_level_apply(SpeciesDev S, DevCtl *ctl, int s, double wstar, uint64_t seed, unsigned step) {
-    const unsigned long long n = ctl->count[s];
-    unsigned long long removed = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const double v = (double)ld<T>(S.w, i);
-        if (!(v > 0.0) || v >= wstar) continue;
-        const uint4 r = event_draw(seed, S.id[i], step, 0xFFFFFFFFu);
-        double u, v_unused;
-        Uniform<double>::draw(r.x, r.y, u, v_unused);
-        if (u < v / wstar) st<T>(S.w, i, (T)wstar);
-        else { st<T>(S.w, i, (T)0); ++removed; }
-    }
-    for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
-    if ((threadIdx.x & 31) == 0 && removed) atomicAdd(&ctl->thinned, removed);
-}
-
-// ---- leveling by weight classes (one pass, no host round trip) ----
-__device__ __forceinline__ void class_flush(LevelWork *lw, int s, unsigned long long b, unsigned long long c) {
-    if (!c) return;
-    unsigned j = (unsigned)((b >> 20) ^ (b >> 40)) & (LEVEL_K - 1);
-    for (int probe = 0; probe < LEVEL_K; ++probe, j = (j + 1) & (LEVEL_K - 1)) {
-        const unsigned long long prev = atomicCAS(&lw->bits[s][j], 0ull, b);
-        if (prev == 0ull || prev == b) {
-            atomicAdd(&lw->cnt[s][j], c);
-            return;
-        }
-    }
-    atomicExch(&lw->overflow[s], 1ull);
-}
-
-// distinct alive weights and their counts; a 4-entry register cache per
-// thread keeps the table atomics rare when few weight values exist
-template <class T>
-__global__ void k_level_classes(const void *w, const DevCtl *ctl, int s, LevelWork *lw, long long cap) {
-    const unsigned long long n = ctl->count[s];
-    if (n <= (unsigned long long)cap) return;
-    unsigned long long cb[4] = {0, 0, 0, 0}, cc[4] = {0, 0, 0, 0};
-    unsigned victim = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const double v = (double)ld<T>(w, i);
-        if (!(v > 0.0)) continue;
-        const unsigned long long b = dbits(v);
-        int hit = -1;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (cc[q] && cb[q] == b) hit = q;
-        if (hit < 0) {
-#pragma unroll
-            for (int q = 3; q >= 0; --q)
-                if (!cc[q]) hit = q;
-        }
-        if (hit < 0) {
-            hit = (int)(victim++ & 3u);
-            class_flush(lw, s, cb[hit], cc[hit]);
-            cc[hit] = 0;
-        }
-        cb[hit] = b;
-        ++cc[hit];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) class_flush(lw, s, cb[q], cc[q]);
-}
-
-// one warp: sort the classes, solve sum_c n_c min(1, v_c / w*) = cap on the
-// piece (v_j, v_{j+1}] where it changes sign (there S = A_j / w + C_j), and
-// set per class the integer keep threshold: u = (m + 1/2) 2^-52 < v_c / w*
-// exactly when m < ceil(2^52 v_c / w* - 1/2)
-__global__ void k_level_solve(DevCtl *ctl, int s, LevelWork *lw, long long cap) {
+__global__ void k_lev_next(LevelWork *lw, int s, int nblocks, long long cap) {
     if (threadIdx.x != 0) return;
-    const unsigned long long n = ctl->count[s];
-    lw->wstar[s] = 0.0;
-    lw->ncls[s] = 0;
-    ctl->need_hist[s] = 0;
-    if (n <= (unsigned long long)cap) return;
-    if (lw->overflow[s]) { ctl->need_hist[s] = 1; return; }
-    double v[LEVEL_K];
-    unsigned long long c[LEVEL_K], bb[LEVEL_K];
-    int k = 0;
-    for (int j = 0; j < LEVEL_K; ++j)
-        if (lw->bits[s][j]) {
-            bb[k] = lw->bits[s][j];
-            v[k] = __longlong_as_double((long long)bb[k]);
-            c[k] = lw->cnt[s][j];
-            ++k;
-        }
-    for (int i = 1; i < k; ++i) {          // insertion sort, ascending weight
-        const double vv = v[i];
-        const unsigned long long cv = c[i], bv = bb[i];
-        int j = i - 1;
-        while (j >= 0 && v[j] > vv) { v[j + 1] = v[j]; c[j + 1] = c[j]; bb[j + 1] = bb[j]; --j; }
-        v[j + 1] = vv; c[j + 1] = cv; bb[j + 1] = bv;
+    LevelIter &it = lw->it[s];
+    if (it.done) return;
+    double A = 0.0, comp = 0.0;
+    unsigned long long C = 0, N = 0, M = 0;
+    for (int b = 0; b < nblocks; ++b) {            // fixed order
+        const double y = lw->partA[b] - comp;
+        const double t = A + y;
+        comp = (t - A) - y;
+        A = t;
+        C += lw->partC[b];
+        N += lw->partN[b];
+        M = max(M, lw->partM[b]);
     }
-    double wstar = 0.0, A = 0.0;
-    unsigned long long C = 0;
-    for (int j = 0; j < k; ++j) C += c[j];
-    for (int j = 0; j < k; ++j) {
-        A += (double)c[j] * v[j];
-        C -= c[j];
-        const double hi = j + 1 < k ? v[j + 1] : INFINITY;
-        // S(hi) = A / hi + C: the solution lies in (v_j, hi] once S(hi) <= cap
-        const double S_hi = j + 1 < k ? A / hi + (double)C : 0.0;
-        if (S_hi <= (double)cap) {
-            wstar = A / ((double)cap - (double)C);
-            if (!(wstar > v[j])) wstar = __longlong_as_double(__double_as_longlong(v[j]) + 1);  // next double up
-            if (wstar > hi) wstar = hi;
-            break;
-        }
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    const double w = it.w;
+    if (it.iters == 0) {                           // first pass: w = +inf, all alive weights below it
+        it.alive = N;
+        if (N <= (unsigned long long)cap) { it.done = 1; it.wstar = 0.0; it.wstar_up = 0.f; it.wstar_f = 0.f; return; }
+        it.hi = __longlong_as_double((long long)M) * (double)N / (double)cap;   // S(hi) <= cap
+        it.lo = 0.0;
+    } else {
+        const double S = A / w + (double)C;
+        if (S > (double)cap) it.lo = w; else it.hi = w;
     }
-    for (int j = 0; j < k; ++j) {
-        lw->cls_bits[s][j] = bb[j];
-        unsigned long long thr = 1ull << 52;          // kept, weight unchanged
-        if (v[j] < wstar) {
-            const double P = (v[j] / wstar) * 0x1p52;  // exact scaling of the keep probability
-            thr = (unsigned long long)ceil(P - 0.5);
-        }
-        lw->cls_thr[s][j] = thr;
+    ++it.iters;
+    double c = (double)cap > (double)C ? A / ((double)cap - (double)C) : inf;
+    if (c == w) {                                          // root of its own piece
+        it.done = 1;
+        it.wstar = w;
+        it.wstar_up = ceil_f(w);
+        it.wstar_f = (float)w;
+        return;
     }
-    lw->ncls[s] = (unsigned long long)k;
-    lw->wstar[s] = wstar;
+    if (!(c > it.lo && c <= it.hi)) c = 0.5 * (it.lo + it.hi);
+    // stop at double resolution of the bracket (hi, evaluated, is the answer)
+    if (!(c > it.lo && c <= it.hi) || (c == it.hi && it.hi == w) || it.iters >= LEVEL_ITERS) {
+        it.done = 1;
+        it.wstar = it.hi;
+        it.wstar_up = ceil_f(it.hi);
+        it.wstar_f = (float)it.hi;
+        return;
+    }
+    it.w = c;
+    it.w_up = ceil_f(c);
 }
 
+// keep particle i (0 < w_i < w*) with probability w_i / w*: the comparison
+// u < w_i / w* is made in FP32 with a relative margin, and in FP64 (the
+// oracle's test) only for draws within that margin of the boundary
 template <class T>
-__global__ void k_level_apply_classes(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw, uint64_t seed,
-                                      unsigned step) {
-    __shared__ unsigned long long sb[LEVEL_K], sthr[LEVEL_K];
-    __shared__ int sk;
-    __shared__ double sw;
-    if (threadIdx.x == 0) { sk = (int)lw->ncls[s]; sw = lw->wstar[s]; }
-    if (threadIdx.x < LEVEL_K) { sb[threadIdx.x] = lw->cls_bits[s][threadIdx.x]; sthr[threadIdx.x] = lw->cls_thr[s][threadIdx.x]; }
-    __syncthreads();
-    const double wstar = sw;
-    if (!(wstar > 0.0)) return;
-    const int k = sk;
+__global__ void __launch_bounds__(256) k_lev_apply(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw,
+                                                   uint64_t seed, unsigned step) {
+    const LevelIter &it = lw->it[s];
+    const double wstar = it.wstar;
+    if (!it.done || !(wstar > 0.0)) return;
+    const float inv_f = (float)(1.0 / wstar);
+    const float wup = it.wstar_up, wnew = it.wstar_f;
     const unsigned long long n = ctl->count[s];
     unsigned long long removed = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const double v = (double)ld<T>(S.w, i);
-        if (!(v > 0.0) || v >= wstar) continue;
-        const unsigned long long b = dbits(v);
-        unsigned long long thr = 0;
-        for (int j = 0; j < k; ++j)
-            if (sb[j] == b) thr = sthr[j];
+        const T v = ld<T>(S.w, i);
+        bool below;
+        if constexpr (sizeof(T) == 4) below = v > 0.f && v < wup;     // v < w* exactly
+        else below = v > 0.0 && v < wstar;
+        if (!below) continue;
         const uint4 r = event_draw(seed, S.id[i], step, 0xFFFFFFFFu);
-        const unsigned long long m = ((unsigned long long)r.x << 20) | (unsigned long long)(r.y >> 12);
-        if (m < thr) st<T>(S.w, i, (T)wstar);
-        else { st<T>(S.w, i, (T)0); ++removed; }
+        const float uf = __uint2float_rn(r.x) * 0x1p-32f;        // u to within 2^-32 + FP32 rounding
+        const float pf = (float)v * inv_f;
+        bool keep;
+        if (uf < pf * (1.0f - 1e-6f) - 0x1p-31f) keep = true;
+        else if (uf > pf * (1.0f + 1e-6f) + 0x1p-31f) keep = false;
+        else {
+            double u, vv;
+            Uniform<double>::draw(r.x, r.y, u, vv);
+            keep = u < (double)v / wstar;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (keep) st<T>(S.w, i, wnew);
+            else { st<T>(S.w, i, 0.f); ++removed; }
+        } else {
+            if (keep) st<T>(S.w, i, wstar);
+            else { st<T>(S.w, i, 0.0); ++removed; }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
     if ((threadIdx.x & 31) == 0 && removed) atomicAdd(&ctl->thinned, removed);
@@ -428,108 +402,39 @@ qed_status compact_impl(qed_ctx *ctx, qed_species *sp, int s) {
     return QED_OK;
 }
 
-// Histogram path, for species with more than LEVEL_K distinct weights.
+// Leveling of one species at `step`: the iteration runs on the device (a
+// fixed number of early-exit launches, no host round trip), then keep/drop
+// and compaction.  sp->count must bound the device count from above.
 template <class T>
-qed_status level_hist(qed_ctx *ctx, qed_species *sp, int s, int64_t step, int64_t n) {
-    const int64_t cap = ctx->cfg.thin_cap;
-    cudaStream_t st = ctx->stream;
-    const int blocks = ctx->sm_count * 4;
-    struct Work { unsigned long long range[2]; double cand[NCAND]; Hist h; };
-    Work *dw = nullptr;
-    SFQ_CUDA(cudaMallocAsync(&dw, sizeof(Work), st));
-    Work hw;
-    hw.range[0] = ~0ull;
-    hw.range[1] = 0ull;
-    SFQ_CUDA(cudaMemcpyAsync(dw->range, hw.range, sizeof(hw.range), cudaMemcpyHostToDevice, st));
-    k_weight_range<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, dw->range);
-    SFQ_LAUNCHED(ctx, 1);
-    SFQ_CUDA(cudaMemcpyAsync(hw.range, dw->range, sizeof(hw.range), cudaMemcpyDeviceToHost, st));
-    SFQ_CUDA(cudaStreamSynchronize(st));
-    double wmin, wmax;
-    memcpy(&wmin, &hw.range[0], 8);
-    memcpy(&wmax, &hw.range[1], 8);
-    double lo = wmin, hi = wmax * (double)n / (double)cap;
-    double wstar = hi;
-    for (int it = 0; it < 24; ++it) {
-        for (int m = 0; m < NCAND; ++m) hw.cand[m] = lo + (hi - lo) * m / (NCAND - 1);
-        hw.cand[NCAND - 1] = hi;
-        memset(&hw.h, 0, sizeof(Hist));
-        SFQ_CUDA(cudaMemcpyAsync(dw->cand, hw.cand, sizeof(hw.cand) + sizeof(Hist), cudaMemcpyHostToDevice, st));
-        k_weight_hist<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, dw->cand, &dw->h);
-        SFQ_LAUNCHED(ctx, 1);
-        SFQ_CUDA(cudaMemcpyAsync(&hw.h, &dw->h, sizeof(Hist), cudaMemcpyDeviceToHost, st));
-        SFQ_CUDA(cudaStreamSynchronize(st));
-        // S(c_m) = (sum of weights below c_m) / c_m + (count at or above c_m)
-        double below = 0.0;
-        unsigned long long above = 0;
-        for (int bi = 0; bi < NBIN; ++bi) above += hw.h.cnt[bi];
-        int m_hit = -1;
-        double A = 0.0;
-        unsigned long long C = 0;
-        for (int m = 0; m < NCAND; ++m) {
-            below += hw.h.sum[m];        // bins 0..m hold weights below c_m
-            above -= hw.h.cnt[m];
-            const double S = below / hw.cand[m] + (double)above;
-            if (S <= (double)cap) { m_hit = m; A = below; C = above; break; }
-        }
-        if (m_hit <= 0) { wstar = hi; break; }
-        const double clo = hw.cand[m_hit - 1], chi_ = hw.cand[m_hit];
-        double bmax;
-        memcpy(&bmax, &hw.h.maxbits[m_hit], 8);
-        if (hw.h.cnt[m_hit] == 0 || bmax <= clo) {
-            // for w in (c_{m-1}, c_m]: S(w) = A / w + C with A over weights < c_m
-            wstar = A / ((double)cap - (double)C);
-            if (!(wstar > clo && wstar <= chi_)) wstar = chi_;
-            break;
-        }
-        lo = clo;
-        hi = chi_;
-        wstar = hi;
-        if (hi - lo <= 4.0 * (nextafter(hi, INFINITY) - hi)) break;
-    }
-    SFQ_CUDA(cudaFreeAsync(dw, st));
-    SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
-                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
-    k_level_apply<T><<<blocks, 256, 0, st>>>(S, ctx->ctl, s, wstar, ctx->cfg.seed, (unsigned)step);
-    SFQ_LAUNCHED(ctx, 1);
-    SFQ_CUDA(cudaGetLastError());
-    return compact_impl<T>(ctx, sp, s);
-}
-
-// Leveling of one species at `step`: weight classes, device-side solve,
-// keep/drop, compaction.  No host round trip unless the species has more
-// than LEVEL_K distinct weights (then the histogram path runs).  sp->count
-// must bound the device count from above; it is refreshed on return when
-// `sync` is set.
-template <class T>
-qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step, bool sync) {
+qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     const int64_t cap = ctx->cfg.thin_cap;
     cudaStream_t st = ctx->stream;
     if (cap <= 0 || sp->count <= cap) return QED_OK;
-    const int blocks = ctx->sm_count * 4;
+    int blocks = ctx->sm_count * 4;
+    blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
     SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
                  reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
-    SFQ_CUDA(cudaMemsetAsync(ctx->lev->bits[s], 0, sizeof(ctx->lev->bits[s]), st));
-    SFQ_CUDA(cudaMemsetAsync(ctx->lev->cnt[s], 0, sizeof(ctx->lev->cnt[s]), st));
-    SFQ_CUDA(cudaMemsetAsync(&ctx->lev->overflow[s], 0, sizeof(unsigned long long), st));
-    k_level_classes<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
-    k_level_solve<<<1, 32, 0, st>>>(ctx->ctl, s, ctx->lev, (long long)cap);
-    k_level_apply_classes<T><<<blocks, 256, 0, st>>>(S, ctx->ctl, s, ctx->lev, ctx->cfg.seed, (unsigned)step);
-    SFQ_LAUNCHED(ctx, 3);
-    SFQ_CUDA(cudaGetLastError());
-    qed_status e = compact_impl<T>(ctx, sp, s);
-    if (e != QED_OK) return e;
-    if (!sync) return QED_OK;
-    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
-    SFQ_CUDA(cudaStreamSynchronize(st));
-    if (ctx->ctl_host->need_hist[s]) {
-        e = level_hist<T>(ctx, sp, s, step, (int64_t)ctx->ctl_host->count[s]);
-        if (e != QED_OK) return e;
-        SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+    k_lev_begin<<<1, 1, 0, st>>>(ctx->lev, s);
+    SFQ_LAUNCHED(ctx, 1);
+    // iterations in chunks of three; the host reads the done flag between chunks
+    // (two to five passes are typical)
+    for (int it = 0; it < LEVEL_ITERS; it += 3) {
+        for (int c = 0; c < 3; ++c) {
+            k_lev_eval<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev);
+            k_lev_next<<<1, 32, 0, st>>>(ctx->lev, s, blocks, (long long)cap);
+        }
+        SFQ_LAUNCHED(ctx, 6);
+        SFQ_CUDA(cudaMemcpyAsync(ctx->pin, &ctx->lev->it[s].done, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        const auto t0 = std::chrono::steady_clock::now();
         SFQ_CUDA(cudaStreamSynchronize(st));
+        ctx->sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ctx->pin[0]) break;
     }
-    sp->count = (int64_t)ctx->ctl_host->count[s];
-    return QED_OK;
+    k_lev_apply<T><<<blocks, 256, 0, st>>>(S, ctx->ctl, s, ctx->lev, ctx->cfg.seed, (unsigned)step);
+    SFQ_LAUNCHED(ctx, 1);
+    SFQ_CUDA(cudaGetLastError());
+    return compact_impl<T>(ctx, sp, s);
 }
 
 }  // namespace
@@ -563,8 +468,8 @@ qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s) {
 }
 
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
-    if (ctx->cfg.precision == QED_FP32) return level_impl<float>(ctx, sp, s, step, true);
-    return level_impl<double>(ctx, sp, s, step, true);
+    if (ctx->cfg.precision == QED_FP32) return level_impl<float>(ctx, sp, s, step);
+    return level_impl<double>(ctx, sp, s, step);
 }
 
 // ---------------------------------------------------------------------------

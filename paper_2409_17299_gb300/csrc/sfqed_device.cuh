@@ -91,19 +91,26 @@ template <> struct Uniform<float> {
 // Fields (analytic descriptors).  FP64 mode: phase t = t_n + tau, as given.
 // FP32 mode: phase from t_n reduced modulo 2 pi plus tau.
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ void eval_field(const PassArgs &a, T x, double tau, T E[3], T B[3]) {
+// A: any argument block with field_kind, prm[6], prm_f[6], t_n (FP64 phase
+// of the step start) and t_n_red_f (the same reduced mod 2 pi, FP32).
+template <class T, class A> __device__ __forceinline__ T prm_of(const A &a, int i) {
+    if constexpr (sizeof(T) == 8) return a.prm[i];
+    else return a.prm_f[i];      // no double-to-float conversion in FP32 mode
+}
+
+template <class T, class A>
+__device__ __forceinline__ void eval_field(const A &a, T x, double tau, T E[3], T B[3]) {
     if (a.field_kind == QED_FIELD_UNIFORM) {
-        E[0] = (T)a.prm[0]; E[1] = (T)a.prm[1]; E[2] = (T)a.prm[2];
-        B[0] = (T)a.prm[3]; B[1] = (T)a.prm[4]; B[2] = (T)a.prm[5];
+        E[0] = prm_of<T, A>(a, 0); E[1] = prm_of<T, A>(a, 1); E[2] = prm_of<T, A>(a, 2);
+        B[0] = prm_of<T, A>(a, 3); B[1] = prm_of<T, A>(a, 4); B[2] = prm_of<T, A>(a, 5);
         return;
     }
     T ph;
-    if (sizeof(T) == 8) ph = (T)(a.t_n + tau);
-    else ph = (T)a.t_n_red + (T)tau;
+    if constexpr (sizeof(T) == 8) ph = a.t_n + tau;
+    else ph = a.t_n_red_f + (float)tau;
     T s, c;
     m_sincos(ph, &s, &c);
-    const T a0 = (T)a.prm[0];
+    const T a0 = prm_of<T, A>(a, 0);
     if (a.field_kind == QED_FIELD_ROTATING_E) {
         E[0] = a0 * c; E[1] = a0 * s; E[2] = 0;
         B[0] = 0; B[1] = 0; B[2] = 0;

@@ -40,21 +40,26 @@ struct DevCtl {
     unsigned long long holes[3];        // compaction: dead entries below alive[s]
     unsigned long long bad_index;       // a bounds check failed (index recorded, access skipped)
     unsigned long long chi_fp64;        // FP32 mode: chi evaluations that fell back to FP64
-    unsigned long long need_hist[3];    // leveling: too many weight classes, use the histogram path
-    unsigned long long pad[4];
+    unsigned long long pad[7];
 };
 
-// Leveling by weight classes: the distinct alive weights of a species (at
-// most LEVEL_K), their counts, and per class the integer keep threshold.
-constexpr int LEVEL_K = 32;
+// Leveling: iteration state per species and per-block partial sums.
+constexpr int LEVEL_MAX_BLOCKS = 4096;
+struct LevelIter {
+    double lo, hi;          // bracket of w*: S(lo) > cap >= S(hi)
+    double w;               // point evaluated by the next pass (+inf first)
+    double wstar;           // result (0: no leveling)
+    float w_up, wstar_up;   // smallest floats >= w and >= wstar (exact FP32 comparisons)
+    float wstar_f;          // wstar rounded to float (the new weight in FP32 mode)
+    float pad_f;
+    unsigned long long done, iters, alive;
+};
 struct LevelWork {
-    unsigned long long bits[3][LEVEL_K];   // hash table: weight as double bits (0 = empty)
-    unsigned long long cnt[3][LEVEL_K];
-    unsigned long long overflow[3];
-    unsigned long long ncls[3];            // compacted classes, ascending weight
-    unsigned long long cls_bits[3][LEVEL_K];
-    unsigned long long cls_thr[3][LEVEL_K]; // keep iff m < thr (m: 52-bit draw); 2^52: always kept, unchanged
-    double wstar[3];                       // 0: no leveling this step
+    LevelIter it[3];
+    double partA[LEVEL_MAX_BLOCKS];             // sum of weights below w (block partials)
+    unsigned long long partC[LEVEL_MAX_BLOCKS]; // count at or above w
+    unsigned long long partN[LEVEL_MAX_BLOCKS]; // alive count
+    unsigned long long partM[LEVEL_MAX_BLOCKS]; // largest weight (double bits)
 };
 
 struct SpeciesDev {
@@ -72,11 +77,13 @@ struct PassArgs {
     const void *icdf_pair;  // PAIR_NCHI * PAIR_NS (T)
     int field_kind;
     double prm[6];
+    float prm_f[6];         // prm rounded to float once (FP32 mode)
     double dt;
     float dt_f;             // (float)dt
     float dt_f_gt;          // smallest float above dt (FP32 first-iteration event test)
     double t_n;             // step * dt
-    double t_n_red;         // (step * dt) reduced modulo 2 pi (FP32 phase)
+    double t_n_red;         // (step * dt) reduced modulo 2 pi
+    float t_n_red_f;        // the same rounded to float (FP32 phase)
     unsigned step;
     unsigned long long seed;
     int pass;               // 0: particles present at the step start (tau = 0)
@@ -109,17 +116,22 @@ struct qed_ctx {
     unsigned long long *slots;    // hole indices
     int64_t slots_cap;
     sfq::LevelWork *lev;          // leveling work (device)
+    unsigned long long *pin;      // small pinned host scratch (flags read back)
     // overflow snapshot
     void *snap;
     int64_t snap_bytes;
     qed_stats acc;           // accumulated statistics (host)
     // profiling: CUDA event pairs around the push kernels
     static constexpr int EVN = 512;
-    cudaEvent_t ev[2][EVN][2];   // [lepton|photon][pair][start|stop]
-    int ev_used[2];
+    cudaEvent_t ev[4][EVN][2];   // [lepton|photon|compaction|leveling][pair][start|stop]
+    int ev_used[4];
     bool ev_ready;
-    double kernel_ms[2];
+    double kernel_ms[4];         // lepton, photon, compaction, leveling
     int64_t launches;            // kernels launched since the last reset
+    double sync_ms;              // host time blocked in stream synchronisation
+    void *batch;                 // batched-push work buffers
+    cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
+    int tuned_threads;           // block shape picked by the autotuner (0: none yet)
 };
 
 // Implemented in sfqed_tables.cu
@@ -133,6 +145,12 @@ qed_status sfq_sample(qed_ctx *ctx, int is_photon, const double *chi, const doub
 qed_status sfq_eval_chi(qed_ctx *ctx, int is_photon, const double *p, const double *E, const double *B, int64_t n,
                         double *chi, int64_t *n_fp64);
 qed_status sfq_philox(const uint32_t *ctr, int64_t n, uint64_t key, uint32_t *out, cudaStream_t s);
+// Implemented in sfqed_batch.cu
+qed_status sfq_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens, double dt,
+                          int nsteps, int64_t step0, qed_stats *out, int threads_override);
+qed_status sfq_batch_autotune(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields, int n_ens,
+                              double dt, int nsteps, int *chosen, double *ms3);
+void sfq_batch_free(qed_ctx *ctx);
 // Implemented in sfqed_compact.cu
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step);

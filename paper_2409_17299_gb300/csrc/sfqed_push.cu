@@ -7,6 +7,9 @@
 // clock and are pushed by the next pass (Algorithm 2): leptons and photons
 // are swept alternately until a pass creates nothing.
 #include <math.h>
+#include <string.h>
+
+#include <chrono>
 
 #include "sfqed_device.cuh"
 #include "sfqed_internal.h"
@@ -60,123 +63,229 @@ __device__ __forceinline__ T photon_chi(T k0, const T k[3], const T E[3], const 
     else return chi_guarded<false>(k0, k, E, B, &n64);
 }
 
-// Event test "tau + dt_hat > dt" and the remaining push length.  In FP32 mode
-// the first iteration (tau = 0) uses FP32 only: the smallest float above dt
-// gives the same decision, and (float)dt the same length.
-template <class T>
-__device__ __forceinline__ bool no_event_before_end(const PassArgs &a, double tau, T dth) {
-    if constexpr (sizeof(T) == 4) {
-        if (tau == 0.0) return dth >= a.dt_f_gt;
-    }
-    return tau + (double)dth > a.dt;
-}
-
-template <class T> __device__ __forceinline__ T remaining(const PassArgs &a, double tau) {
-    if constexpr (sizeof(T) == 4) {
-        if (tau == 0.0) return a.dt_f;
-    }
-    return (T)(a.dt - tau);
-}
-
 __device__ __forceinline__ void note_overflow(DevCtl *ctl, int s, unsigned long long slot) {
     atomicMax(&ctl->needed[s], slot + 1);
     atomicExch(&ctl->overflow, 1ull);
 }
 
 // Algorithm 1 for electrons and positrons (both species of one pass).
+//
+// Divergence control (the GPU form of Algorithm 3's "sort handled particles
+// to the front"): phase 1 pushes every particle of a 256-particle tile to its
+// first event or to the end of the step; particles at an event go to a
+// per-block stack in shared memory.  Whenever the stack holds a full round,
+// the block pops one item per thread and processes it densely: the event
+// (chi at the point, energy draw, recoil, photon append), then the next
+// waiting time, ending either at the step end (state stored) or at the next
+// event (pushed back).  The stack is drained after the last tile.
+constexpr int LB = 256;            // threads per block of the lepton pass
+constexpr int LQ = 2 * LB;         // stack capacity: < LB left + LB pushed
+
+template <class T> struct LeptonStack {
+    T x[3][LQ], p[3][LQ];
+    double tau[LQ];
+    unsigned long long id[LQ];
+    T w[LQ];
+    unsigned idx[LQ];              // index | species << 31
+    unsigned k[LQ];                // events so far in this step (the pending one not counted)
+    uint2 r[LQ];                   // the pending event's energy draw words
+    int n;
+};
+
+template <class T> struct LeptonCtx {
+    const PassArgs &a;
+    DevCtl *ctl;
+    const T *coef;
+    const T *icdf;
+    unsigned long long cap_ph;
+    T alpha_r;
+};
+
+// One waiting-time iteration from (x, p, tau).  Returns true and leaves the
+// particle at its event point (tau advanced, draw words in rz) if an event
+// happens before the step end, else pushes it to the end and returns false.
+// FRESH: tau == 0 (first iteration of a particle present at the step start);
+// then the event test "0 + dt_hat > dt" and the push length need no FP64
+// instruction in FP32 mode (the smallest float above dt decides exactly).
+template <class T, bool FRESH>
+__device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T q, double &tau,
+                                        unsigned long long id, unsigned k, uint2 &rz, unsigned &n64) {
+    const PassArgs &a = c.a;
+    T E[3], B[3];
+    eval_field<T>(a, x[0], FRESH ? 0.0 : tau, E, B);
+    T gam, chi, p2;
+    lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+    const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
+    T dth = t_inf<T>();
+    if (lam > (T)0) {
+        const uint4 r = event_draw(a.seed, id, a.step, k);
+        T uw, vw;
+        Uniform<T>::draw(r.x, r.y, uw, vw);
+        dth = Uniform<T>::neglog(uw, vw) / lam;
+        rz = make_uint2(r.z, r.w);
+    }
+    bool no_event;
+    T h;
+    if constexpr (FRESH && sizeof(T) == 4) { no_event = dth >= a.dt_f_gt; h = a.dt_f; }
+    else if constexpr (FRESH) { no_event = dth > a.dt; h = a.dt; }
+    else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
+    if (no_event) {
+        boris<T>(x, p, q, E, B, h);
+        tau = a.dt;
+        return false;
+    }
+    boris<T>(x, p, q, E, B, dth);
+    if constexpr (FRESH) tau = (double)dth;
+    else tau += (double)dth;
+    return true;
+}
+
+// The event at the particle's current point: chi there, energy fraction from
+// the inverse CDF, collinear energy-conserving recoil, photon appended.
 template <class T>
-__global__ void __launch_bounds__(256) k_lepton_pass(PassArgs a) {
+__device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3], double tau, T w,
+                                     unsigned long long id, unsigned k, uint2 rz, unsigned &n64) {
+    const PassArgs &a = c.a;
+    T E[3], B[3];
+    eval_field<T>(a, x[0], tau, E, B);
+    T gam, chi, p2;
+    lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+    T om, ue, ve;
+    Uniform<T>::draw(rz.x, rz.y, ue, ve);
+    const T delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
+    const T g = gam;
+    T g_after = om * g, k0 = delta * g;
+    if (g_after < (T)1) { g_after = (T)1; k0 = g - (T)1; }
+    const T inv = (T)1 / m_sqrt(p2);
+    const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
+    const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
+    if (!(a.soft_filter && k0 < (T)2)) {
+        const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, k);
+        const unsigned long long slot = warp_append(&c.ctl->count[2], 1);
+        if (slot < c.cap_ph) {
+            const SpeciesDev &P = a.sp[2];
+            st<T>(P.x, slot, x[0]); st<T>(P.y, slot, x[1]); st<T>(P.z, slot, x[2]);
+            st<T>(P.px, slot, k0 * nx); st<T>(P.py, slot, k0 * ny); st<T>(P.pz, slot, k0 * nz);
+            st<T>(P.w, slot, w);
+            P.id[slot] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
+            P.nev[slot] = 0u;
+            if (a.record_newborn_tau) P.tau[slot] = tau;
+        } else {
+            note_overflow(c.ctl, 2, slot);
+        }
+    }
+    p[0] = pa * nx; p[1] = pa * ny; p[2] = pa * nz;
+}
+
+template <class T>
+__device__ __forceinline__ void finish(const PassArgs &a, unsigned idx, const T x[3], const T p[3], unsigned k) {
+    const SpeciesDev &S = a.sp[idx >> 31];
+    const unsigned long long i = idx & 0x7FFFFFFFu;
+    st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
+    st<T>(S.px, i, p[0]); st<T>(S.py, i, p[1]); st<T>(S.pz, i, p[2]);
+    if (k) S.nev[i] += k;
+}
+
+template <class T>
+__device__ __forceinline__ void stack_push(LeptonStack<T> &q, const T x[3], const T p[3], double tau,
+                                           unsigned long long id, T w, unsigned idx, unsigned k, uint2 rz) {
+    const int slot = atomicAdd(&q.n, 1);
+    q.x[0][slot] = x[0]; q.x[1][slot] = x[1]; q.x[2][slot] = x[2];
+    q.p[0][slot] = p[0]; q.p[1][slot] = p[1]; q.p[2][slot] = p[2];
+    q.tau[slot] = tau; q.id[slot] = id; q.w[slot] = w; q.idx[slot] = idx; q.k[slot] = k; q.r[slot] = rz;
+}
+
+// Pop min(n, LB) items, one per thread, and process each to its next event
+// or the step end.  Every thread of the block calls this.
+template <class T>
+__device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T> &q, unsigned long long &ev,
+                                            unsigned &mx, unsigned &n64) {
+    const int n = q.n;
+    const int take = n < LB ? n : LB;
+    const int t = threadIdx.x;
+    T x[3], p[3], w = 0;
+    double tau = 0.0;
+    unsigned long long id = 0;
+    unsigned idx = 0, k = 0;
+    uint2 rz = make_uint2(0, 0);
+    const bool mine = t < take;
+    if (mine) {
+        const int s = n - take + t;
+        x[0] = q.x[0][s]; x[1] = q.x[1][s]; x[2] = q.x[2][s];
+        p[0] = q.p[0][s]; p[1] = q.p[1][s]; p[2] = q.p[2][s];
+        tau = q.tau[s]; id = q.id[s]; w = q.w[s]; idx = q.idx[s]; k = q.k[s]; rz = q.r[s];
+    }
+    __syncthreads();
+    if (t == 0) q.n = n - take;
+    __syncthreads();
+    if (mine) {
+        emit<T>(c, x, p, tau, w, id, k, rz, n64);
+        ++k;
+        ++ev;
+        const T qch = (idx >> 31) ? (T)1 : (T)-1;
+        if (tau < c.a.dt && advance<T, false>(c, x, p, qch, tau, id, k, rz, n64)) {
+            stack_push<T>(q, x, p, tau, id, w, idx, k, rz);
+        } else {
+            finish<T>(c.a, idx, x, p, k);
+            mx = max(mx, k);
+        }
+    }
+    __syncthreads();
+}
+
+template <class T, bool FRESH>
+__global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
     __shared__ T s_coef[NCOEF];
+    __shared__ LeptonStack<T> q;
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    if (threadIdx.x == 0) q.n = 0;
     __syncthreads();
     DevCtl *ctl = a.ctl;
     const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
     const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
     const unsigned long long n = n0 + n1;
-    const unsigned long long cap_ph = ctl->capacity[2];
-    const T *icdf = reinterpret_cast<const T *>(a.icdf_em);
-    const T alpha_r = (T)(ALPHA * RS);
+    const LeptonCtx<T> c{a, ctl, s_coef, reinterpret_cast<const T *>(a.icdf_em), ctl->capacity[2], (T)(ALPHA * RS)};
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
 
-    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        const int s = j < n0 ? 0 : 1;
-        const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
-        const SpeciesDev &S = a.sp[s];
-        const T w = ld<T>(S.w, i);
-        if (!(w > (T)0)) continue;
-        T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
-        T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
-        const unsigned long long id = __ldg(S.id + i);
-        double tau = a.pass ? S.tau[i] : 0.0;
-        const T q = s == 0 ? (T)-1 : (T)1;
-        unsigned k = 0;
-        while (tau < a.dt) {
-            T E[3], B[3];
-            eval_field<T>(a, x[0], tau, E, B);
-            T gam, chi, p2;
-            lepton_chi<T>(p, E, B, gam, chi, p2, n64);
-            const T lam = p2 > (T)0 ? alpha_r / gam * rate_em<T>(s_coef, chi) : (T)0;
-            uint4 r = make_uint4(0, 0, 0, 0);
-            T dth = t_inf<T>();
-            if (lam > (T)0) {
-                r = event_draw(a.seed, id, a.step, k);
-                T uw, vw;
-                Uniform<T>::draw(r.x, r.y, uw, vw);
-                dth = Uniform<T>::neglog(uw, vw) / lam;
-            }
-            if (no_event_before_end<T>(a, tau, dth)) {      // push to the end of the step
-                boris<T>(x, p, q, E, B, remaining<T>(a, tau));
-                tau = a.dt;
-                break;
-            }
-            boris<T>(x, p, q, E, B, dth);
-            tau += (double)dth;
-            // event: chi at the emission point, energy from the inverse CDF
-            eval_field<T>(a, x[0], tau, E, B);
-            lepton_chi<T>(p, E, B, gam, chi, p2, n64);
-            T om, ue, ve;
-            Uniform<T>::draw(r.z, r.w, ue, ve);
-            const T delta = sample_emission<T>(icdf, chi, ue, ve, &om);
-            const T g = gam;
-            T g_after = om * g, k0 = delta * g;
-            if (g_after < (T)1) { g_after = (T)1; k0 = g - (T)1; }
-            const T inv = (T)1 / m_sqrt(p2);
-            const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
-            const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
-            if (!(a.soft_filter && k0 < (T)2)) {
-                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, k);
-                const unsigned long long slot = warp_append(&ctl->count[2], 1);
-                if (slot < cap_ph) {
-                    const SpeciesDev &P = a.sp[2];
-                    st<T>(P.x, slot, x[0]); st<T>(P.y, slot, x[1]); st<T>(P.z, slot, x[2]);
-                    st<T>(P.px, slot, k0 * nx); st<T>(P.py, slot, k0 * ny); st<T>(P.pz, slot, k0 * nz);
-                    st<T>(P.w, slot, w);
-                    P.id[slot] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
-                    P.nev[slot] = 0u;
-                    if (a.record_newborn_tau) P.tau[slot] = tau;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * LB; base < n;
+         base += (unsigned long long)gridDim.x * LB) {
+        const unsigned long long j = base + threadIdx.x;
+        if (j < n) {
+            const int s = j < n0 ? 0 : 1;
+            const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
+            const SpeciesDev &S = a.sp[s];
+            const T w = ld<T>(S.w, i);
+            if (w > (T)0) {
+                T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
+                T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
+                const unsigned long long id = __ldg(S.id + i);
+                double tau = FRESH ? 0.0 : S.tau[i];
+                const unsigned idx = (unsigned)i | ((unsigned)s << 31);
+                ++my_steps;
+                uint2 rz = make_uint2(0, 0);
+                const T qch = s == 0 ? (T)-1 : (T)1;
+                bool event;
+                if constexpr (FRESH) event = advance<T, true>(c, x, p, qch, tau, id, 0u, rz, n64);
+                else event = tau < a.dt && advance<T, false>(c, x, p, qch, tau, id, 0u, rz, n64);
+                if (event) {
+                    stack_push<T>(q, x, p, tau, id, w, idx, 0u, rz);
                 } else {
-                    note_overflow(ctl, 2, slot);
+                    finish<T>(a, idx, x, p, 0u);
                 }
             }
-            p[0] = pa * nx; p[1] = pa * ny; p[2] = pa * nz;
-            ++k;
         }
-        st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
-        st<T>(S.px, i, p[0]); st<T>(S.py, i, p[1]); st<T>(S.pz, i, p[2]);
-        if (k) S.nev[i] += k;
-        ++my_steps;
-        my_ev += k;
-        my_max = max(my_max, k);
+        __syncthreads();
+        while (q.n >= LB) stack_round<T>(c, q, my_ev, my_max, n64);
     }
+    while (q.n > 0) stack_round<T>(c, q, my_ev, my_max, n64);
     __syncwarp();
     flush_stats(ctl, my_steps, my_ev, my_max, false, n64);
 }
 
 // Photon push: straight flight, pair creation at the event, the photon is
 // removed (weight 0) and the pair appended.
-template <class T>
+template <class T, bool FRESH>
 __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
     __shared__ T s_coef[NCOEF];
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
@@ -198,16 +307,17 @@ __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
         T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
         const T kx = ld<T>(S.px, i), ky = ld<T>(S.py, i), kz = ld<T>(S.pz, i);
         const unsigned long long id = __ldg(S.id + i);
-        double tau = a.pass ? S.tau[i] : 0.0;
+        double tau = FRESH ? 0.0 : S.tau[i];
         const T kv[3] = {kx, ky, kz};
         const T k0 = m_sqrt(kx * kx + ky * ky + kz * kz);
         unsigned k = 0;
         if (k0 > (T)0) {
             const T inv = (T)1 / k0;
             const T nx = kx * inv, ny = ky * inv, nz = kz * inv;
-            while (tau < a.dt) {
+            // one waiting time: the photon either reaches the step end or converts
+            if (FRESH || tau < a.dt) {
                 T E[3], B[3];
-                eval_field<T>(a, x[0], tau, E, B);
+                eval_field<T>(a, x[0], FRESH ? 0.0 : tau, E, B);
                 T chi = photon_chi<T>(k0, kv, E, B, n64);
                 const T lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);
                 uint4 r = make_uint4(0, 0, 0, 0);
@@ -218,14 +328,18 @@ __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
                     Uniform<T>::draw(r.x, r.y, uw, vw);
                     dth = Uniform<T>::neglog(uw, vw) / lam;
                 }
-                if (no_event_before_end<T>(a, tau, dth)) {
-                    const T h = remaining<T>(a, tau);
+                bool no_event;
+                T h;
+                if constexpr (FRESH && sizeof(T) == 4) { no_event = dth >= a.dt_f_gt; h = a.dt_f; }
+                else if constexpr (FRESH) { no_event = dth > a.dt; h = a.dt; }
+                else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
+                if (no_event) {
                     x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
                     tau = a.dt;
-                    break;
-                }
+                } else {
                 x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
-                tau += (double)dth;
+                if constexpr (FRESH) tau = (double)dth;
+                else tau += (double)dth;
                 eval_field<T>(a, x[0], tau, E, B);
                 chi = photon_chi<T>(k0, kv, E, B, n64);
                 T om, ue, ve;
@@ -262,7 +376,7 @@ __global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
                 }
                 w = (T)0;       // the photon is eliminated
                 k = 1;
-                break;
+                }
             }
         }
         st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
@@ -408,13 +522,15 @@ static qed_status snapshot(qed_ctx *ctx, qed_particles *p, bool restore) {
 
 static qed_status read_ctl(qed_ctx *ctx) {
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    const auto t0 = std::chrono::steady_clock::now();
     SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return QED_OK;
 }
 
 // Profiling: event pairs around the push kernels, drained into kernel_ms.
 static qed_status drain_events(qed_ctx *ctx) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
         for (int i = 0; i < ctx->ev_used[k]; ++i) {
             float ms = 0.f;
             SFQ_CUDA(cudaEventSynchronize(ctx->ev[k][i][1]));
@@ -428,7 +544,7 @@ static qed_status drain_events(qed_ctx *ctx) {
 
 static qed_status ensure_events(qed_ctx *ctx) {
     if (ctx->ev_ready) return QED_OK;
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 4; ++k)
         for (int i = 0; i < qed_ctx::EVN; ++i)
             for (int j = 0; j < 2; ++j) SFQ_CUDA(cudaEventCreate(&ctx->ev[k][i][j]));
     ctx->ev_ready = true;
@@ -452,17 +568,42 @@ static qed_status timed_launch(qed_ctx *ctx, int which, K launch) {
     return QED_OK;
 }
 
-template <class T>
-static qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons) {
-    const int threads = ctx->cfg.block_threads > 0 ? ctx->cfg.block_threads : 256;
-    const int per_sm = ctx->cfg.blocks_per_sm > 0 ? ctx->cfg.blocks_per_sm : 4;
-    const int blocks = ctx->sm_count * per_sm;
+// Persistent grids: one wave of resident blocks (SM count x blocks per SM
+// from the occupancy calculator unless the configuration fixes it).
+template <class K> static int resident_blocks(const qed_ctx *ctx, K kernel, int threads) {
+    int per_sm = ctx->cfg.blocks_per_sm;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    return ctx->sm_count * per_sm;
+}
+
+// a group of launches timed as one (compaction, leveling)
+template <class F> static qed_status timed_block(qed_ctx *ctx, int which, F body) {
+    if (!ctx->cfg.profile) return body();
+    if (ctx->ev_used[which] == qed_ctx::EVN) {
+        qed_status e = drain_events(ctx);
+        if (e != QED_OK) return e;
+    }
+    const int i = ctx->ev_used[which]++;
+    SFQ_CUDA(cudaEventRecord(ctx->ev[which][i][0], ctx->stream));
+    qed_status e = body();
+    SFQ_CUDA(cudaEventRecord(ctx->ev[which][i][1], ctx->stream));
+    return e;
+}
+
+template <class T, bool FRESH>
+static qed_status launch_pass_t(qed_ctx *ctx, PassArgs &a, bool photons) {
+    const int threads = LB;
+    const int bl = resident_blocks(ctx, k_lepton_pass<T, FRESH>, threads);
+    const int bp = resident_blocks(ctx, k_photon_pass<T, FRESH>, threads);
     cudaStream_t st = ctx->stream;
-    qed_status e = timed_launch(ctx, 0, [&] { k_lepton_pass<T><<<blocks, threads, 0, st>>>(a); });
+    qed_status e = timed_launch(ctx, 0, [&] { k_lepton_pass<T, FRESH><<<bl, threads, 0, st>>>(a); });
     if (e != QED_OK) return e;
     SFQ_LAUNCHED(ctx, 1);
     if (photons) {
-        e = timed_launch(ctx, 1, [&] { k_photon_pass<T><<<blocks, threads, 0, st>>>(a); });
+        e = timed_launch(ctx, 1, [&] { k_photon_pass<T, FRESH><<<bp, threads, 0, st>>>(a); });
         if (e != QED_OK) return e;
         SFQ_LAUNCHED(ctx, 1);
     }
@@ -471,25 +612,42 @@ static qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons) {
 }
 
 template <class T>
+static qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons) {
+    return a.pass == 0 ? launch_pass_t<T, true>(ctx, a, photons) : launch_pass_t<T, false>(ctx, a, photons);
+}
+
+template <class T>
 static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
                             int64_t step0, qed_stats *out) {
     const bool cascade = ctx->cfg.push_photons != 0;
+    const auto call_t0 = std::chrono::steady_clock::now();
     ctx->launches = 0;
-    ctx->kernel_ms[0] = ctx->kernel_ms[1] = 0.0;
+    ctx->sync_ms = 0.0;
+    for (int k = 0; k < 4; ++k) ctx->kernel_ms[k] = 0.0;
     if (ctx->cfg.profile) {
         qed_status e = ensure_events(ctx);
         if (e != QED_OK) return e;
     }
     int64_t count0[3];
     for (int s = 0; s < 3; ++s) count0[s] = p->s[s].count;
-    DevCtl h{};
+    // the pinned mirror stages the upload (a pageable source would block the host)
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    DevCtl &h = *ctx->ctl_host;
+    memset(&h, 0, sizeof(DevCtl));
     for (int s = 0; s < 3; ++s) {
         h.count[s] = (unsigned long long)p->s[s].count;
         h.capacity[s] = (unsigned long long)p->s[s].capacity;
     }
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl, &h, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
+    int64_t cap_max = 0;
     for (int s = 0; s < 3; ++s) {
         qed_status e = ensure_tau(ctx, s, p->s[s].capacity);
+        if (e != QED_OK) return e;
+        cap_max = p->s[s].capacity > cap_max ? p->s[s].capacity : cap_max;
+    }
+    // compaction work buffers sized once for the largest species
+    {
+        qed_status e = sfq_ensure_work(ctx, (cap_max + 1023) / 1024 + 2, cap_max);
         if (e != QED_OK) return e;
     }
     if (ctx->cfg.restore_on_overflow) {
@@ -508,7 +666,10 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.icdf_em = f32 ? (const void *)ctx->icdf_em32 : (const void *)ctx->icdf_em64;
     a.icdf_pair = f32 ? (const void *)ctx->icdf_pair32 : (const void *)ctx->icdf_pair64;
     a.field_kind = field->kind;
-    for (int i = 0; i < 6; ++i) a.prm[i] = field->params[i];
+    for (int i = 0; i < 6; ++i) {
+        a.prm[i] = field->params[i];
+        a.prm_f[i] = (float)field->params[i];
+    }
     a.dt = dt;
     a.dt_f = (float)dt;
     a.dt_f_gt = (double)a.dt_f > dt ? a.dt_f : nextafterf(a.dt_f, INFINITY);
@@ -522,6 +683,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
         a.step = (unsigned)step;
         a.t_n = (double)step * dt;
         a.t_n_red = fmod(a.t_n, 2.0 * 3.14159265358979323846);
+        a.t_n_red_f = (float)a.t_n_red;
         a.pass = 0;
         k_step_begin<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
         SFQ_LAUNCHED(ctx, 1);
@@ -548,15 +710,16 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
             }
             if (ctx->ctl_host->overflow) { rc = QED_ERR_CAPACITY; break; }
             for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)ctx->ctl_host->count[s];
-            if (cascade) {
-                e = sfq_compact_species(ctx, &p->s[2], 2);
-                if (e != QED_OK) return e;
-            }
-            if (ctx->cfg.thin_cap > 0) {
-                for (int s = 0; s < 3; ++s) {
-                    e = sfq_level_species(ctx, &p->s[s], s, step);
-                    if (e != QED_OK) return e;
+            // per species: leveling (it skips dead entries and compacts), else
+            // removal of the photons that converted
+            for (int s = 0; s < 3; ++s) {
+                const bool level = ctx->cfg.thin_cap > 0 && p->s[s].count > ctx->cfg.thin_cap;
+                if (level) {
+                    e = timed_block(ctx, 3, [&] { return sfq_level_species(ctx, &p->s[s], s, step); });
+                } else if (cascade && s == 2) {
+                    e = timed_block(ctx, 2, [&] { return sfq_compact_species(ctx, &p->s[2], 2); });
                 }
+                if (e != QED_OK) return e;
             }
         }
     }
@@ -581,9 +744,10 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
         e = drain_events(ctx);
         if (e != QED_OK) return e;
     }
-    st.kernel_ms[0] = ctx->kernel_ms[0];
-    st.kernel_ms[1] = ctx->kernel_ms[1];
+    for (int k = 0; k < 4; ++k) st.kernel_ms[k] = ctx->kernel_ms[k];
     st.launches = ctx->launches;
+    st.sync_ms = ctx->sync_ms;
+    st.call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - call_t0).count();
     if (rc == QED_ERR_CAPACITY && ctx->cfg.restore_on_overflow) {
         for (int s = 0; s < 3; ++s) p->s[s].count = count0[s];
         e = snapshot(ctx, p, true);
@@ -602,8 +766,9 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     ctx->acc.chi_fp64 += st.chi_fp64;
     ctx->acc.photon_steps += st.photon_steps;
     ctx->acc.launches += st.launches;
-    ctx->acc.kernel_ms[0] += st.kernel_ms[0];
-    ctx->acc.kernel_ms[1] += st.kernel_ms[1];
+    for (int k = 0; k < 4; ++k) ctx->acc.kernel_ms[k] += st.kernel_ms[k];
+    ctx->acc.sync_ms += st.sync_ms;
+    ctx->acc.call_ms += st.call_ms;
     if (st.max_subevents > ctx->acc.max_subevents) ctx->acc.max_subevents = st.max_subevents;
     return rc;
 }
