@@ -44,6 +44,9 @@ def parse():
                              "batched_uniform_b"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time the FP64 mode (extra key)")
+    ap.add_argument("--compare-mlp", type=int, default=1,
+                    help="also train the surrogate sampler (1e8 table draws) and time the cascade with it")
+    ap.add_argument("--mlp-samples", type=float, default=1e8)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e", type=int, default=1)
     ap.add_argument("--scale", type=float, default=1.0, help="scale the seed count (tests only)")
@@ -198,14 +201,17 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def gpu_run(args, w, precision, warm, steps, timed=True, profile=True):
+def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_params=None):
     import torch
     import paper_2409_17299_gb300 as q
     prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
     # capacities are sized for the whole run, so no per-call overflow snapshot
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
-                        profile=int(profile), restore_on_overflow=0)
+                        profile=int(profile), restore_on_overflow=0,
+                        sampler=q.QED_SAMPLER_MLP if mlp_params is not None else q.QED_SAMPLER_TABLE)
     gen = q.Generator(cfg)
+    if mlp_params is not None:
+        q.qed_mlp_set_params(gen.ctx, mlp_params)
     ens = q.DeviceEnsemble.from_host(w.species, capacities(w, warm + steps), prec)
     field = q.make_field(w.field_kind, w.field_prm)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -441,6 +447,24 @@ def main():
         fp64 = {"value": tot64["particle_steps"] / (ms64 / 1e3), "events_per_s":
                 (tot64["emit_events"] + tot64["pair_events"]) / (ms64 / 1e3), "ms_per_step": ms64 / steps}
 
+    mlp = None
+    if args.compare_mlp and world == 1 and args.workload == "rotating_e_cascade":
+        import paper_2409_17299_gb300 as q
+        tg = q.Generator(q.make_config(precision=q.QED_FP32))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = q.qed_train_surrogate(tg.ctx, int(args.mlp_samples), 65536, 2e-3, 7)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        P = q.qed_mlp_get_params(tg.ctx)
+        tg.close()
+        ms_m, _, tot_m, _ = gpu_run(args, w, args.precision, warm, steps, mlp_params=P)
+        mlp = {"value": tot_m["particle_steps"] / (ms_m / 1e3),
+               "events_per_s": (tot_m["emit_events"] + tot_m["pair_events"]) / (ms_m / 1e3),
+               "ms_per_step": ms_m / steps, "lepton_kernel_ms": tot_m["kernel_ms"][0],
+               "train_samples": int(args.mlp_samples), "train_seconds": train_s, "train_final_mse": loss,
+               "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation (mma.sync)"}
+
     e2e = None
     if args.e2e:
         ps_e, ms_e, wall_e, nb = e2e_run(w, args.precision, warm, steps)
@@ -485,6 +509,11 @@ def main():
     if fp64:
         line["fp64"] = fp64
         line["fp32_speedup_over_fp64"] = line["value"] / fp64["value"]
+    if mlp:
+        line["surrogate"] = mlp
+        line["surrogate_speedup_over_table_fp32"] = mlp["value"] / line["value"]
+        if fp64:
+            line["surrogate_speedup_over_fp64_table"] = mlp["value"] / fp64["value"]
     if e2e:
         line["e2e"] = e2e
     if cpu:

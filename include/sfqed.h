@@ -170,6 +170,39 @@ qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc
 qed_status qed_autotune_batch(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields,
                               int n_ens, double dt, int nsteps, int *chosen_threads, double *ms3);
 
+/* ---- learned surrogate of the emission sampler ------------------------
+ * An extension of the method (the paper samples from tables only): a network
+ * 2 -> 64 -> 64 -> 64 -> 1 with SiLU hidden layers, BF16 weights and FP32
+ * accumulation, maps features (log10(chi)/3, logit(u)/16) to zeta/16 + 1/2,
+ * zeta = ln y, y = 2 delta / (3 chi (1 - delta)) (the quantity the emission
+ * table stores).  Parameter layout (8577 floats, W[out][in] row-major):
+ * W1[64][2], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4.
+ * With cfg.sampler == QED_SAMPLER_MLP the lepton push draws photon energies
+ * from the network for chi in [1e-3, 1e3] and |logit u| < 16, and from the
+ * table elsewhere. */
+
+/* Train on n_samples draws (log10 chi uniform on [-3, 3], u uniform) labelled
+ * by the emission table, in batches of `batch` (a multiple of 128): forward
+ * and backward passes on the tensor cores, Adam, learning rate decaying from
+ * lr to lr/100 (cosine).  *final_loss (may be NULL): mean squared error over
+ * the last 16 batches. */
+qed_status qed_train_surrogate(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed,
+                               double *final_loss);
+
+/* Load / read the FP32 master parameters (host arrays of 8577 floats). */
+qed_status qed_mlp_set_params(qed_ctx *ctx, const float *params);
+qed_status qed_mlp_get_params(qed_ctx *ctx, float *params);
+
+/* Network output for n feature pairs (feat_dev: n x 2 floats, y_dev: n
+ * floats, both on the device), with the BF16 weights. */
+qed_status qed_mlp_forward(qed_ctx *ctx, const float *feat_dev, int64_t n, float *y_dev);
+
+/* Gradient of the mean squared error (1/n) sum (y - target)^2 over n given
+ * samples, without updating anything (grad: host array of 8577 floats;
+ * *loss may be NULL). */
+qed_status qed_mlp_grad(qed_ctx *ctx, const float *feat_dev, const float *target_dev, int64_t n,
+                        float *grad, double *loss);
+
 /* Statistics accumulated since the context was created or last reset. */
 qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset);
 

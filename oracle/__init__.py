@@ -103,6 +103,11 @@ def lib():
                 "or_push_and_generate": (i32, [p, p, p, p, p, p, d, i32, i64, p]),
                 "or_rate_lambda": (d, [p, p, i32, p, p, p]),
                 "or_const": (d, [i32]),
+                "or_mlp_nparams": (i32, []),
+                "or_mlp_forward": (None, [p, i64, p, p]),
+                "or_mlp_loss_grad": (d, [p, i64, p, p, p]),
+                "or_mlp_features": (None, [d, d, p]),
+                "or_mlp_delta": (d, [d, d, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -395,3 +400,39 @@ def compact(ens: Ensemble, species: int):
     arr = ens.structs()
     lib().or_compact(C.cast(C.byref(arr[species]), C.c_void_p))
     ens.pull(arr)
+
+
+# --------------------------------------------------------------------------
+# surrogate network (FP64 reference of the forward and backward passes)
+# --------------------------------------------------------------------------
+def mlp_nparams() -> int:
+    return lib().or_mlp_nparams()
+
+
+def mlp_forward(params, feat) -> np.ndarray:
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    F = np.ascontiguousarray(feat, dtype=np.float64).reshape(-1, 2)
+    y = np.zeros(F.shape[0])
+    lib().or_mlp_forward(_ptr(P), F.shape[0], _ptr(F), _ptr(y))
+    return y
+
+
+def mlp_loss_grad(params, feat, target):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    F = np.ascontiguousarray(feat, dtype=np.float64).reshape(-1, 2)
+    T = np.ascontiguousarray(target, dtype=np.float64)
+    g = np.zeros_like(P)
+    loss = lib().or_mlp_loss_grad(_ptr(P), F.shape[0], _ptr(F), _ptr(T), _ptr(g))
+    return loss, g
+
+
+def mlp_features(chi, u):
+    f = np.zeros(2)
+    lib().or_mlp_features(float(chi), float(u), _ptr(f))
+    return f
+
+
+def mlp_delta(chi, y):
+    om = np.zeros(1)
+    d = lib().or_mlp_delta(float(chi), float(y), _ptr(om))
+    return d, float(om[0])

@@ -996,3 +996,127 @@ double or_const(int which)
     default: return 0.0;
     }
 }
+
+/* ================================================================== */
+/* 12. Surrogate of the emission inverse CDF (an extension: the paper  */
+/*     samples energies from tables only).  A network                  */
+/*     2 -> 64 -> 64 -> 64 -> 1 with SiLU on the hidden layers maps     */
+/*     features (log10(chi)/3, logit(u)/16) to zeta/16 + 1/2, where     */
+/*     zeta = ln y is the quantity the emission table stores.           */
+/*     Parameter layout: W1[64][2], b1[64], W2[64][64], b2[64],         */
+/*     W3[64][64], b3[64], W4[64], b4 (8577 numbers, W[out][in]).       */
+/*     Plain forward pass and backward pass of the mean squared error.  */
+/* ================================================================== */
+#define OR_MLP_H 64
+#define OR_MLP_NP (OR_MLP_H * 2 + OR_MLP_H + 2 * (OR_MLP_H * OR_MLP_H + OR_MLP_H) + OR_MLP_H + 1)
+
+static double or_silu(double z) { return z / (1.0 + exp(-z)); }
+static double or_dsilu(double z) { double s = 1.0 / (1.0 + exp(-z)); return s * (1.0 + z * (1.0 - s)); }
+
+int or_mlp_nparams(void) { return OR_MLP_NP; }
+
+/* one sample: pre-activations z1..z3 and activations h1..h3 */
+static double mlp_one(const double *P, const double f[2], double z[3][OR_MLP_H], double h[3][OR_MLP_H])
+{
+    const double *W1 = P, *b1 = W1 + 2 * OR_MLP_H;
+    const double *W2 = b1 + OR_MLP_H, *b2 = W2 + OR_MLP_H * OR_MLP_H;
+    const double *W3 = b2 + OR_MLP_H, *b3 = W3 + OR_MLP_H * OR_MLP_H;
+    const double *W4 = b3 + OR_MLP_H, *b4 = W4 + OR_MLP_H;
+    for (int o = 0; o < OR_MLP_H; ++o) {
+        z[0][o] = W1[2 * o] * f[0] + W1[2 * o + 1] * f[1] + b1[o];
+        h[0][o] = or_silu(z[0][o]);
+    }
+    for (int o = 0; o < OR_MLP_H; ++o) {
+        double s = b2[o];
+        for (int i = 0; i < OR_MLP_H; ++i) s += W2[o * OR_MLP_H + i] * h[0][i];
+        z[1][o] = s;
+        h[1][o] = or_silu(s);
+    }
+    for (int o = 0; o < OR_MLP_H; ++o) {
+        double s = b3[o];
+        for (int i = 0; i < OR_MLP_H; ++i) s += W3[o * OR_MLP_H + i] * h[1][i];
+        z[2][o] = s;
+        h[2][o] = or_silu(s);
+    }
+    double y = b4[0];
+    for (int i = 0; i < OR_MLP_H; ++i) y += W4[i] * h[2][i];
+    return y;
+}
+
+void or_mlp_forward(const double *P, int64_t n, const double *feat /* n x 2 */, double *y)
+{
+    double z[3][OR_MLP_H], h[3][OR_MLP_H];
+    for (int64_t k = 0; k < n; ++k) y[k] = mlp_one(P, feat + 2 * k, z, h);
+}
+
+/* loss = mean_k (y_k - t_k)^2; g = d loss / d P */
+double or_mlp_loss_grad(const double *P, int64_t n, const double *feat, const double *t, double *g)
+{
+    const double *W1 = P, *b1 = W1 + 2 * OR_MLP_H;
+    const double *W2 = b1 + OR_MLP_H, *b2 = W2 + OR_MLP_H * OR_MLP_H;
+    const double *W3 = b2 + OR_MLP_H, *b3 = W3 + OR_MLP_H * OR_MLP_H;
+    const double *W4 = b3 + OR_MLP_H;
+    (void)b2; (void)b3; (void)b1;
+    double *gW1 = g, *gb1 = gW1 + 2 * OR_MLP_H;
+    double *gW2 = gb1 + OR_MLP_H, *gb2 = gW2 + OR_MLP_H * OR_MLP_H;
+    double *gW3 = gb2 + OR_MLP_H, *gb3 = gW3 + OR_MLP_H * OR_MLP_H;
+    double *gW4 = gb3 + OR_MLP_H, *gb4 = gW4 + OR_MLP_H;
+    memset(g, 0, sizeof(double) * OR_MLP_NP);
+    double loss = 0.0;
+    double z[3][OR_MLP_H], h[3][OR_MLP_H], d3[OR_MLP_H], d2[OR_MLP_H], d1[OR_MLP_H];
+    for (int64_t k = 0; k < n; ++k) {
+        const double *f = feat + 2 * k;
+        double y = mlp_one(P, f, z, h);
+        double r = y - t[k];
+        loss += r * r;
+        double dy = 2.0 * r / (double)n;
+        gb4[0] += dy;
+        for (int i = 0; i < OR_MLP_H; ++i) {
+            gW4[i] += dy * h[2][i];
+            d3[i] = dy * W4[i] * or_dsilu(z[2][i]);
+        }
+        for (int o = 0; o < OR_MLP_H; ++o) {
+            gb3[o] += d3[o];
+            for (int i = 0; i < OR_MLP_H; ++i) gW3[o * OR_MLP_H + i] += d3[o] * h[1][i];
+        }
+        for (int i = 0; i < OR_MLP_H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < OR_MLP_H; ++o) s += W3[o * OR_MLP_H + i] * d3[o];
+            d2[i] = s * or_dsilu(z[1][i]);
+        }
+        for (int o = 0; o < OR_MLP_H; ++o) {
+            gb2[o] += d2[o];
+            for (int i = 0; i < OR_MLP_H; ++i) gW2[o * OR_MLP_H + i] += d2[o] * h[0][i];
+        }
+        for (int i = 0; i < OR_MLP_H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < OR_MLP_H; ++o) s += W2[o * OR_MLP_H + i] * d2[o];
+            d1[i] = s * or_dsilu(z[0][i]);
+        }
+        for (int o = 0; o < OR_MLP_H; ++o) {
+            gb1[o] += d1[o];
+            gW1[2 * o] += d1[o] * f[0];
+            gW1[2 * o + 1] += d1[o] * f[1];
+        }
+    }
+    return loss / (double)n;
+}
+
+/* Features and target of the surrogate (the reading that defines it). */
+void or_mlp_features(double chi, double u, double f[2])
+{
+    double s = log(u) - log1p(-u);
+    if (s > OR_SMAX) s = OR_SMAX;
+    if (s < -OR_SMAX) s = -OR_SMAX;
+    f[0] = log10(chi) / 3.0;
+    f[1] = s / OR_SMAX;
+}
+
+/* photon energy fraction from a network output y (zeta = 16 (y - 1/2)) */
+double or_mlp_delta(double chi, double y, double *one_minus)
+{
+    double zeta = 16.0 * (y - 0.5);
+    double a = 3.0 * chi * exp(zeta);
+    if (one_minus) *one_minus = 2.0 / (2.0 + a);
+    return a / (2.0 + a);
+}

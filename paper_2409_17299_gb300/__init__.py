@@ -22,7 +22,8 @@ QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP = 0, 1, 2
 
 EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_batch_push", "qed_autotune_batch", "qed_compact", "qed_get_stats", "qed_strerror",
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
-            "qed_compact_species_noalloc")
+            "qed_compact_species_noalloc", "qed_train_surrogate", "qed_mlp_set_params", "qed_mlp_get_params",
+            "qed_mlp_forward", "qed_mlp_grad")
 QED_NOALLOC_MAX_ENTRIES = 1 << 20
 
 
@@ -101,6 +102,11 @@ def lib():
         "qed_sample": (i32, [p, i32, p, p, i64, p, p]),
         "qed_compact_species_noalloc": (i32, [C.POINTER(QedSpecies), i32, p]),
         "qed_eval_chi": (i32, [p, i32, p, p, p, i64, p, C.POINTER(i64)]),
+        "qed_train_surrogate": (i32, [p, i64, i32, C.c_double, C.c_uint64, C.POINTER(C.c_double)]),
+        "qed_mlp_set_params": (i32, [p, p]),
+        "qed_mlp_get_params": (i32, [p, p]),
+        "qed_mlp_forward": (i32, [p, p, i64, p]),
+        "qed_mlp_grad": (i32, [p, p, p, i64, p, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -216,6 +222,51 @@ def qed_sample(ctx, is_photon: bool, chi_dev_ptr: int, u_dev_ptr: int, n: int, d
         raise QedError(rc, "qed_sample")
 
 
+MLP_NPARAMS = 8577
+
+
+def qed_train_surrogate(ctx, n_samples: int, batch: int = 65536, lr: float = 2e-3, seed: int = 12345) -> float:
+    loss = C.c_double(0.0)
+    rc = lib().qed_train_surrogate(ctx, int(n_samples), int(batch), float(lr), C.c_uint64(seed), C.byref(loss))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_train_surrogate")
+    return loss.value
+
+
+def qed_mlp_set_params(ctx, params_host) -> None:
+    import numpy as np
+    P = np.ascontiguousarray(params_host, dtype=np.float32)
+    rc = lib().qed_mlp_set_params(ctx, P.ctypes.data)
+    if rc != QED_OK:
+        raise QedError(rc, "qed_mlp_set_params")
+
+
+def qed_mlp_get_params(ctx):
+    import numpy as np
+    P = np.zeros(MLP_NPARAMS, dtype=np.float32)
+    rc = lib().qed_mlp_get_params(ctx, P.ctypes.data)
+    if rc != QED_OK:
+        raise QedError(rc, "qed_mlp_get_params")
+    return P
+
+
+def qed_mlp_forward(ctx, feat_dev_ptr: int, n: int, y_dev_ptr: int) -> None:
+    rc = lib().qed_mlp_forward(ctx, C.c_void_p(feat_dev_ptr), int(n), C.c_void_p(y_dev_ptr))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_mlp_forward")
+
+
+def qed_mlp_grad(ctx, feat_dev_ptr: int, target_dev_ptr: int, n: int):
+    import numpy as np
+    g = np.zeros(MLP_NPARAMS, dtype=np.float32)
+    loss = C.c_double(0.0)
+    rc = lib().qed_mlp_grad(ctx, C.c_void_p(feat_dev_ptr), C.c_void_p(target_dev_ptr), int(n), g.ctypes.data,
+                            C.byref(loss))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_mlp_grad")
+    return g, loss.value
+
+
 def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream: int | None = None) -> int:
     """Compaction of one species that allocates no device memory (for callers
     whose device memory is owned by another allocator); species.count is
@@ -230,10 +281,11 @@ def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream
 # small helpers around the ABI structs (no computation)
 # --------------------------------------------------------------------------
 def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0, thin_cap=0,
-                restore_on_overflow=1, block_threads=0, blocks_per_sm=0, profile=0) -> QedConfig:
+                restore_on_overflow=1, block_threads=0, blocks_per_sm=0, profile=0,
+                sampler=QED_SAMPLER_TABLE) -> QedConfig:
     c = QedConfig()
     c.precision = int(precision)
-    c.sampler = QED_SAMPLER_TABLE
+    c.sampler = int(sampler)
     c.seed = int(seed)
     c.push_photons = int(push_photons)
     c.soft_photon_filter = int(soft_photon_filter)

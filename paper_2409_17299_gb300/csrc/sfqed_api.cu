@@ -11,7 +11,8 @@ static void free_ctx(qed_ctx *c) {
     cudaStreamSynchronize(c->stream);
     sfq_batch_free(c);
     void *dev[] = {c->coef64, c->coef32, c->icdf_em64, c->icdf_pair64, c->icdf_em32, c->icdf_pair32, c->gl,
-                   c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap, c->lev};
+                   c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap, c->lev,
+                   c->mlp_p, c->mlp_w16, c->mlp_loss};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
@@ -28,7 +29,7 @@ extern "C" qed_status qed_init_tables(qed_ctx **out, const qed_config *cfg, void
     if (!out || !cfg) return QED_ERR_INVALID;
     *out = nullptr;
     if (cfg->precision != QED_FP64 && cfg->precision != QED_FP32) return QED_ERR_INVALID;
-    if (cfg->sampler != QED_SAMPLER_TABLE) return QED_ERR_INVALID;
+    if (cfg->sampler != QED_SAMPLER_TABLE && cfg->sampler != QED_SAMPLER_MLP) return QED_ERR_INVALID;
     if (cfg->thin_cap < 0 || cfg->block_threads < 0 || cfg->block_threads > 1024 || cfg->block_threads % 32 ||
         cfg->blocks_per_sm < 0)
         return QED_ERR_INVALID;
@@ -165,4 +166,22 @@ extern "C" qed_status qed_eval_chi(qed_ctx *ctx, int is_photon, const double *p_
 extern "C" qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const double *u_dev, int64_t n,
                                  double *delta_dev, double *one_minus_dev) {
     return sfq_sample(ctx, is_photon, chi_dev, u_dev, n, delta_dev, one_minus_dev);
+}
+
+extern "C" qed_status qed_train_surrogate(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed,
+                                          double *final_loss) {
+    return sfq_mlp_train(ctx, n_samples, batch, lr, seed, final_loss);
+}
+
+extern "C" qed_status qed_mlp_set_params(qed_ctx *ctx, const float *params) { return sfq_mlp_set_params(ctx, params); }
+
+extern "C" qed_status qed_mlp_get_params(qed_ctx *ctx, float *params) { return sfq_mlp_get_params(ctx, params); }
+
+extern "C" qed_status qed_mlp_forward(qed_ctx *ctx, const float *feat_dev, int64_t n, float *y_dev) {
+    return sfq_mlp_eval(ctx, feat_dev, n, y_dev);
+}
+
+extern "C" qed_status qed_mlp_grad(qed_ctx *ctx, const float *feat_dev, const float *target_dev, int64_t n,
+                                   float *grad, double *loss) {
+    return sfq_mlp_grad(ctx, feat_dev, target_dev, n, grad, loss);
 }

@@ -1,6 +1,7 @@
 // Internal definitions shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -75,6 +76,7 @@ struct PassArgs {
     const void *coef;       // NCOEF coefficients (T)
     const void *icdf_em;    // EM_NCHI * EM_NS (T)
     const void *icdf_pair;  // PAIR_NCHI * PAIR_NS (T)
+    const __nv_bfloat16 *mlp_w16;   // surrogate network weights, or null (table sampler)
     int field_kind;
     double prm[6];
     float prm_f[6];         // prm rounded to float once (FP32 mode)
@@ -132,6 +134,12 @@ struct qed_ctx {
     void *batch;                 // batched-push work buffers
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
     int tuned_threads;           // block shape picked by the autotuner (0: none yet)
+    // surrogate network: FP32 master parameters, Adam moments and gradient
+    // (4 x 8577 floats), BF16 copy used by the kernels, loss accumulator
+    float *mlp_p;
+    __nv_bfloat16 *mlp_w16;
+    float *mlp_loss;
+    int mlp_ready;
 };
 
 // Implemented in sfqed_tables.cu
@@ -151,6 +159,13 @@ qed_status sfq_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc
 qed_status sfq_batch_autotune(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields, int n_ens,
                               double dt, int nsteps, int *chosen, double *ms3);
 void sfq_batch_free(qed_ctx *ctx);
+// Implemented in sfqed_mlp.cu
+qed_status sfq_mlp_set_params(qed_ctx *ctx, const float *params);
+qed_status sfq_mlp_get_params(qed_ctx *ctx, float *params);
+qed_status sfq_mlp_eval(qed_ctx *ctx, const float *feat, int64_t n, float *y);
+qed_status sfq_mlp_grad(qed_ctx *ctx, const float *feat, const float *target, int64_t n, float *grad_host,
+                        double *loss);
+qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed, double *final_loss);
 // Implemented in sfqed_compact.cu
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step);

@@ -13,6 +13,7 @@
 
 #include "sfqed_device.cuh"
 #include "sfqed_internal.h"
+#include "sfqed_mma.cuh"
 
 namespace sfq {
 namespace {
@@ -140,22 +141,15 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
     return true;
 }
 
-// The event at the particle's current point: chi there, energy fraction from
-// the inverse CDF, collinear energy-conserving recoil, photon appended.
+// Kinematics of an emission with photon fraction delta (and 1 - delta) from a
+// lepton of energy gam and momentum p at x: collinear, energy-conserving
+// recoil; the photon is appended.
 template <class T>
-__device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3], double tau, T w,
-                                     unsigned long long id, unsigned k, uint2 rz, unsigned &n64) {
+__device__ __forceinline__ void emit_with(const LeptonCtx<T> &c, const T x[3], T p[3], double tau, T w,
+                                          unsigned long long id, unsigned k, T gam, T p2, T delta, T om) {
     const PassArgs &a = c.a;
-    T E[3], B[3];
-    eval_field<T>(a, x[0], tau, E, B);
-    T gam, chi, p2;
-    lepton_chi<T>(p, E, B, gam, chi, p2, n64);
-    T om, ue, ve;
-    Uniform<T>::draw(rz.x, rz.y, ue, ve);
-    const T delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
-    const T g = gam;
-    T g_after = om * g, k0 = delta * g;
-    if (g_after < (T)1) { g_after = (T)1; k0 = g - (T)1; }
+    T g_after = om * gam, k0 = delta * gam;
+    if (g_after < (T)1) { g_after = (T)1; k0 = gam - (T)1; }
     const T inv = (T)1 / m_sqrt(p2);
     const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
     const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
@@ -177,6 +171,29 @@ __device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3]
     p[0] = pa * nx; p[1] = pa * ny; p[2] = pa * nz;
 }
 
+// The event at the particle's current point with the table sampler: chi
+// there, energy fraction from the inverse CDF, then the kinematics.
+template <class T>
+__device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3], double tau, T w,
+                                     unsigned long long id, unsigned k, uint2 rz, unsigned &n64) {
+    T E[3], B[3];
+    eval_field<T>(c.a, x[0], tau, E, B);
+    T gam, chi, p2;
+    lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+    T om, ue, ve;
+    Uniform<T>::draw(rz.x, rz.y, ue, ve);
+    const T delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
+    emit_with<T>(c, x, p, tau, w, id, k, gam, p2, delta, om);
+}
+
+// Network sampler state of a block (dynamic shared memory): BF16 weights
+// and two 32 x 64 activation buffers per warp.
+struct MlpSmem {
+    __nv_bfloat16 *W;
+    __nv_bfloat16 *buf;
+};
+constexpr int MLP_SMEM_BYTES = (MLP_NP + 1) * 2 + (LB / 32) * 2 * 32 * MLP_H * 2;
+
 template <class T>
 __device__ __forceinline__ void finish(const PassArgs &a, unsigned idx, const T x[3], const T p[3], unsigned k) {
     const SpeciesDev &S = a.sp[idx >> 31];
@@ -197,9 +214,9 @@ __device__ __forceinline__ void stack_push(LeptonStack<T> &q, const T x[3], cons
 
 // Pop min(n, LB) items, one per thread, and process each to its next event
 // or the step end.  Every thread of the block calls this.
-template <class T>
+template <class T, bool MLP>
 __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T> &q, unsigned long long &ev,
-                                            unsigned &mx, unsigned &n64) {
+                                            unsigned &mx, unsigned &n64, const MlpSmem &ms) {
     const int n = q.n;
     const int take = n < LB ? n : LB;
     const int t = threadIdx.x;
@@ -218,8 +235,40 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
     __syncthreads();
     if (t == 0) q.n = n - take;
     __syncthreads();
+    if constexpr (MLP) {
+        // event-point state per item, then the whole warp evaluates the
+        // network for its 32 items on the tensor cores
+        T gam = (T)1, chi = (T)0, p2 = (T)0, ue = (T)0.5, ve = (T)0.5;
+        float f0 = 0.f, f1 = 0.f;
+        bool use_net = false;
+        if (mine) {
+            T E[3], B[3];
+            eval_field<T>(c.a, x[0], tau, E, B);
+            lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+            Uniform<T>::draw(rz.x, rz.y, ue, ve);
+            const float sl = (float)logit(ue, ve);
+            const float cf = (float)chi;
+            use_net = cf >= 1e-3f && cf <= 1e3f && fabsf(sl) < 16.0f;
+            if (use_net) { f0 = log10f(cf) / 3.0f; f1 = sl / 16.0f; }
+        }
+        const int wid = threadIdx.x >> 5;
+        const float y = mlp_forward_warp(f0, f1, ms.W, ms.buf + wid * 2 * 32 * MLP_H,
+                                         ms.buf + wid * 2 * 32 * MLP_H + 32 * MLP_H);
+        if (mine) {
+            T delta, om;
+            if (use_net) {
+                const T aa = (T)3 * chi * (T)__expf(16.0f * (y - 0.5f));
+                om = (T)2 / ((T)2 + aa);
+                delta = aa / ((T)2 + aa);
+            } else {
+                delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
+            }
+            emit_with<T>(c, x, p, tau, w, id, k, gam, p2, delta, om);
+        }
+    } else {
+        if (mine) emit<T>(c, x, p, tau, w, id, k, rz, n64);
+    }
     if (mine) {
-        emit<T>(c, x, p, tau, w, id, k, rz, n64);
         ++k;
         ++ev;
         const T qch = (idx >> 31) ? (T)1 : (T)-1;
@@ -233,10 +282,17 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
     __syncthreads();
 }
 
-template <class T, bool FRESH>
+template <class T, bool FRESH, bool MLP>
 __global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
     __shared__ T s_coef[NCOEF];
     __shared__ LeptonStack<T> q;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    MlpSmem ms{nullptr, nullptr};
+    if constexpr (MLP) {
+        ms.W = reinterpret_cast<__nv_bfloat16 *>(dyn);
+        ms.buf = ms.W + MLP_NP + 1;
+        for (int i = threadIdx.x; i < MLP_NP; i += blockDim.x) ms.W[i] = a.mlp_w16[i];
+    }
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     if (threadIdx.x == 0) q.n = 0;
     __syncthreads();
@@ -276,9 +332,9 @@ __global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
             }
         }
         __syncthreads();
-        while (q.n >= LB) stack_round<T>(c, q, my_ev, my_max, n64);
+        while (q.n >= LB) stack_round<T, MLP>(c, q, my_ev, my_max, n64, ms);
     }
-    while (q.n > 0) stack_round<T>(c, q, my_ev, my_max, n64);
+    while (q.n > 0) stack_round<T, MLP>(c, q, my_ev, my_max, n64, ms);
     __syncwarp();
     flush_stats(ctl, my_steps, my_ev, my_max, false, n64);
 }
@@ -593,13 +649,32 @@ template <class F> static qed_status timed_block(qed_ctx *ctx, int which, F body
     return e;
 }
 
+template <class K> static int resident_blocks_smem(const qed_ctx *ctx, K kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return ctx->sm_count * per_sm;
+}
+
 template <class T, bool FRESH>
 static qed_status launch_pass_t(qed_ctx *ctx, PassArgs &a, bool photons) {
     const int threads = LB;
-    const int bl = resident_blocks(ctx, k_lepton_pass<T, FRESH>, threads);
     const int bp = resident_blocks(ctx, k_photon_pass<T, FRESH>, threads);
     cudaStream_t st = ctx->stream;
-    qed_status e = timed_launch(ctx, 0, [&] { k_lepton_pass<T, FRESH><<<bl, threads, 0, st>>>(a); });
+    qed_status e;
+    if (a.mlp_w16) {
+        static bool attr_set = false;   // the attribute is per function, set once
+        if (!attr_set) {
+            SFQ_CUDA(cudaFuncSetAttribute(k_lepton_pass<T, FRESH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          MLP_SMEM_BYTES));
+            attr_set = true;
+        }
+        const int bl = resident_blocks_smem(ctx, k_lepton_pass<T, FRESH, true>, threads, MLP_SMEM_BYTES);
+        e = timed_launch(ctx, 0, [&] { k_lepton_pass<T, FRESH, true><<<bl, threads, MLP_SMEM_BYTES, st>>>(a); });
+    } else {
+        const int bl = resident_blocks(ctx, k_lepton_pass<T, FRESH, false>, threads);
+        e = timed_launch(ctx, 0, [&] { k_lepton_pass<T, FRESH, false><<<bl, threads, 0, st>>>(a); });
+    }
     if (e != QED_OK) return e;
     SFQ_LAUNCHED(ctx, 1);
     if (photons) {
@@ -665,6 +740,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.coef = f32 ? (const void *)ctx->coef32 : (const void *)ctx->coef64;
     a.icdf_em = f32 ? (const void *)ctx->icdf_em32 : (const void *)ctx->icdf_em64;
     a.icdf_pair = f32 ? (const void *)ctx->icdf_pair32 : (const void *)ctx->icdf_pair64;
+    a.mlp_w16 = ctx->cfg.sampler == QED_SAMPLER_MLP ? ctx->mlp_w16 : nullptr;
     a.field_kind = field->kind;
     for (int i = 0; i < 6; ++i) {
         a.prm[i] = field->params[i];
@@ -775,6 +851,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
 
 qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
                     int64_t step0, qed_stats *out) {
+    if (ctx && ctx->cfg.sampler == QED_SAMPLER_MLP && !ctx->mlp_ready) return QED_ERR_STATE;
     if (!ctx || !p || !field || nsteps < 0 || !(dt > 0.0) || step0 < 0 || step0 + nsteps > 0xFFFFFFFFll)
         return QED_ERR_INVALID;
     if (field->kind < QED_FIELD_UNIFORM || field->kind > QED_FIELD_STANDING_CP) return QED_ERR_INVALID;

@@ -1,0 +1,165 @@
+"""Surrogate network kernels against the FP64 oracle: forward pass, gradient
+of the loss (BF16 weights and activations, FP32 accumulation: tolerances
+state the BF16 rounding), and training on table draws."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2409_17299_gb300 as q  # noqa: E402
+
+
+def bf16_round(a):
+    """Round float32 values to bfloat16 (nearest even) and back."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    P = rng.normal(size=8577).astype(np.float32)
+    P[:128] *= 1.0
+    P[192:4288] *= 0.18
+    P[4352:8448] *= 0.18
+    P[8512:8576] *= 0.1
+    return P
+
+
+def test_forward_matches_oracle():
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    P = _params(0)
+    q.qed_mlp_set_params(g.ctx, P)
+    assert np.array_equal(q.qed_mlp_get_params(g.ctx), P)
+    rng = np.random.default_rng(1)
+    n = 1000
+    feat = rng.uniform(-1, 1, size=(n, 2)).astype(np.float32)
+    df = torch.from_numpy(feat).cuda()
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    q.qed_mlp_forward(g.ctx, df.data_ptr(), n, y.data_ptr())
+    got = y.cpu().numpy()
+    want = oracle.mlp_forward(bf16_round(P).astype(np.float64), feat.astype(np.float64))
+    # hidden activations are rounded to bf16 between layers (8 significant bits)
+    assert np.max(np.abs(got - want)) < 0.03 * max(1.0, np.abs(want).max())
+    assert np.corrcoef(got, want)[0, 1] > 0.9999
+    g.close()
+
+
+def test_gradient_matches_oracle():
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    P = _params(2)
+    q.qed_mlp_set_params(g.ctx, P)
+    rng = np.random.default_rng(3)
+    n = 512
+    feat = rng.uniform(-1, 1, size=(n, 2)).astype(np.float32)
+    tgt = rng.normal(size=n).astype(np.float32)
+    grad, loss = q.qed_mlp_grad(g.ctx, torch.from_numpy(feat).cuda().data_ptr(),
+                                torch.from_numpy(tgt).cuda().data_ptr(), n)
+    oloss, ograd = oracle.mlp_loss_grad(bf16_round(P).astype(np.float64), feat.astype(np.float64),
+                                        tgt.astype(np.float64))
+    assert loss == pytest.approx(oloss, rel=3e-2)
+    rel = np.linalg.norm(grad - ograd) / np.linalg.norm(ograd)
+    cos = grad @ ograd / (np.linalg.norm(grad) * np.linalg.norm(ograd))
+    assert rel < 5e-2 and cos > 0.998, (rel, cos)
+    # every parameter block carries gradient of the right size
+    for a, b in [(0, 128), (128, 192), (192, 4288), (4288, 4352), (4352, 8448), (8448, 8512), (8512, 8576), (8576, 8577)]:
+        r = np.linalg.norm(grad[a:b] - ograd[a:b]) / max(np.linalg.norm(ograd[a:b]), 1e-12)
+        assert r < 0.1, (a, b, r)
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def trained_params():
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    loss = q.qed_train_surrogate(g.ctx, n_samples=1 << 24, batch=65536, lr=2e-3, seed=7)
+    P = q.qed_mlp_get_params(g.ctx)
+    g.close()
+    assert np.all(np.isfinite(P))
+    return P, loss
+
+
+def _net_delta(ctx, chi, u):
+    feat = np.array([oracle.mlp_features(c, x) for c, x in zip(chi, u)], dtype=np.float32)
+    df = torch.from_numpy(feat).cuda()
+    y = torch.empty(len(u), dtype=torch.float32, device="cuda")
+    q.qed_mlp_forward(ctx, df.data_ptr(), len(u), y.data_ptr())
+    yy = y.cpu().numpy().astype(np.float64)
+    return np.array([oracle.mlp_delta(c, v)[0] for c, v in zip(chi, yy)])
+
+
+def test_trained_network_per_chi_ks(trained_params, otables):
+    """Per chi value: the network's photon fractions against the oracle's
+    table sampler on the same uniforms (two-sample KS, p > 0.01)."""
+    from scipy.stats import ks_2samp
+    P, loss = trained_params
+    assert loss < 2e-4, loss
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    q.qed_mlp_set_params(g.ctx, P)
+    rng = np.random.default_rng(8)
+    n = 20000
+    report = {}
+    for chi in [1e-3, 1e-2, 0.1, 1.0, 10.0, 100.0, 1e3]:
+        u = rng.random(n)
+        dn = _net_delta(g.ctx, np.full(n, chi), u)
+        dt = np.array([otables.sample_emission(chi, x)[0] for x in u])
+        p = ks_2samp(dn, dt).pvalue
+        report[chi] = (p, float(np.median(np.abs(dn / dt - 1))))
+        assert p > 0.01, (chi, report[chi])
+    g.close()
+
+
+def test_what_the_network_gains(trained_params, otables):
+    """The network replaces a 121 x 257 FP32 table (124 KB of shared memory per
+    block) by 8577 BF16 weights (17 KB); its distance to the exact spectrum is
+    measured beside the table's (Kolmogorov distance on a grid of delta)."""
+    P, _ = trained_params
+    table_bytes = 121 * 257 * 4
+    net_bytes = q.MLP_NPARAMS * 2
+    assert table_bytes / net_bytes > 7
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    q.qed_mlp_set_params(g.ctx, P)
+    rng = np.random.default_rng(9)
+    n = 20000
+    for chi in [0.01, 1.0, 100.0]:
+        u = rng.random(n)
+        dn = np.sort(_net_delta(g.ctx, np.full(n, chi), u))
+        dt = np.sort(np.array([otables.sample_emission(chi, x)[0] for x in u]))
+        grid = np.quantile(dt, np.linspace(0.01, 0.99, 30))
+        F = np.array([oracle.em_cdf(chi, x) for x in grid])
+        Dn = np.max(np.abs(np.searchsorted(dn, grid) / n - F))
+        Dt = np.max(np.abs(np.searchsorted(dt, grid) / n - F))
+        # both within the KS band of the exact spectrum at this sample size
+        assert Dn < 1.63 / np.sqrt(n) and Dt < 1.63 / np.sqrt(n), (chi, Dn, Dt)
+    g.close()
+
+
+def test_cascade_with_network_sampler(trained_params, otables):
+    """The rotating-field cascade with the network sampler: event counts and
+    spectra agree with the FP64 oracle's table run (statistically)."""
+    import math
+    from scipy.stats import ks_2samp
+    from paper_2409_17299_gb300 import workloads as W
+    P, _ = trained_params
+    w = W.rotating_e_cascade(n=3000, seed=1, periods=1)
+    cap = [100000, 100000, 300000]
+    g = q.Generator(q.make_config(precision=q.QED_FP32, seed=w.seed, push_photons=1, sampler=q.QED_SAMPLER_MLP))
+    q.qed_mlp_set_params(g.ctx, P)
+    ens = q.DeviceEnsemble.from_host(w.species, cap, q.QED_FP32)
+    st = g.push(ens, q.make_field(w.field_kind, w.field_prm), w.dt, 60, 0)
+    oe = oracle.Ensemble.from_arrays(w.species, cap)
+    ocfg = oracle.make_cfg(seed=w.seed, push_photons=1, field_kind=w.field_kind, field_prm=w.field_prm)
+    ost = oracle.push_and_generate(oe, otables, ocfg, w.dt, 60, 0)
+    for key in ("emit_events", "pair_events"):
+        assert abs(st[key] - ost[key]) < 6 * math.sqrt(ost[key]) + 10, key
+    ka = ens.to_host(2)
+    kb = oe.view(2)
+    ea = np.sqrt(ka["px"] ** 2 + ka["py"] ** 2 + ka["pz"] ** 2)
+    eb = np.sqrt(kb["px"] ** 2 + kb["py"] ** 2 + kb["pz"] ** 2)
+    assert ks_2samp(ea, eb).pvalue > 0.01
+    g.close()
