@@ -453,7 +453,7 @@ def main():
         tg = q.Generator(q.make_config(precision=q.QED_FP32))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        loss = q.qed_train_surrogate(tg.ctx, int(args.mlp_samples), 65536, 2e-3, 7)
+        loss = q.qed_train_surrogate(tg.ctx, int(args.mlp_samples), 8192, 4e-3, 7)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         P = q.qed_mlp_get_params(tg.ctx)

@@ -203,6 +203,52 @@ qed_status qed_mlp_forward(qed_ctx *ctx, const float *feat_dev, int64_t n, float
 qed_status qed_mlp_grad(qed_ctx *ctx, const float *feat_dev, const float *target_dev, int64_t n,
                         float *grad, double *loss);
 
+/* ---- leveling of one species split over several processes ------------
+ * Global leveling (Sec. 5.1) when a species is sharded across GPUs (one
+ * process each): the threshold w* solves sum_i min(1, w_i/w*) = cap over ALL
+ * shards, so each iteration needs the shards' sums added together (an
+ * all-reduce, done by the caller).  Protocol, identical on every rank:
+ *     qed_level_begin(&st);
+ *     while (!st.done) {
+ *         qed_level_eval(ctx, &my_species, s, st.w, &A, &C, &N, &M);
+ *         all-reduce: A, C, N summed, M maximum over the ranks;
+ *         qed_level_advance(&st, A, C, N, M, cap);
+ *     }
+ *     qed_level_apply(ctx, &my_particles, s, st.wstar, step);
+ * The iteration is the one a single GPU runs on the device (piecewise-exact
+ * Newton steps inside a bisection bracket), so every rank holds the same
+ * state after each advance.  Keep/drop draws are keyed on particle id and
+ * step, so the survivors do not depend on how the species is split. */
+typedef struct {
+    double lo, hi;      /* bracket of w*: S(lo) > cap >= S(hi) */
+    double w;           /* point to evaluate next (+inf before the first pass) */
+    double wstar;       /* threshold once done (0: the species fits, no thinning) */
+    int64_t iters;      /* passes taken */
+    int64_t done;       /* nonzero once wstar is final */
+    int64_t alive;      /* alive particles over all shards (set by the first pass) */
+} qed_level_state;
+
+/* Start an iteration (w = +inf, not done).  Host only. */
+void qed_level_begin(qed_level_state *st);
+
+/* Advance with the summed shard values at st->w: A = sum of alive weights
+ * below w, C = alive count at or above w, N = alive count, max_w = largest
+ * alive weight.  Host only (no GPU work).  QED_ERR_INVALID for negative
+ * inputs or cap <= 0. */
+qed_status qed_level_advance(qed_level_state *st, double A, int64_t C, int64_t N, double max_w, int64_t cap);
+
+/* This shard's sums at point w (w > 0, +inf allowed) for species `species`
+ * of the context's precision: one device pass over sp->w (caller-owned).
+ * Synchronises the context's stream. */
+qed_status qed_level_eval(qed_ctx *ctx, const qed_species *sp, int species, double w, double *A, int64_t *C,
+                          int64_t *N, double *max_w);
+
+/* Apply threshold wstar to species `species` of this shard at step index
+ * `step` (keep with probability min(1, w_i/wstar), survivors below wstar get
+ * wstar; wstar = 0: compaction only), then remove dead entries; count in *p
+ * is updated. */
+qed_status qed_level_apply(qed_ctx *ctx, qed_particles *p, int species, double wstar, int64_t step);
+
 /* Statistics accumulated since the context was created or last reset. */
 qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset);
 

@@ -23,7 +23,8 @@ QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP = 0, 1, 2
 EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_batch_push", "qed_autotune_batch", "qed_compact", "qed_get_stats", "qed_strerror",
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
             "qed_compact_species_noalloc", "qed_train_surrogate", "qed_mlp_set_params", "qed_mlp_get_params",
-            "qed_mlp_forward", "qed_mlp_grad")
+            "qed_mlp_forward", "qed_mlp_grad", "qed_level_begin", "qed_level_advance", "qed_level_eval",
+            "qed_level_apply")
 QED_NOALLOC_MAX_ENTRIES = 1 << 20
 
 
@@ -32,6 +33,11 @@ class QedConfig(C.Structure):
                 ("push_photons", C.c_int), ("soft_photon_filter", C.c_int), ("thin_cap", C.c_int64),
                 ("restore_on_overflow", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
                 ("profile", C.c_int), ("reserved", C.c_int * 5)]
+
+
+class QedLevelState(C.Structure):
+    _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("w", C.c_double), ("wstar", C.c_double),
+                ("iters", C.c_int64), ("done", C.c_int64), ("alive", C.c_int64)]
 
 
 class QedSpecies(C.Structure):
@@ -107,6 +113,11 @@ def lib():
         "qed_mlp_get_params": (i32, [p, p]),
         "qed_mlp_forward": (i32, [p, p, i64, p]),
         "qed_mlp_grad": (i32, [p, p, p, i64, p, C.POINTER(C.c_double)]),
+        "qed_level_begin": (None, [C.POINTER(QedLevelState)]),
+        "qed_level_advance": (i32, [C.POINTER(QedLevelState), C.c_double, i64, i64, C.c_double, i64]),
+        "qed_level_eval": (i32, [p, C.POINTER(QedSpecies), i32, C.c_double, C.POINTER(C.c_double),
+                                 C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_double)]),
+        "qed_level_apply": (i32, [p, p, i32, C.c_double, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -171,6 +182,62 @@ def qed_compact(ctx, particles: QedParticles, step: int) -> int:
     return rc
 
 
+def qed_level_begin() -> QedLevelState:
+    st = QedLevelState()
+    lib().qed_level_begin(C.byref(st))
+    return st
+
+
+def qed_level_advance(st: QedLevelState, A: float, C_: int, N: int, max_w: float, cap: int) -> None:
+    rc = lib().qed_level_advance(C.byref(st), float(A), int(C_), int(N), float(max_w), int(cap))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_level_advance")
+
+
+def qed_level_eval(ctx, species: QedSpecies, s: int, w: float):
+    """This shard's (A, C, N, max_w) at point w."""
+    A, Cc, N, M = C.c_double(), C.c_int64(), C.c_int64(), C.c_double()
+    rc = lib().qed_level_eval(ctx, C.byref(species), int(s), float(w), C.byref(A), C.byref(Cc), C.byref(N),
+                              C.byref(M))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_level_eval")
+    return A.value, Cc.value, N.value, M.value
+
+
+def qed_level_apply(ctx, particles: QedParticles, s: int, wstar: float, step: int) -> None:
+    rc = lib().qed_level_apply(ctx, C.byref(particles), int(s), float(wstar), int(step))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_level_apply")
+
+
+def level_threshold_sharded(evaluate, allreduce, cap: int) -> QedLevelState:
+    """Global leveling threshold of a species split over ranks.  evaluate(w)
+    returns this rank's (A, C, N, max_w) at w; allreduce(values) returns
+    them combined over all ranks (A, C, N summed, max_w maximum).  The
+    iteration itself is the library's (qed_level_advance)."""
+    st = qed_level_begin()
+    while not st.done:
+        qed_level_advance(st, *allreduce(evaluate(st.w)), cap)
+    return st
+
+
+def torch_allreduce(group=None):
+    """An allreduce for level_threshold_sharded over a torch.distributed group."""
+    import torch
+    import torch.distributed as dist
+
+    def reduce(v):
+        A, Cc, N, M = v
+        s = torch.tensor([A], dtype=torch.float64)
+        c = torch.tensor([Cc, N], dtype=torch.int64)
+        m = torch.tensor([M], dtype=torch.float64)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX, group=group)
+        return float(s[0]), int(c[0]), int(c[1]), float(m[0])
+    return reduce
+
+
 def qed_get_stats(ctx, reset: bool = False) -> dict:
     st = QedStats()
     rc = lib().qed_get_stats(ctx, C.byref(st), int(reset))
@@ -225,7 +292,7 @@ def qed_sample(ctx, is_photon: bool, chi_dev_ptr: int, u_dev_ptr: int, n: int, d
 MLP_NPARAMS = 8577
 
 
-def qed_train_surrogate(ctx, n_samples: int, batch: int = 65536, lr: float = 2e-3, seed: int = 12345) -> float:
+def qed_train_surrogate(ctx, n_samples: int, batch: int = 8192, lr: float = 4e-3, seed: int = 12345) -> float:
     loss = C.c_double(0.0)
     rc = lib().qed_train_surrogate(ctx, int(n_samples), int(batch), float(lr), C.c_uint64(seed), C.byref(loss))
     if rc != QED_OK:
@@ -413,6 +480,15 @@ class Generator:
         P = ens.struct()
         qed_compact(self.ctx, P, step)
         ens.pull_counts(P)
+
+    def level_sharded(self, ens: DeviceEnsemble, s: int, step: int, cap: int, allreduce) -> float:
+        """Global leveling of species s when it is split over ranks (each rank
+        calls this with its own shard; allreduce combines the shard sums)."""
+        st = level_threshold_sharded(lambda w: qed_level_eval(self.ctx, ens.struct().s[s], s, w), allreduce, cap)
+        arr = ens.struct()
+        qed_level_apply(self.ctx, arr, s, st.wstar, step)
+        ens.pull_counts(arr)
+        return st.wstar
 
     def close(self):
         if self.ctx:

@@ -114,6 +114,53 @@ extern "C" qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step) 
     return QED_OK;
 }
 
+extern "C" void qed_level_begin(qed_level_state *st) {
+    if (!st) return;
+    memset(st, 0, sizeof *st);
+    st->hi = INFINITY;
+    st->w = INFINITY;
+}
+
+extern "C" qed_status qed_level_advance(qed_level_state *st, double A, int64_t C, int64_t N, double max_w,
+                                        int64_t cap) {
+    if (!st || cap <= 0 || C < 0 || N < 0 || !(A >= 0.0) || !(max_w >= 0.0)) return QED_ERR_INVALID;
+    if (st->done) return QED_OK;
+    sfq_level_advance(&st->lo, &st->hi, &st->w, &st->wstar, &st->iters, &st->done, &st->alive, A, C, N, max_w, cap);
+    return QED_OK;
+}
+
+extern "C" qed_status qed_level_eval(qed_ctx *ctx, const qed_species *sp, int species, double w, double *A,
+                                     int64_t *C, int64_t *N, double *max_w) {
+    if (!ctx || !sp || !A || !C || !N || !max_w || species < 0 || species > 2 || !(w > 0.0)) return QED_ERR_INVALID;
+    if (sp->count < 0 || sp->count > sp->capacity || (sp->count > 0 && !sp->w)) return QED_ERR_INVALID;
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    qed_species copy = *sp;
+    return sfq_level_eval(ctx, &copy, species, w, A, C, N, max_w);
+}
+
+extern "C" qed_status qed_level_apply(qed_ctx *ctx, qed_particles *p, int species, double wstar, int64_t step) {
+    if (!ctx || !p || species < 0 || species > 2 || !(wstar >= 0.0) || step < 0 || step > 0xFFFFFFFFll)
+        return QED_ERR_INVALID;
+    for (int s = 0; s < 3; ++s)
+        if (p->s[s].count < 0 || p->s[s].count > p->s[s].capacity) return QED_ERR_INVALID;
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    DevCtl &h = *ctx->ctl_host;                 // pinned staging
+    memset(&h, 0, sizeof(DevCtl));
+    for (int s = 0; s < 3; ++s) {
+        h.count[s] = (unsigned long long)p->s[s].count;
+        h.capacity[s] = (unsigned long long)p->s[s].capacity;
+    }
+    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl, &h, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
+    qed_status e = sfq_level_apply_species(ctx, &p->s[species], species, wstar, step);
+    if (e != QED_OK) return e;
+    SFQ_CUDA(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ctl_host->bad_index) return QED_ERR_STATE;
+    p->s[species].count = (int64_t)ctx->ctl_host->count[species];
+    ctx->acc.thinned += (int64_t)ctx->ctl_host->thinned;
+    return QED_OK;
+}
+
 extern "C" qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset) {
     if (!ctx || !out) return QED_ERR_INVALID;
     *out = ctx->acc;

@@ -197,9 +197,24 @@ __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned
 constexpr int LEVEL_ITERS = 40;
 
 // smallest float >= a positive double (v < d <=> v < ceil_f(d) for floats v)
-__device__ __forceinline__ float ceil_f(double d) {
-    float f = __double2float_ru(d);
+__host__ __device__ __forceinline__ float ceil_f(double d) {
+#ifdef __CUDA_ARCH__
+    return __double2float_ru(d);
+#else
+    float f = (float)d;
+    if ((double)f < d) f = nextafterf(f, INFINITY);
     return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ double double_of_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+#endif
 }
 
 __global__ void k_lev_begin(LevelWork *lw, int s) {
@@ -209,9 +224,12 @@ __global__ void k_lev_begin(LevelWork *lw, int s) {
     it.w = it.hi;
     it.w_up = __int_as_float(0x7f800000);
     it.wstar = 0.0;
+    it.wstar_inv_f = 0.f;
     it.done = 0;
     it.iters = 0;
     it.alive = 0;
+    it.mode = 0;
+    lw->arrive[s] = 0;
 }
 
 // error-free float-float accumulation (TwoSum), accurate to ~2^-48 relative
@@ -226,35 +244,108 @@ struct FF {
     }
 };
 
+// double-double accumulation (TwoSum) for the reduction of block partials
+struct DD {
+    double hi = 0.0, lo = 0.0;
+    __device__ __forceinline__ void add(double b) {
+        const double t = hi + b;
+        const double bp = t - hi;
+        lo += (hi - (t - bp)) + (b - bp);
+        hi = t;
+    }
+};
+
+__host__ __device__ __forceinline__ void lev_finish(LevelIter &it, double wstar) {
+    it.done = 1;
+    it.wstar = wstar;
+    it.wstar_up = wstar > 0.0 ? ceil_f(wstar) : 0.f;
+    it.wstar_f = (float)wstar;
+    it.wstar_inv_f = wstar > 0.0 ? (float)(1.0 / wstar) : 0.f;
+}
+
+// Newton step from the sums at it.w: A (weights below w), C (count at or
+// above w), N (alive count), M (largest weight, double bits)
+__host__ __device__ void lev_advance(LevelIter &it, double A, unsigned long long C, unsigned long long N,
+                                     unsigned long long M, long long cap) {
+    const double inf = double_of_bits(0x7ff0000000000000ull);
+    const double w = it.w;
+    if (it.iters == 0) {                           // first pass: w = +inf, all alive weights below it
+        it.alive = N;
+        if (N <= (unsigned long long)cap) { lev_finish(it, 0.0); return; }
+        it.hi = double_of_bits(M) * (double)N / (double)cap;                    // S(hi) <= cap
+        it.lo = 0.0;
+    } else {
+        const double S = A / w + (double)C;
+        if (S > (double)cap) it.lo = w; else it.hi = w;
+    }
+    ++it.iters;
+    double c = (double)cap > (double)C ? A / ((double)cap - (double)C) : inf;
+    if (c == w) { lev_finish(it, w); return; }     // root of its own piece
+    if (!(c > it.lo && c <= it.hi)) c = 0.5 * (it.lo + it.hi);
+    // stop at double resolution of the bracket (hi, evaluated, is the answer)
+    if (!(c > it.lo && c <= it.hi) || (c == it.hi && it.hi == w) || it.iters >= LEVEL_ITERS) {
+        lev_finish(it, it.hi);
+        return;
+    }
+    it.w = c;
+    it.w_up = ceil_f(c);
+}
+
+// One pass of the iteration.  Every block sums its share of the weights at
+// it.w; the last block to finish reduces the block partials in block order
+// (a fixed order: the result does not depend on which block is last) and
+// advances the iteration, so a pass is one launch and needs no host.
+constexpr int LEV_T = 256;
 template <class T>
-__global__ void __launch_bounds__(256) k_lev_eval(const void *w, const DevCtl *ctl, int s, LevelWork *lw) {
-    const LevelIter &it = lw->it[s];
-    if (it.done) return;
+__global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl *ctl, int s, LevelWork *lw,
+                                                    long long cap) {
+    LevelIter &it = lw->it[s];
+    if (*reinterpret_cast<volatile unsigned long long *>(&it.done)) return;
     const unsigned long long n = ctl->count[s];
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * LEV_T + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * LEV_T;
     double A;
     unsigned long long C = 0, N = 0, M = 0;
     if constexpr (sizeof(T) == 4) {
         // FP32 weights: exact float comparisons and float-float sums, no FP64 per element
         const float wc = it.w_up;
         FF acc;
-        unsigned mb = 0;
-        for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-             i += (unsigned long long)gridDim.x * blockDim.x) {
-            const float v = reinterpret_cast<const float *>(w)[i];
-            if (!(v > 0.f)) continue;
-            ++N;
-            mb = max(mb, __float_as_uint(v));
-            if (v < wc) acc.add(v);
-            else ++C;
+        unsigned mb = 0, c = 0, nn = 0;
+        auto one = [&](float v) {
+            if (v > 0.f) {
+                ++nn;
+                mb = max(mb, __float_as_uint(v));
+                if (v < wc) acc.add(v);
+                else ++c;
+            }
+        };
+        const float *wf = reinterpret_cast<const float *>(w);
+        unsigned long long i0 = 0;
+        if ((reinterpret_cast<uintptr_t>(wf) & 15u) == 0) {
+            const float4 *w4 = reinterpret_cast<const float4 *>(wf);
+            const unsigned long long n4 = n / 4;
+            unsigned long long j = t0;
+            for (; j + stride < n4; j += 2 * stride) {          // two 16-byte loads in flight
+                const float4 a = w4[j], b = w4[j + stride];
+                one(a.x); one(a.y); one(a.z); one(a.w);
+                one(b.x); one(b.y); one(b.z); one(b.w);
+            }
+            if (j < n4) {
+                const float4 a = w4[j];
+                one(a.x); one(a.y); one(a.z); one(a.w);
+            }
+            i0 = n4 * 4;
         }
+        for (unsigned long long i = i0 + t0; i < n; i += stride) one(wf[i]);
         A = (double)acc.hi + (double)acc.lo;
-        M = N ? dbits((double)__uint_as_float(mb)) : 0ull;
+        C = c;
+        N = nn;
+        M = nn ? dbits((double)__uint_as_float(mb)) : 0ull;
     } else {
         const double wc = it.w;
         double comp = 0.0;           // Kahan
         A = 0.0;
-        for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-             i += (unsigned long long)gridDim.x * blockDim.x) {
+        for (unsigned long long i = t0; i < n; i += stride) {
             const double v = (double)ld<T>(w, i);
             if (!(v > 0.0)) continue;
             ++N;
@@ -269,8 +360,9 @@ __global__ void __launch_bounds__(256) k_lev_eval(const void *w, const DevCtl *c
             }
         }
     }
-    __shared__ double sA[8];
-    __shared__ unsigned long long sC[8], sN[8], sM[8];
+    __shared__ double sA[LEV_T / 32];
+    __shared__ unsigned long long sC[LEV_T / 32], sN[LEV_T / 32], sM[LEV_T / 32];
+    __shared__ int s_last;
     for (int o = 16; o > 0; o >>= 1) {
         A += __shfl_down_sync(0xffffffffu, A, o);
         C += __shfl_down_sync(0xffffffffu, C, o);
@@ -283,128 +375,327 @@ __global__ void __launch_bounds__(256) k_lev_eval(const void *w, const DevCtl *c
     if (threadIdx.x == 0) {
         double a = 0.0;
         unsigned long long c = 0, nn = 0, m = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sA[k]; c += sC[k]; nn += sN[k]; m = max(m, sM[k]); }
+        for (int k = 0; k < LEV_T / 32; ++k) { a += sA[k]; c += sC[k]; nn += sN[k]; m = max(m, sM[k]); }
         lw->partA[blockIdx.x] = a;
         lw->partC[blockIdx.x] = c;
         lw->partN[blockIdx.x] = nn;
         lw->partM[blockIdx.x] = m;
+        __threadfence();
+        const unsigned prev = atomicAdd(&lw->arrive[s], 1u);
+        s_last = prev == gridDim.x - 1;
     }
-}
-
-__global__ void k_lev_next(LevelWork *lw, int s, int nblocks, long long cap) {
-    if (threadIdx.x != 0) return;
-    LevelIter &it = lw->it[s];
-    if (it.done) return;
-    double A = 0.0, comp = 0.0;
-    unsigned long long C = 0, N = 0, M = 0;
-    for (int b = 0; b < nblocks; ++b) {            // fixed order
-        const double y = lw->partA[b] - comp;
-        const double t = A + y;
-        comp = (t - A) - y;
-        A = t;
-        C += lw->partC[b];
-        N += lw->partN[b];
-        M = max(M, lw->partM[b]);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last block: partials b = t, t + LEV_T, ... per thread, then a tree of fixed shape
+    __shared__ double rh[LEV_T], rl[LEV_T];
+    __shared__ unsigned long long rc[LEV_T], rn[LEV_T], rm[LEV_T];
+    const int t = threadIdx.x;
+    DD acc;
+    unsigned long long c = 0, nn = 0, m = 0;
+    for (int b = t; b < (int)gridDim.x; b += LEV_T) {
+        acc.add(__ldcg(&lw->partA[b]));
+        c += __ldcg(&lw->partC[b]);
+        nn += __ldcg(&lw->partN[b]);
+        m = max(m, __ldcg(&lw->partM[b]));
     }
-    const double inf = __longlong_as_double(0x7ff0000000000000ll);
-    const double w = it.w;
-    if (it.iters == 0) {                           // first pass: w = +inf, all alive weights below it
-        it.alive = N;
-        if (N <= (unsigned long long)cap) { it.done = 1; it.wstar = 0.0; it.wstar_up = 0.f; it.wstar_f = 0.f; return; }
-        it.hi = __longlong_as_double((long long)M) * (double)N / (double)cap;   // S(hi) <= cap
-        it.lo = 0.0;
-    } else {
-        const double S = A / w + (double)C;
-        if (S > (double)cap) it.lo = w; else it.hi = w;
-    }
-    ++it.iters;
-    double c = (double)cap > (double)C ? A / ((double)cap - (double)C) : inf;
-    if (c == w) {                                          // root of its own piece
-        it.done = 1;
-        it.wstar = w;
-        it.wstar_up = ceil_f(w);
-        it.wstar_f = (float)w;
-        return;
-    }
-    if (!(c > it.lo && c <= it.hi)) c = 0.5 * (it.lo + it.hi);
-    // stop at double resolution of the bracket (hi, evaluated, is the answer)
-    if (!(c > it.lo && c <= it.hi) || (c == it.hi && it.hi == w) || it.iters >= LEVEL_ITERS) {
-        it.done = 1;
-        it.wstar = it.hi;
-        it.wstar_up = ceil_f(it.hi);
-        it.wstar_f = (float)it.hi;
-        return;
-    }
-    it.w = c;
-    it.w_up = ceil_f(c);
-}
-
-// keep particle i (0 < w_i < w*) with probability w_i / w*: the comparison
-// u < w_i / w* is made in FP32 with a relative margin, and in FP64 (the
-// oracle's test) only for draws within that margin of the boundary
-template <class T>
-__global__ void __launch_bounds__(256) k_lev_apply(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw,
-                                                   uint64_t seed, unsigned step) {
-    const LevelIter &it = lw->it[s];
-    const double wstar = it.wstar;
-    if (!it.done || !(wstar > 0.0)) return;
-    const float inv_f = (float)(1.0 / wstar);
-    const float wup = it.wstar_up, wnew = it.wstar_f;
-    const unsigned long long n = ctl->count[s];
-    unsigned long long removed = 0;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const T v = ld<T>(S.w, i);
-        bool below;
-        if constexpr (sizeof(T) == 4) below = v > 0.f && v < wup;     // v < w* exactly
-        else below = v > 0.0 && v < wstar;
-        if (!below) continue;
-        const uint4 r = event_draw(seed, S.id[i], step, 0xFFFFFFFFu);
-        const float uf = __uint2float_rn(r.x) * 0x1p-32f;        // u to within 2^-32 + FP32 rounding
-        const float pf = (float)v * inv_f;
-        bool keep;
-        if (uf < pf * (1.0f - 1e-6f) - 0x1p-31f) keep = true;
-        else if (uf > pf * (1.0f + 1e-6f) + 0x1p-31f) keep = false;
-        else {
-            double u, vv;
-            Uniform<double>::draw(r.x, r.y, u, vv);
-            keep = u < (double)v / wstar;
+    rh[t] = acc.hi; rl[t] = acc.lo; rc[t] = c; rn[t] = nn; rm[t] = m;
+    __syncthreads();
+    for (int o = LEV_T / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            DD x;
+            x.hi = rh[t];
+            x.lo = rl[t];
+            x.add(rh[t + o]);
+            x.lo += rl[t + o];
+            rh[t] = x.hi;
+            rl[t] = x.lo;
+            rc[t] += rc[t + o];
+            rn[t] += rn[t + o];
+            rm[t] = max(rm[t], rm[t + o]);
         }
-        if constexpr (sizeof(T) == 4) {
-            if (keep) st<T>(S.w, i, wnew);
-            else { st<T>(S.w, i, 0.f); ++removed; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (it.mode == 1) {         // sums only: the caller combines them across shards
+            it.sumA = rh[0] + rl[0];
+            it.sumC = rc[0];
+            it.sumN = rn[0];
+            it.sumM = rm[0];
         } else {
-            if (keep) st<T>(S.w, i, wstar);
-            else { st<T>(S.w, i, 0.0); ++removed; }
+            lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap);
         }
+        lw->arrive[s] = 0;
     }
-    for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
-    if ((threadIdx.x & 31) == 0 && removed) atomicAdd(&ctl->thinned, removed);
 }
 
+// ---- compaction by tiles (used after leveling and for converted photons) ----
+// A tile of 4096 entries is one block of 256 threads; warp k owns entries
+// [512 k, 512 k + 512) of the tile, 32 per round (coalesced).  Pass 1 lists
+// the dead entries of each tile in index order (16-bit tile offsets) and
+// counts the alive ones; a scan gives A (alive total) and H (dead entries
+// below A); pass 2 lists the alive entries at or above A (the movers) by
+// rank; pass 3 moves mover r into the r-th dead slot below A.
+constexpr int LT = 256;
+constexpr int LROUNDS = 16;
+constexpr int LTILE = LT * LROUNDS;       // entries per tile (offsets fit 16 bits)
+constexpr int LSPAN = 32 * LROUNDS;       // contiguous entries per warp
+
+// Pass 1.  LEVEL: first keep particle i (0 < w_i < w*) with probability
+// w_i / w*: the comparison u < w_i / w* is made in FP32 with a relative
+// margin, and in FP64 (the oracle's test) only for draws within that margin
+// of the boundary; kept particles get weight w*.
+template <class T, bool LEVEL>
+__global__ void __launch_bounds__(LT) k_tile_dead(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw,
+                                                  uint64_t seed, unsigned step, unsigned long long *blk,
+                                                  unsigned short *dl) {
+    __shared__ unsigned wdead[LT / 32];
+    const unsigned long long n = ctl->count[s];
+    const unsigned long long base = (unsigned long long)blockIdx.x * LTILE;
+    if (base >= n) {
+        if (threadIdx.x == 0) blk[blockIdx.x] = 0;
+        return;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long wbase = base + (unsigned long long)wid * LSPAN;
+    bool thin = false;
+    double wstar = 0.0;
+    float inv_f = 0.f, wup = 0.f, wnew = 0.f;
+    if constexpr (LEVEL) {
+        const LevelIter &it = lw->it[s];
+        wstar = it.wstar;
+        thin = it.done && wstar > 0.0;
+        inv_f = it.wstar_inv_f;
+        wup = it.wstar_up;
+        wnew = it.wstar_f;
+    }
+    unsigned mask[LROUNDS];
+    unsigned cnt = 0, removed = 0;
+#pragma unroll
+    for (int c0 = 0; c0 < LROUNDS; c0 += 8) {
+        T v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const unsigned long long i = wbase + (c0 + r) * 32 + lane;
+            v[r] = i < n ? ld<T>(S.w, i) : (T)0;
+        }
+        unsigned long long idv[8];
+        bool below[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const unsigned long long i = wbase + (c0 + r) * 32 + lane;
+            if constexpr (sizeof(T) == 4) below[r] = LEVEL && thin && v[r] > (T)0 && (float)v[r] < wup;
+            else below[r] = LEVEL && thin && v[r] > (T)0 && (double)v[r] < wstar;
+            idv[r] = below[r] ? S.id[i] : 0ull;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const unsigned long long i = wbase + (c0 + r) * 32 + lane;
+            bool dead = i < n && !(v[r] > (T)0);
+            if (LEVEL && below[r]) {
+                const uint4 q = event_draw(seed, idv[r], step, 0xFFFFFFFFu);
+                const float uf = __uint2float_rn(q.x) * 0x1p-32f;     // u to within 2^-32 + FP32 rounding
+                const float pf = (float)v[r] * inv_f;
+                bool keep;
+                if (uf < pf * (1.0f - 1e-6f) - 0x1p-31f) keep = true;
+                else if (uf > pf * (1.0f + 1e-6f) + 0x1p-31f) keep = false;
+                else {
+                    double u, vv;
+                    Uniform<double>::draw(q.x, q.y, u, vv);
+                    keep = u < (double)v[r] / wstar;
+                }
+                if (keep) {
+                    if constexpr (sizeof(T) == 4) st<T>(S.w, i, wnew);
+                    else st<T>(S.w, i, wstar);
+                } else {
+                    st<T>(S.w, i, (T)0);
+                    dead = true;
+                    ++removed;
+                }
+            }
+            mask[c0 + r] = __ballot_sync(0xffffffffu, dead);
+            cnt += __popc(mask[c0 + r]);
+        }
+    }
+    if (lane == 0) wdead[wid] = cnt;
+    __syncthreads();
+    unsigned before = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < LT / 32; ++k) {
+        const unsigned c = wdead[k];
+        before += k < wid ? c : 0u;
+        total += c;
+    }
+    unsigned short *tdl = dl + base;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned run = before;
+#pragma unroll
+    for (int r = 0; r < LROUNDS; ++r) {
+        if ((mask[r] >> lane) & 1u) tdl[run + __popc(mask[r] & lt)] = (unsigned short)(wid * LSPAN + r * 32 + lane);
+        run += __popc(mask[r]);
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long tn = n - base < (unsigned long long)LTILE ? n - base : (unsigned long long)LTILE;
+        blk[blockIdx.x] = tn - total;
+    }
+    if constexpr (LEVEL) {
+        for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
+        if (lane == 0 && removed) atomicAdd(&ctl->thinned, (unsigned long long)removed);
+    }
+}
+
+// single block: exclusive scan of the tile counts (blk[nb] = A), then H from
+// the alive entries of the tile that holds A
 template <class T>
-qed_status compact_impl(qed_ctx *ctx, qed_species *sp, int s) {
+__global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long nb, DevCtl *ctl, int s) {
+    __shared__ unsigned long long sw[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (long long b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        const unsigned long long v = i < nb ? blk[i] : 0ull;
+        unsigned long long x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sw[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long t = lane < nw ? sw[lane] : 0ull;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            sw[lane] = t;
+        }
+        __syncthreads();
+        const unsigned long long before = carry + (wid > 0 ? sw[wid - 1] : 0ull) + x - v;
+        if (i < nb) blk[i] = before;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += sw[nw - 1];
+        __syncthreads();
+    }
+    const unsigned long long A = carry;
+    const unsigned long long a = A / LTILE;
+    unsigned long long below = A;                   // A on a tile boundary past the data: no holes
+    if ((long long)a < nb) {
+        unsigned c = 0;
+        for (unsigned long long i = a * LTILE + threadIdx.x; i < A; i += blockDim.x) c += alive_at<T>(w, i) ? 1u : 0u;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        __syncthreads();
+        if (lane == 0) sw[wid] = c;
+        __syncthreads();
+        unsigned long long tc = 0;
+        for (int k = 0; k < nw; ++k) tc += sw[k];
+        below = blk[a] + tc;
+    }
+    if (threadIdx.x == 0) {
+        blk[nb] = A;
+        ctl->alive[s] = A;
+        ctl->holes[s] = A - below;
+    }
+}
+
+// pass 2: movers (alive entries at or above A) by rank
+template <class T>
+__global__ void __launch_bounds__(LT) k_tile_movers(const void *w, DevCtl *ctl, int s, const unsigned long long *blk,
+                                                    unsigned long long *movers) {
+    __shared__ unsigned walive[LT / 32];
+    const unsigned long long n = ctl->count[s], A = ctl->alive[s], H = ctl->holes[s];
+    const unsigned long long base = (unsigned long long)blockIdx.x * LTILE;
+    if (H == 0 || base + LTILE <= A || base >= n) return;
+    const unsigned long long below_A = A - H;      // alive entries below A
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long wbase = base + (unsigned long long)wid * LSPAN;
+    unsigned amask[LROUNDS];
+    unsigned cnt = 0;
+#pragma unroll
+    for (int r = 0; r < LROUNDS; ++r) {
+        const unsigned long long i = wbase + r * 32 + lane;
+        amask[r] = __ballot_sync(0xffffffffu, i < n && alive_at<T>(w, i));
+        cnt += __popc(amask[r]);
+    }
+    if (lane == 0) walive[wid] = cnt;
+    __syncthreads();
+    unsigned before = 0;
+    for (int k = 0; k < wid; ++k) before += walive[k];
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long run = blk[blockIdx.x] + before;   // alive entries before this warp's span
+#pragma unroll
+    for (int r = 0; r < LROUNDS; ++r) {
+        const unsigned long long i = wbase + r * 32 + lane;
+        if (((amask[r] >> lane) & 1u) && i >= A) {
+            const unsigned long long ab = run + __popc(amask[r] & lt);
+            const unsigned long long rank = ab - below_A;
+            if (ab >= below_A && rank < H) movers[rank] = i;
+            else atomicExch(&ctl->bad_index, i + 1);
+        }
+        run += __popc(amask[r]);
+    }
+}
+
+// pass 3: the k-th dead entry of tile b has rank (dead entries before the
+// tile) + k; dead entries below A receive the mover of their rank
+template <class T>
+__global__ void __launch_bounds__(LT) k_tile_fill(SpeciesDev S, DevCtl *ctl, int s, const unsigned long long *blk,
+                                                  const unsigned short *dl, const unsigned long long *movers) {
+    const unsigned long long n = ctl->count[s], A = ctl->alive[s], H = ctl->holes[s];
+    const unsigned long long base = (unsigned long long)blockIdx.x * LTILE;
+    if (H == 0 || base >= A) return;
+    const unsigned long long tn = n - base < (unsigned long long)LTILE ? n - base : (unsigned long long)LTILE;
+    const unsigned long long alive_t = blk[blockIdx.x + 1] - blk[blockIdx.x];
+    const unsigned dead_t = (unsigned)(tn - alive_t);
+    const unsigned long long dead_before = base - blk[blockIdx.x];
+    const unsigned short *tdl = dl + base;
+    for (unsigned k = threadIdx.x; k < dead_t; k += LT) {
+        const unsigned long long i = base + tdl[k];
+        if (i >= A) break;                      // offsets ascend: the rest lie at or above A too
+        const unsigned long long r = dead_before + k;
+        if (r < H) {
+            const unsigned long long src = movers[r];
+            if (src >= A && src < n) move_entry<T>(S, i, src);
+            else atomicExch(&ctl->bad_index, i + 1);
+        } else {
+            atomicExch(&ctl->bad_index, i + 1);
+        }
+    }
+}
+
+template <class T, bool LEVEL>
+qed_status compact_tiles(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     const int64_t n = sp->count;   // upper bound; kernels read the device count
     if (n <= 0) return QED_OK;
-    const int64_t nb = (n + CTILE - 1) / CTILE;
+    const int64_t nb = (n + LTILE - 1) / LTILE;
     qed_status e = sfq_ensure_work(ctx, nb + 1, n);
     if (e != QED_OK) return e;
     SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
                  reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
+    // slots: n 16-bit dead-list entries, then at most n/2 mover indices
+    unsigned short *dl = reinterpret_cast<unsigned short *>(ctx->slots);
+    unsigned long long *movers = ctx->slots + (n + 3) / 4;
     cudaStream_t st = ctx->stream;
-    k_count_alive<T><<<(unsigned)nb, CT, 0, st>>>(sp->w, ctx->ctl, s, ctx->blk);
-    k_scan_blocks<<<1, 1024, 0, st>>>(ctx->blk, nb, ctx->ctl, s);
-    k_mark_holes<T><<<(unsigned)nb, CT, 0, st>>>(sp->w, ctx->ctl, s, ctx->blk, ctx->slots);
-    k_fill_holes<T><<<(unsigned)nb, CT, 0, st>>>(S, ctx->ctl, s, ctx->blk, ctx->slots);
+    k_tile_dead<T, LEVEL><<<(unsigned)nb, LT, 0, st>>>(S, ctx->ctl, s, ctx->lev, ctx->cfg.seed, (unsigned)step,
+                                                       ctx->blk, dl);
+    k_scan_tiles<T><<<1, 1024, 0, st>>>(sp->w, ctx->blk, nb, ctx->ctl, s);
+    k_tile_movers<T><<<(unsigned)nb, LT, 0, st>>>(sp->w, ctx->ctl, s, ctx->blk, movers);
+    k_tile_fill<T><<<(unsigned)nb, LT, 0, st>>>(S, ctx->ctl, s, ctx->blk, dl, movers);
     k_set_count<<<1, 1, 0, st>>>(ctx->ctl, s);
     SFQ_LAUNCHED(ctx, 5);
     SFQ_CUDA(cudaGetLastError());
     return QED_OK;
 }
 
-// Leveling of one species at `step`: the iteration runs on the device (a
-// fixed number of early-exit launches, no host round trip), then keep/drop
-// and compaction.  sp->count must bound the device count from above.
+template <class T>
+qed_status compact_impl(qed_ctx *ctx, qed_species *sp, int s) {
+    return compact_tiles<T, false>(ctx, sp, s, 0);
+}
+
+// Leveling of one species at `step`: the iteration runs on the device (one
+// launch per pass, no host round trip inside a chunk), then keep/drop fused
+// with the first compaction pass.  sp->count must bound the device count.
 template <class T>
 qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     const int64_t cap = ctx->cfg.thin_cap;
@@ -412,18 +703,13 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     if (cap <= 0 || sp->count <= cap) return QED_OK;
     int blocks = ctx->sm_count * 4;
     blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
-    SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
-                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
     k_lev_begin<<<1, 1, 0, st>>>(ctx->lev, s);
     SFQ_LAUNCHED(ctx, 1);
-    // iterations in chunks of three; the host reads the done flag between chunks
-    // (two to five passes are typical)
+    // passes in chunks of three (a pass after convergence returns at once);
+    // the host reads the done flag between chunks (two to five passes are typical)
     for (int it = 0; it < LEVEL_ITERS; it += 3) {
-        for (int c = 0; c < 3; ++c) {
-            k_lev_eval<T><<<blocks, 256, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev);
-            k_lev_next<<<1, 32, 0, st>>>(ctx->lev, s, blocks, (long long)cap);
-        }
-        SFQ_LAUNCHED(ctx, 6);
+        for (int c = 0; c < 3; ++c) k_lev_step<T><<<blocks, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
+        SFQ_LAUNCHED(ctx, 3);
         SFQ_CUDA(cudaMemcpyAsync(ctx->pin, &ctx->lev->it[s].done, sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, st));
         const auto t0 = std::chrono::steady_clock::now();
@@ -431,10 +717,51 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
         ctx->sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (ctx->pin[0]) break;
     }
-    k_lev_apply<T><<<blocks, 256, 0, st>>>(S, ctx->ctl, s, ctx->lev, ctx->cfg.seed, (unsigned)step);
-    SFQ_LAUNCHED(ctx, 1);
     SFQ_CUDA(cudaGetLastError());
-    return compact_impl<T>(ctx, sp, s);
+    return compact_tiles<T, true>(ctx, sp, s, step);
+}
+
+// ---- leveling over shards (one species split across processes) ----
+// The threshold is a property of all shards together: each shard evaluates
+// its sums at the current point (level_eval), the caller adds them over the
+// shards (an all-reduce) and advances the iteration with the same step the
+// device uses (sfq_level_advance), then each shard applies w* (level_apply).
+template <class T>
+qed_status level_eval_impl(qed_ctx *ctx, qed_species *sp, int s, double w, double *A, int64_t *C, int64_t *N,
+                           double *M) {
+    cudaStream_t st = ctx->stream;
+    int blocks = ctx->sm_count * 4;
+    blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
+    LevelIter h{};
+    h.w = w;
+    h.w_up = ceil_f(w);
+    h.iters = 1;
+    h.mode = 1;
+    const unsigned long long n = (unsigned long long)sp->count;
+    const unsigned zero = 0;
+    SFQ_CUDA(cudaMemcpyAsync(&ctx->ctl->count[s], &n, sizeof n, cudaMemcpyHostToDevice, st));
+    SFQ_CUDA(cudaMemcpyAsync(&ctx->lev->it[s], &h, sizeof h, cudaMemcpyHostToDevice, st));
+    SFQ_CUDA(cudaMemcpyAsync(&ctx->lev->arrive[s], &zero, sizeof zero, cudaMemcpyHostToDevice, st));
+    if (n > 0) {
+        k_lev_step<T><<<blocks, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, 0);
+        SFQ_LAUNCHED(ctx, 1);
+    }
+    SFQ_CUDA(cudaGetLastError());
+    SFQ_CUDA(cudaMemcpyAsync(&h, &ctx->lev->it[s], sizeof h, cudaMemcpyDeviceToHost, st));
+    SFQ_CUDA(cudaStreamSynchronize(st));
+    *A = n > 0 ? h.sumA : 0.0;
+    *C = n > 0 ? (int64_t)h.sumC : 0;
+    *N = n > 0 ? (int64_t)h.sumN : 0;
+    *M = n > 0 ? double_of_bits(h.sumM) : 0.0;
+    return QED_OK;
+}
+
+template <class T>
+qed_status level_apply_impl(qed_ctx *ctx, qed_species *sp, int s, double wstar, int64_t step) {
+    LevelIter h{};
+    lev_finish(h, wstar > 0.0 ? wstar : 0.0);
+    SFQ_CUDA(cudaMemcpyAsync(&ctx->lev->it[s], &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+    return compact_tiles<T, true>(ctx, sp, s, step);
 }
 
 }  // namespace
@@ -470,6 +797,39 @@ qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s) {
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     if (ctx->cfg.precision == QED_FP32) return level_impl<float>(ctx, sp, s, step);
     return level_impl<double>(ctx, sp, s, step);
+}
+
+qed_status sfq_level_eval(qed_ctx *ctx, qed_species *sp, int s, double w, double *A, int64_t *C, int64_t *N,
+                          double *M) {
+    if (ctx->cfg.precision == QED_FP32) return level_eval_impl<float>(ctx, sp, s, w, A, C, N, M);
+    return level_eval_impl<double>(ctx, sp, s, w, A, C, N, M);
+}
+
+qed_status sfq_level_apply_species(qed_ctx *ctx, qed_species *sp, int s, double wstar, int64_t step) {
+    if (ctx->cfg.precision == QED_FP32) return level_apply_impl<float>(ctx, sp, s, wstar, step);
+    return level_apply_impl<double>(ctx, sp, s, wstar, step);
+}
+
+void sfq_level_advance(double *lo, double *hi, double *w, double *wstar, int64_t *iters, int64_t *done,
+                       int64_t *alive, double A, int64_t C, int64_t N, double M, int64_t cap) {
+    LevelIter it{};
+    it.lo = *lo;
+    it.hi = *hi;
+    it.w = *w;
+    it.wstar = *wstar;
+    it.iters = (unsigned long long)*iters;
+    it.done = (unsigned long long)*done;
+    it.alive = (unsigned long long)*alive;
+    unsigned long long mb;
+    memcpy(&mb, &M, sizeof mb);
+    lev_advance(it, A, (unsigned long long)C, (unsigned long long)N, mb, (long long)cap);
+    *lo = it.lo;
+    *hi = it.hi;
+    *w = it.w;
+    *wstar = it.wstar;
+    *iters = (int64_t)it.iters;
+    *done = (int64_t)it.done;
+    *alive = (int64_t)it.alive;
 }
 
 // ---------------------------------------------------------------------------

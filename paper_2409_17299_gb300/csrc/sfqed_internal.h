@@ -52,11 +52,15 @@ struct LevelIter {
     double wstar;           // result (0: no leveling)
     float w_up, wstar_up;   // smallest floats >= w and >= wstar (exact FP32 comparisons)
     float wstar_f;          // wstar rounded to float (the new weight in FP32 mode)
-    float pad_f;
+    float wstar_inv_f;      // 1 / wstar rounded to float
     unsigned long long done, iters, alive;
+    unsigned long long mode;    // 0: a pass advances the iteration; 1: a pass only stores its sums
+    double sumA;                // sums of the last pass in mode 1
+    unsigned long long sumC, sumN, sumM;
 };
 struct LevelWork {
     LevelIter it[3];
+    unsigned arrive[4];                         // blocks of the current pass that finished (per species)
     double partA[LEVEL_MAX_BLOCKS];             // sum of weights below w (block partials)
     unsigned long long partC[LEVEL_MAX_BLOCKS]; // count at or above w
     unsigned long long partN[LEVEL_MAX_BLOCKS]; // alive count
@@ -169,6 +173,11 @@ qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, 
 // Implemented in sfqed_compact.cu
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step);
+qed_status sfq_level_eval(qed_ctx *ctx, qed_species *sp, int s, double w, double *A, int64_t *C, int64_t *N,
+                          double *M);
+qed_status sfq_level_apply_species(qed_ctx *ctx, qed_species *sp, int s, double wstar, int64_t step);
+void sfq_level_advance(double *lo, double *hi, double *w, double *wstar, int64_t *iters, int64_t *done,
+                       int64_t *alive, double A, int64_t C, int64_t N, double M, int64_t cap);
 qed_status sfq_ensure_work(qed_ctx *ctx, int64_t n_blocks, int64_t n_slots);
 
 #define SFQ_LAUNCHED(ctx, n) ((ctx)->launches += (n))

@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
 // Photon push: straight flight, pair creation at the event, the photon is
 // removed (weight 0) and the pair appended.
 template <class T, bool FRESH>
-__global__ void __launch_bounds__(256) k_photon_pass(PassArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(PassArgs a) {
     __shared__ T s_coef[NCOEF];
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     __syncthreads();

@@ -386,3 +386,51 @@ def test_leveling_matches_oracle(weights):
     for f in ("x", "px", "nevents"):
         assert np.array_equal(got[f], want[f])
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sharded_leveling_matches_oracle(prec):
+    """One species split in three device shards (as on three GPUs): shard
+    sums from qed_level_eval, added on the host, the library's iteration
+    step, then qed_level_apply per shard.  The union of the survivors and
+    their weights equal the oracle's leveling of the whole species."""
+    rng = np.random.default_rng(21)
+    n, cap = 90000, 25000
+    w = np.exp(rng.normal(size=n))
+    w[::13] = 0.0
+    P = q.QED_FP64 if prec == "fp64" else q.QED_FP32
+    if P == q.QED_FP32:
+        w = w.astype(np.float32).astype(np.float64)
+    sp = {"x": rng.normal(size=n), "y": rng.normal(size=n), "z": rng.normal(size=n),
+          "px": rng.normal(size=n), "py": rng.normal(size=n), "pz": rng.normal(size=n), "w": w,
+          "id": rng.permutation(10 * n)[:n].astype(np.uint64)}
+    g = q.Generator(q.make_config(precision=P, seed=9))
+    cuts = [0, 20000, 61000, n]
+    shards = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        part = {k: v[a:b] for k, v in sp.items()}
+        shards.append(q.DeviceEnsemble.from_host([part, W._empty(), W._empty()], [b - a, 1, 1], P))
+
+    def evaluate(at):
+        vals = [q.qed_level_eval(g.ctx, e.struct().s[0], 0, at) for e in shards]
+        return (sum(v[0] for v in vals), sum(v[1] for v in vals), sum(v[2] for v in vals),
+                max(v[3] for v in vals))
+    st = q.level_threshold_sharded(evaluate, lambda v: v, cap)
+    want_ws = oracle.level_threshold(w, cap)
+    assert st.wstar == pytest.approx(want_ws, rel=1e-14)
+    for e in shards:
+        arr = e.struct()
+        q.qed_level_apply(g.ctx, arr, 0, st.wstar, 17)
+        e.pull_counts(arr)
+    got = [e.to_host(0) for e in shards]
+    got = by_id({k: np.concatenate([d[k] for d in got]) for k in got[0]})
+    oe = oracle.Ensemble.from_arrays([sp, None, None], [n, 1, 1])
+    oracle.compact(oe, 0)
+    oracle.level(oe, 0, cap, seed=9, step=17)
+    want = by_id(oe.view(0))
+    assert np.array_equal(got["id"], want["id"])
+    rtol = 1e-14 if P == q.QED_FP64 else 2 ** -23
+    assert np.allclose(got["w"], want["w"], rtol=rtol, atol=0)
+    assert np.array_equal(got["x"] if P == q.QED_FP64 else got["x"].astype(np.float32),
+                          want["x"] if P == q.QED_FP64 else want["x"].astype(np.float32))
+    g.close()
