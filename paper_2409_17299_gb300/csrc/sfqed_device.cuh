@@ -49,8 +49,10 @@ template <class T> __device__ __forceinline__ void st(void *p, size_t i, T v) {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        // one 32 x 32 -> 64-bit product gives both halves
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c.x, m1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(m0 >> 32), lo0 = (uint32_t)m0;
+        const uint32_t hi1 = (uint32_t)(m1 >> 32), lo1 = (uint32_t)m1;
         c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
         k.x += 0x9E3779B9u;
         k.y += 0xBB67AE85u;
@@ -98,18 +100,27 @@ template <class T, class A> __device__ __forceinline__ T prm_of(const A &a, int 
     else return a.prm_f[i];      // no double-to-float conversion in FP32 mode
 }
 
+// sine and cosine of the time phase at t_n + tau (shared by all particles
+// evaluated at the same tau, e.g. every particle at the start of a step)
+template <class T> struct Phase { T s, c; };
+template <class T, class A> __device__ __forceinline__ Phase<T> time_phase(const A &a, double tau) {
+    Phase<T> q{(T)0, (T)1};
+    if (a.field_kind == QED_FIELD_UNIFORM) return q;
+    T ph;
+    if constexpr (sizeof(T) == 8) ph = a.t_n + tau;
+    else ph = a.t_n_red_f + (float)tau;
+    m_sincos(ph, &q.s, &q.c);
+    return q;
+}
+
 template <class T, class A>
-__device__ __forceinline__ void eval_field(const A &a, T x, double tau, T E[3], T B[3]) {
+__device__ __forceinline__ void eval_field_at(const A &a, T x, const Phase<T> &q, T E[3], T B[3]) {
     if (a.field_kind == QED_FIELD_UNIFORM) {
         E[0] = prm_of<T, A>(a, 0); E[1] = prm_of<T, A>(a, 1); E[2] = prm_of<T, A>(a, 2);
         B[0] = prm_of<T, A>(a, 3); B[1] = prm_of<T, A>(a, 4); B[2] = prm_of<T, A>(a, 5);
         return;
     }
-    T ph;
-    if constexpr (sizeof(T) == 8) ph = a.t_n + tau;
-    else ph = a.t_n_red_f + (float)tau;
-    T s, c;
-    m_sincos(ph, &s, &c);
+    const T s = q.s, c = q.c;
     const T a0 = prm_of<T, A>(a, 0);
     if (a.field_kind == QED_FIELD_ROTATING_E) {
         E[0] = a0 * c; E[1] = a0 * s; E[2] = 0;
@@ -121,6 +132,11 @@ __device__ __forceinline__ void eval_field(const A &a, T x, double tau, T E[3], 
         E[0] = 0; E[1] = e * c; E[2] = e * s;
         B[0] = 0; B[1] = b * c; B[2] = b * s;
     }
+}
+
+template <class T, class A>
+__device__ __forceinline__ void eval_field(const A &a, T x, double tau, T E[3], T B[3]) {
+    eval_field_at<T, A>(a, x, time_phase<T, A>(a, tau), E, B);
 }
 
 // ---------------------------------------------------------------------------

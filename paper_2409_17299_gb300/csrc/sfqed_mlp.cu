@@ -240,17 +240,15 @@ __global__ void k_mlp_init(float *P, float *M, float *V, float *G, __nv_bfloat16
 }
 
 // forward of n feature pairs, one warp per 32 samples (component check)
-constexpr int EVAL_T = 64;
+constexpr int EVAL_T = 128;
 __global__ void __launch_bounds__(EVAL_T) k_mlp_eval(const __nv_bfloat16 *W16, const float *feat, long long n,
                                                      float *y) {
-    __shared__ __align__(16) __nv_bfloat16 W[MLP_NP + 1];
-    __shared__ __align__(16) __nv_bfloat16 buf[EVAL_T / 32][2][32 * MLP_H];
-    for (int i = threadIdx.x; i < MLP_NP; i += blockDim.x) W[i] = W16[i];
+    __shared__ __align__(16) unsigned char sm[MLP_INF_BYTES];
+    const MlpInf m = mlp_stage(sm, W16);
     __syncthreads();
-    const int warp = threadIdx.x >> 5;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const float f0 = i < n ? feat[2 * i] : 0.f, f1 = i < n ? feat[2 * i + 1] : 0.f;
-    const float out = mlp_forward_warp(f0, f1, W, buf[warp][0], buf[warp][1]);
+    const float out = mlp_forward_warp(f0, f1, m);
     if (i < n) y[i] = out;
 }
 

@@ -100,6 +100,7 @@ template <class T> struct LeptonCtx {
     const T *icdf;
     unsigned long long cap_ph;
     T alpha_r;
+    Phase<T> ph0;           // time phase at the step start (tau = 0)
 };
 
 // One waiting-time iteration from (x, p, tau).  Returns true and leaves the
@@ -113,7 +114,8 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
                                         unsigned long long id, unsigned k, uint2 &rz, unsigned &n64) {
     const PassArgs &a = c.a;
     T E[3], B[3];
-    eval_field<T>(a, x[0], FRESH ? 0.0 : tau, E, B);
+    if constexpr (FRESH) eval_field_at<T>(a, x[0], c.ph0, E, B);
+    else eval_field<T>(a, x[0], tau, E, B);
     T gam, chi, p2;
     lepton_chi<T>(p, E, B, gam, chi, p2, n64);
     const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
@@ -186,13 +188,8 @@ __device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3]
     emit_with<T>(c, x, p, tau, w, id, k, gam, p2, delta, om);
 }
 
-// Network sampler state of a block (dynamic shared memory): BF16 weights
-// and two 32 x 64 activation buffers per warp.
-struct MlpSmem {
-    __nv_bfloat16 *W;
-    __nv_bfloat16 *buf;
-};
-constexpr int MLP_SMEM_BYTES = (MLP_NP + 1) * 2 + (LB / 32) * 2 * 32 * MLP_H * 2;
+// Network sampler of a block: the staged network (dynamic shared memory)
+constexpr int MLP_SMEM_BYTES = MLP_INF_BYTES;
 
 template <class T>
 __device__ __forceinline__ void finish(const PassArgs &a, unsigned idx, const T x[3], const T p[3], unsigned k) {
@@ -216,7 +213,7 @@ __device__ __forceinline__ void stack_push(LeptonStack<T> &q, const T x[3], cons
 // or the step end.  Every thread of the block calls this.
 template <class T, bool MLP>
 __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T> &q, unsigned long long &ev,
-                                            unsigned &mx, unsigned &n64, const MlpSmem &ms) {
+                                            unsigned &mx, unsigned &n64, const MlpInf &ms) {
     const int n = q.n;
     const int take = n < LB ? n : LB;
     const int t = threadIdx.x;
@@ -251,9 +248,7 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
             use_net = cf >= 1e-3f && cf <= 1e3f && fabsf(sl) < 16.0f;
             if (use_net) { f0 = log10f(cf) / 3.0f; f1 = sl / 16.0f; }
         }
-        const int wid = threadIdx.x >> 5;
-        const float y = mlp_forward_warp(f0, f1, ms.W, ms.buf + wid * 2 * 32 * MLP_H,
-                                         ms.buf + wid * 2 * 32 * MLP_H + 32 * MLP_H);
+        const float y = mlp_forward_warp(f0, f1, ms);
         if (mine) {
             T delta, om;
             if (use_net) {
@@ -287,12 +282,8 @@ __global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
     __shared__ T s_coef[NCOEF];
     __shared__ LeptonStack<T> q;
     extern __shared__ __align__(16) unsigned char dyn[];
-    MlpSmem ms{nullptr, nullptr};
-    if constexpr (MLP) {
-        ms.W = reinterpret_cast<__nv_bfloat16 *>(dyn);
-        ms.buf = ms.W + MLP_NP + 1;
-        for (int i = threadIdx.x; i < MLP_NP; i += blockDim.x) ms.W[i] = a.mlp_w16[i];
-    }
+    MlpInf ms{nullptr, nullptr, nullptr};
+    if constexpr (MLP) ms = mlp_stage(dyn, a.mlp_w16);
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     if (threadIdx.x == 0) q.n = 0;
     __syncthreads();
@@ -300,7 +291,8 @@ __global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
     const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
     const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
     const unsigned long long n = n0 + n1;
-    const LeptonCtx<T> c{a, ctl, s_coef, reinterpret_cast<const T *>(a.icdf_em), ctl->capacity[2], (T)(ALPHA * RS)};
+    const LeptonCtx<T> c{a, ctl, s_coef, reinterpret_cast<const T *>(a.icdf_em), ctl->capacity[2], (T)(ALPHA * RS),
+                         time_phase<T>(a, 0.0)};
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
 
@@ -354,6 +346,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     const SpeciesDev &S = a.sp[2];
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
+    const Phase<T> ph0 = time_phase<T>(a, 0.0);
 
     for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
@@ -373,9 +366,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
             // one waiting time: the photon either reaches the step end or converts
             if (FRESH || tau < a.dt) {
                 T E[3], B[3];
-                eval_field<T>(a, x[0], FRESH ? 0.0 : tau, E, B);
+                if constexpr (FRESH) eval_field_at<T>(a, x[0], ph0, E, B);
+                else eval_field<T>(a, x[0], tau, E, B);
                 T chi = photon_chi<T>(k0, kv, E, B, n64);
-                const T lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);
+                T lam;
+                if constexpr (sizeof(T) == 4) lam = alpha_r * inv * rate_pair<T>(s_coef, chi);
+                else lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);     // the oracle's rounding
                 uint4 r = make_uint4(0, 0, 0, 0);
                 T dth = t_inf<T>();
                 if (lam > (T)0) {

@@ -59,8 +59,9 @@ def test_gradient_matches_oracle():
     n = 512
     feat = rng.uniform(-1, 1, size=(n, 2)).astype(np.float32)
     tgt = rng.normal(size=n).astype(np.float32)
-    grad, loss = q.qed_mlp_grad(g.ctx, torch.from_numpy(feat).cuda().data_ptr(),
-                                torch.from_numpy(tgt).cuda().data_ptr(), n)
+    dfeat = torch.from_numpy(feat).cuda()      # kept alive across the call
+    dtgt = torch.from_numpy(tgt).cuda()
+    grad, loss = q.qed_mlp_grad(g.ctx, dfeat.data_ptr(), dtgt.data_ptr(), n)
     oloss, ograd = oracle.mlp_loss_grad(bf16_round(P).astype(np.float64), feat.astype(np.float64),
                                         tgt.astype(np.float64))
     assert loss == pytest.approx(oloss, rel=3e-2)
