@@ -31,6 +31,14 @@ from paper_2409_17299_gb300 import workloads as W  # noqa: E402  (no CUDA, no me
 # write x,y,z,px,py,pz) and per emission (nevents update + photon record + birth clock)
 LEPTON_BYTES = {"fp32": 7 * 4 + 8 + 6 * 4, "fp64": 7 * 8 + 8 + 6 * 8}
 EMIT_BYTES = {"fp32": 8 + 7 * 4 + 8 + 4 + 8, "fp64": 8 + 7 * 8 + 8 + 4 + 8}
+# photon step: read w, x, k, id; write x.  Pair: photon weight cleared, two
+# lepton records (x, p, w, id, nevents, birth clock)
+PHOTON_BYTES = {"fp32": 4 + 3 * 4 + 3 * 4 + 8 + 3 * 4, "fp64": 8 + 3 * 8 + 3 * 8 + 8 + 3 * 8}
+PAIR_BYTES = {"fp32": 4 + 2 * (7 * 4 + 8 + 4 + 8), "fp64": 8 + 2 * (7 * 8 + 8 + 4 + 8)}
+# DRAM bytes (read + write) per photon-step of the step-start photon pass,
+# from one ncu capture (profiles/k_photon_pass_fp32_rotating_e_cascade.md);
+# None until the current kernel has been captured
+NCU_PHOTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
 
 
 def parse():
@@ -477,8 +485,27 @@ def main():
         return
     prec = args.precision
     lep_bytes = LEPTON_BYTES[prec] * tot["lepton_steps"] + EMIT_BYTES[prec] * tot["emit_events"]
-    lep_ms = tot["kernel_ms"][0]
-    achieved = lep_bytes / (lep_ms / 1e3) / 1e9 if lep_ms > 0 else None
+    ph_bytes = PHOTON_BYTES[prec] * tot["photon_steps"] + PAIR_BYTES[prec] * tot["pair_events"]
+    lep_ms, ph_ms = tot["kernel_ms"][0], tot["kernel_ms"][1]
+    launches = max(1, tot["lepton_launches"])
+    kernels = {
+        "k_lepton_pass": {"achieved": lep_bytes / (lep_ms / 1e3) / 1e9 if lep_ms > 0 else None,
+                          "kernel_ms": lep_ms, "launches": launches,
+                          "bytes_per_particle_step": LEPTON_BYTES[prec], "bytes_per_emission": EMIT_BYTES[prec],
+                          "units": "lepton particle-steps %d, emissions %d" % (tot["lepton_steps"],
+                                                                             tot["emit_events"]),
+                          "traffic": None},
+        "k_photon_pass": {"achieved": ph_bytes / (ph_ms / 1e3) / 1e9 if ph_ms > 0 else None,
+                          "kernel_ms": ph_ms, "launches": launches if w.push_photons else 0,
+                          "bytes_per_photon_step": PHOTON_BYTES[prec], "bytes_per_pair": PAIR_BYTES[prec],
+                          "units": "photon-steps %d, pairs %d" % (tot["photon_steps"], tot["pair_events"]),
+                          "traffic": (NCU_PHOTON_BYTES_PER_STEP[prec] * tot["photon_steps"] / launches
+                                      if NCU_PHOTON_BYTES_PER_STEP[prec] and w.push_photons else None)},
+    }
+    for k in kernels.values():
+        k["frac"] = k["achieved"] / hbm_peak if k["achieved"] else None
+    dom = max(kernels, key=lambda k: kernels[k]["kernel_ms"])
+    achieved = kernels[dom]["achieved"]
     line = {
         "metric": "particle-steps/s", "value": ps_total / tmax, "unit": "particle-steps/s",
         "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": tmax * 1e3 / steps,
@@ -493,12 +520,13 @@ def main():
         "final_counts": counts,
         "gpu_launches": tot["launches"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
-                     "kernel": "k_lepton_pass<%s>" % ("float" if prec == "fp32" else "double"),
+                     "frac": (achieved / hbm_peak) if achieved else None,
+                     "traffic": kernels[dom]["traffic"],
+                     "kernel": "%s<%s>" % (dom, "float" if prec == "fp32" else "double"),
                      "peak_source": peak_src + " hbm_gbs",
-                     "bytes_per_particle_step": LEPTON_BYTES[prec], "bytes_per_emission": EMIT_BYTES[prec],
-                     "lepton_kernel_ms": lep_ms, "photon_kernel_ms": tot["kernel_ms"][1],
-                     "lepton_launches": tot["lepton_launches"]},
+                     "achieved_is": "algorithmic bytes of all launches / summed CUDA-event time of the launches",
+                     "traffic_is": "ncu DRAM bytes per unit x units per launch (average launch)",
+                     "kernels": kernels},
         "breakdown_ms": {"lepton": tot["kernel_ms"][0], "photon": tot["kernel_ms"][1],
                          "compaction": tot["kernel_ms"][2], "leveling": tot["kernel_ms"][3],
                          "host_sync_wait": tot["sync_ms"], "host_call_wall": tot["call_ms"],

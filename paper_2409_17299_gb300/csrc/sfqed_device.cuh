@@ -34,6 +34,15 @@ __device__ __forceinline__ double m_cbrt2(double a) { double c = cbrt(a); return
 __device__ __forceinline__ float m_cbrt2(float a) { float c = cbrtf(a); return c * c; }
 __device__ __forceinline__ void m_sincos(double a, double *s, double *c) { sincos(a, s, c); }
 __device__ __forceinline__ void m_sincos(float a, float *s, float *c) { sincosf(a, s, c); }
+// Rate and waiting-time arithmetic: IEEE in FP64 mode; in FP32 mode the
+// hardware approximations (a few ulp, far below the approximant's own 1e-6
+// error and the statistics of the draws)
+__device__ __forceinline__ double f_log10(double a) { return log10(a); }
+__device__ __forceinline__ float f_log10(float a) { return __log10f(a); }
+__device__ __forceinline__ double f_exp(double a) { return exp(a); }
+__device__ __forceinline__ float f_exp(float a) { return __expf(a); }
+__device__ __forceinline__ double f_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float f_div(float a, float b) { return __fdividef(a, b); }
 
 // particle arrays are read and written by the same kernels: plain loads
 template <class T> __device__ __forceinline__ T ld(const void *p, size_t i) {
@@ -85,8 +94,9 @@ template <> struct Uniform<float> {
         u = fmaf(__uint2float_rn(a), 0x1p-32f, fmaf(__uint2float_rn(b >> 12), 0x1p-52f, 0x1p-53f));
         v = fmaf(__uint2float_rn(~a), 0x1p-32f, fmaf(__uint2float_rn((~b) >> 12), 0x1p-52f, 0x1p-53f));
     }
-    // -ln u, from v = 1 - u when u is near 1
-    static __device__ __forceinline__ float neglog(float u, float v) { return u < 0.5f ? -logf(u) : -log1pf(-v); }
+    // -ln u, from v = 1 - u when u is near 1 (below 1/2 the fast logarithm
+    // is within 3 ulp)
+    static __device__ __forceinline__ float neglog(float u, float v) { return u < 0.5f ? -__logf(u) : -log1pf(-v); }
 };
 
 // ---------------------------------------------------------------------------
@@ -173,9 +183,25 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
     return f + e;
 }
 
+// zero: 1 if B = 0 everywhere (then chi^2 R^2 = [E^2] + |p x E|^2, a sum of
+// squares), 2 if E = 0 everywhere (chi^2 R^2 = |p x B|^2), else 0.
 template <bool LEPTON>
 __device__ __forceinline__ float chi_guarded(float e0, const float p[3], const float E[3], const float B[3],
-                                             unsigned *fp64_used) {
+                                             unsigned *fp64_used, int zero = 0) {
+    if (zero == 1) {
+        const float ax = diff_of_products(p[1], E[2], p[2], E[1]);
+        const float ay = diff_of_products(p[2], E[0], p[0], E[2]);
+        const float az = diff_of_products(p[0], E[1], p[1], E[0]);
+        float S = ax * ax + ay * ay + az * az;
+        if (LEPTON) S += E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
+        return sqrtf(S) * (float)(1.0 / RS);
+    }
+    if (zero == 2) {
+        const float bx = diff_of_products(p[1], B[2], p[2], B[1]);
+        const float by = diff_of_products(p[2], B[0], p[0], B[2]);
+        const float bz = diff_of_products(p[0], B[1], p[1], B[0]);
+        return sqrtf(bx * bx + by * by + bz * bz) * (float)(1.0 / RS);
+    }
     const float ax = diff_of_products(p[1], E[2], p[2], E[1]);
     const float ay = diff_of_products(p[2], E[0], p[0], E[2]);
     const float az = diff_of_products(p[0], E[1], p[1], E[0]);
@@ -242,7 +268,7 @@ template <class T> __device__ __forceinline__ T clenshaw(const T *c, T x) {
 // F_gamma(chi)
 template <class T> __device__ __forceinline__ T rate_em(const T *coef, T chi) {
     if (!(chi > (T)0)) return (T)0;
-    const T s = m_log10(chi);
+    const T s = f_log10(chi);
     if (s < (T)-3) return chi * clenshaw(coef, (T)-1);
     if (s > (T)3) return (T)1e3 * clenshaw(coef + 5 * CHEB_N, (T)1) * m_cbrt2(chi * (T)1e-3);
     int d = (int)m_floor(s + (T)3);
@@ -255,12 +281,12 @@ template <class T> __device__ __forceinline__ T rate_em(const T *coef, T chi) {
 template <class T> __device__ __forceinline__ T rate_pair(const T *coef, T chi) {
     if (!(chi >= (T)PAIR_CHI_MIN)) return (T)0;
     const T *c = coef + EM_NDEC * CHEB_N;
-    const T s = m_log10(chi);
-    if (s > (T)3) return m_exp(clenshaw(c + 4 * CHEB_N, (T)1) - (T)(8.0 / 3e3)) * m_cbrt2(chi * (T)1e-3);
+    const T s = f_log10(chi);
+    if (s > (T)3) return f_exp(clenshaw(c + 4 * CHEB_N, (T)1) - (T)(8.0 / 3e3)) * m_cbrt2(chi * (T)1e-3);
     int d = (int)m_floor(s + (T)2);
     d = d > 4 ? 4 : (d < 0 ? 0 : d);
     const T x = (T)2 * (s - (T)(d - 2)) - (T)1;
-    return m_exp(clenshaw(c + d * CHEB_N, x) - (T)(8.0 / 3.0) / chi);
+    return f_exp(clenshaw(c + d * CHEB_N, x) - f_div((T)(8.0 / 3.0), chi));
 }
 
 // ---------------------------------------------------------------------------

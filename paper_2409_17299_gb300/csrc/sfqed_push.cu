@@ -46,7 +46,7 @@ __device__ __forceinline__ void flush_stats(DevCtl *ctl, unsigned long long step
 // the direct FP64 form; FP32 mode the guarded form with FP64 fallback.
 template <class T>
 __device__ __forceinline__ void lepton_chi(const T p[3], const T E[3], const T B[3], T &gam, T &chi, T &p2,
-                                           unsigned &n64) {
+                                           unsigned &n64, int zero = 0) {
     if constexpr (sizeof(T) == 8) {
         p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
         gam = sqrt(1.0 + p2);
@@ -54,14 +54,14 @@ __device__ __forceinline__ void lepton_chi(const T p[3], const T E[3], const T B
     } else {
         p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
         gam = sqrtf(1.0f + p2);
-        chi = chi_guarded<true>(gam, p, E, B, &n64);
+        chi = chi_guarded<true>(gam, p, E, B, &n64, zero);
     }
 }
 
 template <class T>
-__device__ __forceinline__ T photon_chi(T k0, const T k[3], const T E[3], const T B[3], unsigned &n64) {
+__device__ __forceinline__ T photon_chi(T k0, const T k[3], const T E[3], const T B[3], unsigned &n64, int zero = 0) {
     if constexpr (sizeof(T) == 8) return chi_fp64(k0, k[0], k[1], k[2], E[0], E[1], E[2], B[0], B[1], B[2]);
-    else return chi_guarded<false>(k0, k, E, B, &n64);
+    else return chi_guarded<false>(k0, k, E, B, &n64, zero);
 }
 
 __device__ __forceinline__ void note_overflow(DevCtl *ctl, int s, unsigned long long slot) {
@@ -117,14 +117,14 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
     if constexpr (FRESH) eval_field_at<T>(a, x[0], c.ph0, E, B);
     else eval_field<T>(a, x[0], tau, E, B);
     T gam, chi, p2;
-    lepton_chi<T>(p, E, B, gam, chi, p2, n64);
-    const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
+    lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
+    const T lam = p2 > (T)0 ? f_div(c.alpha_r, gam) * rate_em<T>(c.coef, chi) : (T)0;
     T dth = t_inf<T>();
     if (lam > (T)0) {
         const uint4 r = event_draw(a.seed, id, a.step, k);
         T uw, vw;
         Uniform<T>::draw(r.x, r.y, uw, vw);
-        dth = Uniform<T>::neglog(uw, vw) / lam;
+        dth = f_div(Uniform<T>::neglog(uw, vw), lam);
         rz = make_uint2(r.z, r.w);
     }
     bool no_event;
@@ -181,7 +181,7 @@ __device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3]
     T E[3], B[3];
     eval_field<T>(c.a, x[0], tau, E, B);
     T gam, chi, p2;
-    lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+    lepton_chi<T>(p, E, B, gam, chi, p2, n64, c.a.field_zero);
     T om, ue, ve;
     Uniform<T>::draw(rz.x, rz.y, ue, ve);
     const T delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
         if (mine) {
             T E[3], B[3];
             eval_field<T>(c.a, x[0], tau, E, B);
-            lepton_chi<T>(p, E, B, gam, chi, p2, n64);
+            lepton_chi<T>(p, E, B, gam, chi, p2, n64, c.a.field_zero);
             Uniform<T>::draw(rz.x, rz.y, ue, ve);
             const float sl = (float)logit(ue, ve);
             const float cf = (float)chi;
@@ -304,10 +304,10 @@ __global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
             const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
             const SpeciesDev &S = a.sp[s];
             const T w = ld<T>(S.w, i);
+            T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
+            T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
+            const unsigned long long id = __ldg(S.id + i);
             if (w > (T)0) {
-                T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
-                T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
-                const unsigned long long id = __ldg(S.id + i);
                 double tau = FRESH ? 0.0 : S.tau[i];
                 const unsigned idx = (unsigned)i | ((unsigned)s << 31);
                 ++my_steps;
@@ -351,24 +351,26 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long i = b + j;
+        // all loads issued together (live photons are the rule: the photons
+        // that converted were removed at the end of the previous step)
         T w = ld<T>(S.w, i);
-        if (!(w > (T)0)) continue;
         T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
         const T kx = ld<T>(S.px, i), ky = ld<T>(S.py, i), kz = ld<T>(S.pz, i);
         const unsigned long long id = __ldg(S.id + i);
+        if (!(w > (T)0)) continue;
         double tau = FRESH ? 0.0 : S.tau[i];
         const T kv[3] = {kx, ky, kz};
         const T k0 = m_sqrt(kx * kx + ky * ky + kz * kz);
         unsigned k = 0;
         if (k0 > (T)0) {
-            const T inv = (T)1 / k0;
+            const T inv = f_div((T)1, k0);
             const T nx = kx * inv, ny = ky * inv, nz = kz * inv;
             // one waiting time: the photon either reaches the step end or converts
             if (FRESH || tau < a.dt) {
                 T E[3], B[3];
                 if constexpr (FRESH) eval_field_at<T>(a, x[0], ph0, E, B);
                 else eval_field<T>(a, x[0], tau, E, B);
-                T chi = photon_chi<T>(k0, kv, E, B, n64);
+                T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
                 T lam;
                 if constexpr (sizeof(T) == 4) lam = alpha_r * inv * rate_pair<T>(s_coef, chi);
                 else lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);     // the oracle's rounding
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                     r = event_draw(a.seed, id, a.step, k);
                     T uw, vw;
                     Uniform<T>::draw(r.x, r.y, uw, vw);
-                    dth = Uniform<T>::neglog(uw, vw) / lam;
+                    dth = f_div(Uniform<T>::neglog(uw, vw), lam);
                 }
                 bool no_event;
                 T h;
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 if constexpr (FRESH) tau = (double)dth;
                 else tau += (double)dth;
                 eval_field<T>(a, x[0], tau, E, B);
-                chi = photon_chi<T>(k0, kv, E, B, n64);
+                chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
                 T om, ue, ve;
                 Uniform<T>::draw(r.z, r.w, ue, ve);
                 const T delta = sample_pair<T>(icdf, chi, ue, ve, &om);
@@ -738,6 +740,13 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.icdf_pair = f32 ? (const void *)ctx->icdf_pair32 : (const void *)ctx->icdf_pair64;
     a.mlp_w16 = ctx->cfg.sampler == QED_SAMPLER_MLP ? ctx->mlp_w16 : nullptr;
     a.field_kind = field->kind;
+    // fields that vanish everywhere let chi skip its cancellation guard
+    if (field->kind == QED_FIELD_ROTATING_E) a.field_zero = 1;
+    if (field->kind == QED_FIELD_UNIFORM) {
+        const double *q = field->params;
+        if (q[3] == 0.0 && q[4] == 0.0 && q[5] == 0.0) a.field_zero = 1;
+        else if (q[0] == 0.0 && q[1] == 0.0 && q[2] == 0.0) a.field_zero = 2;
+    }
     for (int i = 0; i < 6; ++i) {
         a.prm[i] = field->params[i];
         a.prm_f[i] = (float)field->params[i];
