@@ -49,6 +49,7 @@ struct BatchArgs {
     const double *t_n;             // per step of the call: step * dt
     const float *t_red_f;          // per step: step * dt reduced mod 2 pi, in FP32
     unsigned long long seed;
+    PhiloxKeys keys;               // round keys of seed
     int soft_filter;
 };
 
@@ -117,7 +118,7 @@ __device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView
     const T lam = p2 > (T)0 ? (T)(ALPHA * RS) / gam * rate_em<T>(coef_of<T>(c), chi) : (T)0;
     T dth = (T)INFINITY;
     if (lam > (T)0) {
-        const uint4 r = event_draw(b.seed, id, step, k);
+        const uint4 r = event_draw(b.keys, id, step, k);
         T uw, vw;
         Uniform<T>::draw(r.x, r.y, uw, vw);
         dth = Uniform<T>::neglog(uw, vw) / lam;
@@ -481,6 +482,7 @@ static qed_status batch_impl(qed_ctx *ctx, qed_particles *ens, const qed_field_d
     b.t_n = w->tn_d;
     b.t_red_f = w->tr_d;
     b.seed = ctx->cfg.seed;
+    b.keys = philox_keys(ctx->cfg.seed);
     b.soft_filter = ctx->cfg.soft_photon_filter;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (ctx->cfg.profile) {

@@ -447,7 +447,7 @@ constexpr int LSPAN = 32 * LROUNDS;       // contiguous entries per warp
 // of the boundary; kept particles get weight w*.
 template <class T, bool LEVEL>
 __global__ void __launch_bounds__(LT) k_tile_dead(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw,
-                                                  uint64_t seed, unsigned step, unsigned long long *blk,
+                                                  const PhiloxKeys keys, unsigned step, unsigned long long *blk,
                                                   unsigned short *dl) {
     __shared__ unsigned wdead[LT / 32];
     const unsigned long long n = ctl->count[s];
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(LT) k_tile_dead(SpeciesDev S, DevCtl *ctl, int
             const unsigned long long i = wbase + (c0 + r) * 32 + lane;
             bool dead = i < n && !(v[r] > (T)0);
             if (LEVEL && below[r]) {
-                const uint4 q = event_draw(seed, idv[r], step, 0xFFFFFFFFu);
+                const uint4 q = event_draw(keys, idv[r], step, 0xFFFFFFFFu);
                 const float uf = __uint2float_rn(q.x) * 0x1p-32f;     // u to within 2^-32 + FP32 rounding
                 const float pf = (float)v[r] * inv_f;
                 bool keep;
@@ -677,8 +677,8 @@ qed_status compact_tiles(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     unsigned short *dl = reinterpret_cast<unsigned short *>(ctx->slots);
     unsigned long long *movers = ctx->slots + (n + 3) / 4;
     cudaStream_t st = ctx->stream;
-    k_tile_dead<T, LEVEL><<<(unsigned)nb, LT, 0, st>>>(S, ctx->ctl, s, ctx->lev, ctx->cfg.seed, (unsigned)step,
-                                                       ctx->blk, dl);
+    k_tile_dead<T, LEVEL><<<(unsigned)nb, LT, 0, st>>>(S, ctx->ctl, s, ctx->lev, philox_keys(ctx->cfg.seed),
+                                                       (unsigned)step, ctx->blk, dl);
     k_scan_tiles<T><<<1, 1024, 0, st>>>(sp->w, ctx->blk, nb, ctx->ctl, s);
     k_tile_movers<T><<<(unsigned)nb, LT, 0, st>>>(sp->w, ctx->ctl, s, ctx->blk, movers);
     k_tile_fill<T><<<(unsigned)nb, LT, 0, st>>>(S, ctx->ctl, s, ctx->blk, dl, movers);

@@ -69,6 +69,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// The key of round r is (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85).  Kernels
+// that draw with one key for every particle take the ten round keys
+// precomputed in their arguments, so each round's key is an operand read
+// from the argument space rather than two additions per draw.
+__host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k[2 * r] = k0;
+        K.k[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c.x, m1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(m1 >> 32) ^ c.y ^ K.k[2 * r], (uint32_t)m1,
+                       (uint32_t)(m0 >> 32) ^ c.w ^ K.k[2 * r + 1], (uint32_t)m0);
+    }
+    return c;
+}
+__device__ __forceinline__ uint4 event_draw(const PhiloxKeys &K, uint64_t id, unsigned step, unsigned k) {
+    return philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, k), K);
+}
+
 __device__ __forceinline__ uint4 event_draw(uint64_t seed, uint64_t id, unsigned step, unsigned k) {
     return philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, k),
                          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));

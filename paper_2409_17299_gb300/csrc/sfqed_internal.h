@@ -67,6 +67,11 @@ struct LevelWork {
     unsigned long long partM[LEVEL_MAX_BLOCKS]; // largest weight (double bits)
 };
 
+// Philox round keys of one seed: k[2 r], k[2 r + 1] are the key of round r
+struct PhiloxKeys {
+    uint32_t k[20];
+};
+
 struct SpeciesDev {
     void *x, *y, *z, *px, *py, *pz, *w;
     unsigned long long *id;
@@ -93,6 +98,7 @@ struct PassArgs {
     float t_n_red_f;        // the same rounded to float (FP32 phase)
     unsigned step;
     unsigned long long seed;
+    PhiloxKeys keys;        // round keys of seed (event draws)
     int pass;               // 0: particles present at the step start (tau = 0)
     int soft_filter;
     int record_newborn_tau; // newborns get their birth clock stored (cascades)
@@ -139,6 +145,7 @@ struct qed_ctx {
     void *batch;                 // batched-push work buffers
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
     int tuned_threads;           // block shape picked by the autotuner (0: none yet)
+    int spec_passes;             // newborn passes enqueued per host check (from the last step)
     // surrogate network: FP32 master parameters, Adam moments and gradient
     // (4 x 8577 floats), BF16 copy used by the kernels, loss accumulator
     float *mlp_p;

@@ -121,7 +121,7 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
     const T lam = p2 > (T)0 ? f_div(c.alpha_r, gam) * rate_em<T>(c.coef, chi) : (T)0;
     T dth = t_inf<T>();
     if (lam > (T)0) {
-        const uint4 r = event_draw(a.seed, id, a.step, k);
+        const uint4 r = event_draw(a.keys, id, a.step, k);
         T uw, vw;
         Uniform<T>::draw(r.x, r.y, uw, vw);
         dth = f_div(Uniform<T>::neglog(uw, vw), lam);
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 uint4 r = make_uint4(0, 0, 0, 0);
                 T dth = t_inf<T>();
                 if (lam > (T)0) {
-                    r = event_draw(a.seed, id, a.step, k);
+                    r = event_draw(a.keys, id, a.step, k);
                     T uw, vw;
                     Uniform<T>::draw(r.x, r.y, uw, vw);
                     dth = f_div(Uniform<T>::neglog(uw, vw), lam);
@@ -755,10 +755,13 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.dt_f = (float)dt;
     a.dt_f_gt = (double)a.dt_f > dt ? a.dt_f : nextafterf(a.dt_f, INFINITY);
     a.seed = ctx->cfg.seed;
+    a.keys = philox_keys(ctx->cfg.seed);
     a.soft_filter = ctx->cfg.soft_photon_filter;
     a.record_newborn_tau = cascade ? 1 : 0;
 
     qed_status rc = QED_OK;
+    int spec_passes = ctx->spec_passes > 0 ? ctx->spec_passes : 2;
+    long long passes_before = 0;
     for (int it = 0; it < nsteps; ++it) {
         const int64_t step = step0 + it;
         a.step = (unsigned)step;
@@ -772,16 +775,33 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
         if (e != QED_OK) return e;
         if (cascade) {
             // Algorithm 2: sweep the newborns until a pass creates nothing.
-            for (int pass = 1; pass < 100000; ++pass) {
-                k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
-                SFQ_LAUNCHED(ctx, 1);
+            // Passes are enqueued in groups without waiting for the host: a
+            // pass whose range is empty (set up after a pass that created
+            // nothing) returns at once, so the host reads the control block
+            // once per group, not once per pass.  The group size follows the
+            // number of passes the previous step needed.
+            // Every pass follows a setup of its range; the host looks at the
+            // last setup of a group.
+            int pass = 1;
+            k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
+            SFQ_LAUNCHED(ctx, 1);
+            for (;;) {
+                const int group = spec_passes;
+                for (int g = 0; g < group; ++g, ++pass) {
+                    a.pass = pass;
+                    e = launch_pass<T>(ctx, a, true);
+                    if (e != QED_OK) return e;
+                    k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
+                    SFQ_LAUNCHED(ctx, 1);
+                }
                 e = read_ctl(ctx);
                 if (e != QED_OK) return e;
-                if (ctx->ctl_host->overflow || !ctx->ctl_host->more) break;
-                a.pass = pass;
-                e = launch_pass<T>(ctx, a, true);
-                if (e != QED_OK) return e;
+                if (ctx->ctl_host->overflow || !ctx->ctl_host->more || pass >= 100000) break;
             }
+            // passes with work in this step (the control block counts them)
+            const long long used = (long long)ctx->ctl_host->passes - passes_before;
+            passes_before = (long long)ctx->ctl_host->passes;
+            spec_passes = used < 1 ? 1 : (used > 8 ? 8 : (int)used);
         }
         if (cascade || ctx->cfg.thin_cap > 0) {
             // merge step (Sec. 4.2): drop dead photons, then level
@@ -804,6 +824,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
             }
         }
     }
+    ctx->spec_passes = spec_passes;
     qed_status e = read_ctl(ctx);
     if (e != QED_OK) return e;
     DevCtl &c = *ctx->ctl_host;
