@@ -44,6 +44,21 @@ __device__ __forceinline__ float f_exp(float a) { return __expf(a); }
 __device__ __forceinline__ double f_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float f_div(float a, float b) { return __fdividef(a, b); }
 
+// Per-thread asynchronous copies global -> shared (cp.async): a thread
+// stages the next particle while it computes on the current one; the
+// hardware wait (wait_group) needs no spinning.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // particle arrays are read and written by the same kernels: plain loads
 template <class T> __device__ __forceinline__ T ld(const void *p, size_t i) {
     return reinterpret_cast<const T *>(p)[i];

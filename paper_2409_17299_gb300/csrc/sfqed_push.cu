@@ -296,17 +296,64 @@ __global__ void __launch_bounds__(LB) k_lepton_pass(PassArgs a) {
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
 
-    for (unsigned long long base = (unsigned long long)blockIdx.x * LB; base < n;
-         base += (unsigned long long)gridDim.x * LB) {
+    // FP32 step-start pass: each thread stages its particle of the block's
+    // next tile in shared memory while the block works on the current tile
+    constexpr bool STAGE = FRESH && sizeof(T) == 4;
+    constexpr int NF = STAGE ? 9 : 1, NT = STAGE ? LB : 1;
+    __shared__ __align__(16) float stg[NF][NT];            // w x y z px py pz id(2 words)
+    const unsigned long long stride = (unsigned long long)gridDim.x * LB;
+    auto stage = [&](unsigned long long jj) {
+        if constexpr (STAGE) {
+            const int sp = jj < n0 ? 0 : 1;
+            const unsigned long long ii = sp == 0 ? b0 + jj : b1 + (jj - n0);
+            const SpeciesDev &P = a.sp[sp];
+            const int t = threadIdx.x;
+            cp_async4(&stg[0][t], reinterpret_cast<const float *>(P.w) + ii);
+            cp_async4(&stg[1][t], reinterpret_cast<const float *>(P.x) + ii);
+            cp_async4(&stg[2][t], reinterpret_cast<const float *>(P.y) + ii);
+            cp_async4(&stg[3][t], reinterpret_cast<const float *>(P.z) + ii);
+            cp_async4(&stg[4][t], reinterpret_cast<const float *>(P.px) + ii);
+            cp_async4(&stg[5][t], reinterpret_cast<const float *>(P.py) + ii);
+            cp_async4(&stg[6][t], reinterpret_cast<const float *>(P.pz) + ii);
+            cp_async4(&stg[7][t], P.id + ii);
+            cp_async4(&stg[8][t], reinterpret_cast<const unsigned *>(P.id + ii) + 1);
+        }
+    };
+    if constexpr (STAGE) {
+        const unsigned long long j0 = (unsigned long long)blockIdx.x * LB + threadIdx.x;
+        if (j0 < n) stage(j0);
+        cp_async_commit();
+    }
+
+    for (unsigned long long base = (unsigned long long)blockIdx.x * LB; base < n; base += stride) {
         const unsigned long long j = base + threadIdx.x;
+        T w = (T)0, x[3], p[3];
+        unsigned long long id = 0;
+        if constexpr (STAGE) {
+            // this thread's staged particle, then the next tile's copies in
+            // flight (the slots are free once read)
+            cp_async_wait_all();
+            if (j < n) {
+                const int t = threadIdx.x;
+                w = stg[0][t];
+                x[0] = stg[1][t]; x[1] = stg[2][t]; x[2] = stg[3][t];
+                p[0] = stg[4][t]; p[1] = stg[5][t]; p[2] = stg[6][t];
+                id = (unsigned long long)__float_as_uint(stg[7][t]) |
+                     ((unsigned long long)__float_as_uint(stg[8][t]) << 32);
+            }
+            if (j + stride < n) stage(j + stride);
+            cp_async_commit();
+        }
         if (j < n) {
             const int s = j < n0 ? 0 : 1;
             const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
             const SpeciesDev &S = a.sp[s];
-            const T w = ld<T>(S.w, i);
-            T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
-            T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
-            const unsigned long long id = __ldg(S.id + i);
+            if constexpr (!STAGE) {
+                w = ld<T>(S.w, i);
+                x[0] = ld<T>(S.x, i); x[1] = ld<T>(S.y, i); x[2] = ld<T>(S.z, i);
+                p[0] = ld<T>(S.px, i); p[1] = ld<T>(S.py, i); p[2] = ld<T>(S.pz, i);
+                id = __ldg(S.id + i);
+            }
             if (w > (T)0) {
                 double tau = FRESH ? 0.0 : S.tau[i];
                 const unsigned idx = (unsigned)i | ((unsigned)s << 31);
@@ -347,16 +394,55 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
     const Phase<T> ph0 = time_phase<T>(a, 0.0);
-
-    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
+    // FP32 step-start pass: each thread stages its next photon in shared
+    // memory (two buffers) while it works on the current one
+    constexpr bool STAGE = FRESH && sizeof(T) == 4;
+    constexpr int NB = STAGE ? 2 : 1, NF = STAGE ? 9 : 1, NT = STAGE ? LB : 1;
+    __shared__ __align__(16) float stg[NB][NF][NT];       // w x y z kx ky kz id(2 words)
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    auto stage = [&](unsigned long long jj, int buf) {
+        if constexpr (STAGE) {
+            const unsigned long long ii = b + jj;
+            const int t = threadIdx.x;
+            cp_async4(&stg[buf][0][t], reinterpret_cast<const float *>(S.w) + ii);
+            cp_async4(&stg[buf][1][t], reinterpret_cast<const float *>(S.x) + ii);
+            cp_async4(&stg[buf][2][t], reinterpret_cast<const float *>(S.y) + ii);
+            cp_async4(&stg[buf][3][t], reinterpret_cast<const float *>(S.z) + ii);
+            cp_async4(&stg[buf][4][t], reinterpret_cast<const float *>(S.px) + ii);
+            cp_async4(&stg[buf][5][t], reinterpret_cast<const float *>(S.py) + ii);
+            cp_async4(&stg[buf][6][t], reinterpret_cast<const float *>(S.pz) + ii);
+            cp_async4(&stg[buf][7][t], S.id + ii);          // id: two 4-byte halves
+            cp_async4(&stg[buf][8][t], reinterpret_cast<const unsigned *>(S.id + ii) + 1);
+        }
+    };
+    const unsigned long long j0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (STAGE) {
+        if (j0 < n) stage(j0, 0);
+        cp_async_commit();
+    }
+    int buf = 0;
+    for (unsigned long long j = j0; j < n; j += stride, buf ^= 1) {
         const unsigned long long i = b + j;
-        // all loads issued together (live photons are the rule: the photons
-        // that converted were removed at the end of the previous step)
-        T w = ld<T>(S.w, i);
-        T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
-        const T kx = ld<T>(S.px, i), ky = ld<T>(S.py, i), kz = ld<T>(S.pz, i);
-        const unsigned long long id = __ldg(S.id + i);
+        T w, x[3], kx, ky, kz;
+        unsigned long long id;
+        if constexpr (STAGE) {
+            if (j + stride < n) stage(j + stride, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait_prev();                // this thread's copies of photon j have landed
+            const int t = threadIdx.x;
+            w = stg[buf][0][t];
+            x[0] = stg[buf][1][t]; x[1] = stg[buf][2][t]; x[2] = stg[buf][3][t];
+            kx = stg[buf][4][t]; ky = stg[buf][5][t]; kz = stg[buf][6][t];
+            id = (unsigned long long)__float_as_uint(stg[buf][7][t]) |
+                 ((unsigned long long)__float_as_uint(stg[buf][8][t]) << 32);
+        } else {
+            // all loads issued together (live photons are the rule: the photons
+            // that converted were removed at the end of the previous step)
+            w = ld<T>(S.w, i);
+            x[0] = ld<T>(S.x, i); x[1] = ld<T>(S.y, i); x[2] = ld<T>(S.z, i);
+            kx = ld<T>(S.px, i); ky = ld<T>(S.py, i); kz = ld<T>(S.pz, i);
+            id = __ldg(S.id + i);
+        }
         if (!(w > (T)0)) continue;
         double tau = FRESH ? 0.0 : S.tau[i];
         const T kv[3] = {kx, ky, kz};
