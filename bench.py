@@ -36,9 +36,10 @@ EMIT_BYTES = {"fp32": 8 + 7 * 4 + 8 + 4 + 8, "fp64": 8 + 7 * 8 + 8 + 4 + 8}
 PHOTON_BYTES = {"fp32": 4 + 3 * 4 + 3 * 4 + 8 + 3 * 4, "fp64": 8 + 3 * 8 + 3 * 8 + 8 + 3 * 8}
 PAIR_BYTES = {"fp32": 4 + 2 * (7 * 4 + 8 + 4 + 8), "fp64": 8 + 2 * (7 * 8 + 8 + 4 + 8)}
 # DRAM bytes (read + write) per photon-step of the step-start photon pass,
-# from one ncu capture (profiles/k_photon_pass_fp32_rotating_e_cascade.md);
-# None until the current kernel has been captured
-NCU_PHOTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
+# from one ncu capture of the current kernel (696 MB for a launch over the
+# ~1.5e7 capped photons of the 0.3-scale cascade; see
+# profiles/k_photon_pass_fp32_rotating_e_cascade.md); None when not captured
+NCU_PHOTON_BYTES_PER_STEP = {"fp32": 46.4, "fp64": None}
 
 
 def parse():
