@@ -383,6 +383,20 @@ def e2e_run(w, precision, warm, steps):
     return ps, a.elapsed_time(b), wall, nb
 
 
+def reduce_over_ranks(particle_steps, events, secs, world):
+    """Whole-job totals: work summed over the ranks, time the slowest rank's
+    (each rank runs its own replica; no data-path exchange)."""
+    if world <= 1:
+        return particle_steps, events, secs
+    import torch
+    import torch.distributed as dist
+    s = torch.tensor([particle_steps, events], dtype=torch.float64)
+    t = torch.tensor([secs], dtype=torch.float64)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(s[0]), float(s[1]), float(t[0])
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -441,14 +455,8 @@ def main():
         ms, wall, tot, counts = gpu_run(args, w, args.precision, warm, steps)
     torch.cuda.synchronize()
     secs = ms / 1e3
-    work = torch.tensor([float(tot["particle_steps"]), float(tot["emit_events"] + tot["pair_events"]), secs])
-    if world > 1:
-        t = torch.tensor([secs])
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        s = work[:2].clone()
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        work = torch.cat([s, t])
-    ps_total, ev_total, tmax = float(work[0]), float(work[1]), float(work[2])
+    ps_total, ev_total, tmax = reduce_over_ranks(float(tot["particle_steps"]),
+                                                 float(tot["emit_events"] + tot["pair_events"]), secs, world)
 
     fp64 = None
     if args.compare_fp64 and args.precision == "fp32" and world == 1:
@@ -557,16 +565,7 @@ def batched_main(args, ws, warm, steps, rank, world, cpu):
     import torch
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         ms, st, counts, tuned = batch_run(ws, args.precision, warm, steps)
-    secs = ms / 1e3
-    ps = float(st["particle_steps"])
-    ev = float(st["emit_events"])
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([secs])
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        s = torch.tensor([ps, ev])
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        secs, ps, ev = float(t[0]), float(s[0]), float(s[1])
+    ps, ev, secs = reduce_over_ranks(float(st["particle_steps"]), float(st["emit_events"]), ms / 1e3, world)
     if rank != 0:
         return
     n_lep = sum(len(w.species[0]["id"]) for w in ws)
