@@ -87,8 +87,9 @@ def capacities(w, nsteps=None):
     nsteps = w.nsteps if nsteps is None else nsteps
     n0 = sum(len(s["id"]) for s in w.species)
     if w.thin_cap:
-        c = int(1.6 * w.thin_cap) + 4 * n0
-        return [c // 3 + n0, c // 3, c]
+        # each species is leveled at the cap after a step: room for the cap
+        # plus one step's growth (photons grow fastest)
+        return [int(1.3 * w.thin_cap) + 4 * n0, int(1.3 * w.thin_cap) + 4 * n0, int(1.6 * w.thin_cap) + 4 * n0]
     return [n0, 16, int(n0 * (1 + 0.15 * nsteps)) + 1024]
 
 

@@ -51,6 +51,7 @@ struct BatchArgs {
     unsigned long long seed;
     PhiloxKeys keys;               // round keys of seed
     int soft_filter;
+    int budget;                    // new steps a particle starts before it is queued again
 };
 
 // field view of one ensemble at one step (eval_field's argument block)
@@ -61,6 +62,8 @@ struct FieldView {
     double t_n;
     float t_n_red_f;
 };
+
+constexpr unsigned PENDING = 0x80000000u;   // stack item flag: the particle is at an event
 
 template <class T, int NT> struct FusedStack {
     static constexpr int Q = 2 * NT;
@@ -81,6 +84,10 @@ struct FusedCtx {
     const float *coef_f;
     const double *coef_d;
 };
+
+// steps a particle runs before it rejoins the block's queue (bounds the
+// work one lane does between block barriers)
+constexpr int BATCH_STEP_BUDGET = 4;
 
 template <class T> __device__ __forceinline__ const T *coef_of(const FusedCtx &c);
 template <> __device__ __forceinline__ const float *coef_of<float>(const FusedCtx &c) { return c.coef_f; }
@@ -140,24 +147,29 @@ __device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView
     return true;
 }
 
-// Carry a particle forward from (step, tau) until its next event (true) or
-// the end of the call (false).  fresh: tau == 0 at the start of `step`.
+// Carry a particle forward from (step, tau) until its next event
+// (RUN_EVENT), the end of the call (RUN_END), or until it has started
+// `budget` new steps (RUN_MORE: resume fresh at the start of `step`).
+// fresh: tau == 0 at the start of `step`.  The budget bounds the work of
+// one item, so the lanes of a block stay busy between block barriers.
+constexpr int RUN_END = 0, RUN_EVENT = 1, RUN_MORE = 2;
 template <class T>
-__device__ __forceinline__ bool fused_run(const FusedCtx &c, FieldView &v, T x[3], T p[3], T q, double &tau,
-                                          unsigned long long id, unsigned &step, unsigned &k, uint2 &rz, bool fresh,
-                                          unsigned &mx, unsigned &n64) {
+__device__ __forceinline__ int fused_run(const FusedCtx &c, FieldView &v, T x[3], T p[3], T q, double &tau,
+                                         unsigned long long id, unsigned &step, unsigned &k, uint2 &rz, bool fresh,
+                                         unsigned &mx, unsigned &n64) {
     const unsigned end = c.b.step0 + (unsigned)c.b.nsteps;
     if (!fresh) {
-        if (tau < c.b.dt && fused_advance<T, false>(c, v, x, p, q, tau, id, step, k, rz, n64)) return true;
+        if (tau < c.b.dt && fused_advance<T, false>(c, v, x, p, q, tau, id, step, k, rz, n64)) return RUN_EVENT;
         mx = max(mx, k);
         ++step;
     }
-    for (; step < end; ++step) {
+    for (unsigned started = 0; step < end; ++step, ++started) {
+        if (started >= (unsigned)c.b.budget) return RUN_MORE;
         set_step(v, c.b, step);
         k = 0;
-        if (fused_advance<T, true>(c, v, x, p, q, tau, id, step, 0u, rz, n64)) return true;
+        if (fused_advance<T, true>(c, v, x, p, q, tau, id, step, 0u, rz, n64)) return RUN_EVENT;
     }
-    return false;
+    return RUN_END;
 }
 
 template <class T>
@@ -233,12 +245,15 @@ __device__ __forceinline__ void fused_round(const FusedCtx &c, FusedStack<T, NT>
     unsigned k = 0, evtot = 0, step = 0;
     uint2 rz = make_uint2(0, 0);
     const bool mine = t < take;
+    bool pend = false;
     if (mine) {
         const int s = n - take + t;
         x[0] = q.x[0][s]; x[1] = q.x[1][s]; x[2] = q.x[2][s];
         p[0] = q.p[0][s]; p[1] = q.p[1][s]; p[2] = q.p[2][s];
         tau = q.tau[s]; id = q.id[s]; ref = q.ref[s]; w = q.w[s]; k = q.k[s]; evtot = q.evtot[s];
         step = q.step[s]; rz = q.r[s];
+        pend = (k & PENDING) != 0u;     // at an event (else: resume at the start of `step`)
+        k &= ~PENDING;
     }
     __syncthreads();
     if (t == 0) q.n = n - take;
@@ -249,15 +264,16 @@ __device__ __forceinline__ void fused_round(const FusedCtx &c, FusedStack<T, NT>
         const EnsDev &e = c.b.ens[ens];
         FieldView v;
         load_view(v, e, c.b, step);
-        fused_emit<T>(c, e, ens, v, x, p, tau, w, id, step, k, rz, n64);
-        ++k;
-        ++evtot;
-        ++ev;
+        if (pend) {
+            fused_emit<T>(c, e, ens, v, x, p, tau, w, id, step, k, rz, n64);
+            ++k;
+            ++evtot;
+            ++ev;
+        }
         const T qch = sp ? (T)1 : (T)-1;
-        if (fused_run<T>(c, v, x, p, qch, tau, id, step, k, rz, false, mx, n64))
-            fused_push<T, NT>(q, x, p, tau, id, ref, w, k, evtot, step, rz);
-        else
-            fused_finish<T>(e, sp, i, x, p, evtot);
+        const int r = fused_run<T>(c, v, x, p, qch, tau, id, step, k, rz, !pend, mx, n64);
+        if (r == RUN_END) fused_finish<T>(e, sp, i, x, p, evtot);
+        else fused_push<T, NT>(q, x, p, tau, id, ref, w, r == RUN_EVENT ? (k | PENDING) : k, evtot, step, rz);
     }
     __syncthreads();
 }
@@ -314,10 +330,9 @@ __global__ void __launch_bounds__(NT) k_emission_fused(BatchArgs b) {
                 uint2 rz = make_uint2(0, 0);
                 my_ps += (unsigned long long)b.nsteps;
                 const T qch = sp ? (T)1 : (T)-1;
-                if (fused_run<T>(c, v, x, p, qch, tau, id, step, k, rz, true, my_max, n64))
-                    fused_push<T, NT>(q, x, p, tau, id, ref, w, 0u, 0u, step, rz);
-                else
-                    fused_finish<T>(e, sp, i, x, p, 0u);
+                const int r = fused_run<T>(c, v, x, p, qch, tau, id, step, k, rz, true, my_max, n64);
+                if (r == RUN_END) fused_finish<T>(e, sp, i, x, p, 0u);
+                else fused_push<T, NT>(q, x, p, tau, id, ref, w, r == RUN_EVENT ? PENDING : 0u, 0u, step, rz);
             }
         }
         __syncthreads();
@@ -483,6 +498,7 @@ static qed_status batch_impl(qed_ctx *ctx, qed_particles *ens, const qed_field_d
     b.t_red_f = w->tr_d;
     b.seed = ctx->cfg.seed;
     b.keys = philox_keys(ctx->cfg.seed);
+    b.budget = BATCH_STEP_BUDGET;
     b.soft_filter = ctx->cfg.soft_photon_filter;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (ctx->cfg.profile) {

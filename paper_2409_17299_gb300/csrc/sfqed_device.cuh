@@ -137,9 +137,23 @@ template <> struct Uniform<float> {
         u = fmaf(__uint2float_rn(a), 0x1p-32f, fmaf(__uint2float_rn(b >> 12), 0x1p-52f, 0x1p-53f));
         v = fmaf(__uint2float_rn(~a), 0x1p-32f, fmaf(__uint2float_rn((~b) >> 12), 0x1p-52f, 0x1p-53f));
     }
-    // -ln u, from v = 1 - u when u is near 1 (below 1/2 the fast logarithm
-    // is within 3 ulp)
-    static __device__ __forceinline__ float neglog(float u, float v) { return u < 0.5f ? -__logf(u) : -log1pf(-v); }
+    // -ln u.  Below 1/2 the hardware logarithm (within 3 ulp).  Above, from
+    // v = 1 - u (held to full relative precision): -ln(1 - v) = 2 atanh(z)
+    // with z = v / (2 - v) in (0, 1/3], summed as the odd series
+    // 2 (z + z^3/3 + ... + z^13/13); the first omitted term is below 1e-8
+    // of the sum.
+    static __device__ __forceinline__ float neglog(float u, float v) {
+        if (u < 0.5f) return -__logf(u);
+        const float z = __fdividef(v, 2.0f - v), z2 = z * z;
+        float t = 1.0f / 13.0f;
+        t = fmaf(t, z2, 1.0f / 11.0f);
+        t = fmaf(t, z2, 1.0f / 9.0f);
+        t = fmaf(t, z2, 1.0f / 7.0f);
+        t = fmaf(t, z2, 1.0f / 5.0f);
+        t = fmaf(t, z2, 1.0f / 3.0f);
+        t = fmaf(t, z2, 1.0f);
+        return 2.0f * z * t;
+    }
 };
 
 // ---------------------------------------------------------------------------
