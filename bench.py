@@ -211,7 +211,36 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_params=None):
+def size_cascade(w, nsteps, precision):
+    """Buffer capacities that hold every step of the run: one untimed pass
+    over the whole cascade, growing a species by 5% beyond the demand
+    whenever a step overflows (the step is replayed identically)."""
+    import torch
+    import paper_2409_17299_gb300 as q
+    prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
+    cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
+                        restore_on_overflow=1)
+    gen = q.Generator(cfg)
+    ens = q.DeviceEnsemble.from_host(w.species, capacities(w, nsteps), prec)
+    field = q.make_field(w.field_kind, w.field_prm)
+    for s in range(nsteps):
+        while True:
+            P = ens.struct()
+            rc, st = q.qed_push_and_generate(gen.ctx, P, field, w.dt, 1, s)
+            ens.pull_counts(P)
+            if rc == q.QED_OK:
+                break
+            if rc != q.QED_ERR_CAPACITY:
+                raise q.QedError(rc, "qed_push_and_generate", st)
+            ens.grow([max(ens.capacity[k], int(1.05 * st["needed_capacity"][k]) + 1024) for k in range(3)])
+    caps = list(ens.capacity)
+    gen.close()
+    del ens
+    torch.cuda.empty_cache()
+    return caps
+
+
+def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_params=None, caps=None):
     import torch
     import paper_2409_17299_gb300 as q
     prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
@@ -222,7 +251,7 @@ def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_param
     gen = q.Generator(cfg)
     if mlp_params is not None:
         q.qed_mlp_set_params(gen.ctx, mlp_params)
-    ens = q.DeviceEnsemble.from_host(w.species, capacities(w, warm + steps), prec)
+    ens = q.DeviceEnsemble.from_host(w.species, caps or capacities(w, warm + steps), prec)
     field = q.make_field(w.field_kind, w.field_prm)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -319,7 +348,7 @@ def batch_run(ws, precision, warm, steps, tune=True):
     return ms, st, counts, tuned
 
 
-def e2e_run(w, precision, warm, steps):
+def e2e_run(w, precision, warm, steps, caps=None):
     """Same steps through the C ABI with the ensemble in pinned host memory:
     every step copies it to the device, pushes one step, and copies it back."""
     import numpy as np
@@ -329,7 +358,7 @@ def e2e_run(w, precision, warm, steps):
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
                         restore_on_overflow=0)
     gen = q.Generator(cfg)
-    caps = capacities(w, warm + steps)
+    caps = caps or capacities(w, warm + steps)
     dev = q.DeviceEnsemble(caps, prec)
     fd = dev.fdtype
     host = []
@@ -449,11 +478,12 @@ def main():
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
 
+    caps = size_cascade(w, warm + steps, args.precision) if w.push_photons else None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        ms, wall, tot, counts = gpu_run(args, w, args.precision, warm, steps)
+        ms, wall, tot, counts = gpu_run(args, w, args.precision, warm, steps, caps=caps)
     torch.cuda.synchronize()
     secs = ms / 1e3
     ps_total, ev_total, tmax = reduce_over_ranks(float(tot["particle_steps"]),
@@ -461,7 +491,7 @@ def main():
 
     fp64 = None
     if args.compare_fp64 and args.precision == "fp32" and world == 1:
-        ms64, wall64, tot64, _ = gpu_run(args, w, "fp64", warm, steps)
+        ms64, wall64, tot64, _ = gpu_run(args, w, "fp64", warm, steps, caps=caps)
         fp64 = {"value": tot64["particle_steps"] / (ms64 / 1e3), "events_per_s":
                 (tot64["emit_events"] + tot64["pair_events"]) / (ms64 / 1e3), "ms_per_step": ms64 / steps}
 
@@ -476,7 +506,7 @@ def main():
         train_s = time.perf_counter() - t0
         P = q.qed_mlp_get_params(tg.ctx)
         tg.close()
-        ms_m, _, tot_m, _ = gpu_run(args, w, args.precision, warm, steps, mlp_params=P)
+        ms_m, _, tot_m, _ = gpu_run(args, w, args.precision, warm, steps, mlp_params=P, caps=caps)
         mlp = {"value": tot_m["particle_steps"] / (ms_m / 1e3),
                "events_per_s": (tot_m["emit_events"] + tot_m["pair_events"]) / (ms_m / 1e3),
                "ms_per_step": ms_m / steps, "lepton_kernel_ms": tot_m["kernel_ms"][0],
@@ -485,7 +515,7 @@ def main():
 
     e2e = None
     if args.e2e:
-        ps_e, ms_e, wall_e, nb = e2e_run(w, args.precision, warm, steps)
+        ps_e, ms_e, wall_e, nb = e2e_run(w, args.precision, warm, steps, caps=caps)
         e2e = {"value": ps_e / (ms_e / 1e3) * world, "unit": "particle-steps/s",
                "h2d_bytes_per_step": nb[0] // max(1, steps), "d2h_bytes_per_step": nb[1] // max(1, steps)}
 

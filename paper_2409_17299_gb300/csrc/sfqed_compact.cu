@@ -473,20 +473,21 @@ __global__ void __launch_bounds__(LT) k_tile_dead(SpeciesDev S, DevCtl *ctl, int
     unsigned cnt = 0, removed = 0;
 #pragma unroll
     for (int c0 = 0; c0 < LROUNDS; c0 += 8) {
+        // weights and (leveling) ids of eight entries issued together: at
+        // the cap nearly every entry is below w* and needs its id
         T v[8];
+        unsigned long long idv[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const unsigned long long i = wbase + (c0 + r) * 32 + lane;
             v[r] = i < n ? ld<T>(S.w, i) : (T)0;
+            idv[r] = (LEVEL && thin && i < n) ? S.id[i] : 0ull;
         }
-        unsigned long long idv[8];
         bool below[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            const unsigned long long i = wbase + (c0 + r) * 32 + lane;
             if constexpr (sizeof(T) == 4) below[r] = LEVEL && thin && v[r] > (T)0 && (float)v[r] < wup;
             else below[r] = LEVEL && thin && v[r] > (T)0 && (double)v[r] < wstar;
-            idv[r] = below[r] ? S.id[i] : 0ull;
         }
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
