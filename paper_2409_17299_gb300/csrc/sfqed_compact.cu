@@ -195,6 +195,7 @@ __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned
 // moves toward it; a bisection bracket keeps every step inside [lo, hi].
 // Block partial sums are reduced in a fixed order (deterministic result).
 constexpr int LEVEL_ITERS = 40;
+constexpr int LEVEL_DEVICE_PASSES = 4;   // full-device Newton passes launched per leveling
 
 // smallest float >= a positive double (v < d <=> v < ceil_f(d) for floats v)
 __host__ __device__ __forceinline__ float ceil_f(double d) {
@@ -296,16 +297,15 @@ __host__ __device__ void lev_advance(LevelIter &it, double A, unsigned long long
 // (a fixed order: the result does not depend on which block is last) and
 // advances the iteration, so a pass is one launch and needs no host.
 constexpr int LEV_T = 256;
+
+// This thread's share of the sums at it.w over entries t0, t0 + stride, ...
 template <class T>
-__global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl *ctl, int s, LevelWork *lw,
-                                                    long long cap) {
-    LevelIter &it = lw->it[s];
-    if (*reinterpret_cast<volatile unsigned long long *>(&it.done)) return;
-    const unsigned long long n = ctl->count[s];
-    const unsigned long long t0 = (unsigned long long)blockIdx.x * LEV_T + threadIdx.x;
-    const unsigned long long stride = (unsigned long long)gridDim.x * LEV_T;
-    double A;
-    unsigned long long C = 0, N = 0, M = 0;
+__device__ __forceinline__ void lev_accumulate(const void *w, unsigned long long n, unsigned long long t0,
+                                               unsigned long long stride, const LevelIter &it, double &A,
+                                               unsigned long long &C, unsigned long long &N, unsigned long long &M) {
+    C = 0;
+    N = 0;
+    M = 0;
     if constexpr (sizeof(T) == 4) {
         // FP32 weights: exact float comparisons and float-float sums, no FP64 per element
         const float wc = it.w_up;
@@ -360,6 +360,23 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
             }
         }
     }
+}
+
+// One pass of the iteration.  Every block sums its share of the weights at
+// it.w; the last block to finish reduces the block partials in block order
+// (a fixed order: the result does not depend on which block is last) and
+// advances the iteration, so a pass is one launch and needs no host.
+template <class T>
+__global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl *ctl, int s, LevelWork *lw,
+                                                    long long cap) {
+    LevelIter &it = lw->it[s];
+    if (*reinterpret_cast<volatile unsigned long long *>(&it.done)) return;
+    const unsigned long long n = ctl->count[s];
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * LEV_T + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * LEV_T;
+    double A;
+    unsigned long long C, N, M;
+    lev_accumulate<T>(w, n, t0, stride, it, A, C, N, M);
     __shared__ double sA[LEV_T / 32];
     __shared__ unsigned long long sC[LEV_T / 32], sN[LEV_T / 32], sM[LEV_T / 32];
     __shared__ int s_last;
@@ -426,6 +443,47 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
             lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap);
         }
         lw->arrive[s] = 0;
+    }
+}
+
+// Completes an iteration the fixed number of k_lev_step launches left
+// unfinished (rare: weights spread over many pieces), with one block: the
+// same sums in a fixed order, the same Newton step.  A no-op once done.
+template <class T>
+__global__ void __launch_bounds__(LEV_T) k_lev_finish(const void *w, const DevCtl *ctl, int s, LevelWork *lw,
+                                                      long long cap) {
+    LevelIter &it = lw->it[s];
+    const unsigned long long n = ctl->count[s];
+    __shared__ double rh[LEV_T], rl[LEV_T];
+    __shared__ unsigned long long rc[LEV_T], rn[LEV_T], rm[LEV_T];
+    __shared__ int s_done;
+    const int t = threadIdx.x;
+    for (;;) {
+        if (t == 0) s_done = it.done || it.iters >= LEVEL_ITERS;
+        __syncthreads();
+        if (s_done) return;
+        double A;
+        unsigned long long C, N, M;
+        lev_accumulate<T>(w, n, t, LEV_T, it, A, C, N, M);
+        rh[t] = A; rl[t] = 0.0; rc[t] = C; rn[t] = N; rm[t] = M;
+        __syncthreads();
+        for (int o = LEV_T / 2; o > 0; o >>= 1) {
+            if (t < o) {
+                DD x;
+                x.hi = rh[t];
+                x.lo = rl[t];
+                x.add(rh[t + o]);
+                x.lo += rl[t + o];
+                rh[t] = x.hi;
+                rl[t] = x.lo;
+                rc[t] += rc[t + o];
+                rn[t] += rn[t + o];
+                rm[t] = max(rm[t], rm[t + o]);
+            }
+            __syncthreads();
+        }
+        if (t == 0) lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap);
+        __syncthreads();
     }
 }
 
@@ -705,19 +763,13 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     int blocks = ctx->sm_count * 4;
     blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
     k_lev_begin<<<1, 1, 0, st>>>(ctx->lev, s);
-    SFQ_LAUNCHED(ctx, 1);
-    // passes in chunks of three (a pass after convergence returns at once);
-    // the host reads the done flag between chunks (two to five passes are typical)
-    for (int it = 0; it < LEVEL_ITERS; it += 3) {
-        for (int c = 0; c < 3; ++c) k_lev_step<T><<<blocks, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
-        SFQ_LAUNCHED(ctx, 3);
-        SFQ_CUDA(cudaMemcpyAsync(ctx->pin, &ctx->lev->it[s].done, sizeof(unsigned long long),
-                                 cudaMemcpyDeviceToHost, st));
-        const auto t0 = std::chrono::steady_clock::now();
-        SFQ_CUDA(cudaStreamSynchronize(st));
-        ctx->sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        if (ctx->pin[0]) break;
-    }
+    // a fixed number of full-device passes (two to three are typical; a pass
+    // after convergence returns at once), then a one-block finisher for the
+    // rare iteration that needs more: no host round trip
+    for (int c = 0; c < LEVEL_DEVICE_PASSES; ++c)
+        k_lev_step<T><<<blocks, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
+    k_lev_finish<T><<<1, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
+    SFQ_LAUNCHED(ctx, 2 + LEVEL_DEVICE_PASSES);
     SFQ_CUDA(cudaGetLastError());
     return compact_tiles<T, true>(ctx, sp, s, step);
 }

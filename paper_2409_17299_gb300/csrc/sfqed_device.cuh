@@ -241,10 +241,23 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 }
 
 // zero: 1 if B = 0 everywhere (then chi^2 R^2 = [E^2] + |p x E|^2, a sum of
-// squares), 2 if E = 0 everywhere (chi^2 R^2 = |p x B|^2), else 0.
+// squares), 2 if E = 0 everywhere (chi^2 R^2 = |p x B|^2), 3 if E and B are
+// parallel everywhere (T = 2 e0 E.(p x B) = 2 e0 p.(B x E) = 0, so
+// chi^2 R^2 = S, again a sum of squares), else 0.
 template <bool LEPTON>
 __device__ __forceinline__ float chi_guarded(float e0, const float p[3], const float E[3], const float B[3],
                                              unsigned *fp64_used, int zero = 0) {
+    if (zero == 3) {
+        const float ax = diff_of_products(p[1], E[2], p[2], E[1]);
+        const float ay = diff_of_products(p[2], E[0], p[0], E[2]);
+        const float az = diff_of_products(p[0], E[1], p[1], E[0]);
+        const float bx = diff_of_products(p[1], B[2], p[2], B[1]);
+        const float by = diff_of_products(p[2], B[0], p[0], B[2]);
+        const float bz = diff_of_products(p[0], B[1], p[1], B[0]);
+        float S = ax * ax + ay * ay + az * az + bx * bx + by * by + bz * bz;
+        if (LEPTON) S += E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
+        return sqrtf(S) * (float)(1.0 / RS);
+    }
     if (zero == 1) {
         const float ax = diff_of_products(p[1], E[2], p[2], E[1]);
         const float ay = diff_of_products(p[2], E[0], p[0], E[2]);

@@ -87,7 +87,7 @@ struct PassArgs {
     const void *icdf_pair;  // PAIR_NCHI * PAIR_NS (T)
     const __nv_bfloat16 *mlp_w16;   // surrogate network weights, or null (table sampler)
     int field_kind;
-    int field_zero;         // 1: B = 0 everywhere, 2: E = 0 everywhere, else 0 (chi shortcuts)
+    int field_zero;         // chi shortcut: 1 B = 0, 2 E = 0, 3 E parallel to B (everywhere), else 0
     double prm[6];
     float prm_f[6];         // prm rounded to float once (FP32 mode)
     double dt;
