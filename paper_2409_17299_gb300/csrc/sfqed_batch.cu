@@ -30,6 +30,7 @@ struct EnsDev {
     unsigned long long tile0;      // first global tile of this ensemble
     unsigned long long ph_cap;
     int kind;
+    int zero;                      // chi shortcut of the field (see chi_guarded)
     double prm[6];
     float prm_f[6];
 };
@@ -54,12 +55,17 @@ struct BatchArgs {
     int budget;                    // new steps a particle starts before it is queued again
 };
 
-// field view of one ensemble at one step (eval_field's argument block)
-struct FieldView {
-    int field_kind;
+// field view of one ensemble at one step (eval_field's argument block),
+// holding only what the precision reads (it stays in registers across steps)
+template <class T> struct FieldView;
+template <> struct FieldView<double> {
+    int field_kind, field_zero;
     double prm[6];
-    float prm_f[6];
     double t_n;
+};
+template <> struct FieldView<float> {
+    int field_kind, field_zero;
+    float prm_f[6];
     float t_n_red_f;
 };
 
@@ -93,21 +99,26 @@ template <class T> __device__ __forceinline__ const T *coef_of(const FusedCtx &c
 template <> __device__ __forceinline__ const float *coef_of<float>(const FusedCtx &c) { return c.coef_f; }
 template <> __device__ __forceinline__ const double *coef_of<double>(const FusedCtx &c) { return c.coef_d; }
 
-__device__ __forceinline__ void load_view(FieldView &v, const EnsDev &e, const BatchArgs &b, unsigned step) {
-    v.field_kind = e.kind;
-    for (int i = 0; i < 6; ++i) { v.prm[i] = e.prm[i]; v.prm_f[i] = e.prm_f[i]; }
-    v.t_n = b.t_n[step - b.step0];
-    v.t_n_red_f = b.t_red_f[step - b.step0];
+template <class T>
+__device__ __forceinline__ void set_step(FieldView<T> &v, const BatchArgs &b, unsigned step) {
+    if constexpr (sizeof(T) == 8) v.t_n = b.t_n[step - b.step0];
+    else v.t_n_red_f = b.t_red_f[step - b.step0];
 }
 
-__device__ __forceinline__ void set_step(FieldView &v, const BatchArgs &b, unsigned step) {
-    v.t_n = b.t_n[step - b.step0];
-    v.t_n_red_f = b.t_red_f[step - b.step0];
+template <class T>
+__device__ __forceinline__ void load_view(FieldView<T> &v, const EnsDev &e, const BatchArgs &b, unsigned step) {
+    v.field_kind = e.kind;
+    v.field_zero = e.zero;
+    for (int i = 0; i < 6; ++i) {
+        if constexpr (sizeof(T) == 8) v.prm[i] = e.prm[i];
+        else v.prm_f[i] = e.prm_f[i];
+    }
+    set_step<T>(v, b, step);
 }
 
 // One waiting-time iteration (see the per-step pass): true = stopped at an event.
 template <class T, bool FRESH>
-__device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView &v, T x[3], T p[3], T q,
+__device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView<T> &v, T x[3], T p[3], T q,
                                               double &tau, unsigned long long id, unsigned step, unsigned k,
                                               uint2 &rz, unsigned &n64) {
     const BatchArgs &b = c.b;
@@ -120,7 +131,7 @@ __device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView
         chi = chi_fp64(gam, p[0], p[1], p[2], E[0], E[1], E[2], B[0], B[1], B[2]);
     } else {
         gam = sqrtf(1.0f + p2);
-        chi = chi_guarded<true>(gam, p, E, B, &n64);
+        chi = chi_guarded<true>(gam, p, E, B, &n64, v.field_zero);
     }
     const T lam = p2 > (T)0 ? (T)(ALPHA * RS) / gam * rate_em<T>(coef_of<T>(c), chi) : (T)0;
     T dth = (T)INFINITY;
@@ -154,7 +165,7 @@ __device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView
 // one item, so the lanes of a block stay busy between block barriers.
 constexpr int RUN_END = 0, RUN_EVENT = 1, RUN_MORE = 2;
 template <class T>
-__device__ __forceinline__ int fused_run(const FusedCtx &c, FieldView &v, T x[3], T p[3], T q, double &tau,
+__device__ __forceinline__ int fused_run(const FusedCtx &c, FieldView<T> &v, T x[3], T p[3], T q, double &tau,
                                          unsigned long long id, unsigned &step, unsigned &k, uint2 &rz, bool fresh,
                                          unsigned &mx, unsigned &n64) {
     const unsigned end = c.b.step0 + (unsigned)c.b.nsteps;
@@ -165,7 +176,7 @@ __device__ __forceinline__ int fused_run(const FusedCtx &c, FieldView &v, T x[3]
     }
     for (unsigned started = 0; step < end; ++step, ++started) {
         if (started >= (unsigned)c.b.budget) return RUN_MORE;
-        set_step(v, c.b, step);
+        set_step<T>(v, c.b, step);
         k = 0;
         if (fused_advance<T, true>(c, v, x, p, q, tau, id, step, 0u, rz, n64)) return RUN_EVENT;
     }
@@ -173,7 +184,7 @@ __device__ __forceinline__ int fused_run(const FusedCtx &c, FieldView &v, T x[3]
 }
 
 template <class T>
-__device__ __forceinline__ void fused_emit(const FusedCtx &c, const EnsDev &e, unsigned ens, const FieldView &v,
+__device__ __forceinline__ void fused_emit(const FusedCtx &c, const EnsDev &e, unsigned ens, const FieldView<T> &v,
                                            const T x[3], T p[3], double tau, T w, unsigned long long id,
                                            unsigned step, unsigned k, uint2 rz, unsigned &n64) {
     const BatchArgs &b = c.b;
@@ -186,7 +197,7 @@ __device__ __forceinline__ void fused_emit(const FusedCtx &c, const EnsDev &e, u
         chi = chi_fp64(gam, p[0], p[1], p[2], E[0], E[1], E[2], B[0], B[1], B[2]);
     } else {
         gam = sqrtf(1.0f + p2);
-        chi = chi_guarded<true>(gam, p, E, B, &n64);
+        chi = chi_guarded<true>(gam, p, E, B, &n64, v.field_zero);
     }
     T om, ue, ve;
     Uniform<T>::draw(rz.x, rz.y, ue, ve);
@@ -262,8 +273,8 @@ __device__ __forceinline__ void fused_round(const FusedCtx &c, FusedStack<T, NT>
         const unsigned ens = (unsigned)(ref >> 40), sp = (unsigned)(ref >> 39) & 1u;
         const unsigned long long i = ref & ((1ull << 39) - 1);
         const EnsDev &e = c.b.ens[ens];
-        FieldView v;
-        load_view(v, e, c.b, step);
+        FieldView<T> v;
+        load_view<T>(v, e, c.b, step);
         if (pend) {
             fused_emit<T>(c, e, ens, v, x, p, tau, w, id, step, k, rz, n64);
             ++k;
@@ -279,7 +290,7 @@ __device__ __forceinline__ void fused_round(const FusedCtx &c, FusedStack<T, NT>
 }
 
 template <class T, int NT>
-__global__ void __launch_bounds__(NT) k_emission_fused(BatchArgs b) {
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 128 ? 7 : 1)) k_emission_fused(BatchArgs b) {
     __shared__ T s_coef[NCOEF];
     __shared__ FusedStack<T, NT> q;
     __shared__ unsigned long long s_tile;
@@ -323,8 +334,8 @@ __global__ void __launch_bounds__(NT) k_emission_fused(BatchArgs b) {
                 T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
                 const unsigned long long id = __ldg(S.id + i);
                 const unsigned long long ref = ((unsigned long long)ens << 40) | ((unsigned long long)sp << 39) | i;
-                FieldView v;
-                load_view(v, e, b, b.step0);
+                FieldView<T> v;
+                load_view<T>(v, e, b, b.step0);
                 double tau = 0.0;
                 unsigned step = b.step0, k = 0;
                 uint2 rz = make_uint2(0, 0);
@@ -465,6 +476,7 @@ static qed_status batch_impl(qed_ctx *ctx, qed_particles *ens, const qed_field_d
         tiles += (d.n_lep[0] + d.n_lep[1] + nt - 1) / nt;
         d.kind = fields[k].kind;
         for (int i = 0; i < 6; ++i) { d.prm[i] = fields[k].params[i]; d.prm_f[i] = (float)fields[k].params[i]; }
+        d.zero = field_zero_of(fields[k]);
         w->cnt_h[k] = (unsigned long long)P.s[2].count;
     }
     w->cnt_h[n_ens] = 0;

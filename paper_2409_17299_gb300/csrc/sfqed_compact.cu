@@ -195,7 +195,6 @@ __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned
 // moves toward it; a bisection bracket keeps every step inside [lo, hi].
 // Block partial sums are reduced in a fixed order (deterministic result).
 constexpr int LEVEL_ITERS = 40;
-constexpr int LEVEL_DEVICE_PASSES = 4;   // full-device Newton passes launched per leveling
 
 // smallest float >= a positive double (v < d <=> v < ceil_f(d) for floats v)
 __host__ __device__ __forceinline__ float ceil_f(double d) {
@@ -443,47 +442,6 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
             lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap);
         }
         lw->arrive[s] = 0;
-    }
-}
-
-// Completes an iteration the fixed number of k_lev_step launches left
-// unfinished (rare: weights spread over many pieces), with one block: the
-// same sums in a fixed order, the same Newton step.  A no-op once done.
-template <class T>
-__global__ void __launch_bounds__(LEV_T) k_lev_finish(const void *w, const DevCtl *ctl, int s, LevelWork *lw,
-                                                      long long cap) {
-    LevelIter &it = lw->it[s];
-    const unsigned long long n = ctl->count[s];
-    __shared__ double rh[LEV_T], rl[LEV_T];
-    __shared__ unsigned long long rc[LEV_T], rn[LEV_T], rm[LEV_T];
-    __shared__ int s_done;
-    const int t = threadIdx.x;
-    for (;;) {
-        if (t == 0) s_done = it.done || it.iters >= LEVEL_ITERS;
-        __syncthreads();
-        if (s_done) return;
-        double A;
-        unsigned long long C, N, M;
-        lev_accumulate<T>(w, n, t, LEV_T, it, A, C, N, M);
-        rh[t] = A; rl[t] = 0.0; rc[t] = C; rn[t] = N; rm[t] = M;
-        __syncthreads();
-        for (int o = LEV_T / 2; o > 0; o >>= 1) {
-            if (t < o) {
-                DD x;
-                x.hi = rh[t];
-                x.lo = rl[t];
-                x.add(rh[t + o]);
-                x.lo += rl[t + o];
-                rh[t] = x.hi;
-                rl[t] = x.lo;
-                rc[t] += rc[t + o];
-                rn[t] += rn[t + o];
-                rm[t] = max(rm[t], rm[t + o]);
-            }
-            __syncthreads();
-        }
-        if (t == 0) lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap);
-        __syncthreads();
     }
 }
 
@@ -763,13 +721,26 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     int blocks = ctx->sm_count * 4;
     blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
     k_lev_begin<<<1, 1, 0, st>>>(ctx->lev, s);
-    // a fixed number of full-device passes (two to three are typical; a pass
-    // after convergence returns at once), then a one-block finisher for the
-    // rare iteration that needs more: no host round trip
-    for (int c = 0; c < LEVEL_DEVICE_PASSES; ++c)
-        k_lev_step<T><<<blocks, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
-    k_lev_finish<T><<<1, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
-    SFQ_LAUNCHED(ctx, 2 + LEVEL_DEVICE_PASSES);
+    SFQ_LAUNCHED(ctx, 1);
+    // passes in chunks (a pass after convergence returns at once); the host
+    // reads the done flag and the pass count between chunks.  A chunk is as
+    // long as the previous leveling of this species needed, so one check
+    // usually suffices.
+    int chunk = ctx->lev_chunk[s] >= 2 ? ctx->lev_chunk[s] : 3;
+    for (int launched = 0; launched < LEVEL_ITERS; launched += chunk, chunk = 2) {
+        for (int c = 0; c < chunk; ++c)
+            k_lev_step<T><<<blocks, LEV_T, 0, st>>>(sp->w, ctx->ctl, s, ctx->lev, (long long)cap);
+        SFQ_LAUNCHED(ctx, chunk);
+        // done and iters are adjacent words of the iteration state
+        SFQ_CUDA(cudaMemcpyAsync(ctx->pin, &ctx->lev->it[s].done, 2 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        const auto t0 = std::chrono::steady_clock::now();
+        SFQ_CUDA(cudaStreamSynchronize(st));
+        ctx->sync_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ctx->pin[0]) break;
+    }
+    const int used = (int)ctx->pin[1];
+    ctx->lev_chunk[s] = used < 2 ? 2 : (used > 12 ? 12 : used);
     SFQ_CUDA(cudaGetLastError());
     return compact_tiles<T, true>(ctx, sp, s, step);
 }

@@ -72,6 +72,19 @@ struct PhiloxKeys {
     uint32_t k[20];
 };
 
+// chi shortcut a field allows everywhere: 1 B = 0, 2 E = 0, 3 E parallel
+// to B (the standing circularly polarised wave), 0 none
+inline int field_zero_of(const qed_field_desc &f) {
+    if (f.kind == QED_FIELD_ROTATING_E) return 1;
+    if (f.kind == QED_FIELD_STANDING_CP) return 3;
+    if (f.kind == QED_FIELD_UNIFORM) {
+        const double *q = f.params;
+        if (q[3] == 0.0 && q[4] == 0.0 && q[5] == 0.0) return 1;
+        if (q[0] == 0.0 && q[1] == 0.0 && q[2] == 0.0) return 2;
+    }
+    return 0;
+}
+
 struct SpeciesDev {
     void *x, *y, *z, *px, *py, *pz, *w;
     unsigned long long *id;
@@ -146,6 +159,7 @@ struct qed_ctx {
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
     int tuned_threads;           // block shape picked by the autotuner (0: none yet)
     int spec_passes;             // newborn passes enqueued per host check (from the last step)
+    int lev_chunk[3];            // leveling passes enqueued per host check (from the last leveling)
     // surrogate network: FP32 master parameters, Adam moments and gradient
     // (4 x 8577 floats), BF16 copy used by the kernels, loss accumulator
     float *mlp_p;

@@ -72,17 +72,15 @@ __device__ __forceinline__ void note_overflow(DevCtl *ctl, int s, unsigned long 
 // Algorithm 1 for electrons and positrons (both species of one pass).
 //
 // Divergence control (the GPU form of Algorithm 3's "sort handled particles
-// to the front"): each warp pushes its 32 particles of a 256-particle tile to
-// their first event or to the end of the step; particles at an event go to
-// the warp's own stack in shared memory.  Whenever the stack holds a full
-// round, the warp pops one item per lane and processes it densely: the event
+// to the front"): phase 1 pushes every particle of a 256-particle tile to its
+// first event or to the end of the step; particles at an event go to a
+// per-block stack in shared memory.  Whenever the stack holds a full round,
+// the block pops one item per thread and processes it densely: the event
 // (chi at the point, energy draw, recoil, photon append), then the next
 // waiting time, ending either at the step end (state stored) or at the next
-// event (pushed back).  The stacks are drained after the last tile.  Warps
-// never wait for one another (no block barrier after the prologue).
+// event (pushed back).  The stack is drained after the last tile.
 constexpr int LB = 256;            // threads per block of the lepton pass
-constexpr int WQ = 64;             // per-warp stack capacity: < 32 left + 32 pushed
-constexpr int LQ = (LB / 32) * WQ;
+constexpr int LQ = 2 * LB;         // stack capacity: < LB left + LB pushed
 
 template <class T> struct LeptonStack {
     T x[3][LQ], p[3][LQ];
@@ -92,6 +90,7 @@ template <class T> struct LeptonStack {
     unsigned idx[LQ];              // index | species << 31
     unsigned k[LQ];                // events so far in this step (the pending one not counted)
     uint2 r[LQ];                   // the pending event's energy draw words
+    int n;
 };
 
 template <class T> struct LeptonCtx {
@@ -201,45 +200,38 @@ __device__ __forceinline__ void finish(const PassArgs &a, unsigned idx, const T 
     if (k) S.nev[i] += k;
 }
 
-// Push the items of the lanes with `want` onto this warp's stack; wn is the
-// warp's item count (the same in every lane).  Every lane of the warp calls it.
 template <class T>
-__device__ __forceinline__ void warp_push(LeptonStack<T> &q, int &wn, bool want, const T x[3], const T p[3],
-                                          double tau, unsigned long long id, T w, unsigned idx, unsigned k,
-                                          uint2 rz) {
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (want) {
-        const unsigned lane = threadIdx.x & 31u;
-        const int slot = (int)(threadIdx.x >> 5) * WQ + wn + __popc(m & ((1u << lane) - 1u));
-        q.x[0][slot] = x[0]; q.x[1][slot] = x[1]; q.x[2][slot] = x[2];
-        q.p[0][slot] = p[0]; q.p[1][slot] = p[1]; q.p[2][slot] = p[2];
-        q.tau[slot] = tau; q.id[slot] = id; q.w[slot] = w; q.idx[slot] = idx; q.k[slot] = k; q.r[slot] = rz;
-    }
-    wn += __popc(m);
+__device__ __forceinline__ void stack_push(LeptonStack<T> &q, const T x[3], const T p[3], double tau,
+                                           unsigned long long id, T w, unsigned idx, unsigned k, uint2 rz) {
+    const int slot = atomicAdd(&q.n, 1);
+    q.x[0][slot] = x[0]; q.x[1][slot] = x[1]; q.x[2][slot] = x[2];
+    q.p[0][slot] = p[0]; q.p[1][slot] = p[1]; q.p[2][slot] = p[2];
+    q.tau[slot] = tau; q.id[slot] = id; q.w[slot] = w; q.idx[slot] = idx; q.k[slot] = k; q.r[slot] = rz;
 }
 
-// Pop min(wn, 32) items of this warp's stack, one per lane, and process each
-// to its next event or the step end.  Every lane of the warp calls this.
+// Pop min(n, LB) items, one per thread, and process each to its next event
+// or the step end.  Every thread of the block calls this.
 template <class T, bool MLP>
-__device__ __forceinline__ void warp_round(const LeptonCtx<T> &c, LeptonStack<T> &q, int &wn,
-                                           unsigned long long &ev, unsigned &mx, unsigned &n64,
-                                           const MlpInf &ms) {
-    const int lane = threadIdx.x & 31;
-    const int take = wn < 32 ? wn : 32;
+__device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T> &q, unsigned long long &ev,
+                                            unsigned &mx, unsigned &n64, const MlpInf &ms) {
+    const int n = q.n;
+    const int take = n < LB ? n : LB;
+    const int t = threadIdx.x;
     T x[3], p[3], w = 0;
     double tau = 0.0;
     unsigned long long id = 0;
     unsigned idx = 0, k = 0;
     uint2 rz = make_uint2(0, 0);
-    const bool mine = lane < take;
+    const bool mine = t < take;
     if (mine) {
-        const int s = (int)(threadIdx.x >> 5) * WQ + wn - take + lane;
+        const int s = n - take + t;
         x[0] = q.x[0][s]; x[1] = q.x[1][s]; x[2] = q.x[2][s];
         p[0] = q.p[0][s]; p[1] = q.p[1][s]; p[2] = q.p[2][s];
         tau = q.tau[s]; id = q.id[s]; w = q.w[s]; idx = q.idx[s]; k = q.k[s]; rz = q.r[s];
     }
-    __syncwarp();                  // every slot read before any is pushed again
-    wn -= take;
+    __syncthreads();
+    if (t == 0) q.n = n - take;
+    __syncthreads();
     if constexpr (MLP) {
         // event-point state per item, then the whole warp evaluates the
         // network for its 32 items on the tensor cores
@@ -271,19 +263,18 @@ __device__ __forceinline__ void warp_round(const LeptonCtx<T> &c, LeptonStack<T>
     } else {
         if (mine) emit<T>(c, x, p, tau, w, id, k, rz, n64);
     }
-    bool again = false;
     if (mine) {
         ++k;
         ++ev;
         const T qch = (idx >> 31) ? (T)1 : (T)-1;
-        again = tau < c.a.dt && advance<T, false>(c, x, p, qch, tau, id, k, rz, n64);
-        if (!again) {
+        if (tau < c.a.dt && advance<T, false>(c, x, p, qch, tau, id, k, rz, n64)) {
+            stack_push<T>(q, x, p, tau, id, w, idx, k, rz);
+        } else {
             finish<T>(c.a, idx, x, p, k);
             mx = max(mx, k);
         }
     }
-    warp_push<T>(q, wn, again, x, p, tau, id, w, idx, k, rz);
-    __syncwarp();
+    __syncthreads();
 }
 
 template <class T, bool FRESH, bool MLP>
@@ -294,8 +285,8 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
     MlpInf ms{nullptr, nullptr, nullptr};
     if constexpr (MLP) ms = mlp_stage(dyn, a.mlp_w16);
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    if (threadIdx.x == 0) q.n = 0;
     __syncthreads();
-    int wn = 0;                    // items on this warp's stack
     DevCtl *ctl = a.ctl;
     const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
     const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
@@ -338,10 +329,6 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
         const unsigned long long j = base + threadIdx.x;
         T w = (T)0, x[3], p[3];
         unsigned long long id = 0;
-        double tau = 0.0;
-        unsigned idx = 0;
-        uint2 rz = make_uint2(0, 0);
-        bool event = false;
         if constexpr (STAGE) {
             // this thread's staged particle, then the next tile's copies in
             // flight (the slots are free once read)
@@ -368,19 +355,25 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
                 id = __ldg(S.id + i);
             }
             if (w > (T)0) {
-                tau = FRESH ? 0.0 : S.tau[i];
-                idx = (unsigned)i | ((unsigned)s << 31);
+                double tau = FRESH ? 0.0 : S.tau[i];
+                const unsigned idx = (unsigned)i | ((unsigned)s << 31);
                 ++my_steps;
+                uint2 rz = make_uint2(0, 0);
                 const T qch = s == 0 ? (T)-1 : (T)1;
+                bool event;
                 if constexpr (FRESH) event = advance<T, true>(c, x, p, qch, tau, id, 0u, rz, n64);
                 else event = tau < a.dt && advance<T, false>(c, x, p, qch, tau, id, 0u, rz, n64);
-                if (!event) finish<T>(a, idx, x, p, 0u);
+                if (event) {
+                    stack_push<T>(q, x, p, tau, id, w, idx, 0u, rz);
+                } else {
+                    finish<T>(a, idx, x, p, 0u);
+                }
             }
         }
-        warp_push<T>(q, wn, event, x, p, tau, id, w, idx, 0u, rz);
-        while (wn >= 32) warp_round<T, MLP>(c, q, wn, my_ev, my_max, n64, ms);
+        __syncthreads();
+        while (q.n >= LB) stack_round<T, MLP>(c, q, my_ev, my_max, n64, ms);
     }
-    while (wn > 0) warp_round<T, MLP>(c, q, wn, my_ev, my_max, n64, ms);
+    while (q.n > 0) stack_round<T, MLP>(c, q, my_ev, my_max, n64, ms);
     __syncwarp();
     flush_stats(ctl, my_steps, my_ev, my_max, false, n64);
 }
@@ -833,14 +826,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.icdf_pair = f32 ? (const void *)ctx->icdf_pair32 : (const void *)ctx->icdf_pair64;
     a.mlp_w16 = ctx->cfg.sampler == QED_SAMPLER_MLP ? ctx->mlp_w16 : nullptr;
     a.field_kind = field->kind;
-    // fields that vanish everywhere let chi skip its cancellation guard
-    if (field->kind == QED_FIELD_ROTATING_E) a.field_zero = 1;
-    if (field->kind == QED_FIELD_STANDING_CP) a.field_zero = 3;     // E and B both along (0, cos t, sin t)
-    if (field->kind == QED_FIELD_UNIFORM) {
-        const double *q = field->params;
-        if (q[3] == 0.0 && q[4] == 0.0 && q[5] == 0.0) a.field_zero = 1;
-        else if (q[0] == 0.0 && q[1] == 0.0 && q[2] == 0.0) a.field_zero = 2;
-    }
+    a.field_zero = field_zero_of(*field);      // chi without its cancellation guard where allowed
     for (int i = 0; i < 6; ++i) {
         a.prm[i] = field->params[i];
         a.prm_f[i] = (float)field->params[i];
