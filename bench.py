@@ -330,6 +330,7 @@ def batch_run(ws, precision, warm, steps, threads=0):
     if not threads:                         # else the block shape is fixed by the caller
         ens, arr = fresh(caps)
         tuned = q.qed_autotune_batch(gen.ctx, arr, fields, ws[0].dt, 2)
+        tuned = (tuned[0], tuned[1], q.qed_batch_shape(gen.ctx)[1])
         del ens, arr
     ens, arr = fresh(caps)
     if warm:
@@ -614,7 +615,8 @@ def batched_main(args, ws, warm, steps, rank, world, cpu):
                    "l2": "inputs larger than L2 (%d MB of leptons)" % (n_lep * 40 // 2 ** 20)},
         "events_per_s": ev / secs,
         "gpu_launches": st["launches"],
-        "autotune": {"chosen_threads": tuned[0], "ms_128_256_512": tuned[1]} if tuned else None,
+        "autotune": ({"chosen_threads": tuned[0], "chosen_step_budget": tuned[2],
+                      "ms_128_256_512_at_best_budget": tuned[1]} if tuned else None),
         "roofline": {"bound": "alu", "note": "step-fused: leptons stay in registers across steps",
                      "kernel": "k_emission_fused", "kernel_ms": st["kernel_ms"][0]},
         "clocks": clk.summary(),

@@ -74,7 +74,9 @@ typedef struct {
     int blocks_per_sm;        /* resident blocks per SM of the push kernels; 0 = default */
     int profile;              /* 1: time the push kernels with CUDA events on the context's
                                  stream (qed_stats.kernel_ms) */
-    int reserved[5];
+    int batch_step_budget;    /* qed_batch_push: steps a lepton runs before it rejoins its
+                                 block's queue (1..64); 0 = the autotuner's choice, else 4 */
+    int reserved[4];
 } qed_config;
 
 /* One species: structure of arrays (Sec. 4.1), one array set per particle
@@ -163,12 +165,17 @@ qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc
                           double dt, int nsteps, int64_t step0, qed_stats *out);
 
 /* Autotuner of qed_batch_push: times block shapes of 128, 256 and 512
- * threads (one tile of particles per block) for nsteps steps on scratch
- * copies of up to 2^20 leptons sampled from ens (the caller's buffers are
- * not modified) and keeps the fastest for this context.  *chosen_threads and
- * ms3[3] (device ms per candidate) may be NULL. */
+ * threads (one tile of particles per block), each with step budgets of 1, 2
+ * and 4 (cfg.batch_step_budget), for nsteps steps on scratch copies of up to
+ * 2^20 leptons sampled from ens (the caller's buffers are not modified) and
+ * keeps the fastest pair for this context.  *chosen_threads and ms3[3]
+ * (device ms per block shape, at its best budget) may be NULL. */
 qed_status qed_autotune_batch(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields,
                               int n_ens, double dt, int nsteps, int *chosen_threads, double *ms3);
+
+/* The block shape and step budget qed_batch_push uses in this context (the
+ * configured ones, else the autotuner's, else 256 and 4).  Host only. */
+qed_status qed_batch_shape(qed_ctx *ctx, int *threads, int *step_budget);
 
 /* ---- learned surrogate of the emission sampler ------------------------
  * An extension of the method (the paper samples from tables only): a network

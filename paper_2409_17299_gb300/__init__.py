@@ -24,7 +24,7 @@ EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_batch_push", "qed_a
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
             "qed_compact_species_noalloc", "qed_train_surrogate", "qed_mlp_set_params", "qed_mlp_get_params",
             "qed_mlp_forward", "qed_mlp_grad", "qed_level_begin", "qed_level_advance", "qed_level_eval",
-            "qed_level_apply")
+            "qed_level_apply", "qed_batch_shape")
 QED_NOALLOC_MAX_ENTRIES = 1 << 20
 
 
@@ -32,7 +32,7 @@ class QedConfig(C.Structure):
     _fields_ = [("precision", C.c_int), ("sampler", C.c_int), ("seed", C.c_uint64),
                 ("push_photons", C.c_int), ("soft_photon_filter", C.c_int), ("thin_cap", C.c_int64),
                 ("restore_on_overflow", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
-                ("profile", C.c_int), ("reserved", C.c_int * 5)]
+                ("profile", C.c_int), ("batch_step_budget", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class QedLevelState(C.Structure):
@@ -118,6 +118,7 @@ def lib():
         "qed_level_eval": (i32, [p, C.POINTER(QedSpecies), i32, C.c_double, C.POINTER(C.c_double),
                                  C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_double)]),
         "qed_level_apply": (i32, [p, p, i32, C.c_double, i64]),
+        "qed_batch_shape": (i32, [p, C.POINTER(i32), C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -180,6 +181,15 @@ def qed_compact(ctx, particles: QedParticles, step: int) -> int:
     if rc != QED_OK:
         raise QedError(rc, "qed_compact")
     return rc
+
+
+def qed_batch_shape(ctx):
+    """(threads, step budget) of qed_batch_push in this context."""
+    t, b = C.c_int(), C.c_int()
+    rc = lib().qed_batch_shape(ctx, C.byref(t), C.byref(b))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_batch_shape")
+    return t.value, b.value
 
 
 def qed_level_begin() -> QedLevelState:
@@ -349,7 +359,7 @@ def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream
 # --------------------------------------------------------------------------
 def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0, thin_cap=0,
                 restore_on_overflow=1, block_threads=0, blocks_per_sm=0, profile=0,
-                sampler=QED_SAMPLER_TABLE) -> QedConfig:
+                sampler=QED_SAMPLER_TABLE, batch_step_budget=0) -> QedConfig:
     c = QedConfig()
     c.precision = int(precision)
     c.sampler = int(sampler)
@@ -361,6 +371,7 @@ def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0
     c.block_threads = int(block_threads)
     c.blocks_per_sm = int(blocks_per_sm)
     c.profile = int(profile)
+    c.batch_step_budget = int(batch_step_budget)
     return c
 
 

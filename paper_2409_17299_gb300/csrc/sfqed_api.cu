@@ -80,7 +80,11 @@ extern "C" qed_status qed_push_and_generate(qed_ctx *ctx, qed_particles *p, cons
 
 extern "C" qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens,
                                      double dt, int nsteps, int64_t step0, qed_stats *out) {
-    return sfq_batch_push(ctx, ens, fields, n_ens, dt, nsteps, step0, out, 0);
+    return sfq_batch_push(ctx, ens, fields, n_ens, dt, nsteps, step0, out, 0, 0);
+}
+
+extern "C" qed_status qed_batch_shape(qed_ctx *ctx, int *threads, int *step_budget) {
+    return sfq_batch_shape(ctx, threads, step_budget);
 }
 
 extern "C" qed_status qed_autotune_batch(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields,

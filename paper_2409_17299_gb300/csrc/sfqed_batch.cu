@@ -91,8 +91,8 @@ struct FusedCtx {
     const double *coef_d;
 };
 
-// steps a particle runs before it rejoins the block's queue (bounds the
-// work one lane does between block barriers)
+// default number of steps a particle runs before it rejoins the block's
+// queue (bounds the work one lane does between block barriers)
 constexpr int BATCH_STEP_BUDGET = 4;
 
 template <class T> __device__ __forceinline__ const T *coef_of(const FusedCtx &c);
@@ -451,9 +451,14 @@ static int chosen_threads(const qed_ctx *ctx) {
     return ctx->tuned_threads > 0 ? ctx->tuned_threads : 256;
 }
 
+static int chosen_budget(const qed_ctx *ctx) {
+    if (ctx->cfg.batch_step_budget >= 1 && ctx->cfg.batch_step_budget <= 64) return ctx->cfg.batch_step_budget;
+    return ctx->tuned_budget > 0 ? ctx->tuned_budget : BATCH_STEP_BUDGET;
+}
+
 template <class T>
 static qed_status batch_impl(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens, double dt,
-                             int nsteps, int64_t step0, qed_stats *out, int threads_override) {
+                             int nsteps, int64_t step0, qed_stats *out, int threads_override, int budget_override) {
     const auto call_t0 = std::chrono::steady_clock::now();
     qed_status e = batch_reserve(ctx, n_ens, nsteps);
     if (e != QED_OK) return e;
@@ -510,7 +515,7 @@ static qed_status batch_impl(qed_ctx *ctx, qed_particles *ens, const qed_field_d
     b.t_red_f = w->tr_d;
     b.seed = ctx->cfg.seed;
     b.keys = philox_keys(ctx->cfg.seed);
-    b.budget = BATCH_STEP_BUDGET;
+    b.budget = budget_override > 0 ? budget_override : chosen_budget(ctx);
     b.soft_filter = ctx->cfg.soft_photon_filter;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (ctx->cfg.profile) {
@@ -579,7 +584,7 @@ static qed_status batch_impl(qed_ctx *ctx, qed_particles *ens, const qed_field_d
 }
 
 qed_status sfq_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens, double dt,
-                          int nsteps, int64_t step0, qed_stats *out, int threads_override) {
+                          int nsteps, int64_t step0, qed_stats *out, int threads_override, int budget_override) {
     if (!ctx || !ens || !fields || n_ens <= 0 || nsteps < 0 || !(dt > 0.0) || step0 < 0 ||
         step0 + nsteps > 0xFFFFFFFFll)
         return QED_ERR_INVALID;
@@ -597,8 +602,8 @@ qed_status sfq_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc
         }
     }
     if (ctx->cfg.precision == QED_FP32)
-        return batch_impl<float>(ctx, ens, fields, n_ens, dt, nsteps, step0, out, threads_override);
-    return batch_impl<double>(ctx, ens, fields, n_ens, dt, nsteps, step0, out, threads_override);
+        return batch_impl<float>(ctx, ens, fields, n_ens, dt, nsteps, step0, out, threads_override, budget_override);
+    return batch_impl<double>(ctx, ens, fields, n_ens, dt, nsteps, step0, out, threads_override, budget_override);
 }
 
 // Autotuner: time each block shape of the fused kernel on scratch copies of
@@ -662,22 +667,27 @@ qed_status sfq_batch_autotune(qed_ctx *ctx, const qed_particles *ens, const qed_
         return QED_OK;
     };
     const int cand[3] = {128, 256, 512};
+    const int budgets[3] = {1, 2, 4};
     double best = 1e300;
-    int best_nt = 256;
+    int best_nt = 256, best_b = BATCH_STEP_BUDGET;
     const int saved_profile = ctx->cfg.profile;
     ctx->cfg.profile = 1;
     for (int c = 0; c < 3 && rc == QED_OK; ++c) {
-        double ms = 0.0;
-        for (int rep = 0; rep < 2 && rc == QED_OK; ++rep) {   // first repetition warms up
-            rc = refill();
-            if (rc != QED_OK) break;
-            qed_stats s{};
-            rc = sfq_batch_push(ctx, cp, fields, nk, dt, nsteps, 0, &s, cand[c]);
-            if (rc == QED_ERR_CAPACITY) rc = QED_OK;             // timing is still valid
-            ms = s.kernel_ms[0];
+        double best_c = 1e300;
+        for (int bi = 0; bi < 3 && rc == QED_OK; ++bi) {
+            double ms = 0.0;
+            for (int rep = 0; rep < 2 && rc == QED_OK; ++rep) {   // first repetition warms up
+                rc = refill();
+                if (rc != QED_OK) break;
+                qed_stats s{};
+                rc = sfq_batch_push(ctx, cp, fields, nk, dt, nsteps, 0, &s, cand[c], budgets[bi]);
+                if (rc == QED_ERR_CAPACITY) rc = QED_OK;             // timing is still valid
+                ms = s.kernel_ms[0];
+            }
+            if (ms < best_c) best_c = ms;
+            if (ms < best) { best = ms; best_nt = cand[c]; best_b = budgets[bi]; }
         }
-        if (ms3) ms3[c] = ms;
-        if (ms < best) { best = ms; best_nt = cand[c]; }
+        if (ms3) ms3[c] = best_c;
     }
     ctx->cfg.profile = saved_profile;
     cudaStreamSynchronize(st);
@@ -685,6 +695,14 @@ qed_status sfq_batch_autotune(qed_ctx *ctx, const qed_particles *ens, const qed_
     free(cp);
     if (rc != QED_OK) return rc;
     ctx->tuned_threads = best_nt;
+    ctx->tuned_budget = best_b;
     if (chosen) *chosen = best_nt;
+    return QED_OK;
+}
+
+qed_status sfq_batch_shape(qed_ctx *ctx, int *threads, int *budget) {
+    if (!ctx) return QED_ERR_INVALID;
+    if (threads) *threads = chosen_threads(ctx);
+    if (budget) *budget = chosen_budget(ctx);
     return QED_OK;
 }

@@ -158,6 +158,7 @@ struct qed_ctx {
     void *batch;                 // batched-push work buffers
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
     int tuned_threads;           // block shape picked by the autotuner (0: none yet)
+    int tuned_budget;            // step budget picked by the autotuner (0: none yet)
     int spec_passes;             // newborn passes enqueued per host check (from the last step)
     int lev_chunk[3];            // leveling passes enqueued per host check (from the last leveling)
     // surrogate network: FP32 master parameters, Adam moments and gradient
@@ -181,7 +182,9 @@ qed_status sfq_eval_chi(qed_ctx *ctx, int is_photon, const double *p, const doub
 qed_status sfq_philox(const uint32_t *ctr, int64_t n, uint64_t key, uint32_t *out, cudaStream_t s);
 // Implemented in sfqed_batch.cu
 qed_status sfq_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens, double dt,
-                          int nsteps, int64_t step0, qed_stats *out, int threads_override);
+                          int nsteps, int64_t step0, qed_stats *out, int threads_override,
+                          int budget_override);
+qed_status sfq_batch_shape(qed_ctx *ctx, int *threads, int *budget);
 qed_status sfq_batch_autotune(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields, int n_ens,
                               double dt, int nsteps, int *chosen, double *ms3);
 void sfq_batch_free(qed_ctx *ctx);

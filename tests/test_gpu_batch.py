@@ -80,6 +80,8 @@ def test_autotuner_leaves_buffers_and_picks_a_shape():
     before = [e.to_host(0) for e in ens]
     chosen, ms = q.qed_autotune_batch(g.ctx, arr, fields, ws[0].dt, 4)
     assert chosen in (128, 256, 512) and all(m > 0 for m in ms)
+    threads, budget = q.qed_batch_shape(g.ctx)
+    assert threads == chosen and budget in (1, 2, 4)
     for e, b in zip(ens, before):
         a = e.to_host(0)
         for f in b:
@@ -172,3 +174,29 @@ def test_batch_rejects_cascade_config():
     with pytest.raises(q.QedError):
         q.qed_batch_push(g.ctx, arr, fields, ws[0].dt, 2, 0)
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_budget_changes_nothing(prec):
+    """The step budget only decides when a lepton rejoins its block's queue:
+    the same kernel instantiation computes every particle, so any budget
+    gives bit-identical ensembles."""
+    ws = _batch([900, 6000], nsteps=12)
+    P = q.QED_FP64 if prec == "fp64" else q.QED_FP32
+    res = []
+    for budget in (1, 3, 64):
+        g = q.Generator(q.make_config(precision=P, seed=6, push_photons=0, block_threads=256,
+                                      batch_step_budget=budget))
+        assert q.qed_batch_shape(g.ctx) == (256, budget)
+        ens, arr, fields = _device(ws, P)
+        rc, _ = q.qed_batch_push(g.ctx, arr, fields, ws[0].dt, 12, 0)
+        assert rc == q.QED_OK
+        _pull(ens, arr)
+        res.append([(by_id(e.to_host(0)), by_id(e.to_host(2))) for e in ens])
+        g.close()
+    for other in res[1:]:
+        for (a0, a2), (b0, b2) in zip(res[0], other):
+            for f in a0:
+                assert np.array_equal(a0[f], b0[f]), f
+            for f in a2:
+                assert np.array_equal(a2[f], b2[f]), ("photon", f)
