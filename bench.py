@@ -598,6 +598,31 @@ def main():
         dist.destroy_process_group()
 
 
+# Instruction issue peak of one GB300: 152 SMs x 4 schedulers x 2.07 GHz,
+# one warp instruction per scheduler per clock.
+ISSUE_PEAK_WARP_INSTR = 152 * 4 * 2.07e9
+# Warp instructions per lepton-step of the step-fused batch kernel (128
+# threads, step budget 4) from one ncu capture of the current kernel
+# (profiles/k_emission_fused_batched_uniform_b.md); None when not captured
+NCU_FUSED_WARP_INSTR_PER_STEP = {"fp32": None, "fp64": None}
+
+
+def batch_roofline(st, precision):
+    """The step-fused kernel reads and writes each lepton once per call, so
+    it is bound by instruction issue, not HBM: achieved = warp instructions
+    per lepton-step (ncu) x lepton-steps / kernel time, against the issue
+    peak."""
+    ms = st["kernel_ms"][0]
+    per = NCU_FUSED_WARP_INSTR_PER_STEP.get(precision)
+    ach = per * st["lepton_steps"] / (ms / 1e3) if (per and ms > 0) else None
+    return {"bound": "alu", "unit": "warp instructions/s", "achieved": ach, "peak": ISSUE_PEAK_WARP_INSTR,
+            "frac": ach / ISSUE_PEAK_WARP_INSTR if ach else None, "traffic": None,
+            "peak_source": "152 SMs x 4 schedulers x 2.07 GHz (one warp instruction per scheduler per clock)",
+            "warp_instr_per_lepton_step": per, "kernel": "k_emission_fused<%s>" % (
+                "float" if precision == "fp32" else "double"), "kernel_ms": ms,
+            "note": "step-fused: leptons stay in registers across steps; HBM traffic is per call, not per step"}
+
+
 def batched_main(args, ws, warm, steps, rank, world, cpu):
     import torch
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
@@ -617,8 +642,7 @@ def batched_main(args, ws, warm, steps, rank, world, cpu):
         "gpu_launches": st["launches"],
         "autotune": ({"chosen_threads": tuned[0], "chosen_step_budget": tuned[2],
                       "ms_128_256_512_at_best_budget": tuned[1]} if tuned else None),
-        "roofline": {"bound": "alu", "note": "step-fused: leptons stay in registers across steps",
-                     "kernel": "k_emission_fused", "kernel_ms": st["kernel_ms"][0]},
+        "roofline": batch_roofline(st, args.precision),
         "clocks": clk.summary(),
     }
     if cpu:
