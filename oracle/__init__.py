@@ -30,7 +30,7 @@ EM_NCHI, EM_NS = 121, 257
 PAIR_NCHI, PAIR_NS = 101, 129
 CHEB_N = 11
 
-FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_STANDING_CP = 0, 1, 2
+FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_STANDING_CP, FIELD_GRID = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -95,6 +95,7 @@ def lib():
                 "or_sample_emission": (d, [p, d, d, p]),
                 "or_sample_pair": (d, [p, d, d, p]),
                 "or_field": (None, [i32, p, p, d, p, p]),
+                "or_set_field_grid": (None, [p]),
                 "or_chi": (d, [d, p, p, p]),
                 "or_boris": (None, [p, p, d, p, p, d]),
                 "or_compact": (None, [p]),
@@ -253,6 +254,18 @@ def field(kind: int, prm, x, t):
     B = np.zeros(3)
     lib().or_field(int(kind), _ptr(prm16), _ptr(x), float(t), _ptr(E), _ptr(B))
     return E, B
+
+
+_grid_keep = None
+
+
+def set_field_grid(g):
+    """Node values of the gridded field (FIELD_GRID), shape (6, nz, ny, nx):
+    E_x, E_y, E_z, B_x, B_y, B_z.  The oracle keeps a reference until the
+    next call; field_prm of the run is (nx, ny, nz, Lx, Ly, Lz)."""
+    global _grid_keep
+    _grid_keep = np.ascontiguousarray(g, dtype=np.float64)
+    lib().or_set_field_grid(_ptr(_grid_keep))
 
 
 def chi(e0, p, E, B) -> float:

@@ -556,11 +556,56 @@ double or_sample_pair(const double *icdf_pair, double chi, double u, double *one
 /* ================================================================== */
 /* 6. Fields (Sec. 5.1 test problem; analytic field descriptors).       */
 /* ================================================================== */
-enum { OR_FIELD_UNIFORM = 0, OR_FIELD_ROTATING_E = 1, OR_FIELD_STANDING_CP = 2 };
+enum { OR_FIELD_UNIFORM = 0, OR_FIELD_ROTATING_E = 1, OR_FIELD_STANDING_CP = 2, OR_FIELD_GRID = 3 };
+
+/* Gridded field (a PIC step's fields, held constant during the step):
+ * node values E_x, E_y, E_z, B_x, B_y, B_z on a periodic nx x ny x nz grid
+ * over [0, Lx) x [0, Ly) x [0, Lz), node (i, j, k) at (i Lx/nx, j Ly/ny,
+ * k Lz/nz); layout [component][k][j][i].  prm = (nx, ny, nz, Lx, Ly, Lz).
+ * Trilinear interpolation: linear in x along the four x-edges of the cell,
+ * then in y, then in z; each lerp a + f (b - a) as one fused multiply-add. */
+static const double *or_grid = NULL;
+
+void or_set_field_grid(const double *g) { or_grid = g; }
+
+static void grid_axis(double x, int n, double inv_h, int *i0, int *i1, double *f)
+{
+    const double u = x * inv_h;
+    const double fl = floor(u);
+    long long i = (long long)fl % n;
+    if (i < 0) i += n;
+    *i0 = (int)i;
+    *i1 = (int)((i + 1) % n);
+    *f = u - fl;
+}
+
+void or_field_grid(const double *prm, const double x[3], double E[3], double B[3])
+{
+    const int nx = (int)prm[0], ny = (int)prm[1], nz = (int)prm[2];
+    int i0, i1, j0, j1, k0, k1;
+    double fx, fy, fz;
+    grid_axis(x[0], nx, (double)nx / prm[3], &i0, &i1, &fx);
+    grid_axis(x[1], ny, (double)ny / prm[4], &j0, &j1, &fy);
+    grid_axis(x[2], nz, (double)nz / prm[5], &k0, &k1, &fz);
+    const long long plane = (long long)nx * ny, vol = plane * nz;
+    for (int c = 0; c < 6; ++c) {
+        const double *g = or_grid + c * vol;
+        const double a00 = fma(fx, g[k0 * plane + j0 * nx + i1] - g[k0 * plane + j0 * nx + i0], g[k0 * plane + j0 * nx + i0]);
+        const double a10 = fma(fx, g[k0 * plane + j1 * nx + i1] - g[k0 * plane + j1 * nx + i0], g[k0 * plane + j1 * nx + i0]);
+        const double a01 = fma(fx, g[k1 * plane + j0 * nx + i1] - g[k1 * plane + j0 * nx + i0], g[k1 * plane + j0 * nx + i0]);
+        const double a11 = fma(fx, g[k1 * plane + j1 * nx + i1] - g[k1 * plane + j1 * nx + i0], g[k1 * plane + j1 * nx + i0]);
+        const double b0 = fma(fy, a10 - a00, a00);
+        const double b1 = fma(fy, a11 - a01, a01);
+        const double v = fma(fz, b1 - b0, b0);
+        if (c < 3) E[c] = v; else B[c - 3] = v;
+    }
+}
 
 void or_field(int kind, const double *prm, const double x[3], double t, double E[3], double B[3])
 {
-    if (kind == OR_FIELD_UNIFORM) {
+    if (kind == OR_FIELD_GRID) {
+        or_field_grid(prm, x, E, B);
+    } else if (kind == OR_FIELD_UNIFORM) {
         E[0] = prm[0]; E[1] = prm[1]; E[2] = prm[2];
         B[0] = prm[3]; B[1] = prm[4]; B[2] = prm[5];
     } else if (kind == OR_FIELD_ROTATING_E) {
