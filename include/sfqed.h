@@ -58,7 +58,12 @@ enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 };
  *  QED_FIELD_STANDING_CP params[0] = a0:  standing circularly polarised wave
  *                        E = a0 cos x (0, cos t, sin t), B = a0 sin x (0, cos t, sin t)
  *                        (electric antinode at x = 0; Sec. 5.1 test problem) */
-enum { QED_FIELD_UNIFORM = 0, QED_FIELD_ROTATING_E = 1, QED_FIELD_STANDING_CP = 2 };
+/*  QED_FIELD_GRID        a PIC step's fields on a periodic node grid, held
+ *                        constant during the step: params = (nx, ny, nz, Lx,
+ *                        Ly, Lz); node (i, j, k) at (i Lx/nx, j Ly/ny, k Lz/nz);
+ *                        values from qed_set_field_grid; trilinear
+ *                        interpolation (lerp in x, then y, then z) */
+enum { QED_FIELD_UNIFORM = 0, QED_FIELD_ROTATING_E = 1, QED_FIELD_STANDING_CP = 2, QED_FIELD_GRID = 3 };
 
 typedef struct {
     int precision;            /* QED_FP64 or QED_FP32 */
@@ -255,6 +260,15 @@ qed_status qed_level_eval(qed_ctx *ctx, const qed_species *sp, int species, doub
  * wstar; wstar = 0: compaction only), then remove dead entries; count in *p
  * is updated. */
 qed_status qed_level_apply(qed_ctx *ctx, qed_particles *p, int species, double wstar, int64_t step);
+
+/* Node values of the gridded field (QED_FIELD_GRID) for the following calls:
+ * grid_dev holds 6 * nz * ny * nx values of the context's precision (double
+ * for QED_FP64, float for QED_FP32), layout [component][k][j][i] with the
+ * components E_x, E_y, E_z, B_x, B_y, B_z.  Caller-owned device memory,
+ * read (not copied) by every push with a QED_FIELD_GRID descriptor; the
+ * caller may rewrite it between calls (a PIC code's new fields each step).
+ * NULL detaches it.  The batched push does not take gridded fields. */
+qed_status qed_set_field_grid(qed_ctx *ctx, const void *grid_dev);
 
 /* Statistics accumulated since the context was created or last reset. */
 qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset);

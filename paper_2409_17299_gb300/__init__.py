@@ -18,13 +18,13 @@ QED_OK, QED_ERR_INVALID, QED_ERR_CAPACITY, QED_ERR_CUDA, QED_ERR_TIMEOUT, QED_ER
 QED_FP64, QED_FP32 = 0, 1
 QED_SAMPLER_TABLE, QED_SAMPLER_MLP = 0, 1
 QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
-QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP = 0, 1, 2
+QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP, QED_FIELD_GRID = 0, 1, 2, 3
 
 EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_batch_push", "qed_autotune_batch", "qed_compact", "qed_get_stats", "qed_strerror",
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
             "qed_compact_species_noalloc", "qed_train_surrogate", "qed_mlp_set_params", "qed_mlp_get_params",
             "qed_mlp_forward", "qed_mlp_grad", "qed_level_begin", "qed_level_advance", "qed_level_eval",
-            "qed_level_apply", "qed_batch_shape")
+            "qed_level_apply", "qed_batch_shape", "qed_set_field_grid")
 QED_NOALLOC_MAX_ENTRIES = 1 << 20
 
 
@@ -119,6 +119,7 @@ def lib():
                                  C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_double)]),
         "qed_level_apply": (i32, [p, p, i32, C.c_double, i64]),
         "qed_batch_shape": (i32, [p, C.POINTER(i32), C.POINTER(i32)]),
+        "qed_set_field_grid": (i32, [p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -181,6 +182,14 @@ def qed_compact(ctx, particles: QedParticles, step: int) -> int:
     if rc != QED_OK:
         raise QedError(rc, "qed_compact")
     return rc
+
+
+def qed_set_field_grid(ctx, grid_dev_ptr) -> None:
+    """Attach the gridded field's node values (device pointer, 6 x nz x ny x nx
+    values of the context's precision); 0/None detaches."""
+    rc = lib().qed_set_field_grid(ctx, C.c_void_p(grid_dev_ptr or 0))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_set_field_grid")
 
 
 def qed_batch_shape(ctx):

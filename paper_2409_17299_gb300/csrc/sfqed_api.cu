@@ -83,6 +83,14 @@ extern "C" qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed
     return sfq_batch_push(ctx, ens, fields, n_ens, dt, nsteps, step0, out, 0, 0);
 }
 
+extern "C" qed_status qed_set_field_grid(qed_ctx *ctx, const void *grid_dev) {
+    if (!ctx) return QED_ERR_INVALID;
+    if (grid_dev && (reinterpret_cast<uintptr_t>(grid_dev) % (ctx->cfg.precision == QED_FP32 ? 4 : 8)))
+        return QED_ERR_INVALID;
+    ctx->field_grid = grid_dev;
+    return QED_OK;
+}
+
 extern "C" qed_status qed_batch_shape(qed_ctx *ctx, int *threads, int *step_budget) {
     return sfq_batch_shape(ctx, threads, step_budget);
 }

@@ -123,7 +123,7 @@ __device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView
                                               uint2 &rz, unsigned &n64) {
     const BatchArgs &b = c.b;
     T E[3], B[3];
-    eval_field<T>(v, x[0], FRESH ? 0.0 : tau, E, B);
+    eval_field<T>(v, x, FRESH ? 0.0 : tau, E, B);
     T p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
     T gam, chi;
     if constexpr (sizeof(T) == 8) {
@@ -189,7 +189,7 @@ __device__ __forceinline__ void fused_emit(const FusedCtx &c, const EnsDev &e, u
                                            unsigned step, unsigned k, uint2 rz, unsigned &n64) {
     const BatchArgs &b = c.b;
     T E[3], B[3];
-    eval_field<T>(v, x[0], tau, E, B);
+    eval_field<T>(v, x, tau, E, B);
     T p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
     T gam, chi;
     if constexpr (sizeof(T) == 8) {

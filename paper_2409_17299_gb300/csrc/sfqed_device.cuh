@@ -180,8 +180,69 @@ template <class T, class A> __device__ __forceinline__ Phase<T> time_phase(const
     return q;
 }
 
+// Gridded field: trilinear interpolation on the periodic node grid (lerp
+// a + f (b - a) as one fused multiply-add: in x along the four x-edges of
+// the cell, then y, then z).  The scaled coordinate is rounded on its own
+// (no contraction with the fraction), as in the oracle.
+template <class T> __device__ __forceinline__ T mul_rn(T a, T b);
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+
+template <class T>
+__device__ __forceinline__ void grid_axis(T x, int n, T inv_h, int &i0, int &i1, T &f) {
+    const T u = mul_rn<T>(x, inv_h);
+    const T fl = floor(u);
+    long long i = (long long)fl % n;
+    if (i < 0) i += n;
+    i0 = (int)i;
+    i1 = i0 + 1 == n ? 0 : i0 + 1;
+    f = u - fl;
+}
+
 template <class T, class A>
-__device__ __forceinline__ void eval_field_at(const A &a, T x, const Phase<T> &q, T E[3], T B[3]) {
+__device__ __forceinline__ void eval_grid(const A &a, const T x[3], T E[3], T B[3]) {
+    const int nx = a.gn[0], ny = a.gn[1], nz = a.gn[2];
+    int i0, i1, j0, j1, k0, k1;
+    T fx, fy, fz;
+    if constexpr (sizeof(T) == 8) {
+        grid_axis<T>(x[0], nx, a.ginv[0], i0, i1, fx);
+        grid_axis<T>(x[1], ny, a.ginv[1], j0, j1, fy);
+        grid_axis<T>(x[2], nz, a.ginv[2], k0, k1, fz);
+    } else {
+        grid_axis<T>(x[0], nx, a.ginv_f[0], i0, i1, fx);
+        grid_axis<T>(x[1], ny, a.ginv_f[1], j0, j1, fy);
+        grid_axis<T>(x[2], nz, a.ginv_f[2], k0, k1, fz);
+    }
+    const long long plane = (long long)nx * ny, vol = plane * nz;
+    const long long o00 = k0 * plane + j0 * nx, o10 = k0 * plane + j1 * nx;
+    const long long o01 = k1 * plane + j0 * nx, o11 = k1 * plane + j1 * nx;
+    const T *g = reinterpret_cast<const T *>(a.grid);
+#pragma unroll
+    for (int c = 0; c < 6; ++c, g += vol) {
+        const T a00 = fma(fx, __ldg(g + o00 + i1) - __ldg(g + o00 + i0), __ldg(g + o00 + i0));
+        const T a10 = fma(fx, __ldg(g + o10 + i1) - __ldg(g + o10 + i0), __ldg(g + o10 + i0));
+        const T a01 = fma(fx, __ldg(g + o01 + i1) - __ldg(g + o01 + i0), __ldg(g + o01 + i0));
+        const T a11 = fma(fx, __ldg(g + o11 + i1) - __ldg(g + o11 + i0), __ldg(g + o11 + i0));
+        const T b0 = fma(fy, a10 - a00, a00);
+        const T b1 = fma(fy, a11 - a01, a01);
+        const T v = fma(fz, b1 - b0, b0);
+        if (c < 3) E[c] = v;
+        else B[c - 3] = v;
+    }
+}
+
+template <class A> struct HasGrid { static constexpr bool value = false; };
+template <> struct HasGrid<PassArgs> { static constexpr bool value = true; };
+
+template <class T, class A>
+__device__ __forceinline__ void eval_field_at(const A &a, const T xv[3], const Phase<T> &q, T E[3], T B[3]) {
+    if constexpr (HasGrid<A>::value) {
+        if (a.field_kind == QED_FIELD_GRID) {
+            eval_grid<T, A>(a, xv, E, B);
+            return;
+        }
+    }
+    const T x = xv[0];
     if (a.field_kind == QED_FIELD_UNIFORM) {
         E[0] = prm_of<T, A>(a, 0); E[1] = prm_of<T, A>(a, 1); E[2] = prm_of<T, A>(a, 2);
         B[0] = prm_of<T, A>(a, 3); B[1] = prm_of<T, A>(a, 4); B[2] = prm_of<T, A>(a, 5);
@@ -202,7 +263,7 @@ __device__ __forceinline__ void eval_field_at(const A &a, T x, const Phase<T> &q
 }
 
 template <class T, class A>
-__device__ __forceinline__ void eval_field(const A &a, T x, double tau, T E[3], T B[3]) {
+__device__ __forceinline__ void eval_field(const A &a, const T x[3], double tau, T E[3], T B[3]) {
     eval_field_at<T, A>(a, x, time_phase<T, A>(a, tau), E, B);
 }
 

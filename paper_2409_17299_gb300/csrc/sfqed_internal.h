@@ -100,6 +100,10 @@ struct PassArgs {
     const void *icdf_pair;  // PAIR_NCHI * PAIR_NS (T)
     const __nv_bfloat16 *mlp_w16;   // surrogate network weights, or null (table sampler)
     int field_kind;
+    const void *grid;       // QED_FIELD_GRID: node values [6][nz][ny][nx] (T)
+    int gn[3];              // grid nodes per axis
+    double ginv[3];         // nodes per unit length (n / L)
+    float ginv_f[3];
     int field_zero;         // chi shortcut: 1 B = 0, 2 E = 0, 3 E parallel to B (everywhere), else 0
     double prm[6];
     float prm_f[6];         // prm rounded to float once (FP32 mode)
@@ -157,6 +161,7 @@ struct qed_ctx {
     double sync_ms;              // host time blocked in stream synchronisation
     void *batch;                 // batched-push work buffers
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
+    const void *field_grid;      // caller's gridded field values (QED_FIELD_GRID)
     int tuned_threads;           // block shape picked by the autotuner (0: none yet)
     int tuned_budget;            // step budget picked by the autotuner (0: none yet)
     int spec_passes;             // newborn passes enqueued per host check (from the last step)

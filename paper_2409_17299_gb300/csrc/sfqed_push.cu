@@ -114,8 +114,8 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
                                         unsigned long long id, unsigned k, uint2 &rz, unsigned &n64) {
     const PassArgs &a = c.a;
     T E[3], B[3];
-    if constexpr (FRESH) eval_field_at<T>(a, x[0], c.ph0, E, B);
-    else eval_field<T>(a, x[0], tau, E, B);
+    if constexpr (FRESH) eval_field_at<T>(a, x, c.ph0, E, B);
+    else eval_field<T>(a, x, tau, E, B);
     T gam, chi, p2;
     lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
     const T lam = p2 > (T)0 ? f_div(c.alpha_r, gam) * rate_em<T>(c.coef, chi) : (T)0;
@@ -179,7 +179,7 @@ template <class T>
 __device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3], double tau, T w,
                                      unsigned long long id, unsigned k, uint2 rz, unsigned &n64) {
     T E[3], B[3];
-    eval_field<T>(c.a, x[0], tau, E, B);
+    eval_field<T>(c.a, x, tau, E, B);
     T gam, chi, p2;
     lepton_chi<T>(p, E, B, gam, chi, p2, n64, c.a.field_zero);
     T om, ue, ve;
@@ -240,7 +240,7 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
         bool use_net = false;
         if (mine) {
             T E[3], B[3];
-            eval_field<T>(c.a, x[0], tau, E, B);
+            eval_field<T>(c.a, x, tau, E, B);
             lepton_chi<T>(p, E, B, gam, chi, p2, n64, c.a.field_zero);
             Uniform<T>::draw(rz.x, rz.y, ue, ve);
             const float sl = (float)logit(ue, ve);
@@ -454,8 +454,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
             // one waiting time: the photon either reaches the step end or converts
             if (FRESH || tau < a.dt) {
                 T E[3], B[3];
-                if constexpr (FRESH) eval_field_at<T>(a, x[0], ph0, E, B);
-                else eval_field<T>(a, x[0], tau, E, B);
+                if constexpr (FRESH) eval_field_at<T>(a, x, ph0, E, B);
+                else eval_field<T>(a, x, tau, E, B);
                 T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
                 T lam;
                 if constexpr (sizeof(T) == 4) lam = alpha_r * inv * rate_pair<T>(s_coef, chi);
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
                 if constexpr (FRESH) tau = (double)dth;
                 else tau += (double)dth;
-                eval_field<T>(a, x[0], tau, E, B);
+                eval_field<T>(a, x, tau, E, B);
                 chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
                 T om, ue, ve;
                 Uniform<T>::draw(r.z, r.w, ue, ve);
@@ -826,6 +826,14 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.icdf_pair = f32 ? (const void *)ctx->icdf_pair32 : (const void *)ctx->icdf_pair64;
     a.mlp_w16 = ctx->cfg.sampler == QED_SAMPLER_MLP ? ctx->mlp_w16 : nullptr;
     a.field_kind = field->kind;
+    if (field->kind == QED_FIELD_GRID) {
+        a.grid = ctx->field_grid;
+        for (int d = 0; d < 3; ++d) {
+            a.gn[d] = (int)field->params[d];
+            a.ginv[d] = (double)a.gn[d] / field->params[3 + d];
+            a.ginv_f[d] = (float)a.ginv[d];
+        }
+    }
     a.field_zero = field_zero_of(*field);      // chi without its cancellation guard where allowed
     for (int i = 0; i < 6; ++i) {
         a.prm[i] = field->params[i];
@@ -960,7 +968,14 @@ qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field,
     if (ctx && ctx->cfg.sampler == QED_SAMPLER_MLP && !ctx->mlp_ready) return QED_ERR_STATE;
     if (!ctx || !p || !field || nsteps < 0 || !(dt > 0.0) || step0 < 0 || step0 + nsteps > 0xFFFFFFFFll)
         return QED_ERR_INVALID;
-    if (field->kind < QED_FIELD_UNIFORM || field->kind > QED_FIELD_STANDING_CP) return QED_ERR_INVALID;
+    if (field->kind < QED_FIELD_UNIFORM || field->kind > QED_FIELD_GRID) return QED_ERR_INVALID;
+    if (field->kind == QED_FIELD_GRID) {
+        if (!ctx->field_grid) return QED_ERR_STATE;
+        for (int d = 0; d < 3; ++d) {
+            const double n = field->params[d], len = field->params[3 + d];
+            if (!(n >= 1.0 && n <= 65536.0 && n == floor(n)) || !(len > 0.0)) return QED_ERR_INVALID;
+        }
+    }
     for (int s = 0; s < 3; ++s) {
         qed_status e = check_species(p->s[s]);
         if (e != QED_OK) return e;
