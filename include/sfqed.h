@@ -79,8 +79,9 @@ typedef struct {
     int blocks_per_sm;        /* resident blocks per SM of the push kernels; 0 = default */
     int profile;              /* 1: time the push kernels with CUDA events on the context's
                                  stream (qed_stats.kernel_ms) */
-    int batch_step_budget;    /* qed_batch_push: steps a lepton runs before it rejoins its
-                                 block's queue (1..64); 0 = the autotuner's choice, else 4 */
+    int batch_step_budget;    /* qed_batch_push: waiting-time iterations a lepton runs before
+                                 it rejoins its block's queue (1..64); 0 = the autotuner's
+                                 choice, else 4 */
     int reserved[4];
 } qed_config;
 

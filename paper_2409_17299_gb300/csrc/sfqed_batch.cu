@@ -52,7 +52,7 @@ struct BatchArgs {
     unsigned long long seed;
     PhiloxKeys keys;               // round keys of seed
     int soft_filter;
-    int budget;                    // new steps a particle starts before it is queued again
+    int budget;                    // waiting-time iterations per item before it is queued again (>= 1)
 };
 
 // field view of one ensemble at one step (eval_field's argument block),
@@ -91,8 +91,9 @@ struct FusedCtx {
     const double *coef_d;
 };
 
-// default number of steps a particle runs before it rejoins the block's
-// queue (bounds the work one lane does between block barriers)
+// default number of waiting-time iterations a particle runs before it
+// rejoins the block's queue (bounds the work one lane does between block
+// barriers)
 constexpr int BATCH_STEP_BUDGET = 4;
 
 template <class T> __device__ __forceinline__ const T *coef_of(const FusedCtx &c);
@@ -159,23 +160,30 @@ __device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView
 }
 
 // Carry a particle forward from (step, tau) until its next event
-// (RUN_EVENT), the end of the call (RUN_END), or until it has started
-// `budget` new steps (RUN_MORE: resume fresh at the start of `step`).
-// fresh: tau == 0 at the start of `step`.  The budget bounds the work of
-// one item, so the lanes of a block stay busy between block barriers.
+// (RUN_EVENT), the end of the call (RUN_END), or until it has used its
+// budget of waiting-time iterations (RUN_MORE: resume fresh at the start of
+// `step`).  fresh: tau == 0 at the start of `step`.  The budget bounds the
+// work of one item per round, so the lanes of a block do similar work
+// between block barriers; a budget of one makes every item of a round one
+// iteration (plus the pending emission).
 constexpr int RUN_END = 0, RUN_EVENT = 1, RUN_MORE = 2;
 template <class T>
 __device__ __forceinline__ int fused_run(const FusedCtx &c, FieldView<T> &v, T x[3], T p[3], T q, double &tau,
                                          unsigned long long id, unsigned &step, unsigned &k, uint2 &rz, bool fresh,
                                          unsigned &mx, unsigned &n64) {
     const unsigned end = c.b.step0 + (unsigned)c.b.nsteps;
+    unsigned left = (unsigned)c.b.budget;
     if (!fresh) {
-        if (tau < c.b.dt && fused_advance<T, false>(c, v, x, p, q, tau, id, step, k, rz, n64)) return RUN_EVENT;
+        if (tau < c.b.dt) {
+            --left;
+            if (fused_advance<T, false>(c, v, x, p, q, tau, id, step, k, rz, n64)) return RUN_EVENT;
+        }
         mx = max(mx, k);
         ++step;
     }
-    for (unsigned started = 0; step < end; ++step, ++started) {
-        if (started >= (unsigned)c.b.budget) return RUN_MORE;
+    for (; step < end; ++step) {
+        if (left == 0) return RUN_MORE;
+        --left;
         set_step<T>(v, c.b, step);
         k = 0;
         if (fused_advance<T, true>(c, v, x, p, q, tau, id, step, 0u, rz, n64)) return RUN_EVENT;
