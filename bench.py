@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rotating_e_cascade",
-                    choices=["rotating_e_cascade", "uniform_b_emission", "standing_wave_cascade",
+                    choices=["rotating_e_cascade", "uniform_b_emission", "standing_wave_cascade", "standing_wave_grid",
                              "batched_uniform_b"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time the FP64 mode (extra key)")
@@ -71,6 +71,9 @@ def make_workload(name, scale=1.0, rank=0):
     elif name == "standing_wave_cascade":
         w = W.standing_wave_cascade(n=int(1_000_000 * scale), seed=4 + 1000 * rank,
                                     thin_cap=int(200_000_000 * scale))
+    elif name == "standing_wave_grid":
+        w = W.standing_wave_grid(n=int(1_000_000 * scale), seed=4 + 1000 * rank,
+                                 thin_cap=int(200_000_000 * scale))
     elif name == "batched_uniform_b":
         w = W.batched_uniform_b(seed=2 + 1000 * rank, size_scale=scale)
     else:
@@ -115,10 +118,22 @@ def _oracle_shard(args):
     ens = oracle.Ensemble.from_arrays(ws.species, cap)
     cfg = oracle.make_cfg(seed=w.seed, push_photons=w.push_photons, thin_cap=int(w.thin_cap * frac),
                           field_kind=w.field_kind, field_prm=w.field_prm)
+    if w.field_kind == W.FIELD_GRID:              # the caller refills the grid every step
+        def run(s0, k):
+            tot = {"particle_steps": 0, "emit_events": 0, "pair_events": 0}
+            for s in range(s0, s0 + k):
+                oracle.set_field_grid(W.grid_values(w.notes["a0"], s * w.dt))
+                st1 = oracle.push_and_generate(ens, tabs, cfg, w.dt, 1, s)
+                for key in tot:
+                    tot[key] += st1[key]
+            return tot
+    else:
+        def run(s0, k):
+            return oracle.push_and_generate(ens, tabs, cfg, w.dt, k, s0)
     if warm:
-        oracle.push_and_generate(ens, tabs, cfg, w.dt, warm, 0)
+        run(0, warm)
     t0 = time.perf_counter()
-    st = oracle.push_and_generate(ens, tabs, cfg, w.dt, steps, warm)
+    st = run(warm, steps)
     dt = time.perf_counter() - t0
     return st["particle_steps"], st["emit_events"] + st["pair_events"], dt
 
@@ -133,7 +148,7 @@ def oracle_run(name, warm, steps, target_s=15.0, procs=None):
     # seeds per shard sized from a nominal oracle rate of ~3e6 particle-steps/s
     if name == "rotating_e_cascade":
         per = 250
-    elif name == "standing_wave_cascade":
+    elif name in ("standing_wave_cascade", "standing_wave_grid"):
         per = 60
     elif name == "batched_uniform_b":
         per = 400
@@ -213,6 +228,31 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class GridFeed:
+    """The caller's side of a gridded field: the node values of step s are
+    written to a device buffer the library reads (outside the timed pushes)."""
+
+    def __init__(self, w, gen, prec):
+        import torch
+        import paper_2409_17299_gb300 as q
+        self.w = w
+        self.dev = None
+        if w.field_kind != W.FIELD_GRID:
+            return
+        nx, ny, nz = (int(v) for v in w.field_prm[:3])
+        self.dev = torch.empty((6, nz, ny, nx), device="cuda",
+                               dtype=torch.float32 if prec == q.QED_FP32 else torch.float64)
+        q.qed_set_field_grid(gen.ctx, self.dev.data_ptr())
+
+    def feed(self, step):
+        if self.dev is not None:
+            import torch
+            self.dev.copy_(torch.from_numpy(W.grid_values(self.w.notes["a0"], step * self.w.dt)))
+
+    def nbytes(self):
+        return 0 if self.dev is None else self.dev.numel() * self.dev.element_size()
+
+
 def size_cascade(w, nsteps, precision):
     """Buffer capacities that hold every step of the run: one untimed pass
     over the whole cascade, growing a species by 5% beyond the demand
@@ -225,7 +265,9 @@ def size_cascade(w, nsteps, precision):
     gen = q.Generator(cfg)
     ens = q.DeviceEnsemble.from_host(w.species, capacities(w, nsteps), prec)
     field = q.make_field(w.field_kind, w.field_prm)
+    grid = GridFeed(w, gen, prec)
     for s in range(nsteps):
+        grid.feed(s)
         while True:
             P = ens.struct()
             rc, st = q.qed_push_and_generate(gen.ctx, P, field, w.dt, 1, s)
@@ -257,7 +299,9 @@ def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_param
     field = q.make_field(w.field_kind, w.field_prm)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    grid = GridFeed(w, gen, prec)
     for s in range(warm):
+        grid.feed(s)
         gen.push(ens, field, w.dt, 1, s, auto_grow=False)
     torch.cuda.synchronize()
     evs = []
@@ -267,6 +311,7 @@ def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_param
     lepton_launches = 0
     t0 = time.perf_counter()
     for s in range(warm, warm + steps):
+        grid.feed(s)
         flush.fill_(float(s))
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -378,8 +423,11 @@ def e2e_run(w, precision, warm, steps, caps=None):
     count = [len(sp["id"]) for sp in w.species]
     field = q.make_field(w.field_kind, w.field_prm)
     stream = torch.cuda.current_stream()
+    grid = GridFeed(w, gen, prec)
 
     def one_step(s, nb):
+        grid.feed(s)                              # the step's field is an input too
+        nb[0] += grid.nbytes()
         for k in range(3):
             n = count[k]
             for f in host[k]:

@@ -24,7 +24,7 @@ TWO_PI = 2.0 * math.pi
 # these units, at which chi = 1 for a particle at rest.
 R_SCHWINGER = 329718.75885517005
 
-FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_STANDING_CP = 0, 1, 2
+FIELD_UNIFORM, FIELD_ROTATING_E, FIELD_STANDING_CP, FIELD_GRID = 0, 1, 2, 3
 SPECIES = ("electron", "positron", "photon")
 
 
@@ -99,6 +99,38 @@ def standing_wave_cascade(n=1_000_000, seed=4, a0=2000.0, steps_per_period=100, 
     return Workload("standing_wave_cascade", [e, _empty(), _empty()], FIELD_STANDING_CP, [a0],
                     TWO_PI / steps_per_period, steps_per_period * periods, push_photons=1,
                     thin_cap=thin_cap, seed=seed, notes={"n": n, "a0": a0})
+
+
+GRID_SHAPE = (128, 4, 4)          # the paper's box: one wavelength, 128 x 4 x 4 cells (Sec. 5.1)
+
+
+def standing_wave_grid(n=1_000_000, seed=4, a0=2000.0, steps_per_period=100, periods=10,
+                       thin_cap=200_000_000):
+    """The standing-wave cascade with its field given on a periodic node grid
+    (one wavelength cubed, 128 x 4 x 4 nodes) that the caller refills each
+    step with grid_values(a0, t): the input a PIC code would pass."""
+    w = standing_wave_cascade(n=n, seed=seed, a0=a0, steps_per_period=steps_per_period, periods=periods,
+                              thin_cap=thin_cap)
+    nx, ny, nz = GRID_SHAPE
+    w.name = "standing_wave_grid"
+    w.field_kind = FIELD_GRID
+    w.field_prm = [nx, ny, nz, TWO_PI, TWO_PI, TWO_PI]
+    w.notes["a0"] = a0
+    return w
+
+
+def grid_values(a0, t, shape=GRID_SHAPE):
+    """Node values (6, nz, ny, nx) of the standing circularly polarised wave
+    E = a0 cos x (0, cos t, sin t), B = a0 sin x (0, cos t, sin t) at time t
+    on the one-wavelength grid."""
+    nx, ny, nz = shape
+    x = np.arange(nx) * TWO_PI / nx
+    g = np.zeros((6, nz, ny, nx))
+    g[1] = a0 * np.cos(x) * math.cos(t)
+    g[2] = a0 * np.cos(x) * math.sin(t)
+    g[4] = a0 * np.sin(x) * math.cos(t)
+    g[5] = a0 * np.sin(x) * math.sin(t)
+    return g
 
 
 def batched_uniform_b(n_ens=64, seed=2, size_lo=1e3, size_hi=1e6, chi_lo=1e-2, chi_hi=1e2,
