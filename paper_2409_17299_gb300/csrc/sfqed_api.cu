@@ -17,6 +17,7 @@ static void free_ctx(qed_ctx *c) {
         if (p) cudaFree(p);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
     if (c->pin) cudaFreeHost(c->pin);
+    if (c->grid_il) cudaFree(c->grid_il);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_ready)
         for (int k = 0; k < 4; ++k)

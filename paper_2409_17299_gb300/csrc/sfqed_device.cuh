@@ -199,8 +199,36 @@ __device__ __forceinline__ void grid_axis(T x, int n, T inv_h, int &i0, int &i1,
     f = u - fl;
 }
 
+// The kernels read the grid interleaved, eight values per node (the six
+// components and two pads), so a node is one 32-byte (FP32) or three
+// 16-byte (FP64) vector loads.
+template <class T> __device__ __forceinline__ void load_node(const T *g, long long node, T v[6]);
+template <> __device__ __forceinline__ void load_node<float>(const float *g, long long node, float v[6]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(g + 8 * node));
+    const float2 b = __ldg(reinterpret_cast<const float2 *>(g + 8 * node + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+template <> __device__ __forceinline__ void load_node<double>(const double *g, long long node, double v[6]) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(g + 8 * node));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(g + 8 * node + 2));
+    const double2 c = __ldg(reinterpret_cast<const double2 *>(g + 8 * node + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
+// lerp in x along the cell edge at row (j, k), then into acc with weight fy
+// (first edge of a y pair: acc = the x-lerp itself)
+template <class T>
+__device__ __forceinline__ void edge_x(const T *g, long long row, int i0, int i1, T fx, T out[6]) {
+    T v0[6], v1[6];
+    load_node<T>(g, row + i0, v0);
+    load_node<T>(g, row + i1, v1);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) out[c] = fma(fx, v1[c] - v0[c], v0[c]);
+}
+
+// out of line: its register demand stays off the analytic-field path
 template <class T, class A>
-__device__ __forceinline__ void eval_grid(const A &a, const T x[3], T E[3], T B[3]) {
+__device__ __noinline__ void eval_grid(const A &a, const T x[3], T E[3], T B[3]) {
     const int nx = a.gn[0], ny = a.gn[1], nz = a.gn[2];
     int i0, i1, j0, j1, k0, k1;
     T fx, fy, fz;
@@ -213,19 +241,19 @@ __device__ __forceinline__ void eval_grid(const A &a, const T x[3], T E[3], T B[
         grid_axis<T>(x[1], ny, a.ginv_f[1], j0, j1, fy);
         grid_axis<T>(x[2], nz, a.ginv_f[2], k0, k1, fz);
     }
-    const long long plane = (long long)nx * ny, vol = plane * nz;
-    const long long o00 = k0 * plane + j0 * nx, o10 = k0 * plane + j1 * nx;
-    const long long o01 = k1 * plane + j0 * nx, o11 = k1 * plane + j1 * nx;
-    const T *g = reinterpret_cast<const T *>(a.grid);
+    const long long plane = (long long)nx * ny;
+    const T *g = reinterpret_cast<const T *>(a.grid_il);
+    T b0[6], e0[6], e1[6];
+    edge_x<T>(g, k0 * plane + (long long)j0 * nx, i0, i1, fx, e0);
+    edge_x<T>(g, k0 * plane + (long long)j1 * nx, i0, i1, fx, e1);
 #pragma unroll
-    for (int c = 0; c < 6; ++c, g += vol) {
-        const T a00 = fma(fx, __ldg(g + o00 + i1) - __ldg(g + o00 + i0), __ldg(g + o00 + i0));
-        const T a10 = fma(fx, __ldg(g + o10 + i1) - __ldg(g + o10 + i0), __ldg(g + o10 + i0));
-        const T a01 = fma(fx, __ldg(g + o01 + i1) - __ldg(g + o01 + i0), __ldg(g + o01 + i0));
-        const T a11 = fma(fx, __ldg(g + o11 + i1) - __ldg(g + o11 + i0), __ldg(g + o11 + i0));
-        const T b0 = fma(fy, a10 - a00, a00);
-        const T b1 = fma(fy, a11 - a01, a01);
-        const T v = fma(fz, b1 - b0, b0);
+    for (int c = 0; c < 6; ++c) b0[c] = fma(fy, e1[c] - e0[c], e0[c]);
+    edge_x<T>(g, k1 * plane + (long long)j0 * nx, i0, i1, fx, e0);
+    edge_x<T>(g, k1 * plane + (long long)j1 * nx, i0, i1, fx, e1);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const T b1 = fma(fy, e1[c] - e0[c], e0[c]);
+        const T v = fma(fz, b1 - b0[c], b0[c]);
         if (c < 3) E[c] = v;
         else B[c - 3] = v;
     }

@@ -100,7 +100,7 @@ struct PassArgs {
     const void *icdf_pair;  // PAIR_NCHI * PAIR_NS (T)
     const __nv_bfloat16 *mlp_w16;   // surrogate network weights, or null (table sampler)
     int field_kind;
-    const void *grid;       // QED_FIELD_GRID: node values [6][nz][ny][nx] (T)
+    const void *grid_il;    // QED_FIELD_GRID: node values interleaved [nz][ny][nx][8] (T)
     int gn[3];              // grid nodes per axis
     double ginv[3];         // nodes per unit length (n / L)
     float ginv_f[3];
@@ -162,6 +162,8 @@ struct qed_ctx {
     void *batch;                 // batched-push work buffers
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
     const void *field_grid;      // caller's gridded field values (QED_FIELD_GRID)
+    void *grid_il;               // the same interleaved per node (8 values), refreshed each call
+    size_t grid_il_bytes;
     int tuned_threads;           // block shape picked by the autotuner (0: none yet)
     int tuned_budget;            // step budget picked by the autotuner (0: none yet)
     int spec_passes;             // newborn passes enqueued per host check (from the last step)

@@ -529,6 +529,17 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     flush_stats(ctl, my_steps, my_ev, my_max, true, n64);
 }
 
+// Gridded field: [6][nodes] (caller's layout) -> [nodes][8] (two pads)
+template <class T>
+__global__ void k_grid_interleave(const T *src, T *dst, long long nodes) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nodes) return;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) dst[8 * n + c] = src[c * nodes + n];
+    dst[8 * n + 6] = (T)0;
+    dst[8 * n + 7] = (T)0;
+}
+
 // Pass ranges: at the step start every particle present; afterwards the
 // particles appended since the previous pass.
 __global__ void k_step_begin(DevCtl *ctl) {
@@ -827,12 +838,28 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.mlp_w16 = ctx->cfg.sampler == QED_SAMPLER_MLP ? ctx->mlp_w16 : nullptr;
     a.field_kind = field->kind;
     if (field->kind == QED_FIELD_GRID) {
-        a.grid = ctx->field_grid;
+        long long nodes = 1;
         for (int d = 0; d < 3; ++d) {
             a.gn[d] = (int)field->params[d];
             a.ginv[d] = (double)a.gn[d] / field->params[3 + d];
             a.ginv_f[d] = (float)a.ginv[d];
+            nodes *= a.gn[d];
         }
+        // the caller's [component][node] values, interleaved per node for the
+        // kernels (the grid is constant during the call)
+        const size_t bytes = (size_t)nodes * 8 * sizeof(T);
+        if (ctx->grid_il_bytes < bytes) {
+            if (ctx->grid_il) SFQ_CUDA(cudaFreeAsync(ctx->grid_il, ctx->stream));
+            ctx->grid_il = nullptr;
+            ctx->grid_il_bytes = 0;
+            if (cudaMallocAsync(&ctx->grid_il, bytes, ctx->stream) != cudaSuccess) return QED_ERR_NOMEM;
+            ctx->grid_il_bytes = bytes;
+        }
+        k_grid_interleave<T><<<(unsigned)((nodes + 255) / 256), 256, 0, ctx->stream>>>(
+            reinterpret_cast<const T *>(ctx->field_grid), reinterpret_cast<T *>(ctx->grid_il), nodes);
+        SFQ_LAUNCHED(ctx, 1);
+        SFQ_CUDA(cudaGetLastError());
+        a.grid_il = ctx->grid_il;
     }
     a.field_zero = field_zero_of(*field);      // chi without its cancellation guard where allowed
     for (int i = 0; i < 6; ++i) {
