@@ -226,9 +226,8 @@ __device__ __forceinline__ void edge_x(const T *g, long long row, int i0, int i1
     for (int c = 0; c < 6; ++c) out[c] = fma(fx, v1[c] - v0[c], v0[c]);
 }
 
-// out of line: its register demand stays off the analytic-field path
 template <class T, class A>
-__device__ __noinline__ void eval_grid(const A &a, const T x[3], T E[3], T B[3]) {
+__device__ __forceinline__ void eval_grid(const A &a, const T x[3], T E[3], T B[3]) {
     const int nx = a.gn[0], ny = a.gn[1], nz = a.gn[2];
     int i0, i1, j0, j1, k0, k1;
     T fx, fy, fz;
@@ -259,17 +258,8 @@ __device__ __noinline__ void eval_grid(const A &a, const T x[3], T E[3], T B[3])
     }
 }
 
-template <class A> struct HasGrid { static constexpr bool value = false; };
-template <> struct HasGrid<PassArgs> { static constexpr bool value = true; };
-
 template <class T, class A>
 __device__ __forceinline__ void eval_field_at(const A &a, const T xv[3], const Phase<T> &q, T E[3], T B[3]) {
-    if constexpr (HasGrid<A>::value) {
-        if (a.field_kind == QED_FIELD_GRID) {
-            eval_grid<T, A>(a, xv, E, B);
-            return;
-        }
-    }
     const T x = xv[0];
     if (a.field_kind == QED_FIELD_UNIFORM) {
         E[0] = prm_of<T, A>(a, 0); E[1] = prm_of<T, A>(a, 1); E[2] = prm_of<T, A>(a, 2);
@@ -378,6 +368,27 @@ __device__ __forceinline__ float chi_guarded(float e0, const float p[3], const f
     const double pd0 = p[0], pd1 = p[1], pd2 = p[2];
     const double e0d = LEPTON ? sqrt(1.0 + (pd0 * pd0 + pd1 * pd1 + pd2 * pd2)) : sqrt(pd0 * pd0 + pd1 * pd1 + pd2 * pd2);
     return (float)chi_fp64(e0d, pd0, pd1, pd2, E[0], E[1], E[2], B[0], B[1], B[2]);
+}
+
+// chi of a lepton (also gamma and p^2) or a photon in the mode's precision
+template <class T>
+__device__ __forceinline__ void lepton_chi(const T p[3], const T E[3], const T B[3], T &gam, T &chi, T &p2,
+                                           unsigned &n64, int zero = 0) {
+    if constexpr (sizeof(T) == 8) {
+        p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        gam = sqrt(1.0 + p2);
+        chi = chi_fp64(gam, p[0], p[1], p[2], E[0], E[1], E[2], B[0], B[1], B[2]);
+    } else {
+        p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        gam = sqrtf(1.0f + p2);
+        chi = chi_guarded<true>(gam, p, E, B, &n64, zero);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T photon_chi(T k0, const T k[3], const T E[3], const T B[3], unsigned &n64, int zero = 0) {
+    if constexpr (sizeof(T) == 8) return chi_fp64(k0, k[0], k[1], k[2], E[0], E[1], E[2], B[0], B[1], B[2]);
+    else return chi_guarded<false>(k0, k, E, B, &n64, zero);
 }
 
 // ---------------------------------------------------------------------------

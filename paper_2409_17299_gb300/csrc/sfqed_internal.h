@@ -210,6 +210,16 @@ qed_status sfq_level_eval(qed_ctx *ctx, qed_species *sp, int s, double w, double
 qed_status sfq_level_apply_species(qed_ctx *ctx, qed_species *sp, int s, double wstar, int64_t step);
 void sfq_level_advance(double *lo, double *hi, double *w, double *wstar, int64_t *iters, int64_t *done,
                        int64_t *alive, double A, int64_t C, int64_t N, double M, int64_t cap);
+qed_status sfq_drain_events(qed_ctx *ctx);
+// pass launchers, one per field variant (sfqed_pass_analytic.cu, sfqed_pass_grid.cu)
+namespace sfq {
+namespace pass_analytic {
+template <class T> qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons);
+}
+namespace pass_grid {
+template <class T> qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons);
+}
+}  // namespace sfq
 qed_status sfq_ensure_work(qed_ctx *ctx, int64_t n_blocks, int64_t n_slots);
 
 #define SFQ_LAUNCHED(ctx, n) ((ctx)->launches += (n))
