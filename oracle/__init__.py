@@ -96,6 +96,7 @@ def lib():
                 "or_sample_pair": (d, [p, d, d, p]),
                 "or_field": (None, [i32, p, p, d, p, p]),
                 "or_set_field_grid": (None, [p]),
+                "or_rejection_run": (C.c_int64, [p, p, d, i32, i32, C.c_uint64, p, C.c_int64, p]),
                 "or_chi": (d, [d, p, p, p]),
                 "or_boris": (None, [p, p, d, p, p, d]),
                 "or_compact": (None, [p]),
@@ -266,6 +267,20 @@ def set_field_grid(g):
     global _grid_keep
     _grid_keep = np.ascontiguousarray(g, dtype=np.float64)
     lib().or_set_field_grid(_ptr(_grid_keep))
+
+
+def rejection_run(ens: "Ensemble", cfg: "RunCfg", dt: float, nsteps: int, nsub: int, seed: int,
+                  delta_cap: int = 1 << 22):
+    """The subcycled rejection generator on the electrons of ens (species 0,
+    updated in place): returns (photon energies, emission count, largest
+    acceptance probability)."""
+    arr = ens.structs()
+    out = np.zeros(delta_cap)
+    amax = np.zeros(1)
+    n = lib().or_rejection_run(C.cast(C.byref(arr[0]), C.c_void_p), C.byref(cfg), float(dt), int(nsteps),
+                               int(nsub), C.c_uint64(seed), _ptr(out), int(delta_cap), _ptr(amax))
+    ens.pull(arr)
+    return out[: min(n, delta_cap)].copy(), int(n), float(amax[0])
 
 
 def chi(e0, p, E, B) -> float:

@@ -1033,6 +1033,76 @@ double or_rate_lambda(const double *cheb_em, const double *cheb_pair, int is_pho
     return OR_ALPHA * OR_R / e0 * or_rate_F(cheb_em, cheb_pair, is_photon, chi);
 }
 
+/* ================================================================== */
+/* 11. Independent cross-check: the subcycled rejection generator.     */
+/*     The classic alternative to Algorithm 1 (Sec. 2): the step is     */
+/*     split into nsub sub-steps h; in each, a candidate photon energy  */
+/*     fraction delta = r^3 (r uniform; the substitution keeps the      */
+/*     acceptance bounded although dW/d delta ~ delta^(-2/3) at small   */
+/*     delta) is accepted with probability 3 r^2 (dW/d delta) h, the    */
+/*     differential LCFA rate evaluated from the Bessel functions       */
+/*     directly (no rate approximant, no inverse-CDF table).  Then the  */
+/*     lepton is Boris-pushed by h.  Photons are recorded, not pushed.  */
+/*     Its own random stream (splitmix64 per particle), so the          */
+/*     comparison with Algorithm 1 is statistical.                      */
+/* ================================================================== */
+static uint64_t splitmix64(uint64_t *s)
+{
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double splitmix_u(uint64_t *s) { return ((double)(splitmix64(s) >> 11) + 0.5) * 0x1p-53; }
+
+/* Electrons of E (species 0) only.  Returns the number of emissions; fills
+ * delta_out[0..min(n, cap)) with the photon energies (m c^2) and max_accept
+ * with the largest acceptance probability met (it must stay well below 1
+ * for the method to hold). */
+int64_t or_rejection_run(or_species *E, const or_run_cfg *cfg, double dt, int nsteps, int nsub, uint64_t seed,
+                         double *delta_out, int64_t delta_cap, double *max_accept)
+{
+    const double h = dt / nsub;
+    const double pref = OR_ALPHA * OR_R / (sqrt(3.0) * M_PI);
+    int64_t nev = 0;
+    double amax = 0.0;
+    for (int64_t i = 0; i < E->count; ++i) {
+        uint64_t st = seed ^ (E->id[i] * 0xD1B54A32D192ED03ull);
+        double x[3] = { E->x[i], E->y[i], E->z[i] }, p[3] = { E->px[i], E->py[i], E->pz[i] };
+        for (int s = 0; s < nsteps; ++s) {
+            for (int k = 0; k < nsub; ++k) {
+                const double t = (s + (double)k / nsub) * dt;
+                double Ef[3], Bf[3];
+                or_field(cfg->field_kind, cfg->field_prm, x, t, Ef, Bf);
+                const double p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+                const double gamma = sqrt(1.0 + p2);
+                const double chi = or_chi(gamma, p, Ef, Bf);
+                const double r = splitmix_u(&st), u = splitmix_u(&st);
+                if (p2 > 0.0 && chi > 0.0) {
+                    const double delta = r * r * r;
+                    const double a = 3.0 * r * r * pref / gamma * or_em_bracket(chi, delta) * h;
+                    if (a > amax) amax = a;
+                    if (u < a) {
+                        /* the same energy-conserving collinear recoil as Algorithm 1 */
+                        double g_after = (1.0 - delta) * gamma;
+                        if (g_after < 1.0) g_after = 1.0;
+                        const double pa = sqrt((g_after - 1.0) * (g_after + 1.0)), inv = 1.0 / sqrt(p2);
+                        for (int d = 0; d < 3; ++d) p[d] = pa * p[d] * inv;
+                        if (nev < delta_cap) delta_out[nev] = gamma - g_after;   /* photon energy */
+                        ++nev;
+                    }
+                }
+                or_boris(x, p, -1.0, Ef, Bf, h);              /* electrons */
+            }
+        }
+        E->x[i] = x[0]; E->y[i] = x[1]; E->z[i] = x[2];
+        E->px[i] = p[0]; E->py[i] = p[1]; E->pz[i] = p[2];
+    }
+    if (max_accept) *max_accept = amax;
+    return nev;
+}
+
 double or_const(int which)
 {
     switch (which) {
