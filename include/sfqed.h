@@ -82,8 +82,27 @@ typedef struct {
     int batch_step_budget;    /* qed_batch_push: waiting-time iterations a lepton runs before
                                  it rejoins its block's queue (1..64); 0 = the autotuner's
                                  choice, else 4 */
-    int reserved[4];
+    int event_method;         /* QED_METHOD_SUBSTEP (Algorithm 1, default) or
+                                 QED_METHOD_OPTICAL_DEPTH (see below) */
+    int reserved[3];
 } qed_config;
+
+/* Event methods of qed_push_and_generate.
+ *  QED_METHOD_SUBSTEP        Algorithm 1 (Sec. 3): waiting times drawn inside the
+ *                            step, any number of events per step, newborns pushed
+ *                            to the step end (Algorithm 2).
+ *  QED_METHOD_OPTICAL_DEPTH  the classic scheme the paper compares against (Sec. 2):
+ *                            each particle carries its remaining optical depth od
+ *                            (FP64, arrays from qed_set_optical_depth).  Per step:
+ *                            the rate lambda at the step start; od <= 0 means "not
+ *                            drawn yet" and draws od = -ln u, u from Philox(id, step,
+ *                            0xFFFFFFFE) words 0-1; od -= lambda dt; push by dt; if
+ *                            od <= 0 the event happens at the end of the step (chi
+ *                            at the end point, energy from Philox(id, step, 0) words
+ *                            2-3) and od = -ln u with words 0-1.  At most one event
+ *                            per particle and step; newborns (od = 0) start at the
+ *                            next step. */
+enum { QED_METHOD_SUBSTEP = 0, QED_METHOD_OPTICAL_DEPTH = 1 };
 
 /* One species: structure of arrays (Sec. 4.1), one array set per particle
  * type.  x..w are double (QED_FP64) or float (QED_FP32) device arrays of
@@ -270,6 +289,14 @@ qed_status qed_level_apply(qed_ctx *ctx, qed_particles *p, int species, double w
  * caller may rewrite it between calls (a PIC code's new fields each step).
  * NULL detaches it.  The batched push does not take gridded fields. */
 qed_status qed_set_field_grid(qed_ctx *ctx, const void *grid_dev);
+
+/* Optical-depth arrays for QED_METHOD_OPTICAL_DEPTH: od_dev[s] holds one
+ * double per particle of species s (caller-owned device memory, at least the
+ * species' capacity), parallel to the species arrays: the library reads and
+ * writes it in the pushes, moves it with the particles in compaction and
+ * leveling, and writes 0 for every particle it appends.  Rebind after
+ * reallocating.  NULL entries detach. */
+qed_status qed_set_optical_depth(qed_ctx *ctx, double *const od_dev[3]);
 
 /* Statistics accumulated since the context was created or last reset. */
 qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset);

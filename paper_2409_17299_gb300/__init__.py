@@ -17,6 +17,7 @@ from .build import LIB, up_to_date  # noqa: F401
 QED_OK, QED_ERR_INVALID, QED_ERR_CAPACITY, QED_ERR_CUDA, QED_ERR_TIMEOUT, QED_ERR_NOMEM, QED_ERR_STATE = range(7)
 QED_FP64, QED_FP32 = 0, 1
 QED_SAMPLER_TABLE, QED_SAMPLER_MLP = 0, 1
+QED_METHOD_SUBSTEP, QED_METHOD_OPTICAL_DEPTH = 0, 1
 QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
 QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP, QED_FIELD_GRID = 0, 1, 2, 3
 
@@ -24,7 +25,7 @@ EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_batch_push", "qed_a
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
             "qed_compact_species_noalloc", "qed_train_surrogate", "qed_mlp_set_params", "qed_mlp_get_params",
             "qed_mlp_forward", "qed_mlp_grad", "qed_level_begin", "qed_level_advance", "qed_level_eval",
-            "qed_level_apply", "qed_batch_shape", "qed_set_field_grid")
+            "qed_level_apply", "qed_batch_shape", "qed_set_field_grid", "qed_set_optical_depth")
 QED_NOALLOC_MAX_ENTRIES = 1 << 20
 
 
@@ -32,7 +33,8 @@ class QedConfig(C.Structure):
     _fields_ = [("precision", C.c_int), ("sampler", C.c_int), ("seed", C.c_uint64),
                 ("push_photons", C.c_int), ("soft_photon_filter", C.c_int), ("thin_cap", C.c_int64),
                 ("restore_on_overflow", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
-                ("profile", C.c_int), ("batch_step_budget", C.c_int), ("reserved", C.c_int * 4)]
+                ("profile", C.c_int), ("batch_step_budget", C.c_int), ("event_method", C.c_int),
+                ("reserved", C.c_int * 3)]
 
 
 class QedLevelState(C.Structure):
@@ -120,6 +122,7 @@ def lib():
         "qed_level_apply": (i32, [p, p, i32, C.c_double, i64]),
         "qed_batch_shape": (i32, [p, C.POINTER(i32), C.POINTER(i32)]),
         "qed_set_field_grid": (i32, [p, p]),
+        "qed_set_optical_depth": (i32, [p, C.POINTER(C.c_void_p)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -182,6 +185,15 @@ def qed_compact(ctx, particles: QedParticles, step: int) -> int:
     if rc != QED_OK:
         raise QedError(rc, "qed_compact")
     return rc
+
+
+def qed_set_optical_depth(ctx, ptrs) -> None:
+    """Bind the three per-species optical-depth arrays (device pointers of
+    float64 arrays, or 0) for QED_METHOD_OPTICAL_DEPTH."""
+    arr = (C.c_void_p * 3)(*[C.c_void_p(int(v or 0)) for v in ptrs])
+    rc = lib().qed_set_optical_depth(ctx, arr)
+    if rc != QED_OK:
+        raise QedError(rc, "qed_set_optical_depth")
 
 
 def qed_set_field_grid(ctx, grid_dev_ptr) -> None:
@@ -368,7 +380,7 @@ def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream
 # --------------------------------------------------------------------------
 def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0, thin_cap=0,
                 restore_on_overflow=1, block_threads=0, blocks_per_sm=0, profile=0,
-                sampler=QED_SAMPLER_TABLE, batch_step_budget=0) -> QedConfig:
+                sampler=QED_SAMPLER_TABLE, batch_step_budget=0, event_method=QED_METHOD_SUBSTEP) -> QedConfig:
     c = QedConfig()
     c.precision = int(precision)
     c.sampler = int(sampler)
@@ -381,6 +393,7 @@ def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0
     c.blocks_per_sm = int(blocks_per_sm)
     c.profile = int(profile)
     c.batch_step_budget = int(batch_step_budget)
+    c.event_method = int(event_method)
     return c
 
 
@@ -399,7 +412,7 @@ class DeviceEnsemble:
     """Three species of structure-of-arrays particle buffers in torch device
     memory (caller-owned memory in the sense of the ABI)."""
 
-    def __init__(self, capacity, precision=QED_FP64, device="cuda"):
+    def __init__(self, capacity, precision=QED_FP64, device="cuda", optical_depth=False):
         import torch
         self.torch = torch
         self.precision = precision
@@ -413,13 +426,15 @@ class DeviceEnsemble:
             d = {f: torch.zeros(c, dtype=self.fdtype, device=device) for f in _FIELDS}
             d["id"] = torch.zeros(c, dtype=torch.int64, device=device)
             d["nevents"] = torch.zeros(c, dtype=torch.int32, device=device)
+            if optical_depth:               # QED_METHOD_OPTICAL_DEPTH: remaining optical depth (0: not drawn)
+                d["od"] = torch.zeros(c, dtype=torch.float64, device=device)
             self.arr.append(d)
 
     @classmethod
-    def from_host(cls, species, capacity, precision=QED_FP64, device="cuda"):
-        """species: 3 dicts of numpy arrays (x..w float64, id uint64[, nevents])."""
+    def from_host(cls, species, capacity, precision=QED_FP64, device="cuda", optical_depth=False):
+        """species: 3 dicts of numpy arrays (x..w float64, id uint64[, nevents][, od])."""
         import numpy as np
-        e = cls(capacity, precision, device)
+        e = cls(capacity, precision, device, optical_depth)
         for s, sp in enumerate(species):
             n = len(sp["id"])
             if n > e.capacity[s]:
@@ -431,6 +446,8 @@ class DeviceEnsemble:
             e.arr[s]["id"][:n].copy_(e.torch.from_numpy(np.asarray(sp["id"], dtype=np.uint64).view(np.int64)))
             if "nevents" in sp:
                 e.arr[s]["nevents"][:n].copy_(e.torch.from_numpy(np.asarray(sp["nevents"], dtype=np.uint32).view(np.int32)))
+            if optical_depth and "od" in sp:
+                e.arr[s]["od"][:n].copy_(e.torch.from_numpy(np.asarray(sp["od"], dtype=np.float64)))
             e.count[s] = n
         return e
 
@@ -458,7 +475,12 @@ class DeviceEnsemble:
         out = {f: d[f][:n].double().cpu().numpy() for f in _FIELDS}
         out["id"] = d["id"][:n].cpu().numpy().view(np.uint64)
         out["nevents"] = d["nevents"][:n].cpu().numpy().view(np.uint32)
+        if "od" in d:
+            out["od"] = d["od"][:n].cpu().numpy()
         return out
+
+    def od_ptrs(self):
+        return [d["od"].data_ptr() if "od" in d else 0 for d in self.arr]
 
     def grow(self, capacity):
         torch = self.torch
@@ -486,6 +508,7 @@ class Generator:
     def push(self, ens: DeviceEnsemble, field: QedFieldDesc, dt: float, nsteps: int, step0: int = 0,
              auto_grow: bool = True):
         while True:
+            self._bind(ens)
             P = ens.struct()
             rc, st = qed_push_and_generate(self.ctx, P, field, dt, nsteps, step0)
             ens.pull_counts(P)
@@ -496,7 +519,14 @@ class Generator:
             need = [max(2 * ens.capacity[s], 2 * st["needed_capacity"][s]) for s in range(3)]
             ens.grow(need)
 
+    def _bind(self, ens):
+        """The ensemble's optical-depth arrays (bound on every call: buffers
+        move when an ensemble grows)."""
+        if self.cfg.event_method == QED_METHOD_OPTICAL_DEPTH or any(ens.od_ptrs()):
+            qed_set_optical_depth(self.ctx, ens.od_ptrs())
+
     def compact(self, ens: DeviceEnsemble, step: int):
+        self._bind(ens)
         P = ens.struct()
         qed_compact(self.ctx, P, step)
         ens.pull_counts(P)

@@ -84,6 +84,15 @@ extern "C" qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed
     return sfq_batch_push(ctx, ens, fields, n_ens, dt, nsteps, step0, out, 0, 0);
 }
 
+extern "C" qed_status qed_set_optical_depth(qed_ctx *ctx, double *const od_dev[3]) {
+    if (!ctx || !od_dev) return QED_ERR_INVALID;
+    for (int s = 0; s < 3; ++s) {
+        if (od_dev[s] && (reinterpret_cast<uintptr_t>(od_dev[s]) & 7u)) return QED_ERR_INVALID;
+        ctx->od[s] = od_dev[s];
+    }
+    return QED_OK;
+}
+
 extern "C" qed_status qed_set_field_grid(qed_ctx *ctx, const void *grid_dev) {
     if (!ctx) return QED_ERR_INVALID;
     if (grid_dev && (reinterpret_cast<uintptr_t>(grid_dev) % (ctx->cfg.precision == QED_FP32 ? 4 : 8)))

@@ -597,6 +597,7 @@ qed_status sfq_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc
         step0 + nsteps > 0xFFFFFFFFll)
         return QED_ERR_INVALID;
     if (ctx->cfg.push_photons || ctx->cfg.thin_cap > 0) return QED_ERR_INVALID;  // step fusion needs both off
+    if (ctx->cfg.event_method != QED_METHOD_SUBSTEP) return QED_ERR_INVALID;      // Algorithm 1 only
     if (n_ens >= (1 << 20)) return QED_ERR_INVALID;
     for (int k = 0; k < n_ens; ++k) {
         if (fields[k].kind < QED_FIELD_UNIFORM || fields[k].kind > QED_FIELD_STANDING_CP) return QED_ERR_INVALID;

@@ -146,6 +146,7 @@ template <class T> __device__ __forceinline__ void move_entry(const SpeciesDev &
     st<T>(S.w, d, ld<T>(S.w, i));
     S.id[d] = S.id[i];
     S.nev[d] = S.nev[i];
+    if (S.od) S.od[d] = S.od[i];
 }
 
 // alive entries at or above A move into the holes, in rank order: the mover
@@ -689,7 +690,7 @@ qed_status compact_tiles(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     qed_status e = sfq_ensure_work(ctx, nb + 1, n);
     if (e != QED_OK) return e;
     SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
-                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
+                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr, ctx->od[s]};
     // slots: n 16-bit dead-list entries, then at most n/2 mover indices
     unsigned short *dl = reinterpret_cast<unsigned short *>(ctx->slots);
     unsigned long long *movers = ctx->slots + (n + 3) / 4;
@@ -899,7 +900,7 @@ static qed_status noalloc_compact(qed_species *sp, cudaStream_t st, unsigned lon
     const long long n = sp->count;
     const long long nb = (n + CTILE - 1) / CTILE;
     SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
-                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr};
+                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr, nullptr};
     k_noalloc_begin<<<1, 1, 0, st>>>(ctl, (unsigned long long)n);
     k_count_alive<T><<<(unsigned)nb, CT, 0, st>>>(sp->w, ctl, 0, blk);
     k_scan_blocks<<<1, 1024, 0, st>>>(blk, nb, ctl, 0);

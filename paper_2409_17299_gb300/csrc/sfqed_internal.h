@@ -90,6 +90,7 @@ struct SpeciesDev {
     unsigned long long *id;
     unsigned *nev;
     double *tau;            // birth clock of newborns (context work buffer)
+    double *od;             // remaining optical depth (QED_METHOD_OPTICAL_DEPTH), or null
 };
 
 struct PassArgs {
@@ -161,6 +162,7 @@ struct qed_ctx {
     double sync_ms;              // host time blocked in stream synchronisation
     void *batch;                 // batched-push work buffers
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
+    double *od[3];               // caller's optical-depth arrays (QED_METHOD_OPTICAL_DEPTH)
     const void *field_grid;      // caller's gridded field values (QED_FIELD_GRID)
     void *grid_il;               // the same interleaved per node (8 values), refreshed each call
     size_t grid_il_bytes;
@@ -215,9 +217,11 @@ qed_status sfq_drain_events(qed_ctx *ctx);
 namespace sfq {
 namespace pass_analytic {
 template <class T> qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons);
+template <class T> qed_status launch_od(qed_ctx *ctx, PassArgs &a, bool photons);
 }
 namespace pass_grid {
 template <class T> qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons);
+template <class T> qed_status launch_od(qed_ctx *ctx, PassArgs &a, bool photons);
 }
 }  // namespace sfq
 qed_status sfq_ensure_work(qed_ctx *ctx, int64_t n_blocks, int64_t n_slots);

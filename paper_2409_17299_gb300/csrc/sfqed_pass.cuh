@@ -176,6 +176,7 @@ __device__ __forceinline__ void emit_with(const LeptonCtx<T> &c, const T x[3], T
             P.id[slot] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
             P.nev[slot] = 0u;
             if (a.record_newborn_tau) P.tau[slot] = tau;
+            if (P.od) P.od[slot] = 0.0;       // optical depth not drawn yet
         } else {
             note_overflow(c.ctl, 2, slot);
         }
@@ -510,6 +511,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                     P.id[se] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
                     P.nev[se] = 0u;
                     P.tau[se] = tau;
+                    if (P.od) P.od[se] = 0.0;
                 } else {
                     note_overflow(ctl, 0, se);
                 }
@@ -521,6 +523,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                     P.id[sp] = (unsigned long long)rid.z | ((unsigned long long)rid.w << 32);
                     P.nev[sp] = 0u;
                     P.tau[sp] = tau;
+                    if (P.od) P.od[sp] = 0.0;
                 } else {
                     note_overflow(ctl, 1, sp);
                 }
@@ -539,6 +542,171 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     flush_stats(ctl, my_steps, my_ev, my_max, true, n64);
 }
 
+
+// ---- the classic accumulated-optical-depth method (QED_METHOD_OPTICAL_DEPTH) ----
+// Per particle and step: the rate at the step start; an optical depth not
+// drawn yet (od <= 0) is drawn as -ln u from Philox(id, step, OD_DRAW); od
+// decreases by lambda dt; the particle is pushed by dt; if od <= 0 the event
+// happens at the end of the step (chi at the end point, energy from
+// Philox(id, step, 0) words 2-3) and a fresh od = -ln u from words 0-1.  At
+// most one event per particle and step; the children start at the next step.
+constexpr unsigned OD_DRAW = 0xFFFFFFFEu;
+
+template <class T>
+__device__ __forceinline__ double od_draw(const PassArgs &a, unsigned long long id, unsigned k) {
+    const uint4 r = event_draw(a.keys, id, a.step, k);
+    double u, v;
+    Uniform<double>::draw(r.x, r.y, u, v);
+    return -log(u);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_lepton_od(PassArgs a) {
+    __shared__ T s_coef[NCOEF];
+    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    __syncthreads();
+    DevCtl *ctl = a.ctl;
+    const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
+    const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
+    const unsigned long long n = n0 + n1;
+    const LeptonCtx<T> c{a, ctl, s_coef, reinterpret_cast<const T *>(a.icdf_em), ctl->capacity[2], (T)(ALPHA * RS),
+                         time_phase<T>(a, 0.0)};
+    unsigned long long my_steps = 0, my_ev = 0;
+    unsigned my_max = 0, n64 = 0;
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const int s = j < n0 ? 0 : 1;
+        const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
+        const SpeciesDev &S = a.sp[s];
+        const T w = ld<T>(S.w, i);
+        if (!(w > (T)0)) continue;
+        T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
+        T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
+        const unsigned long long id = S.id[i];
+        double od = S.od[i];
+        ++my_steps;
+        T E[3], B[3];
+        field_at<T>(a, x, c.ph0, E, B);
+        T gam, chi, p2;
+        lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
+        const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
+        if (!(od > 0.0)) od = od_draw<T>(a, id, OD_DRAW);
+        od = od - __dmul_rn((double)lam, a.dt);       // two roundings, as in the oracle
+        const T qch = s == 0 ? (T)-1 : (T)1;
+        boris<T>(x, p, qch, E, B, (T)a.dt);
+        unsigned k = 0;
+        if (od <= 0.0) {
+            // the event at the end of the step
+            field_tau<T>(a, x, a.dt, E, B);
+            lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
+            const uint4 r = event_draw(a.keys, id, a.step, 0u);
+            T om, ue, ve;
+            Uniform<T>::draw(r.z, r.w, ue, ve);
+            const T delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
+            emit_with<T>(c, x, p, a.dt, w, id, 0u, gam, p2, delta, om);
+            double u, v;
+            Uniform<double>::draw(r.x, r.y, u, v);
+            od = -log(u);
+            k = 1;
+        }
+        st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
+        st<T>(S.px, i, p[0]); st<T>(S.py, i, p[1]); st<T>(S.pz, i, p[2]);
+        S.od[i] = od;
+        if (k) S.nev[i] += 1u;
+        my_ev += k;
+        my_max = max(my_max, k);
+    }
+    __syncwarp();
+    flush_stats(ctl, my_steps, my_ev, my_max, false, n64);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_photon_od(PassArgs a) {
+    __shared__ T s_coef[NCOEF];
+    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    __syncthreads();
+    DevCtl *ctl = a.ctl;
+    const unsigned long long b = ctl->begin[2], n = ctl->end[2] - b;
+    const unsigned long long cap_e = ctl->capacity[0], cap_p = ctl->capacity[1];
+    const T *icdf = reinterpret_cast<const T *>(a.icdf_pair);
+    const T alpha_r = (T)(ALPHA * RS);
+    const SpeciesDev &S = a.sp[2];
+    unsigned long long my_steps = 0, my_ev = 0;
+    unsigned my_max = 0, n64 = 0;
+    const Phase<T> ph0 = time_phase<T>(a, 0.0);
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = b + j;
+        T w = ld<T>(S.w, i);
+        if (!(w > (T)0)) continue;
+        T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
+        const T kv[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
+        const unsigned long long id = S.id[i];
+        double od = S.od[i];
+        ++my_steps;
+        const T k0 = m_sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+        unsigned k = 0;
+        if (k0 > (T)0) {
+            const T inv = (T)1 / k0;
+            const T nx = kv[0] * inv, ny = kv[1] * inv, nz = kv[2] * inv;
+            T E[3], B[3];
+            field_at<T>(a, x, ph0, E, B);
+            T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
+            const T lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);
+            if (!(od > 0.0)) od = od_draw<T>(a, id, OD_DRAW);
+            od = od - __dmul_rn((double)lam, a.dt);       // two roundings, as in the oracle
+            const T h = (T)a.dt;
+            x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
+            if (od <= 0.0) {
+                // pair creation at the end of the step
+                field_tau<T>(a, x, a.dt, E, B);
+                chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
+                const uint4 r = event_draw(a.keys, id, a.step, 0u);
+                T om, ue, ve;
+                Uniform<T>::draw(r.z, r.w, ue, ve);
+                const T delta = sample_pair<T>(icdf, chi, ue, ve, &om);
+                T em = delta * k0, ep = om * k0;
+                em = em < (T)1 ? (T)1 : em;
+                ep = ep < (T)1 ? (T)1 : ep;
+                const T pm = m_sqrt((em - (T)1) * (em + (T)1)), pp = m_sqrt((ep - (T)1) * (ep + (T)1));
+                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, 0u);
+                const unsigned long long se = warp_append(&ctl->count[0], 1);
+                const unsigned long long sp = warp_append(&ctl->count[1], 1);
+                if (se < cap_e) {
+                    const SpeciesDev &P = a.sp[0];
+                    st<T>(P.x, se, x[0]); st<T>(P.y, se, x[1]); st<T>(P.z, se, x[2]);
+                    st<T>(P.px, se, pm * nx); st<T>(P.py, se, pm * ny); st<T>(P.pz, se, pm * nz);
+                    st<T>(P.w, se, w);
+                    P.id[se] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
+                    P.nev[se] = 0u;
+                    P.od[se] = 0.0;
+                } else {
+                    note_overflow(ctl, 0, se);
+                }
+                if (sp < cap_p) {
+                    const SpeciesDev &P = a.sp[1];
+                    st<T>(P.x, sp, x[0]); st<T>(P.y, sp, x[1]); st<T>(P.z, sp, x[2]);
+                    st<T>(P.px, sp, pp * nx); st<T>(P.py, sp, pp * ny); st<T>(P.pz, sp, pp * nz);
+                    st<T>(P.w, sp, w);
+                    P.id[sp] = (unsigned long long)rid.z | ((unsigned long long)rid.w << 32);
+                    P.nev[sp] = 0u;
+                    P.od[sp] = 0.0;
+                } else {
+                    note_overflow(ctl, 1, sp);
+                }
+                w = (T)0;
+                k = 1;
+            }
+        }
+        st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
+        S.od[i] = od;
+        if (k) { st<T>(S.w, i, w); S.nev[i] += 1u; }
+        my_ev += k;
+        my_max = max(my_max, k);
+    }
+    __syncwarp();
+    flush_stats(ctl, my_steps, my_ev, my_max, true, n64);
+}
 
 // ---- host side ----
 template <class K>
@@ -613,6 +781,24 @@ qed_status launch_pass_t(qed_ctx *ctx, PassArgs &a, bool photons) {
     SFQ_LAUNCHED(ctx, 1);
     if (photons) {
         e = timed_launch(ctx, 1, [&] { k_photon_pass<T, FRESH><<<bp, threads, 0, st>>>(a); });
+        if (e != QED_OK) return e;
+        SFQ_LAUNCHED(ctx, 1);
+    }
+    SFQ_CUDA(cudaGetLastError());
+    return QED_OK;
+}
+
+// the optical-depth method: one launch per species kind and step
+template <class T>
+qed_status launch_od(qed_ctx *ctx, PassArgs &a, bool photons) {
+    cudaStream_t st = ctx->stream;
+    const int bl = resident_blocks(ctx, k_lepton_od<T>, 256);
+    qed_status e = timed_launch(ctx, 0, [&] { k_lepton_od<T><<<bl, 256, 0, st>>>(a); });
+    if (e != QED_OK) return e;
+    SFQ_LAUNCHED(ctx, 1);
+    if (photons) {
+        const int bp = resident_blocks(ctx, k_photon_od<T>, 256);
+        e = timed_launch(ctx, 1, [&] { k_photon_od<T><<<bp, 256, 0, st>>>(a); });
         if (e != QED_OK) return e;
         SFQ_LAUNCHED(ctx, 1);
     }

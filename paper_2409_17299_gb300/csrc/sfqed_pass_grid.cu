@@ -6,3 +6,5 @@
 
 template qed_status sfq::pass_grid::launch_pass<float>(qed_ctx *, sfq::PassArgs &, bool);
 template qed_status sfq::pass_grid::launch_pass<double>(qed_ctx *, sfq::PassArgs &, bool);
+template qed_status sfq::pass_grid::launch_od<float>(qed_ctx *, sfq::PassArgs &, bool);
+template qed_status sfq::pass_grid::launch_od<double>(qed_ctx *, sfq::PassArgs &, bool);

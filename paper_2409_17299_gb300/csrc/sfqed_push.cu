@@ -130,7 +130,7 @@ static size_t elem_bytes(const qed_ctx *ctx) { return ctx->cfg.precision == QED_
 static qed_status snapshot(qed_ctx *ctx, qed_particles *p, bool restore) {
     const size_t eb = elem_bytes(ctx);
     size_t need = 0;
-    for (int s = 0; s < 3; ++s) need += (size_t)p->s[s].count * (7 * eb + 8 + 4);
+    for (int s = 0; s < 3; ++s) need += (size_t)p->s[s].count * (7 * eb + 8 + 4 + (ctx->od[s] ? 8 : 0));
     if (!restore && (int64_t)need > ctx->snap_bytes) {
         if (ctx->snap) SFQ_CUDA(cudaFreeAsync(ctx->snap, ctx->stream));
         ctx->snap = nullptr;
@@ -155,6 +155,11 @@ static qed_status snapshot(qed_ctx *ctx, qed_particles *p, bool restore) {
         if (restore) SFQ_CUDA(cudaMemcpyAsync(S.nevents, b, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
         else SFQ_CUDA(cudaMemcpyAsync(b, S.nevents, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
         b += n * 4;
+        if (ctx->od[s]) {
+            if (restore) SFQ_CUDA(cudaMemcpyAsync(ctx->od[s], b, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            else SFQ_CUDA(cudaMemcpyAsync(b, ctx->od[s], n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            b += n * 8;
+        }
     }
     return QED_OK;
 }
@@ -212,6 +217,12 @@ static qed_status launch_pass(qed_ctx *ctx, PassArgs &a, bool photons) {
 }
 
 template <class T>
+static qed_status launch_od(qed_ctx *ctx, PassArgs &a, bool photons) {
+    if (a.field_kind == QED_FIELD_GRID) return pass_grid::launch_od<T>(ctx, a, photons);
+    return pass_analytic::launch_od<T>(ctx, a, photons);
+}
+
+template <class T>
 static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
                             int64_t step0, qed_stats *out) {
     const bool cascade = ctx->cfg.push_photons != 0;
@@ -253,7 +264,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     for (int s = 0; s < 3; ++s) {
         const qed_species &S = p->s[s];
         a.sp[s] = SpeciesDev{S.x, S.y, S.z, S.px, S.py, S.pz, S.w,
-                             reinterpret_cast<unsigned long long *>(S.id), S.nevents, ctx->tau[s]};
+                             reinterpret_cast<unsigned long long *>(S.id), S.nevents, ctx->tau[s], ctx->od[s]};
     }
     a.ctl = ctx->ctl;
     const bool f32 = sizeof(T) == 4;
@@ -311,9 +322,14 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
         a.pass = 0;
         k_step_begin<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
         SFQ_LAUNCHED(ctx, 1);
-        qed_status e = launch_pass<T>(ctx, a, cascade);
+        const bool od_method = ctx->cfg.event_method == QED_METHOD_OPTICAL_DEPTH;
+        qed_status e = od_method ? launch_od<T>(ctx, a, cascade) : launch_pass<T>(ctx, a, cascade);
         if (e != QED_OK) return e;
-        if (cascade) {
+        if (cascade && od_method) {
+            // one event at most per step: the children start at the next step
+            e = read_ctl(ctx);
+            if (e != QED_OK) return e;
+        } else if (cascade) {
             // Algorithm 2: sweep the newborns until a pass creates nothing.
             // Passes are enqueued in groups without waiting for the host: a
             // pass whose range is empty (set up after a pass that created
@@ -421,6 +437,13 @@ qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field,
     if (!ctx || !p || !field || nsteps < 0 || !(dt > 0.0) || step0 < 0 || step0 + nsteps > 0xFFFFFFFFll)
         return QED_ERR_INVALID;
     if (field->kind < QED_FIELD_UNIFORM || field->kind > QED_FIELD_GRID) return QED_ERR_INVALID;
+    if (ctx->cfg.event_method == QED_METHOD_OPTICAL_DEPTH) {
+        for (int s = 0; s < 3; ++s)
+            if (p->s[s].capacity > 0 && !ctx->od[s]) return QED_ERR_STATE;   // qed_set_optical_depth first
+        if (ctx->cfg.sampler == QED_SAMPLER_MLP) return QED_ERR_INVALID;     // the table sampler only
+    } else if (ctx->cfg.event_method != QED_METHOD_SUBSTEP) {
+        return QED_ERR_INVALID;
+    }
     if (field->kind == QED_FIELD_GRID) {
         if (!ctx->field_grid) return QED_ERR_STATE;
         for (int d = 0; d < 3; ++d) {
