@@ -52,13 +52,14 @@ class Species(C.Structure):
     _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("px", C.c_void_p), ("py", C.c_void_p), ("pz", C.c_void_p),
                 ("w", C.c_void_p), ("id", C.c_void_p), ("nevents", C.c_void_p),
-                ("count", C.c_int64), ("capacity", C.c_int64)]
+                ("od", C.c_void_p), ("count", C.c_int64), ("capacity", C.c_int64)]
 
 
 class RunCfg(C.Structure):
     _fields_ = [("push_photons", C.c_int), ("soft_photon_filter", C.c_int),
                 ("thin_cap", C.c_int64), ("seed", C.c_uint64),
-                ("field_kind", C.c_int), ("field_prm", C.c_double * 16)]
+                ("field_kind", C.c_int), ("field_prm", C.c_double * 16),
+                ("event_method", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -303,6 +304,8 @@ def boris(x, p, q, E, B, h):
 # ensembles and the step
 # --------------------------------------------------------------------------
 _FIELDS = ("x", "y", "z", "px", "py", "pz", "w")
+_ALL = _FIELDS + ("id", "nevents", "od")
+METHOD_SUBSTEP, METHOD_OPTICAL_DEPTH = 0, 1
 
 
 class Ensemble:
@@ -314,12 +317,13 @@ class Ensemble:
             d = {f: np.zeros(cap) for f in _FIELDS}
             d["id"] = np.zeros(cap, dtype=np.uint64)
             d["nevents"] = np.zeros(cap, dtype=np.uint32)
+            d["od"] = np.zeros(cap)       # remaining optical depth, 0 = not drawn yet
             d["count"] = 0
             self.sp.append(d)
 
     @classmethod
     def from_arrays(cls, species_arrays, capacity):
-        """species_arrays: list of 3 dicts with x,y,z,px,py,pz,w,id[,nevents]."""
+        """species_arrays: list of 3 dicts with x,y,z,px,py,pz,w,id[,nevents][,od]."""
         e = cls(capacity)
         for s, arr in enumerate(species_arrays):
             n = len(arr["id"]) if arr is not None else 0
@@ -330,8 +334,9 @@ class Ensemble:
                     e.sp[s][f][:n] = arr[f]
             if n:
                 e.sp[s]["id"][:n] = arr["id"]
-                if "nevents" in arr:
-                    e.sp[s]["nevents"][:n] = arr["nevents"]
+                for f in ("nevents", "od"):
+                    if f in arr:
+                        e.sp[s][f][:n] = arr[f]
             e.sp[s]["count"] = n
         return e
 
@@ -339,7 +344,7 @@ class Ensemble:
         arr = (Species * 3)()
         for s in range(3):
             d = self.sp[s]
-            for f in _FIELDS + ("id", "nevents"):
+            for f in _ALL:
                 setattr(arr[s], f, d[f].ctypes.data)
             arr[s].count = d["count"]
             arr[s].capacity = len(d["id"])
@@ -355,7 +360,7 @@ class Ensemble:
             cap = max(capacity[s], len(d["id"]))
             if cap == len(d["id"]):
                 continue
-            for f in _FIELDS + ("id", "nevents"):
+            for f in _ALL:
                 a = np.zeros(cap, dtype=d[f].dtype)
                 a[: len(d[f])] = d[f]
                 d[f] = a
@@ -363,7 +368,7 @@ class Ensemble:
     def copy(self):
         e = Ensemble([len(d["id"]) for d in self.sp])
         for s in range(3):
-            for f in _FIELDS + ("id", "nevents"):
+            for f in _ALL:
                 e.sp[s][f][:] = self.sp[s][f]
             e.sp[s]["count"] = self.sp[s]["count"]
         return e
@@ -371,12 +376,13 @@ class Ensemble:
     def view(self, s):
         d = self.sp[s]
         n = d["count"]
-        return {f: d[f][:n].copy() for f in _FIELDS + ("id", "nevents")}
+        return {f: d[f][:n].copy() for f in _ALL}
 
 
 def make_cfg(seed=0, push_photons=1, soft_photon_filter=0, thin_cap=0,
-             field_kind=FIELD_UNIFORM, field_prm=()):
+             field_kind=FIELD_UNIFORM, field_prm=(), event_method=METHOD_SUBSTEP):
     c = RunCfg()
+    c.event_method = int(event_method)
     c.push_photons = int(push_photons)
     c.soft_photon_filter = int(soft_photon_filter)
     c.thin_cap = int(thin_cap)

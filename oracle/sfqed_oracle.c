@@ -15,6 +15,8 @@
  *                        pushed to the end of the same step
  *   Sec. 3               rates from an approximation of precomputed rates,
  *                        energies by inverse sampling of 2-D (chi, energy) tables
+ *   Sec. 3               the accumulated optical-depth scheme of other codes
+ *                        (rate once per step, at most one event per step)
  *   Sec. 4.2             per-thread buffers merged after the push; filtering
  *                        and thinning at the merge
  *   Sec. 5.1             "global leveling" resampling keeps the count bounded
@@ -32,7 +34,10 @@
  * tables against the exact CDF (KS, node round trip); Boris against the
  * closed forms for uniform B and uniform E; the event loop against Poisson and
  * waiting-time laws, energy and charge conservation; leveling against its
- * defining equation and weight conservation in expectation.
+ * defining equation and weight conservation in expectation; the optical-depth
+ * scheme against the per-step event probability 1 - exp(-lambda dt) integrated
+ * over its renewal process, against a hand-stepped single particle and
+ * against Algorithm 1 in the limit lambda dt -> 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -672,6 +677,7 @@ typedef struct {
     double *x, *y, *z, *px, *py, *pz, *w;
     uint64_t *id;
     uint32_t *nevents;
+    double *od;                /* remaining optical depth (optical-depth method); may be NULL */
     int64_t count, capacity;
 } or_species;
 
@@ -682,6 +688,7 @@ typedef struct {
     uint64_t seed;
     int field_kind;
     double field_prm[16];
+    int event_method;          /* 0: Algorithm 1 sub-stepping; 1: accumulated optical depth */
 } or_run_cfg;
 
 typedef struct {
@@ -694,7 +701,7 @@ typedef struct {
 /* one particle while it is being pushed through the step */
 typedef struct {
     int sp;                    /* 0 e-, 1 e+, 2 photon */
-    double x[3], p[3], w, tau;
+    double x[3], p[3], w, tau, od;
     uint64_t id;
     uint32_t nevents, k;
     int64_t slot;              /* index in the ensemble, -1 for a newborn */
@@ -857,6 +864,7 @@ static void load_particle(or_species *S, int sp, int64_t i, or_particle *P)
     P->x[0] = S->x[i]; P->x[1] = S->y[i]; P->x[2] = S->z[i];
     P->p[0] = S->px[i]; P->p[1] = S->py[i]; P->p[2] = S->pz[i];
     P->w = S->w[i]; P->id = S->id[i]; P->nevents = S->nevents[i];
+    P->od = S->od ? S->od[i] : 0.0;
     P->tau = 0.0; P->k = 0; P->slot = i;
 }
 
@@ -865,6 +873,7 @@ static void store_particle(or_species *S, int64_t i, const or_particle *P)
     S->x[i] = P->x[0]; S->y[i] = P->x[1]; S->z[i] = P->x[2];
     S->px[i] = P->p[0]; S->py[i] = P->p[1]; S->pz[i] = P->p[2];
     S->w[i] = P->w; S->id[i] = P->id; S->nevents[i] = P->nevents;
+    if (S->od) S->od[i] = P->od;
 }
 
 /* Returns 0, or 2 when a species ran out of capacity (needed_capacity set). */
@@ -917,6 +926,122 @@ static int run_avalanche(const or_step_ctx *c, or_species *sp, int species, int6
     return rc;
 }
 
+/* ------------------------------------------------------------------ */
+/* The accumulated optical-depth scheme (Sec. 3, the inverse-sampling  */
+/* method used by other PIC codes, no sub-cycling).  Reading: the rate */
+/* is taken once, at the start of the step; the optical depth d falls  */
+/* by lambda * dt (first-order Euler); a particle whose d reaches 0    */
+/* has its event at the end of the step (chi at the end point) and     */
+/* draws a fresh d.  At most one event per particle and step; the      */
+/* children start at the next step with d not drawn yet (0).  A d that  */
+/* is not positive on entry is drawn first, from counter word 3 =       */
+/* 0xFFFFFFFE; the event uses word 3 = 0 (words 0-1: the new d, 2-3:    */
+/* the energy), child ids as in Algorithm 1.                            */
+/* ------------------------------------------------------------------ */
+#define OR_OD_DRAW 0xFFFFFFFEu
+
+static double od_initial(const or_step_ctx *c, uint64_t id)
+{
+    uint32_t r[4];
+    philox_event(c, id, OR_OD_DRAW, c->cfg->seed, r);
+    return -log(or_u52(r[0], r[1]));
+}
+
+static void lepton_step_od(const or_step_ctx *c, or_species *sp, int species, int64_t i, int *rc)
+{
+    const or_run_cfg *cfg = c->cfg;
+    or_particle P;
+    load_particle(&sp[species], species, i, &P);
+    double q = (species == 0) ? -1.0 : 1.0;
+    double E[3], B[3];
+    or_field(cfg->field_kind, cfg->field_prm, P.x, c->t_n, E, B);
+    double p2 = P.p[0] * P.p[0] + P.p[1] * P.p[1] + P.p[2] * P.p[2];
+    double gamma = sqrt(1.0 + p2);
+    double chi = or_chi(gamma, P.p, E, B);
+    double lambda = (p2 > 0.0) ? OR_ALPHA * OR_R / gamma * or_rate_F(c->cheb_em, c->cheb_pair, 0, chi) : 0.0;
+    if (!(P.od > 0.0)) P.od = od_initial(c, P.id);
+    P.od -= lambda * c->dt;
+    or_boris(P.x, P.p, q, E, B, c->dt);
+    c->st->particle_steps += 1;
+    if (P.od <= 0.0) {
+        uint32_t r[4];
+        philox_event(c, P.id, 0, cfg->seed, r);
+        or_field(cfg->field_kind, cfg->field_prm, P.x, c->t_n + c->dt, E, B);
+        double pm2 = P.p[0] * P.p[0] + P.p[1] * P.p[1] + P.p[2] * P.p[2];
+        double g = sqrt(1.0 + pm2);
+        double one_m;
+        double delta = or_sample_emission(c->icdf_em, or_chi(g, P.p, E, B), or_u52(r[2], r[3]), &one_m);
+        double g_after = one_m * g, k0 = delta * g;
+        if (g_after < 1.0) { g_after = 1.0; k0 = g - 1.0; }
+        double pabs = sqrt(pm2);
+        double nx = P.p[0] / pabs, ny = P.p[1] / pabs, nz = P.p[2] / pabs;
+        double pa = sqrt((g_after - 1.0) * (g_after + 1.0));
+        if (!(cfg->soft_photon_filter && k0 < 2.0)) {
+            or_particle ph;
+            memset(&ph, 0, sizeof ph);         /* od = 0: drawn at its first step */
+            ph.sp = 2;
+            for (int d = 0; d < 3; ++d) ph.x[d] = P.x[d];
+            ph.p[0] = k0 * nx; ph.p[1] = k0 * ny; ph.p[2] = k0 * nz;
+            ph.w = P.w; ph.slot = -1;
+            uint32_t rid[4];
+            philox_event(c, P.id, 0, cfg->seed ^ OR_CHILD_KEY_XOR, rid);
+            ph.id = (uint64_t)rid[0] | ((uint64_t)rid[1] << 32);
+            if (append_particle(sp, &ph, c->st)) *rc = 2;
+        }
+        P.p[0] = pa * nx; P.p[1] = pa * ny; P.p[2] = pa * nz;
+        P.od = -log(or_u52(r[0], r[1]));
+        P.nevents += 1;
+        c->st->emit_events += 1;
+        if (c->st->max_subevents < 1) c->st->max_subevents = 1;
+    }
+    store_particle(&sp[species], i, &P);
+}
+
+static void photon_step_od(const or_step_ctx *c, or_species *sp, int64_t i, int *rc)
+{
+    const or_run_cfg *cfg = c->cfg;
+    or_particle G;
+    load_particle(&sp[2], 2, i, &G);
+    c->st->particle_steps += 1;
+    double k0 = sqrt(G.p[0] * G.p[0] + G.p[1] * G.p[1] + G.p[2] * G.p[2]);
+    if (!(k0 > 0.0)) return;                    /* a photon without momentum stays put */
+    double E[3], B[3];
+    or_field(cfg->field_kind, cfg->field_prm, G.x, c->t_n, E, B);
+    double lambda = OR_ALPHA * OR_R / k0 * or_rate_F(c->cheb_em, c->cheb_pair, 1, or_chi(k0, G.p, E, B));
+    if (!(G.od > 0.0)) G.od = od_initial(c, G.id);
+    G.od -= lambda * c->dt;
+    double nx = G.p[0] / k0, ny = G.p[1] / k0, nz = G.p[2] / k0;
+    G.x[0] += nx * c->dt; G.x[1] += ny * c->dt; G.x[2] += nz * c->dt;
+    if (G.od <= 0.0) {
+        uint32_t r[4], rid[4];
+        philox_event(c, G.id, 0, cfg->seed, r);
+        or_field(cfg->field_kind, cfg->field_prm, G.x, c->t_n + c->dt, E, B);
+        double one_m;
+        double delta = or_sample_pair(c->icdf_pair, or_chi(k0, G.p, E, B), or_u52(r[2], r[3]), &one_m);
+        double em = delta * k0, ep = one_m * k0;
+        if (em < 1.0) em = 1.0;
+        if (ep < 1.0) ep = 1.0;
+        double pm = sqrt((em - 1.0) * (em + 1.0)), pp = sqrt((ep - 1.0) * (ep + 1.0));
+        philox_event(c, G.id, 0, cfg->seed ^ OR_CHILD_KEY_XOR, rid);
+        or_particle a, b;
+        memset(&a, 0, sizeof a); memset(&b, 0, sizeof b);
+        a.sp = 0; b.sp = 1;
+        for (int d = 0; d < 3; ++d) { a.x[d] = G.x[d]; b.x[d] = G.x[d]; }
+        a.p[0] = pm * nx; a.p[1] = pm * ny; a.p[2] = pm * nz;
+        b.p[0] = pp * nx; b.p[1] = pp * ny; b.p[2] = pp * nz;
+        a.w = b.w = G.w; a.slot = b.slot = -1;
+        a.id = (uint64_t)rid[0] | ((uint64_t)rid[1] << 32);
+        b.id = (uint64_t)rid[2] | ((uint64_t)rid[3] << 32);
+        if (append_particle(sp, &a, c->st)) *rc = 2;
+        if (append_particle(sp, &b, c->st)) *rc = 2;
+        G.w = 0.0;                      /* the photon is eliminated */
+        G.nevents += 1;
+        c->st->pair_events += 1;
+        if (c->st->max_subevents < 1) c->st->max_subevents = 1;
+    }
+    store_particle(&sp[2], i, &G);
+}
+
 /* Stable removal of dead entries (weight 0), Sec. 4.2 merge step. */
 void or_compact(or_species *S)
 {
@@ -927,6 +1052,7 @@ void or_compact(or_species *S)
                 S->x[n] = S->x[i]; S->y[n] = S->y[i]; S->z[n] = S->z[i];
                 S->px[n] = S->px[i]; S->py[n] = S->py[i]; S->pz[n] = S->pz[i];
                 S->w[n] = S->w[i]; S->id[n] = S->id[i]; S->nevents[n] = S->nevents[i];
+                if (S->od) S->od[n] = S->od[i];
             }
             ++n;
         }
@@ -1011,7 +1137,12 @@ int or_push_and_generate(or_species *sp /* [3] */, const double *cheb_em, const 
             if (species == 2 && !cfg->push_photons) continue;
             for (int64_t i = 0; i < n0[species]; ++i) {
                 if (!(sp[species].w[i] > 0.0)) continue;
-                if (run_avalanche(&c, sp, species, i)) rc = 2;
+                if (cfg->event_method == 1) {
+                    if (species == 2) photon_step_od(&c, sp, i, &rc);
+                    else lepton_step_od(&c, sp, species, i, &rc);
+                } else if (run_avalanche(&c, sp, species, i)) {
+                    rc = 2;
+                }
             }
         }
         if (rc) return rc;
