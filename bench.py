@@ -35,6 +35,10 @@ EMIT_BYTES = {"fp32": 8 + 7 * 4 + 8 + 4 + 8, "fp64": 8 + 7 * 8 + 8 + 4 + 8}
 # lepton records (x, p, w, id, nevents, birth clock)
 PHOTON_BYTES = {"fp32": 4 + 3 * 4 + 3 * 4 + 8 + 3 * 4, "fp64": 8 + 3 * 8 + 3 * 8 + 8 + 3 * 8}
 PAIR_BYTES = {"fp32": 4 + 2 * (7 * 4 + 8 + 4 + 8), "fp64": 8 + 2 * (7 * 8 + 8 + 4 + 8)}
+# optical-depth scheme, per particle-step: the same records plus the optical
+# depth (working precision) read and written
+OD_LEPTON_BYTES = {"fp32": LEPTON_BYTES["fp32"] + 8, "fp64": LEPTON_BYTES["fp64"] + 16}
+OD_PHOTON_BYTES = {"fp32": PHOTON_BYTES["fp32"] + 8, "fp64": PHOTON_BYTES["fp64"] + 16}
 # DRAM bytes (read + write) per photon-step of the step-start photon pass,
 # from one ncu capture of the current kernel (696 MB for a launch over the
 # ~1.5e7 capped photons of the 0.3-scale cascade; see
@@ -56,6 +60,8 @@ def parse():
     ap.add_argument("--compare-mlp", type=int, default=1,
                     help="also train the surrogate sampler (1e8 table draws) and time the cascade with it")
     ap.add_argument("--mlp-samples", type=float, default=1e8)
+    ap.add_argument("--compare-od", type=int, default=1,
+                    help="also time the accumulated optical-depth scheme on the same workload (extra key)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e", type=int, default=1)
     ap.add_argument("--scale", type=float, default=1.0, help="scale the seed count (tests only)")
@@ -253,7 +259,7 @@ class GridFeed:
         return 0 if self.dev is None else self.dev.numel() * self.dev.element_size()
 
 
-def size_cascade(w, nsteps, precision):
+def size_cascade(w, nsteps, precision, method=0):
     """Buffer capacities that hold every step of the run: one untimed pass
     over the whole cascade, growing a species by 5% beyond the demand
     whenever a step overflows (the step is replayed identically)."""
@@ -261,14 +267,15 @@ def size_cascade(w, nsteps, precision):
     import paper_2409_17299_gb300 as q
     prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
-                        restore_on_overflow=1)
+                        restore_on_overflow=1, event_method=method)
     gen = q.Generator(cfg)
-    ens = q.DeviceEnsemble.from_host(w.species, capacities(w, nsteps), prec)
+    ens = q.DeviceEnsemble.from_host(w.species, capacities(w, nsteps), prec, optical_depth=method != 0)
     field = q.make_field(w.field_kind, w.field_prm)
     grid = GridFeed(w, gen, prec)
     for s in range(nsteps):
         grid.feed(s)
         while True:
+            gen._bind(ens)
             P = ens.struct()
             rc, st = q.qed_push_and_generate(gen.ctx, P, field, w.dt, 1, s)
             ens.pull_counts(P)
@@ -284,18 +291,19 @@ def size_cascade(w, nsteps, precision):
     return caps
 
 
-def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_params=None, caps=None):
+def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_params=None, caps=None, method=0):
     import torch
     import paper_2409_17299_gb300 as q
     prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
     # capacities are sized for the whole run, so no per-call overflow snapshot
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
-                        profile=int(profile), restore_on_overflow=0,
+                        profile=int(profile), restore_on_overflow=0, event_method=method,
                         sampler=q.QED_SAMPLER_MLP if mlp_params is not None else q.QED_SAMPLER_TABLE)
     gen = q.Generator(cfg)
     if mlp_params is not None:
         q.qed_mlp_set_params(gen.ctx, mlp_params)
-    ens = q.DeviceEnsemble.from_host(w.species, caps or capacities(w, warm + steps), prec)
+    ens = q.DeviceEnsemble.from_host(w.species, caps or capacities(w, warm + steps), prec,
+                                     optical_depth=method != 0)
     field = q.make_field(w.field_kind, w.field_prm)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -564,6 +572,27 @@ def main():
                "train_samples": int(args.mlp_samples), "train_seconds": train_s, "train_final_mse": loss,
                "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation (mma.sync)"}
 
+    od = None
+    if args.compare_od and world == 1 and args.workload != "batched_uniform_b":
+        import paper_2409_17299_gb300 as q
+        M = q.QED_METHOD_OPTICAL_DEPTH
+        caps_od = size_cascade(w, warm + steps, args.precision, M) if w.push_photons else None
+        ms_o, _, tot_o, counts_o = gpu_run(args, w, args.precision, warm, steps, caps=caps_od, method=M)
+        prec = args.precision
+        lep_b = OD_LEPTON_BYTES[prec] * tot_o["lepton_steps"] + EMIT_BYTES[prec] * tot_o["emit_events"]
+        ph_b = OD_PHOTON_BYTES[prec] * tot_o["photon_steps"] + PAIR_BYTES[prec] * tot_o["pair_events"]
+        lk, pk = tot_o["kernel_ms"][0], tot_o["kernel_ms"][1]
+        od = {"value": tot_o["particle_steps"] / (ms_o / 1e3),
+              "events_per_s": (tot_o["emit_events"] + tot_o["pair_events"]) / (ms_o / 1e3),
+              "ms_per_step": ms_o / steps, "final_counts": counts_o,
+              "kernels": {"k_lepton_od": {"kernel_ms": lk, "bytes_per_particle_step": OD_LEPTON_BYTES[prec],
+                                          "achieved_gbs": lep_b / (lk / 1e3) / 1e9 if lk > 0 else None},
+                          "k_photon_od": {"kernel_ms": pk, "bytes_per_particle_step": OD_PHOTON_BYTES[prec],
+                                          "achieved_gbs": ph_b / (pk / 1e3) / 1e9 if pk > 0 else None}},
+              "method": "accumulated optical depth: rate once per step, at most one event per step"}
+        for k in od["kernels"].values():
+            k["frac"] = k["achieved_gbs"] / hbm_peak if k["achieved_gbs"] else None
+
     e2e = None
     if args.e2e:
         ps_e, ms_e, wall_e, nb = e2e_run(w, args.precision, warm, steps, caps=caps)
@@ -636,6 +665,8 @@ def main():
         line["surrogate_speedup_over_table_fp32"] = mlp["value"] / line["value"]
         if fp64:
             line["surrogate_speedup_over_fp64_table"] = mlp["value"] / fp64["value"]
+    if od:
+        line["optical_depth_method"] = od
     if e2e:
         line["e2e"] = e2e
     if cpu:

@@ -91,9 +91,11 @@ typedef struct {
  *  QED_METHOD_SUBSTEP        Algorithm 1 (Sec. 3): waiting times drawn inside the
  *                            step, any number of events per step, newborns pushed
  *                            to the step end (Algorithm 2).
- *  QED_METHOD_OPTICAL_DEPTH  the classic scheme the paper compares against (Sec. 2):
- *                            each particle carries its remaining optical depth od
- *                            (FP64, arrays from qed_set_optical_depth).  Per step:
+ *  QED_METHOD_OPTICAL_DEPTH  the inverse-sampling scheme of other PIC codes that
+ *                            Sec. 3 describes (accumulated optical depth, no
+ *                            sub-cycling): each particle carries its remaining
+ *                            optical depth od (the context's precision, arrays
+ *                            from qed_set_optical_depth).  Per step:
  *                            the rate lambda at the step start; od <= 0 means "not
  *                            drawn yet" and draws od = -ln u, u from Philox(id, step,
  *                            0xFFFFFFFE) words 0-1; od -= lambda dt; push by dt; if
@@ -290,13 +292,15 @@ qed_status qed_level_apply(qed_ctx *ctx, qed_particles *p, int species, double w
  * NULL detaches it.  The batched push does not take gridded fields. */
 qed_status qed_set_field_grid(qed_ctx *ctx, const void *grid_dev);
 
-/* Optical-depth arrays for QED_METHOD_OPTICAL_DEPTH: od_dev[s] holds one
- * double per particle of species s (caller-owned device memory, at least the
- * species' capacity), parallel to the species arrays: the library reads and
- * writes it in the pushes, moves it with the particles in compaction and
- * leveling, and writes 0 for every particle it appends.  Rebind after
- * reallocating.  NULL entries detach. */
-qed_status qed_set_optical_depth(qed_ctx *ctx, double *const od_dev[3]);
+/* Optical-depth arrays for QED_METHOD_OPTICAL_DEPTH: od_dev[s] holds one value
+ * of the context's precision (double for QED_FP64, float for QED_FP32) per
+ * particle of species s (caller-owned device memory, at least the species'
+ * capacity, aligned to the element size), parallel to the species arrays: the
+ * library reads and writes it in the pushes, moves it with the particles in
+ * compaction and leveling, and writes 0 for every particle it appends.
+ * Rebind after reallocating.  NULL entries detach.  QED_ERR_INVALID for a
+ * misaligned pointer. */
+qed_status qed_set_optical_depth(qed_ctx *ctx, void *const od_dev[3]);
 
 /* Statistics accumulated since the context was created or last reset. */
 qed_status qed_get_stats(qed_ctx *ctx, qed_stats *out, int reset);

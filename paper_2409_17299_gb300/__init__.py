@@ -189,7 +189,7 @@ def qed_compact(ctx, particles: QedParticles, step: int) -> int:
 
 def qed_set_optical_depth(ctx, ptrs) -> None:
     """Bind the three per-species optical-depth arrays (device pointers of
-    float64 arrays, or 0) for QED_METHOD_OPTICAL_DEPTH."""
+    arrays of the context's precision, or 0) for QED_METHOD_OPTICAL_DEPTH."""
     arr = (C.c_void_p * 3)(*[C.c_void_p(int(v or 0)) for v in ptrs])
     rc = lib().qed_set_optical_depth(ctx, arr)
     if rc != QED_OK:
@@ -427,7 +427,7 @@ class DeviceEnsemble:
             d["id"] = torch.zeros(c, dtype=torch.int64, device=device)
             d["nevents"] = torch.zeros(c, dtype=torch.int32, device=device)
             if optical_depth:               # QED_METHOD_OPTICAL_DEPTH: remaining optical depth (0: not drawn)
-                d["od"] = torch.zeros(c, dtype=torch.float64, device=device)
+                d["od"] = torch.zeros(c, dtype=self.fdtype, device=device)
             self.arr.append(d)
 
     @classmethod
@@ -447,7 +447,7 @@ class DeviceEnsemble:
             if "nevents" in sp:
                 e.arr[s]["nevents"][:n].copy_(e.torch.from_numpy(np.asarray(sp["nevents"], dtype=np.uint32).view(np.int32)))
             if optical_depth and "od" in sp:
-                e.arr[s]["od"][:n].copy_(e.torch.from_numpy(np.asarray(sp["od"], dtype=np.float64)))
+                e.arr[s]["od"][:n].copy_(e.torch.from_numpy(np.asarray(sp["od"], dtype=np.float64)).to(e.fdtype))
             e.count[s] = n
         return e
 
@@ -476,7 +476,7 @@ class DeviceEnsemble:
         out["id"] = d["id"][:n].cpu().numpy().view(np.uint64)
         out["nevents"] = d["nevents"][:n].cpu().numpy().view(np.uint32)
         if "od" in d:
-            out["od"] = d["od"][:n].cpu().numpy()
+            out["od"] = d["od"][:n].double().cpu().numpy()
         return out
 
     def od_ptrs(self):

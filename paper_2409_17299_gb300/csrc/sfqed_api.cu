@@ -84,10 +84,11 @@ extern "C" qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed
     return sfq_batch_push(ctx, ens, fields, n_ens, dt, nsteps, step0, out, 0, 0);
 }
 
-extern "C" qed_status qed_set_optical_depth(qed_ctx *ctx, double *const od_dev[3]) {
+extern "C" qed_status qed_set_optical_depth(qed_ctx *ctx, void *const od_dev[3]) {
     if (!ctx || !od_dev) return QED_ERR_INVALID;
+    const uintptr_t align = ctx->cfg.precision == QED_FP32 ? 4u : 8u;
     for (int s = 0; s < 3; ++s) {
-        if (od_dev[s] && (reinterpret_cast<uintptr_t>(od_dev[s]) & 7u)) return QED_ERR_INVALID;
+        if (od_dev[s] && (reinterpret_cast<uintptr_t>(od_dev[s]) % align)) return QED_ERR_INVALID;
         ctx->od[s] = od_dev[s];
     }
     return QED_OK;

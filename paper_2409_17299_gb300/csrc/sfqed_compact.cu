@@ -146,7 +146,7 @@ template <class T> __device__ __forceinline__ void move_entry(const SpeciesDev &
     st<T>(S.w, d, ld<T>(S.w, i));
     S.id[d] = S.id[i];
     S.nev[d] = S.nev[i];
-    if (S.od) S.od[d] = S.od[i];
+    if (S.od) st<T>(S.od, d, ld<T>(S.od, i));
 }
 
 // alive entries at or above A move into the holes, in rank order: the mover

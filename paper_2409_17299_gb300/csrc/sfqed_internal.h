@@ -90,7 +90,7 @@ struct SpeciesDev {
     unsigned long long *id;
     unsigned *nev;
     double *tau;            // birth clock of newborns (context work buffer)
-    double *od;             // remaining optical depth (QED_METHOD_OPTICAL_DEPTH), or null
+    void *od;               // remaining optical depth (QED_METHOD_OPTICAL_DEPTH, T), or null
 };
 
 struct PassArgs {
@@ -162,7 +162,7 @@ struct qed_ctx {
     double sync_ms;              // host time blocked in stream synchronisation
     void *batch;                 // batched-push work buffers
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
-    double *od[3];               // caller's optical-depth arrays (QED_METHOD_OPTICAL_DEPTH)
+    void *od[3];                 // caller's optical-depth arrays (QED_METHOD_OPTICAL_DEPTH, T)
     const void *field_grid;      // caller's gridded field values (QED_FIELD_GRID)
     void *grid_il;               // the same interleaved per node (8 values), refreshed each call
     size_t grid_il_bytes;

@@ -176,7 +176,7 @@ __device__ __forceinline__ void emit_with(const LeptonCtx<T> &c, const T x[3], T
             P.id[slot] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
             P.nev[slot] = 0u;
             if (a.record_newborn_tau) P.tau[slot] = tau;
-            if (P.od) P.od[slot] = 0.0;       // optical depth not drawn yet
+            if (P.od) st<T>(P.od, slot, (T)0);       // optical depth not drawn yet
         } else {
             note_overflow(c.ctl, 2, slot);
         }
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                     P.id[se] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
                     P.nev[se] = 0u;
                     P.tau[se] = tau;
-                    if (P.od) P.od[se] = 0.0;
+                    if (P.od) st<T>(P.od, se, (T)0);
                 } else {
                     note_overflow(ctl, 0, se);
                 }
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                     P.id[sp] = (unsigned long long)rid.z | ((unsigned long long)rid.w << 32);
                     P.nev[sp] = 0u;
                     P.tau[sp] = tau;
-                    if (P.od) P.od[sp] = 0.0;
+                    if (P.od) st<T>(P.od, sp, (T)0);
                 } else {
                     note_overflow(ctl, 1, sp);
                 }
@@ -543,25 +543,39 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
 }
 
 
-// ---- the classic accumulated-optical-depth method (QED_METHOD_OPTICAL_DEPTH) ----
+// ---- the accumulated-optical-depth method (QED_METHOD_OPTICAL_DEPTH) ----
 // Per particle and step: the rate at the step start; an optical depth not
 // drawn yet (od <= 0) is drawn as -ln u from Philox(id, step, OD_DRAW); od
 // decreases by lambda dt; the particle is pushed by dt; if od <= 0 the event
 // happens at the end of the step (chi at the end point, energy from
 // Philox(id, step, 0) words 2-3) and a fresh od = -ln u from words 0-1.  At
 // most one event per particle and step; the children start at the next step.
+// od is held in the context's precision: a particle that does not convert
+// draws no random number and does no FP64 arithmetic in FP32 mode.
 constexpr unsigned OD_DRAW = 0xFFFFFFFEu;
 
-template <class T>
-__device__ __forceinline__ double od_draw(const PassArgs &a, unsigned long long id, unsigned k) {
-    const uint4 r = event_draw(a.keys, id, a.step, k);
-    double u, v;
-    Uniform<double>::draw(r.x, r.y, u, v);
-    return -log(u);
+// -ln u from words 0-1 of a draw (the FP32 form keeps full relative precision
+// for u near 1)
+template <class T> __device__ __forceinline__ T od_exp1(const uint4 &r) {
+    T u, v;
+    Uniform<T>::draw(r.x, r.y, u, v);
+    return Uniform<T>::neglog(u, v);
+}
+
+// the step in the working precision (FP32: rounded once on the host)
+template <class T> __device__ __forceinline__ T dt_of(const PassArgs &a);
+template <> __device__ __forceinline__ float dt_of<float>(const PassArgs &a) { return a.dt_f; }
+template <> __device__ __forceinline__ double dt_of<double>(const PassArgs &a) { return a.dt; }
+
+// od after this step's decrement, drawn first when not drawn yet.  The
+// product is rounded on its own (no contraction), as in the oracle.
+template <class T> __device__ __forceinline__ T od_advance(const PassArgs &a, unsigned long long id, T od, T lam) {
+    if (!(od > (T)0)) od = od_exp1<T>(event_draw(a.keys, id, a.step, OD_DRAW));
+    return od - mul_rn<T>(lam, dt_of<T>(a));
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_lepton_od(PassArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(PassArgs a) {
     __shared__ T s_coef[NCOEF];
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     __syncthreads();
@@ -582,20 +596,19 @@ __global__ void __launch_bounds__(256) k_lepton_od(PassArgs a) {
         if (!(w > (T)0)) continue;
         T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
         T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
-        const unsigned long long id = S.id[i];
-        double od = S.od[i];
+        const unsigned long long id = __ldg(S.id + i);
+        T od = ld<T>(S.od, i);
         ++my_steps;
         T E[3], B[3];
         field_at<T>(a, x, c.ph0, E, B);
         T gam, chi, p2;
         lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
         const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
-        if (!(od > 0.0)) od = od_draw<T>(a, id, OD_DRAW);
-        od = od - __dmul_rn((double)lam, a.dt);       // two roundings, as in the oracle
+        od = od_advance<T>(a, id, od, lam);
         const T qch = s == 0 ? (T)-1 : (T)1;
-        boris<T>(x, p, qch, E, B, (T)a.dt);
+        boris<T>(x, p, qch, E, B, dt_of<T>(a));
         unsigned k = 0;
-        if (od <= 0.0) {
+        if (od <= (T)0) {
             // the event at the end of the step
             field_tau<T>(a, x, a.dt, E, B);
             lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
@@ -604,14 +617,12 @@ __global__ void __launch_bounds__(256) k_lepton_od(PassArgs a) {
             Uniform<T>::draw(r.z, r.w, ue, ve);
             const T delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
             emit_with<T>(c, x, p, a.dt, w, id, 0u, gam, p2, delta, om);
-            double u, v;
-            Uniform<double>::draw(r.x, r.y, u, v);
-            od = -log(u);
+            od = od_exp1<T>(r);
             k = 1;
         }
         st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
         st<T>(S.px, i, p[0]); st<T>(S.py, i, p[1]); st<T>(S.pz, i, p[2]);
-        S.od[i] = od;
+        st<T>(S.od, i, od);
         if (k) S.nev[i] += 1u;
         my_ev += k;
         my_max = max(my_max, k);
@@ -621,7 +632,7 @@ __global__ void __launch_bounds__(256) k_lepton_od(PassArgs a) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_photon_od(PassArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(PassArgs a) {
     __shared__ T s_coef[NCOEF];
     for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     __syncthreads();
@@ -634,15 +645,57 @@ __global__ void __launch_bounds__(256) k_photon_od(PassArgs a) {
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
     const Phase<T> ph0 = time_phase<T>(a, 0.0);
-    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
+    // FP32: each thread stages its next photon in shared memory (two
+    // buffers) while it works on the current one, as in the step-start pass
+    constexpr bool STAGE = sizeof(T) == 4;
+    constexpr int NB = STAGE ? 2 : 1, NF = STAGE ? 10 : 1, NT = STAGE ? 256 : 1;
+    __shared__ __align__(16) float stg[NB][NF][NT];       // w x y z kx ky kz id(2 words) od
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    auto stage = [&](unsigned long long jj, int buf) {
+        if constexpr (STAGE) {
+            const unsigned long long ii = b + jj;
+            const int t = threadIdx.x;
+            cp_async4(&stg[buf][0][t], reinterpret_cast<const float *>(S.w) + ii);
+            cp_async4(&stg[buf][1][t], reinterpret_cast<const float *>(S.x) + ii);
+            cp_async4(&stg[buf][2][t], reinterpret_cast<const float *>(S.y) + ii);
+            cp_async4(&stg[buf][3][t], reinterpret_cast<const float *>(S.z) + ii);
+            cp_async4(&stg[buf][4][t], reinterpret_cast<const float *>(S.px) + ii);
+            cp_async4(&stg[buf][5][t], reinterpret_cast<const float *>(S.py) + ii);
+            cp_async4(&stg[buf][6][t], reinterpret_cast<const float *>(S.pz) + ii);
+            cp_async4(&stg[buf][7][t], S.id + ii);
+            cp_async4(&stg[buf][8][t], reinterpret_cast<const unsigned *>(S.id + ii) + 1);
+            cp_async4(&stg[buf][9][t], reinterpret_cast<const float *>(S.od) + ii);
+        }
+    };
+    const unsigned long long j0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (STAGE) {
+        if (j0 < n) stage(j0, 0);
+        cp_async_commit();
+    }
+    int buf = 0;
+    for (unsigned long long j = j0; j < n; j += stride, buf ^= 1) {
         const unsigned long long i = b + j;
-        T w = ld<T>(S.w, i);
+        T w, x[3], kv[3], od;
+        unsigned long long id;
+        if constexpr (STAGE) {
+            if (j + stride < n) stage(j + stride, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait_prev();                // this thread's copies of photon j have landed
+            const int t = threadIdx.x;
+            w = stg[buf][0][t];
+            x[0] = stg[buf][1][t]; x[1] = stg[buf][2][t]; x[2] = stg[buf][3][t];
+            kv[0] = stg[buf][4][t]; kv[1] = stg[buf][5][t]; kv[2] = stg[buf][6][t];
+            id = (unsigned long long)__float_as_uint(stg[buf][7][t]) |
+                 ((unsigned long long)__float_as_uint(stg[buf][8][t]) << 32);
+            od = stg[buf][9][t];
+        } else {
+            w = ld<T>(S.w, i);
+            x[0] = ld<T>(S.x, i); x[1] = ld<T>(S.y, i); x[2] = ld<T>(S.z, i);
+            kv[0] = ld<T>(S.px, i); kv[1] = ld<T>(S.py, i); kv[2] = ld<T>(S.pz, i);
+            id = __ldg(S.id + i);
+            od = ld<T>(S.od, i);
+        }
         if (!(w > (T)0)) continue;
-        T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
-        const T kv[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
-        const unsigned long long id = S.id[i];
-        double od = S.od[i];
         ++my_steps;
         const T k0 = m_sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
         unsigned k = 0;
@@ -653,11 +706,10 @@ __global__ void __launch_bounds__(256) k_photon_od(PassArgs a) {
             field_at<T>(a, x, ph0, E, B);
             T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
             const T lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);
-            if (!(od > 0.0)) od = od_draw<T>(a, id, OD_DRAW);
-            od = od - __dmul_rn((double)lam, a.dt);       // two roundings, as in the oracle
-            const T h = (T)a.dt;
+            od = od_advance<T>(a, id, od, lam);
+            const T h = dt_of<T>(a);
             x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
-            if (od <= 0.0) {
+            if (od <= (T)0) {
                 // pair creation at the end of the step
                 field_tau<T>(a, x, a.dt, E, B);
                 chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
@@ -679,7 +731,7 @@ __global__ void __launch_bounds__(256) k_photon_od(PassArgs a) {
                     st<T>(P.w, se, w);
                     P.id[se] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
                     P.nev[se] = 0u;
-                    P.od[se] = 0.0;
+                    st<T>(P.od, se, (T)0);
                 } else {
                     note_overflow(ctl, 0, se);
                 }
@@ -690,7 +742,7 @@ __global__ void __launch_bounds__(256) k_photon_od(PassArgs a) {
                     st<T>(P.w, sp, w);
                     P.id[sp] = (unsigned long long)rid.z | ((unsigned long long)rid.w << 32);
                     P.nev[sp] = 0u;
-                    P.od[sp] = 0.0;
+                    st<T>(P.od, sp, (T)0);
                 } else {
                     note_overflow(ctl, 1, sp);
                 }
@@ -699,7 +751,7 @@ __global__ void __launch_bounds__(256) k_photon_od(PassArgs a) {
             }
         }
         st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
-        S.od[i] = od;
+        st<T>(S.od, i, od);
         if (k) { st<T>(S.w, i, w); S.nev[i] += 1u; }
         my_ev += k;
         my_max = max(my_max, k);

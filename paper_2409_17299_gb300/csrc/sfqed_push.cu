@@ -130,7 +130,7 @@ static size_t elem_bytes(const qed_ctx *ctx) { return ctx->cfg.precision == QED_
 static qed_status snapshot(qed_ctx *ctx, qed_particles *p, bool restore) {
     const size_t eb = elem_bytes(ctx);
     size_t need = 0;
-    for (int s = 0; s < 3; ++s) need += (size_t)p->s[s].count * (7 * eb + 8 + 4 + (ctx->od[s] ? 8 : 0));
+    for (int s = 0; s < 3; ++s) need += (size_t)p->s[s].count * (7 * eb + 8 + 4 + (ctx->od[s] ? eb : 0));
     if (!restore && (int64_t)need > ctx->snap_bytes) {
         if (ctx->snap) SFQ_CUDA(cudaFreeAsync(ctx->snap, ctx->stream));
         ctx->snap = nullptr;
@@ -156,9 +156,9 @@ static qed_status snapshot(qed_ctx *ctx, qed_particles *p, bool restore) {
         else SFQ_CUDA(cudaMemcpyAsync(b, S.nevents, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
         b += n * 4;
         if (ctx->od[s]) {
-            if (restore) SFQ_CUDA(cudaMemcpyAsync(ctx->od[s], b, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-            else SFQ_CUDA(cudaMemcpyAsync(b, ctx->od[s], n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-            b += n * 8;
+            if (restore) SFQ_CUDA(cudaMemcpyAsync(ctx->od[s], b, n * eb, cudaMemcpyDeviceToDevice, ctx->stream));
+            else SFQ_CUDA(cudaMemcpyAsync(b, ctx->od[s], n * eb, cudaMemcpyDeviceToDevice, ctx->stream));
+            b += n * eb;
         }
     }
     return QED_OK;
