@@ -44,7 +44,7 @@ extern "C" qed_status qed_init_tables(qed_ctx **out, const qed_config *cfg, void
         return QED_ERR_CUDA;
     }
     bool ok = cudaMalloc(&c->coef64, sizeof(double) * NCOEF) == cudaSuccess &&
-              cudaMalloc(&c->coef32, sizeof(float) * NCOEF) == cudaSuccess &&
+              cudaMalloc(&c->coef32, sizeof(float) * NRATE32) == cudaSuccess &&
               cudaMalloc(&c->icdf_em64, sizeof(double) * EM_NCHI * EM_NS) == cudaSuccess &&
               cudaMalloc(&c->icdf_pair64, sizeof(double) * PAIR_NCHI * PAIR_NS) == cudaSuccess &&
               cudaMalloc(&c->icdf_em32, sizeof(float) * EM_NCHI * EM_NS) == cudaSuccess &&

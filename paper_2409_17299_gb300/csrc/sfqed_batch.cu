@@ -299,11 +299,11 @@ __device__ __forceinline__ void fused_round(const FusedCtx &c, FusedStack<T, NT>
 
 template <class T, int NT>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 128 ? 7 : 1)) k_emission_fused(BatchArgs b) {
-    __shared__ T s_coef[NCOEF];
+    __shared__ __align__(16) T s_coef[RateWords<T>::N];
     __shared__ FusedStack<T, NT> q;
     __shared__ unsigned long long s_tile;
     __shared__ int s_ens;
-    for (int i = threadIdx.x; i < NCOEF; i += NT) s_coef[i] = reinterpret_cast<const T *>(b.coef)[i];
+    for (int i = threadIdx.x; i < RateWords<T>::N; i += NT) s_coef[i] = reinterpret_cast<const T *>(b.coef)[i];
     if (threadIdx.x == 0) q.n = 0;
     __syncthreads();
     FusedCtx c{b, reinterpret_cast<const float *>(s_coef), reinterpret_cast<const double *>(s_coef)};

@@ -18,6 +18,16 @@ constexpr int CHEB_N = 11;       // degree-10 Chebyshev interpolant per decade
 constexpr int EM_NDEC = 6;
 constexpr int PAIR_NDEC = 5;
 constexpr int NCOEF = (EM_NDEC + PAIR_NDEC) * CHEB_N;   // 121 coefficients
+// FP32 mode: the same approximant as cubic pieces, RSEG per decade of
+// log10 chi, each four floats (monomial coefficients in the piece's local
+// coordinate t in [0, 1)), fitted in FP64 to the Chebyshev form
+constexpr int RSEG = 16;
+constexpr int EM_NSEG = EM_NDEC * RSEG, PAIR_NSEG = PAIR_NDEC * RSEG;
+constexpr int NRATE32 = 4 * (EM_NSEG + PAIR_NSEG);    // 704 floats
+// words of the rate representation in the working precision
+template <class T> struct RateWords;
+template <> struct RateWords<double> { static constexpr int N = NCOEF; };
+template <> struct RateWords<float> { static constexpr int N = NRATE32; };
 
 // Device-resident control block: counts, pass ranges and statistics.  Every
 // counter is 64-bit so that appends can count demand beyond capacity.

@@ -290,12 +290,12 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
 
 template <class T, bool FRESH, bool MLP>
 __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_lepton_pass(PassArgs a) {
-    __shared__ T s_coef[NCOEF];
+    __shared__ __align__(16) T s_coef[RateWords<T>::N];
     __shared__ LeptonStack<T> q;
     extern __shared__ __align__(16) unsigned char dyn[];
     MlpInf ms{nullptr, nullptr, nullptr};
     if constexpr (MLP) ms = mlp_stage(dyn, a.mlp_w16);
-    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     if (threadIdx.x == 0) q.n = 0;
     __syncthreads();
     DevCtl *ctl = a.ctl;
@@ -393,8 +393,8 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
 // removed (weight 0) and the pair appended.
 template <class T, bool FRESH>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(PassArgs a) {
-    __shared__ T s_coef[NCOEF];
-    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    __shared__ __align__(16) T s_coef[RateWords<T>::N];
+    for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     __syncthreads();
     DevCtl *ctl = a.ctl;
     const unsigned long long b = ctl->begin[2], n = ctl->end[2] - b;
@@ -576,8 +576,8 @@ template <class T> __device__ __forceinline__ T od_advance(const PassArgs &a, un
 
 template <class T>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(PassArgs a) {
-    __shared__ T s_coef[NCOEF];
-    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    __shared__ __align__(16) T s_coef[RateWords<T>::N];
+    for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     __syncthreads();
     DevCtl *ctl = a.ctl;
     const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
@@ -633,8 +633,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(Pas
 
 template <class T>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(PassArgs a) {
-    __shared__ T s_coef[NCOEF];
-    for (int i = threadIdx.x; i < NCOEF; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    __shared__ __align__(16) T s_coef[RateWords<T>::N];
+    for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
     __syncthreads();
     DevCtl *ctl = a.ctl;
     const unsigned long long b = ctl->begin[2], n = ctl->end[2] - b;

@@ -174,15 +174,43 @@ __global__ void k_rate_nodes(const double *gl, double *fnode) {
 }
 
 // Chebyshev coefficients from the node values (discrete cosine transform).
-__global__ void k_cheb_coef(const double *fnode, double *coef64, float *coef32) {
+__global__ void k_cheb_coef(const double *fnode, double *coef64) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NCOEF) return;
     const int dec = i / CHEB_N, j = i % CHEB_N;
     double s = 0.0;
     for (int k = 0; k < CHEB_N; ++k) s += fnode[dec * CHEB_N + k] * cos(PI * j * (k + 0.5) / CHEB_N);
-    const double c = 2.0 * s / CHEB_N;
-    coef64[i] = c;
-    coef32[i] = (float)c;
+    coef64[i] = 2.0 * s / CHEB_N;
+}
+
+// FP32 cubic pieces: piece i of a decade interpolates the FP64 Chebyshev form
+// at t = 0, 1/3, 2/3, 1 (so neighbouring pieces meet), written as monomial
+// coefficients in t from the forward differences.  Interpolation error below
+// 1e-8 of the function; the FP32 evaluation rounds at ~3e-7.
+__global__ void k_rate_segments(const double *coef64, float *seg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= EM_NSEG + PAIR_NSEG) return;
+    const bool pair = i >= EM_NSEG;
+    const int k = pair ? i - EM_NSEG : i;
+    const int dec = k / RSEG, r = k % RSEG;
+    const double *c = coef64 + (pair ? EM_NDEC * CHEB_N : 0) + dec * CHEB_N;
+    double f[4];
+    for (int q = 0; q < 4; ++q) {
+        const double x = 2.0 * ((r + q / 3.0) / RSEG) - 1.0;    // Chebyshev variable of the decade
+        double b1 = 0.0, b2 = 0.0;
+        for (int j = CHEB_N - 1; j >= 1; --j) {
+            const double b0 = c[j] + 2.0 * x * b1 - b2;
+            b2 = b1;
+            b1 = b0;
+        }
+        f[q] = 0.5 * c[0] + x * b1 - b2;
+    }
+    const double d1 = f[1] - f[0], d2 = f[2] - 2.0 * f[1] + f[0], d3 = f[3] - 3.0 * f[2] + 3.0 * f[1] - f[0];
+    // p(t) = f0 + d1 tau + d2 tau (tau - 1)/2 + d3 tau (tau - 1)(tau - 2)/6, tau = 3 t
+    seg[4 * i + 0] = (float)f[0];
+    seg[4 * i + 1] = (float)(3.0 * (d1 - d2 / 2.0 + d3 / 3.0));
+    seg[4 * i + 2] = (float)(9.0 * (d2 / 2.0 - d3 / 2.0));
+    seg[4 * i + 3] = (float)(27.0 * (d3 / 6.0));
 }
 
 // Newton's method inside one panel [za, zb] for int_za^z g = target
@@ -280,7 +308,8 @@ qed_status sfq_build_tables(qed_ctx *ctx) {
     SFQ_CUDA(cudaMallocAsync(&fnode, sizeof(double) * NCOEF, st));
     k_gauss_legendre<<<1, 32, 0, st>>>(ctx->gl);
     k_rate_nodes<<<NCOEF, 128, 0, st>>>(ctx->gl, fnode);
-    k_cheb_coef<<<1, 128, 0, st>>>(fnode, ctx->coef64, ctx->coef32);
+    k_cheb_coef<<<1, 128, 0, st>>>(fnode, ctx->coef64);
+    k_rate_segments<<<1, 256, 0, st>>>(ctx->coef64, ctx->coef32);
     k_icdf_rows<<<EM_NCHI + PAIR_NCHI, 128, 0, st>>>(ctx->gl, ctx->icdf_em64, ctx->icdf_pair64);
     k_to_f32<<<(EM_NCHI * EM_NS + 255) / 256, 256, 0, st>>>(ctx->icdf_em64, ctx->icdf_em32, EM_NCHI * EM_NS);
     k_to_f32<<<(PAIR_NCHI * PAIR_NS + 255) / 256, 256, 0, st>>>(ctx->icdf_pair64, ctx->icdf_pair32,
