@@ -309,55 +309,59 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT == 128 ? 7 : 1)) k_e
     FusedCtx c{b, reinterpret_cast<const float *>(s_coef), reinterpret_cast<const double *>(s_coef)};
     unsigned long long my_ev = 0, my_ps = 0;
     unsigned my_max = 0, n64 = 0;
+    // One loop with one call of fused_round: the queue is refilled from the
+    // next tile while it holds less than a round, and drained at the end.
+    // fused_round (and the step arithmetic in it) therefore has a single
+    // inlined copy, so the budget cannot change how a result is rounded.
+    bool tiles_left = true;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned long long t = atomicAdd(b.tile_next, 1ull);
-            s_tile = t;
-            int e = -1;
-            if (t < b.n_tiles) {                   // last ensemble with tile0 <= t
-                int lo = 0, hi = b.n_ens - 1;
-                while (lo < hi) {
-                    const int m = (lo + hi + 1) >> 1;
-                    if (b.ens[m].tile0 <= t) lo = m; else hi = m - 1;
+        if (tiles_left && q.n < NT) {
+            if (threadIdx.x == 0) {
+                const unsigned long long t = atomicAdd(b.tile_next, 1ull);
+                s_tile = t;
+                int e = -1;
+                if (t < b.n_tiles) {                   // last ensemble with tile0 <= t
+                    int lo = 0, hi = b.n_ens - 1;
+                    while (lo < hi) {
+                        const int m = (lo + hi + 1) >> 1;
+                        if (b.ens[m].tile0 <= t) lo = m; else hi = m - 1;
+                    }
+                    e = lo;
                 }
-                e = lo;
+                s_ens = e;
             }
-            s_ens = e;
-        }
-        __syncthreads();
-        const unsigned long long tile = s_tile;
-        const int ens = s_ens;
-        __syncthreads();
-        if (tile >= b.n_tiles) break;
-        const EnsDev &e = b.ens[ens];
-        const unsigned long long j = (tile - e.tile0) * NT + threadIdx.x;
-        const unsigned long long n0 = e.n_lep[0], n = n0 + e.n_lep[1];
-        if (j < n) {
-            const unsigned sp = j < n0 ? 0u : 1u;
-            const unsigned long long i = sp ? j - n0 : j;
-            const SpeciesDev &S = e.lep[sp];
-            const T w = ld<T>(S.w, i);
-            if (w > (T)0) {
-                T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
-                T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
-                const unsigned long long id = __ldg(S.id + i);
-                const unsigned long long ref = ((unsigned long long)ens << 40) | ((unsigned long long)sp << 39) | i;
-                FieldView<T> v;
-                load_view<T>(v, e, b, b.step0);
-                double tau = 0.0;
-                unsigned step = b.step0, k = 0;
-                uint2 rz = make_uint2(0, 0);
-                my_ps += (unsigned long long)b.nsteps;
-                const T qch = sp ? (T)1 : (T)-1;
-                const int r = fused_run<T>(c, v, x, p, qch, tau, id, step, k, rz, true, my_max, n64);
-                if (r == RUN_END) fused_finish<T>(e, sp, i, x, p, 0u);
-                else fused_push<T, NT>(q, x, p, tau, id, ref, w, r == RUN_EVENT ? PENDING : 0u, 0u, step, rz);
+            __syncthreads();
+            const unsigned long long tile = s_tile;
+            const int ens = s_ens;
+            __syncthreads();
+            if (tile >= b.n_tiles) {
+                tiles_left = false;
+                continue;
             }
+            const EnsDev &e = b.ens[ens];
+            const unsigned long long j = (tile - e.tile0) * NT + threadIdx.x;
+            const unsigned long long n0 = e.n_lep[0], n = n0 + e.n_lep[1];
+            if (j < n) {
+                const unsigned sp = j < n0 ? 0u : 1u;
+                const unsigned long long i = sp ? j - n0 : j;
+                const SpeciesDev &S = e.lep[sp];
+                const T w = ld<T>(S.w, i);
+                if (w > (T)0) {
+                    const T x[3] = {ld<T>(S.x, i), ld<T>(S.y, i), ld<T>(S.z, i)};
+                    const T p[3] = {ld<T>(S.px, i), ld<T>(S.py, i), ld<T>(S.pz, i)};
+                    const unsigned long long id = __ldg(S.id + i);
+                    const unsigned long long ref =
+                        ((unsigned long long)ens << 40) | ((unsigned long long)sp << 39) | i;
+                    my_ps += (unsigned long long)b.nsteps;
+                    fused_push<T, NT>(q, x, p, 0.0, id, ref, w, 0u, 0u, b.step0, make_uint2(0, 0));
+                }
+            }
+            __syncthreads();
+            continue;
         }
-        __syncthreads();
-        while (q.n >= NT) fused_round<T, NT>(c, q, my_ev, my_max, n64);
+        if (q.n == 0) break;
+        fused_round<T, NT>(c, q, my_ev, my_max, n64);
     }
-    while (q.n > 0) fused_round<T, NT>(c, q, my_ev, my_max, n64);
     __syncwarp();
     for (int o = 16; o > 0; o >>= 1) {
         my_ps += __shfl_down_sync(0xffffffffu, my_ps, o);

@@ -461,29 +461,38 @@ template <class T> __device__ __forceinline__ T rate_pair(const T *coef, T chi) 
 
 // FP32: the cubic pieces (tab: EM_NSEG then PAIR_NSEG float4 pieces, 16-byte
 // aligned).  Outside [1e-3, 1e3] the same limit forms as above, from the end
-// values of the first and last pieces.
+// values of the first and last pieces.  Every operation is rounded
+// explicitly, so each inlined copy computes the same bits whatever the
+// compiler fuses around it.
+constexpr float PIECES_PER_LOG2 = (float)(RSEG * 0.30102999566398119521);   // RSEG log10(2)
+
 __device__ __forceinline__ float piece_eval(const float *tab, int i, float t) {
     const float4 c = reinterpret_cast<const float4 *>(tab)[i];
-    return fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
+    return __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, c.w, c.z), c.y), c.x);
+}
+
+// piece coordinate RSEG (log10 chi - s0)
+__device__ __forceinline__ float piece_coord(float chi, int s0_times_rseg) {
+    return __fmaf_rn(__log2f(chi), PIECES_PER_LOG2, (float)s0_times_rseg);
 }
 
 template <> __device__ __forceinline__ float rate_em<float>(const float *tab, float chi) {
     if (!(chi > 0.f)) return 0.f;
-    const float u = fmaf(f_log10(chi), (float)RSEG, (float)(3 * RSEG));
-    if (u < 0.f) return chi * tab[0];
+    const float u = piece_coord(chi, 3 * RSEG);
+    if (u < 0.f) return __fmul_rn(chi, tab[0]);
     if (u >= (float)EM_NSEG) return 1e3f * piece_eval(tab, EM_NSEG - 1, 1.f) * m_cbrt2(chi * 1e-3f);
     const int i = (int)u;
-    return chi * piece_eval(tab, i, u - (float)i);
+    return __fmul_rn(chi, piece_eval(tab, i, __fsub_rn(u, (float)i)));
 }
 
 template <> __device__ __forceinline__ float rate_pair<float>(const float *tab, float chi) {
     if (!(chi >= (float)PAIR_CHI_MIN)) return 0.f;
     const float *c = tab + 4 * EM_NSEG;
-    const float u = fmaf(f_log10(chi), (float)RSEG, (float)(2 * RSEG));
+    const float u = piece_coord(chi, 2 * RSEG);
     if (u >= (float)PAIR_NSEG)
         return f_exp(piece_eval(c, PAIR_NSEG - 1, 1.f) - (float)(8.0 / 3e3)) * m_cbrt2(chi * 1e-3f);
     const int i = u > 0.f ? (int)u : 0;      // chi = 0.01 may land a rounding below the first piece
-    return f_exp(piece_eval(c, i, u - (float)i) - f_div(8.0f / 3.0f, chi));
+    return f_exp(__fsub_rn(piece_eval(c, i, __fsub_rn(u, (float)i)), f_div(8.0f / 3.0f, chi)));
 }
 
 // ---------------------------------------------------------------------------
