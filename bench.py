@@ -683,7 +683,7 @@ ISSUE_PEAK_WARP_INSTR = 152 * 4 * 2.07e9
 # Warp instructions per lepton-step of the step-fused batch kernel (128
 # threads, budget 4) from one ncu capture of the current kernel
 # (profiles/k_emission_fused_batched_uniform_b.md); None when not captured
-NCU_FUSED_WARP_INSTR_PER_STEP = {"fp32": 52.1, "fp64": None}
+NCU_FUSED_WARP_INSTR_PER_STEP = {"fp32": 47.9, "fp64": None}
 
 
 def batch_roofline(st, precision):
