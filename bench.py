@@ -19,6 +19,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -184,12 +185,15 @@ def oracle_run(name, warm, steps, target_s=15.0, procs=None):
 class ClockSampler:
     def __init__(self, index=0):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # raw samples: QED_CLOCKS_CSV if set, else a temporary file (the JSON
+        # line carries the summary)
+        self.path = os.environ.get("QED_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "qed_clocks_%d_%d.csv" % (os.getpid(), index))
         self.index = index
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
