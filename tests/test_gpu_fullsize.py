@@ -1,0 +1,184 @@
+"""Full-size parity of the default cascade in the benchmark's own launch
+configuration: the rotating-E cascade with 1e5 seed electrons and a cap of
+5e7 per species (FP32 mode), driven to the cap with the benchmark's sizing,
+then one more step.
+
+The whole population is too large for the oracle, so the check is sampled:
+particles drawn at random from the state at the step start are pushed one
+by one by the oracle (their avalanches are independent of the rest under an
+analytic field), and every particle the oracle produces is looked up by id in
+the GPU's full arrays.  Bars: at least 98% of the oracle's particles found
+with equal event counts; momenta and positions within 1e-3 relative on
+those; sampled photons that converted are gone.  Leveling at full size: the
+threshold equals the oracle's on the whole photon weight array (1e-12), the
+keep/drop decision of sampled photons follows the rule keyed by (id, step),
+and the count lands at the cap within the statistics.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_17299_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import bench  # noqa: E402  (its workload, sizing and step calls are what the benchmark times)
+import paper_2409_17299_gb300 as q  # noqa: E402
+
+STEPS = 230          # the photon population sits at the cap from step ~200
+NSAMPLE = 1500       # sampled particles per species
+
+
+def _gather(ens, s, idx):
+    """Host copy of entries idx of species s (device gather first)."""
+    d = ens.arr[s]
+    ii = torch.as_tensor(idx, dtype=torch.int64, device="cuda")
+    out = {f: d[f].index_select(0, ii).double().cpu().numpy() for f in ("x", "y", "z", "px", "py", "pz", "w")}
+    out["id"] = d["id"].index_select(0, ii).cpu().numpy().view(np.uint64)
+    out["nevents"] = d["nevents"].index_select(0, ii).cpu().numpy().view(np.uint32)
+    return out
+
+
+def _lookup(ens, s, ids):
+    """GPU entries of species s whose id is in ids: dict of host arrays, by id."""
+    d = ens.arr[s]
+    n = ens.count[s]
+    want = torch.as_tensor(np.asarray(ids, dtype=np.uint64).view(np.int64), device="cuda")
+    hit = torch.isin(d["id"][:n], want).nonzero().flatten()
+    out = {f: d[f].index_select(0, hit).double().cpu().numpy() for f in ("x", "y", "z", "px", "py", "pz", "w")}
+    out["id"] = d["id"].index_select(0, hit).cpu().numpy().view(np.uint64)
+    out["nevents"] = d["nevents"].index_select(0, hit).cpu().numpy().view(np.uint32)
+    return {int(i): k for k, i in enumerate(out["id"])}, out
+
+
+def _keep(seed, ids, step, w, wstar):
+    """Leveling's rule per particle: keep with probability w / w*, uniform
+    from Philox(id, step, 0xFFFFFFFF) words 0-1 under the run's seed."""
+    ids = np.asarray(ids, dtype=np.uint64)
+    ctr = np.zeros((len(ids), 4), dtype=np.uint32)
+    ctr[:, 0] = (ids & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    ctr[:, 1] = (ids >> np.uint64(32)).astype(np.uint32)
+    ctr[:, 2] = step
+    ctr[:, 3] = 0xFFFFFFFF
+    r = oracle.philox(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+    u = np.array([oracle.u52(int(a), int(b)) for a, b in zip(r[:, 0], r[:, 1])])
+    return (w >= wstar) | (u < w / wstar)
+
+
+@pytest.fixture(scope="module")
+def saturated():
+    from paper_2409_17299_gb300 import build
+    build.build()
+    w = bench.make_workload("rotating_e_cascade")
+    assert len(w.species[0]["id"]) == 100000 and w.thin_cap == 50_000_000
+    caps = bench.size_cascade(w, STEPS + 1, "fp32")
+    field = q.make_field(w.field_kind, w.field_prm)
+    gen = q.Generator(q.make_config(precision=q.QED_FP32, seed=w.seed, push_photons=1, thin_cap=w.thin_cap,
+                                    restore_on_overflow=0))
+    ens = q.DeviceEnsemble.from_host(w.species, caps, q.QED_FP32)
+    for s in range(STEPS):
+        gen.push(ens, field, w.dt, 1, s, auto_grow=False)
+    torch.cuda.synchronize()
+    assert ens.count[2] > 0.95 * w.thin_cap          # at the cap
+    yield w, gen, ens, field, caps
+    gen.close()
+
+
+def test_full_size_sampled_particles_match_oracle(saturated, otables):
+    w, _, ens, field, caps = saturated
+    rng = np.random.default_rng(7)
+    picks = [rng.choice(ens.count[s], size=min(NSAMPLE, ens.count[s]), replace=False) for s in range(3)]
+    start = [_gather(ens, s, np.sort(picks[s])) for s in range(3)]
+    # the same step on a copy of the full state, without leveling (every
+    # particle's outcome is then its own)
+    work = q.DeviceEnsemble(caps, q.QED_FP32)
+    for s in range(3):
+        for f, a in ens.arr[s].items():
+            work.arr[s][f].copy_(a)
+    work.count = list(ens.count)
+    g0 = q.Generator(q.make_config(precision=q.QED_FP32, seed=w.seed, push_photons=1, thin_cap=0,
+                                   restore_on_overflow=0))
+    st = g0.push(work, field, w.dt, 1, STEPS, auto_grow=False)
+    torch.cuda.synchronize()
+    g0.close()
+    assert st["pair_events"] > 0 and st["emit_events"] > 0
+    # the oracle pushes the sampled particles alone
+    oe = oracle.Ensemble.from_arrays(start, [200000, 200000, 400000])
+    cfg = oracle.make_cfg(seed=w.seed, push_photons=1, thin_cap=0, field_kind=w.field_kind, field_prm=w.field_prm)
+    ost = oracle.push_and_generate(oe, otables, cfg, w.dt, 1, STEPS)
+    assert ost["pair_events"] > 0 and ost["emit_events"] > 0
+    total = found = 0
+    for s in range(3):
+        o = oe.view(s)
+        pos, g = _lookup(work, s, o["id"])
+        total += len(o["id"])
+        ok = []
+        for k, i in enumerate(o["id"]):
+            j = pos.get(int(i))
+            if j is not None and g["nevents"][j] == o["nevents"][k]:
+                ok.append((k, j))
+        found += len(ok)
+        if ok:
+            ko, kg = np.array(ok).T
+            for keys in (("px", "py", "pz"), ("x", "y", "z")):
+                ov = np.stack([o[f][ko] for f in keys], 1)
+                gv = np.stack([g[f][kg] for f in keys], 1)
+                err = np.linalg.norm(gv - ov, axis=1) / np.maximum(np.linalg.norm(ov, axis=1), 1e-3)
+                assert err.max() < 1e-3, (s, keys, err.max())
+    assert total > 4000
+    assert found >= 0.98 * total, (found, total)
+    # sampled photons that converted in the oracle are gone on the GPU too
+    conv = np.setdiff1d(start[2]["id"], oe.view(2)["id"])
+    assert len(conv) > 0
+    pos, _ = _lookup(work, 2, conv)
+    assert len(pos) <= 0.02 * len(conv) + 1
+
+
+def test_full_size_leveling(saturated, otables):
+    w, gen, ens, field, caps = saturated
+    # pre-leveling state of the next step: the push without leveling
+    pre = q.DeviceEnsemble(caps, q.QED_FP32)
+    post = q.DeviceEnsemble(caps, q.QED_FP32)
+    for e in (pre, post):
+        for s in range(3):
+            for f, a in ens.arr[s].items():
+                e.arr[s][f].copy_(a)
+        e.count = list(ens.count)
+    g0 = q.Generator(q.make_config(precision=q.QED_FP32, seed=w.seed, push_photons=1, thin_cap=0,
+                                   restore_on_overflow=0))
+    g0.push(pre, field, w.dt, 1, STEPS, auto_grow=False)
+    g0.close()
+    # the benchmark's step: push, compaction and leveling
+    gen.push(post, field, w.dt, 1, STEPS, auto_grow=False)
+    torch.cuda.synchronize()
+    n_pre = pre.count[2]
+    assert n_pre > w.thin_cap                          # this step levels the photons
+    wpre = pre.arr[2]["w"][:n_pre].double().cpu().numpy()
+    wstar = oracle.level_threshold(wpre, w.thin_cap)
+    assert wstar > 0
+    # count at the cap within the statistics of the keep/drop draws
+    assert abs(post.count[2] - w.thin_cap) < 6 * math.sqrt(w.thin_cap)
+    # survivors: weights raised to w* (as float) or kept above it
+    wpost = post.arr[2]["w"][:post.count[2]]
+    wf = float(np.float32(wstar))
+    assert float(wpost.min()) >= wf * (1 - 2 ** -23)
+    # expected weight is conserved: sum over survivors vs the sum before
+    assert abs(float(wpost.double().sum()) / wpre.sum() - 1) < 6 * math.sqrt(wstar / wpre.sum())
+    # sampled photons: kept or dropped by the rule keyed by (id, step)
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(n_pre, size=NSAMPLE, replace=False))
+    smp = _gather(pre, 2, idx)
+    keep = _keep(w.seed, smp["id"], STEPS, smp["w"], wstar)
+    pos, g = _lookup(post, 2, smp["id"])
+    present = np.array([int(i) in pos for i in smp["id"]])
+    assert 0 < keep.sum() < len(keep)
+    assert np.array_equal(present, keep)
+    kw = np.array([g["w"][pos[int(i)]] for i in smp["id"][keep]])
+    want = np.where(smp["w"][keep] >= wstar, smp["w"][keep], wf)
+    assert np.allclose(kw, want, rtol=2 ** -23, atol=0)
