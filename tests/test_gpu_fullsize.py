@@ -1,7 +1,8 @@
-"""Full-size parity of the default cascade in the benchmark's own launch
+"""Full-size parity of the cascades in the benchmark's own launch
 configuration: the rotating-E cascade with 1e5 seed electrons and a cap of
-5e7 per species (FP32 mode), driven to the cap with the benchmark's sizing,
-then one more step.
+5e7 per species, and the standing-wave cascade with 1e6 seeds and a cap of
+2e8 (FP32 mode), each driven to its cap with the benchmark's sizing, then one
+more step.
 
 The whole population is too large for the oracle, so the check is sampled:
 particles drawn at random from the state at the step start are pushed one
@@ -31,7 +32,6 @@ if not torch.cuda.is_available():
 import bench  # noqa: E402  (its workload, sizing and step calls are what the benchmark times)
 import paper_2409_17299_gb300 as q  # noqa: E402
 
-STEPS = 230          # the photon population sits at the cap from step ~200
 NSAMPLE = 1500       # sampled particles per species
 
 
@@ -71,29 +71,40 @@ def _keep(seed, ids, step, w, wstar):
     return (w >= wstar) | (u < w / wstar)
 
 
-@pytest.fixture(scope="module")
-def saturated():
+# workload: (steps before the checked step, seed electrons, cap); both
+# cascades sit at their cap by then
+FULL = {"rotating_e_cascade": (230, 100000, 50_000_000), "standing_wave_cascade": (600, 1_000_000, 200_000_000)}
+
+
+@pytest.fixture(scope="module", params=sorted(FULL))
+def saturated(request):
     from paper_2409_17299_gb300 import build
     build.build()
-    w = bench.make_workload("rotating_e_cascade")
-    assert len(w.species[0]["id"]) == 100000 and w.thin_cap == 50_000_000
-    caps = bench.size_cascade(w, STEPS + 1, "fp32")
+    steps, n0, cap = FULL[request.param]
+    w = bench.make_workload(request.param)
+    assert len(w.species[0]["id"]) == n0 and w.thin_cap == cap
+    caps = bench.size_cascade(w, steps + 1, "fp32")
     field = q.make_field(w.field_kind, w.field_prm)
     gen = q.Generator(q.make_config(precision=q.QED_FP32, seed=w.seed, push_photons=1, thin_cap=w.thin_cap,
                                     restore_on_overflow=0))
     ens = q.DeviceEnsemble.from_host(w.species, caps, q.QED_FP32)
-    for s in range(STEPS):
+    for s in range(steps):
         gen.push(ens, field, w.dt, 1, s, auto_grow=False)
     torch.cuda.synchronize()
     assert ens.count[2] > 0.95 * w.thin_cap          # at the cap
-    yield w, gen, ens, field, caps
+    yield w, gen, ens, field, caps, steps
     gen.close()
+    del ens
+    torch.cuda.empty_cache()
 
 
 def test_full_size_sampled_particles_match_oracle(saturated, otables):
-    w, _, ens, field, caps = saturated
+    w, _, ens, field, caps, step = saturated
     rng = np.random.default_rng(7)
-    picks = [rng.choice(ens.count[s], size=min(NSAMPLE, ens.count[s]), replace=False) for s in range(3)]
+    # photons convert rarely (~1e-3 per step): sample more of them (array
+    # order depends on the appends, so each run samples other particles)
+    size = [NSAMPLE, NSAMPLE, 20 * NSAMPLE]
+    picks = [rng.choice(ens.count[s], size=min(size[s], ens.count[s]), replace=False) for s in range(3)]
     start = [_gather(ens, s, np.sort(picks[s])) for s in range(3)]
     # the same step on a copy of the full state, without leveling (every
     # particle's outcome is then its own)
@@ -104,14 +115,14 @@ def test_full_size_sampled_particles_match_oracle(saturated, otables):
     work.count = list(ens.count)
     g0 = q.Generator(q.make_config(precision=q.QED_FP32, seed=w.seed, push_photons=1, thin_cap=0,
                                    restore_on_overflow=0))
-    st = g0.push(work, field, w.dt, 1, STEPS, auto_grow=False)
+    st = g0.push(work, field, w.dt, 1, step, auto_grow=False)
     torch.cuda.synchronize()
     g0.close()
     assert st["pair_events"] > 0 and st["emit_events"] > 0
     # the oracle pushes the sampled particles alone
-    oe = oracle.Ensemble.from_arrays(start, [200000, 200000, 400000])
+    oe = oracle.Ensemble.from_arrays(start, [200000, 200000, 800000])
     cfg = oracle.make_cfg(seed=w.seed, push_photons=1, thin_cap=0, field_kind=w.field_kind, field_prm=w.field_prm)
-    ost = oracle.push_and_generate(oe, otables, cfg, w.dt, 1, STEPS)
+    ost = oracle.push_and_generate(oe, otables, cfg, w.dt, 1, step)
     assert ost["pair_events"] > 0 and ost["emit_events"] > 0
     total = found = 0
     for s in range(3):
@@ -141,7 +152,7 @@ def test_full_size_sampled_particles_match_oracle(saturated, otables):
 
 
 def test_full_size_leveling(saturated, otables):
-    w, gen, ens, field, caps = saturated
+    w, gen, ens, field, caps, step = saturated
     # pre-leveling state of the next step: the push without leveling
     pre = q.DeviceEnsemble(caps, q.QED_FP32)
     post = q.DeviceEnsemble(caps, q.QED_FP32)
@@ -152,10 +163,10 @@ def test_full_size_leveling(saturated, otables):
         e.count = list(ens.count)
     g0 = q.Generator(q.make_config(precision=q.QED_FP32, seed=w.seed, push_photons=1, thin_cap=0,
                                    restore_on_overflow=0))
-    g0.push(pre, field, w.dt, 1, STEPS, auto_grow=False)
+    g0.push(pre, field, w.dt, 1, step, auto_grow=False)
     g0.close()
     # the benchmark's step: push, compaction and leveling
-    gen.push(post, field, w.dt, 1, STEPS, auto_grow=False)
+    gen.push(post, field, w.dt, 1, step, auto_grow=False)
     torch.cuda.synchronize()
     n_pre = pre.count[2]
     assert n_pre > w.thin_cap                          # this step levels the photons
@@ -174,7 +185,7 @@ def test_full_size_leveling(saturated, otables):
     rng = np.random.default_rng(11)
     idx = np.sort(rng.choice(n_pre, size=NSAMPLE, replace=False))
     smp = _gather(pre, 2, idx)
-    keep = _keep(w.seed, smp["id"], STEPS, smp["w"], wstar)
+    keep = _keep(w.seed, smp["id"], step, smp["w"], wstar)
     pos, g = _lookup(post, 2, smp["id"])
     present = np.array([int(i) in pos for i in smp["id"]])
     assert 0 < keep.sum() < len(keep)
