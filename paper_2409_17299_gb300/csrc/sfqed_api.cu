@@ -10,6 +10,7 @@ static void free_ctx(qed_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     sfq_batch_free(c);
+    sfq_level_graphs_free(c);
     void *dev[] = {c->coef64, c->coef32, c->icdf_em64, c->icdf_pair64, c->icdf_em32, c->icdf_pair32, c->gl,
                    c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap, c->lev,
                    c->mlp_p, c->mlp_w16, c->mlp_loss};

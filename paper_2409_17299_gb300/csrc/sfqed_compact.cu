@@ -231,6 +231,7 @@ __global__ void k_lev_begin(LevelWork *lw, int s) {
     it.alive = 0;
     it.mode = 0;
     lw->arrive[s] = 0;
+    lw->passes[s] = 0;
 }
 
 // error-free float-float accumulation (TwoSum), accurate to ~2^-48 relative
@@ -444,6 +445,17 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
         }
         lw->arrive[s] = 0;
     }
+}
+
+// Graph-driven leveling: after each pass, one thread decides whether the
+// graph's while loop runs another (the only setter of the condition, so no
+// two writes race).  The loop ends when the iteration is done, and in any
+// case after LEVEL_ITERS + 1 passes (the iteration itself finishes by then).
+__global__ void k_lev_cond(LevelWork *lw, int s, DevCtl *ctl, cudaGraphConditionalHandle h) {
+    const LevelIter &it = lw->it[s];
+    const unsigned long long n = ++lw->passes[s];
+    ctl->graph_kernels += 2;                 // this pass: k_lev_step and this kernel
+    cudaGraphSetConditional(h, (!it.done && n <= (unsigned long long)LEVEL_ITERS) ? 1u : 0u);
 }
 
 // ---- compaction by tiles (used after leveling and for converted photons) ----
@@ -711,9 +723,110 @@ qed_status compact_impl(qed_ctx *ctx, qed_species *sp, int s) {
     return compact_tiles<T, false>(ctx, sp, s, 0);
 }
 
-// Leveling of one species at `step`: the iteration runs on the device (one
-// launch per pass, no host round trip inside a chunk), then keep/drop fused
-// with the first compaction pass.  sp->count must bound the device count.
+// The leveling iteration of one species as a CUDA graph: k_lev_begin, then
+// a while node whose body is one pass (k_lev_step) and k_lev_cond.  The
+// graph is kept while the weight array, the cap and the grid stay the same.
+struct LevGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *w = nullptr;
+    long long cap = 0;
+    int blocks = 0;
+};
+
+static void lev_graph_drop(LevGraph *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+template <class T>
+static cudaError_t lev_graph_build(qed_ctx *ctx, LevGraph *G, const void *w, int s, long long cap, int blocks) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    LevelWork *lw = ctx->lev;
+    DevCtl *ctl = ctx->ctl;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t nb, nw, n1, n2;
+    cudaKernelNodeParams kb{}, ks{}, kc{};
+    cudaGraphNodeParams cp{};
+    void *args_b[] = {&lw, &s};
+    void *args_s[] = {const_cast<void **>(&w), &ctl, &s, &lw, &cap};
+    void *args_c[] = {&lw, &s, &ctl, &h};
+    cudaGraph_t body = nullptr;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) goto fail;
+    kb.func = reinterpret_cast<void *>(k_lev_begin);
+    kb.gridDim = dim3(1);
+    kb.blockDim = dim3(1);
+    kb.kernelParams = args_b;
+    e = cudaGraphAddKernelNode(&nb, g, nullptr, 0, &kb);
+    if (e != cudaSuccess) goto fail;
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&nw, g, &nb, nullptr, 1, &cp);
+    if (e != cudaSuccess) goto fail;
+    body = cp.conditional.phGraph_out[0];
+    ks.func = reinterpret_cast<void *>(k_lev_step<T>);
+    ks.gridDim = dim3((unsigned)blocks);
+    ks.blockDim = dim3(LEV_T);
+    ks.kernelParams = args_s;
+    e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &ks);
+    if (e != cudaSuccess) goto fail;
+    kc.func = reinterpret_cast<void *>(k_lev_cond);
+    kc.gridDim = dim3(1);
+    kc.blockDim = dim3(1);
+    kc.kernelParams = args_c;
+    e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &kc);
+    if (e != cudaSuccess) goto fail;
+    e = cudaGraphInstantiate(&G->exec, g, 0);
+    if (e != cudaSuccess) goto fail;
+    G->graph = g;
+    G->w = w;
+    G->cap = cap;
+    G->blocks = blocks;
+    return cudaSuccess;
+fail:
+    cudaGraphDestroy(g);
+    return e;
+}
+
+// Launch species s's leveling graph (building it when needed).  false: the
+// graph could not be built (conditional nodes unavailable); the caller then
+// checks the passes from the host.
+template <class T>
+static bool lev_graph_launch(qed_ctx *ctx, const void *w, int s, long long cap, int blocks) {
+    if (ctx->lev_graph_failed) return false;
+    LevGraph *G = static_cast<LevGraph *>(ctx->lev_graph[s]);
+    if (!G || G->w != w || G->cap != cap || G->blocks != blocks) {
+        lev_graph_drop(G);
+        G = new LevGraph;
+        ctx->lev_graph[s] = nullptr;
+        if (lev_graph_build<T>(ctx, G, w, s, cap, blocks) != cudaSuccess) {
+            delete G;
+            cudaGetLastError();                  // clear the failed call's error
+            ctx->lev_graph_failed = 1;
+            return false;
+        }
+        ctx->lev_graph[s] = G;
+    }
+    if (cudaGraphLaunch(G->exec, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->lev_graph_failed = 1;
+        return false;
+    }
+    return true;
+}
+
+// Leveling of one species at `step`: the iteration runs on the device (a
+// graph whose while loop runs one pass per iteration; without conditional
+// graph nodes, one launch per pass with a host check per chunk), then
+// keep/drop fused with the first compaction pass.  sp->count must bound the
+// device count.
 template <class T>
 qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     const int64_t cap = ctx->cfg.thin_cap;
@@ -721,6 +834,11 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     if (cap <= 0 || sp->count <= cap) return QED_OK;
     int blocks = ctx->sm_count * 4;
     blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
+    if (lev_graph_launch<T>(ctx, sp->w, s, (long long)cap, blocks)) {
+        SFQ_LAUNCHED(ctx, 1);                    // k_lev_begin; the passes are counted on the device
+        SFQ_CUDA(cudaGetLastError());
+        return compact_tiles<T, true>(ctx, sp, s, step);
+    }
     k_lev_begin<<<1, 1, 0, st>>>(ctx->lev, s);
     SFQ_LAUNCHED(ctx, 1);
     // passes in chunks (a pass after convergence returns at once); the host
@@ -817,6 +935,13 @@ qed_status sfq_ensure_work(qed_ctx *ctx, int64_t n_blocks, int64_t n_slots) {
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s) {
     if (ctx->cfg.precision == QED_FP32) return compact_impl<float>(ctx, sp, s);
     return compact_impl<double>(ctx, sp, s);
+}
+
+void sfq_level_graphs_free(qed_ctx *ctx) {
+    for (int s = 0; s < 3; ++s) {
+        lev_graph_drop(static_cast<LevGraph *>(ctx->lev_graph[s]));
+        ctx->lev_graph[s] = nullptr;
+    }
 }
 
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {

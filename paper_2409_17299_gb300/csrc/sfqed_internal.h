@@ -51,7 +51,8 @@ struct DevCtl {
     unsigned long long holes[3];        // compaction: dead entries below alive[s]
     unsigned long long bad_index;       // a bounds check failed (index recorded, access skipped)
     unsigned long long chi_fp64;        // FP32 mode: chi evaluations that fell back to FP64
-    unsigned long long pad[7];
+    unsigned long long graph_kernels;   // kernels run inside graphs (their launches are on the device)
+    unsigned long long pad[6];
 };
 
 // Leveling: iteration state per species and per-block partial sums.
@@ -71,6 +72,7 @@ struct LevelIter {
 struct LevelWork {
     LevelIter it[3];
     unsigned arrive[4];                         // blocks of the current pass that finished (per species)
+    unsigned long long passes[4];               // passes of the current graph-driven leveling
     double partA[LEVEL_MAX_BLOCKS];             // sum of weights below w (block partials)
     unsigned long long partC[LEVEL_MAX_BLOCKS]; // count at or above w
     unsigned long long partN[LEVEL_MAX_BLOCKS]; // alive count
@@ -171,6 +173,8 @@ struct qed_ctx {
     int64_t launches;            // kernels launched since the last reset
     double sync_ms;              // host time blocked in stream synchronisation
     void *batch;                 // batched-push work buffers
+    void *lev_graph[3];          // per species: the graph-driven leveling iteration (or null)
+    int lev_graph_failed;        // graphs with conditional nodes unavailable: host-checked passes
     cudaStream_t cap_stream;     // private stream for graph capture (the caller's may be the legacy stream)
     void *od[3];                 // caller's optical-depth arrays (QED_METHOD_OPTICAL_DEPTH, T)
     const void *field_grid;      // caller's gridded field values (QED_FIELD_GRID)
@@ -216,6 +220,7 @@ qed_status sfq_mlp_grad(qed_ctx *ctx, const float *feat, const float *target, in
 qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed, double *final_loss);
 // Implemented in sfqed_compact.cu
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);
+void sfq_level_graphs_free(qed_ctx *ctx);
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step);
 qed_status sfq_level_eval(qed_ctx *ctx, qed_species *sp, int s, double w, double *A, int64_t *C, int64_t *N,
                           double *M);

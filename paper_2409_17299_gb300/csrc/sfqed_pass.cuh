@@ -336,55 +336,65 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
         cp_async_commit();
     }
 
-    for (unsigned long long base = (unsigned long long)blockIdx.x * LB; base < n; base += stride) {
-        const unsigned long long j = base + threadIdx.x;
-        T w = (T)0, x[3], p[3];
-        unsigned long long id = 0;
-        if constexpr (STAGE) {
-            // this thread's staged particle, then the next tile's copies in
-            // flight (the slots are free once read)
-            cp_async_wait_all();
+    // One loop with one call of stack_round: the next tile is taken while the
+    // stack holds less than a round, the stack is drained at the end.  The
+    // round (and the event arithmetic in it) then has a single inlined copy,
+    // so which round processes a particle, which depends on the order of the
+    // arrays, cannot change how its results are rounded.
+    unsigned long long base = (unsigned long long)blockIdx.x * LB;
+    for (;;) {
+        if (base < n && q.n < LB) {
+            const unsigned long long j = base + threadIdx.x;
+            T w = (T)0, x[3], p[3];
+            unsigned long long id = 0;
+            if constexpr (STAGE) {
+                // this thread's staged particle, then the next tile's copies in
+                // flight (the slots are free once read)
+                cp_async_wait_all();
+                if (j < n) {
+                    const int t = threadIdx.x;
+                    w = stg[0][t];
+                    x[0] = stg[1][t]; x[1] = stg[2][t]; x[2] = stg[3][t];
+                    p[0] = stg[4][t]; p[1] = stg[5][t]; p[2] = stg[6][t];
+                    id = (unsigned long long)__float_as_uint(stg[7][t]) |
+                         ((unsigned long long)__float_as_uint(stg[8][t]) << 32);
+                }
+                if (j + stride < n) stage(j + stride);
+                cp_async_commit();
+            }
             if (j < n) {
-                const int t = threadIdx.x;
-                w = stg[0][t];
-                x[0] = stg[1][t]; x[1] = stg[2][t]; x[2] = stg[3][t];
-                p[0] = stg[4][t]; p[1] = stg[5][t]; p[2] = stg[6][t];
-                id = (unsigned long long)__float_as_uint(stg[7][t]) |
-                     ((unsigned long long)__float_as_uint(stg[8][t]) << 32);
-            }
-            if (j + stride < n) stage(j + stride);
-            cp_async_commit();
-        }
-        if (j < n) {
-            const int s = j < n0 ? 0 : 1;
-            const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
-            const SpeciesDev &S = a.sp[s];
-            if constexpr (!STAGE) {
-                w = ld<T>(S.w, i);
-                x[0] = ld<T>(S.x, i); x[1] = ld<T>(S.y, i); x[2] = ld<T>(S.z, i);
-                p[0] = ld<T>(S.px, i); p[1] = ld<T>(S.py, i); p[2] = ld<T>(S.pz, i);
-                id = __ldg(S.id + i);
-            }
-            if (w > (T)0) {
-                double tau = FRESH ? 0.0 : S.tau[i];
-                const unsigned idx = (unsigned)i | ((unsigned)s << 31);
-                ++my_steps;
-                uint2 rz = make_uint2(0, 0);
-                const T qch = s == 0 ? (T)-1 : (T)1;
-                bool event;
-                if constexpr (FRESH) event = advance<T, true>(c, x, p, qch, tau, id, 0u, rz, n64);
-                else event = tau < a.dt && advance<T, false>(c, x, p, qch, tau, id, 0u, rz, n64);
-                if (event) {
-                    stack_push<T>(q, x, p, tau, id, w, idx, 0u, rz);
-                } else {
-                    finish<T>(a, idx, x, p, 0u);
+                const int s = j < n0 ? 0 : 1;
+                const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
+                const SpeciesDev &S = a.sp[s];
+                if constexpr (!STAGE) {
+                    w = ld<T>(S.w, i);
+                    x[0] = ld<T>(S.x, i); x[1] = ld<T>(S.y, i); x[2] = ld<T>(S.z, i);
+                    p[0] = ld<T>(S.px, i); p[1] = ld<T>(S.py, i); p[2] = ld<T>(S.pz, i);
+                    id = __ldg(S.id + i);
+                }
+                if (w > (T)0) {
+                    double tau = FRESH ? 0.0 : S.tau[i];
+                    const unsigned idx = (unsigned)i | ((unsigned)s << 31);
+                    ++my_steps;
+                    uint2 rz = make_uint2(0, 0);
+                    const T qch = s == 0 ? (T)-1 : (T)1;
+                    bool event;
+                    if constexpr (FRESH) event = advance<T, true>(c, x, p, qch, tau, id, 0u, rz, n64);
+                    else event = tau < a.dt && advance<T, false>(c, x, p, qch, tau, id, 0u, rz, n64);
+                    if (event) {
+                        stack_push<T>(q, x, p, tau, id, w, idx, 0u, rz);
+                    } else {
+                        finish<T>(a, idx, x, p, 0u);
+                    }
                 }
             }
+            base += stride;
+            __syncthreads();
+            continue;
         }
-        __syncthreads();
-        while (q.n >= LB) stack_round<T, MLP>(c, q, my_ev, my_max, n64, ms);
+        if (q.n == 0) break;
+        stack_round<T, MLP>(c, q, my_ev, my_max, n64, ms);
     }
-    while (q.n > 0) stack_round<T, MLP>(c, q, my_ev, my_max, n64, ms);
     __syncwarp();
     flush_stats(ctl, my_steps, my_ev, my_max, false, n64);
 }

@@ -403,7 +403,7 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
         if (e != QED_OK) return e;
     }
     for (int k = 0; k < 4; ++k) st.kernel_ms[k] = ctx->kernel_ms[k];
-    st.launches = ctx->launches;
+    st.launches = ctx->launches + (int64_t)c.graph_kernels;
     st.sync_ms = ctx->sync_ms;
     st.call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - call_t0).count();
     if (rc == QED_ERR_CAPACITY && ctx->cfg.restore_on_overflow) {
