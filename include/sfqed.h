@@ -262,7 +262,11 @@ typedef struct {
     int64_t alive;      /* alive particles over all shards (set by the first pass) */
 } qed_level_state;
 
-/* Start an iteration (w = +inf, not done).  Host only. */
+/* Start an iteration (w = +inf, not done).  Host only.  The caller may set
+ * st->w to a finite warm start (for example the previous step's wstar)
+ * before the first advance: the first sums are then taken there, which
+ * changes the number of passes, not the threshold.  The single-GPU leveling
+ * starts each species at its previous threshold in this way. */
 void qed_level_begin(qed_level_state *st);
 
 /* Advance with the summed shard values at st->w: A = sum of alive weights

@@ -218,12 +218,18 @@ __host__ __device__ __forceinline__ double double_of_bits(unsigned long long b) 
 #endif
 }
 
+// Warm start: the first pass evaluates at the species' previous threshold
+// (after a leveling most weights equal it, and the next root usually lies
+// in the piece just above it), else at +inf.  The start changes only the
+// path: the root of its own piece is the same from any start.
 __global__ void k_lev_begin(LevelWork *lw, int s) {
     LevelIter &it = lw->it[s];
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    const double w0 = lw->prev[s] > 0.0 && lw->prev[s] < inf ? lw->prev[s] : inf;
     it.lo = 0.0;
-    it.hi = __longlong_as_double(0x7ff0000000000000ll);
-    it.w = it.hi;
-    it.w_up = __int_as_float(0x7f800000);
+    it.hi = inf;
+    it.w = w0;
+    it.w_up = w0 < inf ? ceil_f(w0) : __int_as_float(0x7f800000);
     it.wstar = 0.0;
     it.wstar_inv_f = 0.f;
     it.done = 0;
@@ -271,11 +277,16 @@ __host__ __device__ void lev_advance(LevelIter &it, double A, unsigned long long
                                      unsigned long long M, long long cap) {
     const double inf = double_of_bits(0x7ff0000000000000ull);
     const double w = it.w;
-    if (it.iters == 0) {                           // first pass: w = +inf, all alive weights below it
+    if (it.iters == 0) {                           // first pass: at +inf or at a warm start w
         it.alive = N;
         if (N <= (unsigned long long)cap) { lev_finish(it, 0.0); return; }
         it.hi = double_of_bits(M) * (double)N / (double)cap;                    // S(hi) <= cap
         it.lo = 0.0;
+        if (w < inf) {
+            const double S = A / w + (double)C;
+            if (S > (double)cap) it.lo = w;
+            else if (w < it.hi) it.hi = w;
+        }
     } else {
         const double S = A / w + (double)C;
         if (S > (double)cap) it.lo = w; else it.hi = w;
@@ -442,6 +453,7 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
             it.sumM = rm[0];
         } else {
             lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap);
+            if (it.done && it.wstar > 0.0) lw->prev[s] = it.wstar;
         }
         lw->arrive[s] = 0;
     }

@@ -73,6 +73,7 @@ struct LevelWork {
     LevelIter it[3];
     unsigned arrive[4];                         // blocks of the current pass that finished (per species)
     unsigned long long passes[4];               // passes of the current graph-driven leveling
+    double prev[4];                             // last threshold found per species (the next start)
     double partA[LEVEL_MAX_BLOCKS];             // sum of weights below w (block partials)
     unsigned long long partC[LEVEL_MAX_BLOCKS]; // count at or above w
     unsigned long long partN[LEVEL_MAX_BLOCKS]; // alive count

@@ -109,3 +109,21 @@ def test_advance_rejects_bad_input():
         q.qed_level_advance(st, -1.0, 0, 10, 1.0, 5)
     with pytest.raises(q.QedError):
         q.qed_level_advance(st, 1.0, 0, 10, 1.0, 0)
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_warm_start_reaches_the_same_threshold(case):
+    """The device starts a species' iteration at its previous threshold.  The
+    first pass then evaluates at a finite w: from below, at or above the
+    root the iteration (the library's own step, compiled for the host) must
+    end at the threshold the oracle finds, in few passes."""
+    kind, n, cap = case
+    w = _weights(kind, n, seed=31)
+    want = oracle.level_threshold(w, cap)
+    for f in (0.3, 0.9, 0.999999, 1.0, 1.000001, 1.1, 3.0):
+        st = q.qed_level_begin()
+        st.w = want * f
+        while not st.done:
+            q.qed_level_advance(st, *_shard_sums(w, st.w), cap)
+        assert st.wstar == pytest.approx(want, rel=1e-13), (kind, f)
+        assert st.iters <= 12, (kind, f, st.iters)
