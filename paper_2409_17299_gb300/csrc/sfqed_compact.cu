@@ -487,7 +487,7 @@ constexpr int LSPAN = 32 * LROUNDS;       // contiguous entries per warp
 // margin, and in FP64 (the oracle's test) only for draws within that margin
 // of the boundary; kept particles get weight w*.
 template <class T, bool LEVEL>
-__global__ void __launch_bounds__(LT) k_tile_dead(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw,
+__global__ void __launch_bounds__(LT, 4) k_tile_dead(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw,
                                                   const PhiloxKeys keys, unsigned step, unsigned long long *blk,
                                                   unsigned short *dl) {
     __shared__ unsigned wdead[LT / 32];
