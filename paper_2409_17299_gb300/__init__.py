@@ -452,14 +452,26 @@ class DeviceEnsemble:
         return e
 
     def struct(self) -> QedParticles:
-        P = QedParticles()
+        """The ABI view of the ensemble.  The pointers are cached while the
+        arrays stay the same tensors (a per-step call then only refreshes the
+        counts); the returned object is shared between calls."""
+        key = tuple(id(t) for d in self.arr for t in d.values())
+        P = getattr(self, "_P", None)
+        if P is None or self._P_key != key:
+            P = QedParticles()
+            for s in range(3):
+                d = self.arr[s]
+                S = P.s[s]
+                for f in _FIELDS:
+                    setattr(S, f, d[f].data_ptr())
+                S.id = d["id"].data_ptr()
+                S.nevents = d["nevents"].data_ptr()
+            # the cache holds the tensors, so no other object can take one of
+            # their ids while the cached pointers are in use
+            self._P, self._P_key = P, key
+            self._P_refs = [t for d in self.arr for t in d.values()]
         for s in range(3):
-            d = self.arr[s]
             S = P.s[s]
-            for f in _FIELDS:
-                setattr(S, f, d[f].data_ptr())
-            S.id = d["id"].data_ptr()
-            S.nevents = d["nevents"].data_ptr()
             S.count = self.count[s]
             S.capacity = self.capacity[s]
         return P

@@ -123,6 +123,8 @@ struct PassArgs {
     float prm_f[6];         // prm rounded to float once (FP32 mode)
     double dt;
     float dt_f;             // (float)dt
+    double lam_skip;        // 2^-54 / dt: below this rate no event can happen in a step (see the passes)
+    float lam_skip_f;
     float dt_f_gt;          // smallest float above dt (FP32 first-iteration event test)
     double t_n;             // step * dt
     double t_n_red;         // (step * dt) reduced modulo 2 pi

@@ -113,6 +113,15 @@ template <class T> struct LeptonCtx {
     Phase<T> ph0;           // time phase at the step start (tau = 0)
 };
 
+// A rate below 2^-54 / dt cannot give an event in a step: the waiting time
+// -ln u / lambda is at least 2^-53 / lambda > 2 dt, because 1 - u is never
+// below 2^-53 (FP64 and FP32 draws alike).  Such particles skip the draw (no
+// draw is consumed without an event, so the counter sequence is unchanged);
+// in the cascades this is most photons with chi below ~0.1.
+template <class T> __device__ __forceinline__ T lam_skip(const PassArgs &a);
+template <> __device__ __forceinline__ float lam_skip<float>(const PassArgs &a) { return a.lam_skip_f; }
+template <> __device__ __forceinline__ double lam_skip<double>(const PassArgs &a) { return a.lam_skip; }
+
 // One waiting-time iteration from (x, p, tau).  Returns true and leaves the
 // particle at its event point (tau advanced, draw words in rz) if an event
 // happens before the step end, else pushes it to the end and returns false.
@@ -130,7 +139,7 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
     lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
     const T lam = p2 > (T)0 ? f_div(c.alpha_r, gam) * rate_em<T>(c.coef, chi) : (T)0;
     T dth = t_inf<T>();
-    if (lam > (T)0) {
+    if (lam > lam_skip<T>(a)) {
         const uint4 r = event_draw(a.keys, id, a.step, k);
         T uw, vw;
         Uniform<T>::draw(r.x, r.y, uw, vw);
@@ -483,7 +492,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 else lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);     // the oracle's rounding
                 uint4 r = make_uint4(0, 0, 0, 0);
                 T dth = t_inf<T>();
-                if (lam > (T)0) {
+                if (lam > lam_skip<T>(a)) {
                     r = event_draw(a.keys, id, a.step, k);
                     T uw, vw;
                     Uniform<T>::draw(r.x, r.y, uw, vw);

@@ -304,6 +304,8 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     }
     a.dt = dt;
     a.dt_f = (float)dt;
+    a.lam_skip = ldexp(1.0, -54) / dt;
+    a.lam_skip_f = (float)a.lam_skip;
     a.dt_f_gt = (double)a.dt_f > dt ? a.dt_f : nextafterf(a.dt_f, INFINITY);
     a.seed = ctx->cfg.seed;
     a.keys = philox_keys(ctx->cfg.seed);
