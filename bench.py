@@ -556,8 +556,9 @@ def main():
     assert abs(tot["particle_steps"] / tot_plain["particle_steps"] - 1) < 1e-3
     torch.cuda.synchronize()
     secs = ms / 1e3
-    ps_total, ev_total, tmax = reduce_over_ranks(float(tot["particle_steps"]),
-                                                 float(tot["emit_events"] + tot["pair_events"]), secs, world)
+    ps_total, ev_total, tmax = reduce_over_ranks(float(tot_plain["particle_steps"]),
+                                                 float(tot_plain["emit_events"] + tot_plain["pair_events"]), secs,
+                                                 world)
 
     fp64 = None
     if args.compare_fp64 and args.precision == "fp32" and world == 1:
