@@ -652,7 +652,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single"},
         "events_per_s": ev_total / tmax,
         "final_counts": counts,
-        "gpu_launches": tot["launches"],
+        "gpu_launches": tot_plain["launches"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": (achieved / hbm_peak) if achieved else None,
                      "traffic": kernels[dom]["traffic"],
