@@ -156,3 +156,44 @@ def test_rejected_configurations():
     with pytest.raises(q.QedError):
         q.qed_set_optical_depth(g.ctx, [buf.data_ptr() + 4, 0, 0])
     g.close()
+
+
+def test_grid_field_fp64_matches_oracle(otables):
+    """The optical-depth kernels are compiled for the gridded field too: the
+    standing-wave cascade in a field held on the 128 x 4 x 4 node grid,
+    FP64, against the oracle's optical-depth run in the same grid."""
+    from test_gpu_grid import PRM, _grid_workload, standing_wave_grid
+    w = _grid_workload(300, seed=8)
+    grid = standing_wave_grid(1500.0, 0.0)       # one PIC step's fields, held for the call
+    nsteps, cap = 40, [40000, 40000, 120000]
+    g = q.Generator(q.make_config(precision=q.QED_FP64, seed=w.seed, push_photons=1, event_method=OD))
+    dev = torch.tensor(grid, dtype=torch.float64, device="cuda")
+    q.qed_set_field_grid(g.ctx, dev.data_ptr())
+    ens = q.DeviceEnsemble.from_host(w.species, cap, q.QED_FP64, optical_depth=True)
+    gs = g.push(ens, q.make_field(w.field_kind, w.field_prm), w.dt, nsteps, 0)
+    torch.cuda.synchronize()
+    g.close()
+    oracle.set_field_grid(grid)
+    oe = oracle.Ensemble.from_arrays(w.species, cap)
+    cfg = oracle.make_cfg(seed=w.seed, push_photons=1, field_kind=oracle.FIELD_GRID, field_prm=PRM,
+                          event_method=oracle.METHOD_OPTICAL_DEPTH)
+    os_ = oracle.push_and_generate(oe, otables, cfg, w.dt, nsteps, 0)
+    assert os_["emit_events"] > 0
+    for k in ("emit_events", "pair_events", "particle_steps"):
+        assert gs[k] == os_[k], k
+    for s in range(3):
+        got = ens.to_host(s)
+        assert_same_fp64(got, oe.view(s), what="species %d" % s)
+        _same_od(got, oe.view(s), "species %d" % s)
+
+
+def test_network_sampler_rejected():
+    """The optical-depth kernels sample energies from the tables only."""
+    w = W.uniform_b_emission(n=64, seed=1, nsteps=1)
+    g = q.Generator(q.make_config(precision=q.QED_FP32, seed=1, push_photons=0, event_method=OD,
+                                  sampler=q.QED_SAMPLER_MLP))
+    q.qed_mlp_set_params(g.ctx, np.zeros(oracle.mlp_nparams()))     # a network is loaded
+    ens = q.DeviceEnsemble.from_host(w.species, [64, 8, 64], q.QED_FP32, optical_depth=True)
+    with pytest.raises(q.QedError):
+        g.push(ens, q.make_field(w.field_kind, w.field_prm), w.dt, 1, 0, auto_grow=False)
+    g.close()
