@@ -7,7 +7,12 @@ Default workload: the rotating-field cascade (1e5 electrons at rest in a
 species).  One bench "step" is one PIC step of the whole ensemble through the
 library (push with sub-stepping, avalanche passes, dead-photon removal,
 leveling).  W warm-up steps (0..W-1) run untimed, then K steps are timed with
-CUDA events on the library's stream, with L2 flushed between steps.
+CUDA events on the library's stream, with L2 flushed between steps.  The
+headline pass runs without the library's per-kernel events; a second pass
+over the same steps records them for the per-kernel breakdown and the
+roofline of the dominant kernel.  Extra keys compare the FP64 mode, the
+network sampler, the optical-depth method and the end-to-end path through
+pinned host buffers, and time the FP64 oracle on the host cores.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 a bounded sample of the same workload on the host cores.
