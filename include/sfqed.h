@@ -22,8 +22,12 @@
  *    Calls that return host-side values (counts, statistics) synchronise
  *    that stream before returning.
  *  - Randomness is counter-based (Philox4x32-10, key = seed, counter =
- *    (id low, id high, step, k)), so results do not depend on thread
- *    scheduling or append order, and any call can be replayed exactly.
+ *    (id low, id high, step, k)), so a particle's draws do not depend on
+ *    thread scheduling or append order, and a call can be replayed (the
+ *    capacity-overflow replay relies on it).  In FP32 mode the leveling
+ *    threshold's sums depend on the array order in their last bits, so a
+ *    keep/drop decision lying within ~1e-15 of its boundary may differ
+ *    between runs whose appends landed in another order.
  */
 #ifndef SFQED_H
 #define SFQED_H
@@ -47,8 +51,10 @@ typedef enum {
 } qed_status;
 
 enum { QED_FP64 = 0,        /* all arithmetic and storage in FP64 */
-       QED_FP32 = 1 };      /* FP32 storage, push, rates and sampling; chi and the
-                               event clock in FP64 */
+       QED_FP32 = 1 };      /* FP32 storage, push, rates and sampling; chi in a
+                               cancellation-free FP32 form with an FP64 fallback
+                               where cancellation is detected; the event clock of
+                               the sub-steps after a particle's first in FP64 */
 enum { QED_SAMPLER_TABLE = 0, QED_SAMPLER_MLP = 1 };
 enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 };
 
