@@ -650,7 +650,7 @@ def main():
         "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": tmax * 1e3 / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "precision": prec + ("+fp64-chi-clock" if prec == "fp32" else ""),
+        "config": {"workload": args.workload, "precision": prec + (" (fp64 sub-step clock, fp64 chi fallback)" if prec == "fp32" else ""),
                    "seed_electrons": len(w.species[0]["id"]), "thin_cap": w.thin_cap,
                    "steps_total": w.nsteps, "dt": "T/%d" % round(2 * math.pi / w.dt),
                    "l2": "flushed between timed steps (256 MB write)",
