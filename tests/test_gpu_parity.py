@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
 Bars (written in each test): Philox and per-particle event counts bit-exact;
-FP64 momenta within 1e-5 relative (observed ~1e-12); FP32 (+FP64 chi/clock)
+FP64 momenta within 1e-5 relative (observed ~1e-12); FP32 (FP64 sub-step clock)
 within 1e-3 relative on particles whose event sequence matches, with the
 fraction of mismatching particles bounded; spectra by two-sample KS.
 """
@@ -245,7 +245,7 @@ def test_thinning_fp64_matches_oracle(otables):
 
 
 def test_fp32_against_fp64_oracle(otables):
-    """FP32 storage/push/rates/sampling with FP64 chi and clock: momenta within
+    """FP32 storage/push/rates/sampling (FP64 sub-step clock): momenta within
     1e-3 of the FP64 oracle for particles whose event count matches; at most
     1% of particles may take a different event sequence after 20 steps."""
     w = W.uniform_b_emission(n=16384, seed=0, nsteps=20)
