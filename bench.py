@@ -6,16 +6,23 @@ Default workload: the rotating-field cascade (1e5 electrons at rest in a
 3 periods = 300 steps, Compton + Breit-Wheeler, leveling cap 5e7 per
 species).  One bench "step" is one PIC step of the whole ensemble through the
 library (push with sub-stepping, avalanche passes, dead-photon removal,
-leveling).  W warm-up steps (0..W-1) run untimed, then K steps are timed with
-CUDA events on the library's stream, with L2 flushed between steps.  The
-headline pass runs without the library's per-kernel events; a second pass
-over the same steps records them for the per-kernel breakdown and the
-roofline of the dominant kernel.  Extra keys compare the FP64 mode, the
-network sampler, the optical-depth method and the end-to-end path through
-pinned host buffers, and time the FP64 oracle on the host cores.
+leveling).
+
+Timed window (cascades with a cap): the last W + K steps of the run, where
+the photons are leveled at their cap every step.  The steps before the window
+run untimed, then W warm-up steps, then K timed steps.  Each timed step is
+enqueued with qed_push_async (one CUDA graph launch; the host never waits
+inside the loop) between an L2 flush and CUDA events on the library's
+stream; qed_push_wait after the loop reads the counts back.  A second pass
+over the same window through the host-driven launches (cfg.profile) times
+each kernel for the breakdown and the roofline of the dominant kernel.
+Extra keys: the same K steps at the start of the cascade (early_window), the
+whole run, the FP64 mode, the network sampler, the optical-depth method, the
+end-to-end path through pinned host buffers, and the FP64 oracle timed on
+the host cores.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
-a bounded sample of the same workload on the host cores.
+a bounded sample of the same workload and window on the host cores.
 """
 from __future__ import annotations
 
@@ -45,11 +52,11 @@ PAIR_BYTES = {"fp32": 4 + 2 * (7 * 4 + 8 + 4 + 8), "fp64": 8 + 2 * (7 * 8 + 8 + 
 # depth (working precision) read and written
 OD_LEPTON_BYTES = {"fp32": LEPTON_BYTES["fp32"] + 8, "fp64": LEPTON_BYTES["fp64"] + 16}
 OD_PHOTON_BYTES = {"fp32": PHOTON_BYTES["fp32"] + 8, "fp64": PHOTON_BYTES["fp64"] + 16}
-# DRAM bytes (read + write) per photon-step of the step-start photon pass,
-# from one ncu capture of the current kernel (696 MB for a launch over the
-# ~1.5e7 capped photons of the 0.3-scale cascade; see
-# profiles/k_photon_pass_fp32_rotating_e_cascade.md); None when not captured
-NCU_PHOTON_BYTES_PER_STEP = {"fp32": 46.4, "fp64": None}
+# DRAM bytes (read + write) per particle-step of the step-start passes, from
+# one ncu capture of the current kernels in the timed window (profiles/);
+# None when the kernel changed since its capture
+NCU_PHOTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
+NCU_LEPTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
 
 
 def parse():
@@ -96,7 +103,17 @@ def make_workload(name, scale=1.0, rank=0):
 def default_steps(w):
     if isinstance(w, list):
         return 3, w[0].nsteps
+    if w.thin_cap:
+        return 5, 20
     return 3, w.nsteps - 3
+
+
+def window_start(w, warm, steps):
+    """First step of the warm-up: cascades with a cap end their window at the
+    last step of the run (leveled at the cap); otherwise the run's start."""
+    if isinstance(w, list) or not w.thin_cap:
+        return 0
+    return max(0, w.nsteps - warm - steps)
 
 
 def capacities(w, nsteps=None):
@@ -114,7 +131,7 @@ def capacities(w, nsteps=None):
 # CPU oracle legs (spawned processes; never touch CUDA)
 # ---------------------------------------------------------------------------
 def _oracle_shard(args):
-    name, scale_seed, lo, hi, warm, steps = args
+    name, scale_seed, lo, hi, warm, steps = args     # warm: steps run untimed first
     sys.path.insert(0, ROOT)
     import oracle
     w = make_workload(name, 1.0)
@@ -152,7 +169,9 @@ def _oracle_shard(args):
 
 def oracle_run(name, warm, steps, target_s=15.0, procs=None):
     """Time the oracle on disjoint seed subsets of the workload, one process
-    per host core.  Returns particle-steps/s, events/s, cores, sample text."""
+    per host core: steps 0..warm-1 untimed (a cascade's cap scaled to the
+    subset), then steps warm..warm+steps-1 timed.  Returns particle-steps/s,
+    events/s, cores, sample text."""
     import multiprocessing as mp
     procs = procs or min(16, os.cpu_count() or 1)
     w = make_workload(name, 1.0)
@@ -179,8 +198,9 @@ def oracle_run(name, warm, steps, target_s=15.0, procs=None):
     ps = sum(r[0] for r in res)
     ev = sum(r[1] for r in res)
     tmax = max(r[2] for r in res)
-    sample = ("%d disjoint subsets of %d seed electrons each (%d of %d) of %s, steps %d..%d, "
-              "FP64 oracle, one process per core" % (procs, per, procs * per, total, name, warm, warm + steps - 1))
+    sample = ("%d disjoint subsets of %d seed electrons each (%d of %d) of %s (leveling cap scaled to the "
+              "subset), steps 0..%d untimed, %d..%d timed, FP64 oracle, one process per core"
+              % (procs, per, procs * per, total, name, warm - 1, warm, warm + steps - 1))
     return ps / tmax, ev / tmax, procs, sample, wall
 
 
@@ -300,57 +320,74 @@ def size_cascade(w, nsteps, precision, method=0):
     return caps
 
 
-def gpu_run(args, w, precision, warm, steps, timed=True, profile=True, mlp_params=None, caps=None, method=0):
+def gpu_run(args, w, precision, start, warm, steps, profile=False, mlp_params=None, caps=None, method=0):
+    """Steps 0..start+warm-1 untimed (one batch, one wait), then `steps`
+    timed steps: per step an L2 flush, then the step enqueued between two
+    CUDA events (qed_push_async; no host wait inside the loop); one
+    qed_push_wait after the loop.  Returns the summed device time of the
+    timed steps, their statistics, the counts at the window's start and end,
+    the GPU time between steps not spent flushing (host-induced idling), and
+    the host's waits inside and after the loop."""
     import torch
     import paper_2409_17299_gb300 as q
     prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
-    # capacities are sized for the whole run, so no per-call overflow snapshot
+    # capacities are sized for the whole run, so no overflow snapshot
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
                         profile=int(profile), restore_on_overflow=0, event_method=method,
                         sampler=q.QED_SAMPLER_MLP if mlp_params is not None else q.QED_SAMPLER_TABLE)
     gen = q.Generator(cfg)
     if mlp_params is not None:
         q.qed_mlp_set_params(gen.ctx, mlp_params)
-    ens = q.DeviceEnsemble.from_host(w.species, caps or capacities(w, warm + steps), prec,
+    s0 = start + warm
+    ens = q.DeviceEnsemble.from_host(w.species, caps or capacities(w, s0 + steps), prec,
                                      optical_depth=method != 0)
     field = q.make_field(w.field_kind, w.field_prm)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     grid = GridFeed(w, gen, prec)
-    for s in range(warm):
-        grid.feed(s)
-        gen.push(ens, field, w.dt, 1, s, auto_grow=False)
+    if grid.dev is None:
+        if s0:
+            gen.push_async(ens, field, w.dt, s0, 0)
+            gen.wait(ens)
+    else:                                  # the caller refills the grid every step
+        for s in range(s0):
+            grid.feed(s)
+            gen.push(ens, field, w.dt, 1, s, auto_grow=False)
     torch.cuda.synchronize()
-    evs = []
-    tot = {"particle_steps": 0, "emit_events": 0, "pair_events": 0, "lepton_steps": 0, "photon_steps": 0,
-           "launches": 0, "kernel_ms": [0.0, 0.0, 0.0, 0.0], "passes": 0, "thinned": 0, "sync_ms": 0.0,
-           "call_ms": 0.0, "chi_fp64": 0}
-    lepton_launches = 0
+    counts0 = list(ens.count)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
     t0 = time.perf_counter()
-    for s in range(warm, warm + steps):
+    host_in_loop = 0.0
+    for k, s in enumerate(range(s0, s0 + steps)):
         grid.feed(s)
+        f, a, b = ev[k]
+        f.record(stream)
         flush.fill_(float(s))
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        st = gen.push(ens, field, w.dt, 1, s, auto_grow=False)
+        th = time.perf_counter()
+        gen.push_async(ens, field, w.dt, 1, s)
+        host_in_loop += time.perf_counter() - th
         b.record(stream)
-        evs.append((a, b))
-        for k in ("particle_steps", "emit_events", "pair_events", "lepton_steps", "photon_steps", "launches",
-                  "passes", "thinned", "sync_ms", "call_ms", "chi_fp64"):
-            tot[k] += st[k]
-        for k in range(4):
-            tot["kernel_ms"][k] += st["kernel_ms"][k]
-        lepton_launches += 1 + st["passes"]
+    tw = time.perf_counter()
+    st = gen.wait(ens)
+    drain = time.perf_counter() - tw
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms = sum(a.elapsed_time(b) for _, a, b in ev)
+    # device time between the end of a step and the next flush: the GPU
+    # waiting for the host
+    idle = sum(ev[k - 1][2].elapsed_time(ev[k][0]) for k in range(1, steps))
     counts = list(ens.count)
     gen.close()
     del ens, flush
     torch.cuda.empty_cache()
-    tot["lepton_launches"] = lepton_launches
-    return ms, wall, tot, counts
+    st["lepton_launches"] = steps + st["passes"]
+    st["counts_start"] = counts0
+    st["gpu_idle_ms"] = idle
+    st["host_enqueue_ms"] = host_in_loop * 1e3
+    st["drain_wait_ms"] = drain * 1e3
+    st["window"] = [s0, s0 + steps - 1]
+    return ms, wall, st, counts
 
 
 def batch_run(ws, precision, warm, steps, threads=0):
@@ -413,9 +450,11 @@ def batch_run(ws, precision, warm, steps, threads=0):
     return ms, st, counts, tuned
 
 
-def e2e_run(w, precision, warm, steps, caps=None):
+def e2e_run(w, precision, start, warm, steps, caps=None):
     """Same steps through the C ABI with the ensemble in pinned host memory:
-    every step copies it to the device, pushes one step, and copies it back."""
+    every step copies it to the device, pushes one step, and copies it back.
+    Steps before the window (0..start-1) run on the device untimed, and their
+    result is copied to the host buffers first."""
     import numpy as np
     import torch
     import paper_2409_17299_gb300 as q
@@ -423,7 +462,7 @@ def e2e_run(w, precision, warm, steps, caps=None):
     cfg = q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap,
                         restore_on_overflow=0)
     gen = q.Generator(cfg)
-    caps = caps or capacities(w, warm + steps)
+    caps = caps or capacities(w, start + warm + steps)
     dev = q.DeviceEnsemble(caps, prec)
     fd = dev.fdtype
     host = []
@@ -460,8 +499,26 @@ def e2e_run(w, precision, warm, steps, caps=None):
             count[k] = n
         stream.synchronize()
 
+    if start:
+        for k in range(3):
+            n = count[k]
+            for f in host[k]:
+                dev.arr[k][f][:n].copy_(host[k][f][:n])
+        dev.count = list(count)
+        gen.push_async(dev, field, w.dt, start, 0) if grid.dev is None else None
+        if grid.dev is None:
+            gen.wait(dev)
+        else:
+            for s in range(start):
+                grid.feed(s)
+                gen.push(dev, field, w.dt, 1, s, auto_grow=False)
+        for k in range(3):
+            n = dev.count[k]
+            for f in host[k]:
+                host[k][f][:n].copy_(dev.arr[k][f][:n])
+            count[k] = n
     nbw = [0, 0]
-    for s in range(warm):
+    for s in range(start, start + warm):
         one_step(s, nbw)
     torch.cuda.synchronize()
     nb = [0, 0]
@@ -470,7 +527,7 @@ def e2e_run(w, precision, warm, steps, caps=None):
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
     t0 = time.perf_counter()
-    for s in range(warm, warm + steps):
+    for s in range(start + warm, start + warm + steps):
         before = q.qed_get_stats(gen.ctx)["particle_steps"]
         one_step(s, nb)
         ps += q.qed_get_stats(gen.ctx)["particle_steps"] - before
@@ -503,15 +560,17 @@ def main():
     dw, ds = default_steps(w0)
     warm = args.warmup if args.warmup is not None else dw
     steps = args.steps if args.steps is not None else ds
+    start = window_start(w0, warm, steps)
 
     if args.impl == "reference":
         if rank != 0:
             return
-        ps_rate, ev_rate, cores, sample, wall = oracle_run(args.workload, warm, steps)
+        ps_rate, ev_rate, cores, sample, wall = oracle_run(args.workload, start + warm, steps)
         line = {"impl": "reference", "metric": "particle-steps/s", "value": ps_rate, "unit": "particle-steps/s",
                 "n_gpus": args.gpus, "steps": steps, "warmup": warm, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "precision": "fp64", "l2": "n/a (CPU)"},
+                "config": {"workload": args.workload, "precision": "fp64", "l2": "n/a (CPU)",
+                           "window": [start + warm, start + warm + steps - 1]},
                 "events_per_s": ev_rate,
                 "cpu_baseline": {"value": ps_rate, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                                  "sample": sample},
@@ -523,7 +582,7 @@ def main():
     # CPU baseline first: its process pool is spawned before CUDA is initialised
     cpu = None
     if args.cpu_baseline and rank == 0 and world == 1:
-        cpu = oracle_run(args.workload, warm, steps)
+        cpu = oracle_run(args.workload, start + warm, steps)
 
     import torch
     if world > 1:
@@ -546,16 +605,17 @@ def main():
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
 
-    caps = size_cascade(w, warm + steps, args.precision) if w.push_photons else None
+    n_total = start + warm + steps
+    caps = size_cascade(w, n_total, args.precision) if w.push_photons else None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     # the headline without per-kernel events; then the same steps again with
     # the library's per-kernel CUDA events for the breakdown and the roofline
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        ms, wall, tot_plain, counts = gpu_run(args, w, args.precision, warm, steps, caps=caps, profile=False)
+        ms, wall, tot_plain, counts = gpu_run(args, w, args.precision, start, warm, steps, caps=caps)
     torch.cuda.synchronize()
-    ms_prof, _, tot, _ = gpu_run(args, w, args.precision, warm, steps, caps=caps, profile=True)
+    ms_prof, _, tot, _ = gpu_run(args, w, args.precision, start, warm, steps, caps=caps, profile=True)
     # the same work, instrumented (FP32 leveling sums depend on the array
     # order, so a rare keep/drop decision may differ between the two passes)
     assert abs(tot["particle_steps"] / tot_plain["particle_steps"] - 1) < 1e-3
@@ -565,9 +625,33 @@ def main():
                                                  float(tot_plain["emit_events"] + tot_plain["pair_events"]), secs,
                                                  world)
 
+    def host_side(t, dev_ms):
+        # waits inside the timed loop: the library's stream waits minus the
+        # one wait after the loop (the graph path issues no other)
+        inside = max(0.0, t["sync_ms"] - t["drain_wait_ms"])
+        return {"host_sync_wait_in_loop_ms": inside, "drain_wait_after_loop_ms": t["drain_wait_ms"],
+                "host_enqueue_ms": t["host_enqueue_ms"], "gpu_idle_between_steps_ms": t["gpu_idle_ms"],
+                "device_ms": dev_ms, "host_sync_wait_frac_of_device": inside / dev_ms if dev_ms > 0 else None}
+
+    other_windows = {}
+    if start > 0 and world == 1:
+        # the same K steps at the start of the cascade (about 1e5 leptons), and
+        # the whole run step by step
+        ms_e, _, tot_e, _ = gpu_run(args, w, args.precision, 0, warm, steps, caps=caps)
+        other_windows["early_window"] = {
+            "value": tot_e["particle_steps"] / (ms_e / 1e3), "ms_per_step": ms_e / steps,
+            "steps": tot_e["window"], "counts_at_start": tot_e["counts_start"],
+            "events_per_s": (tot_e["emit_events"] + tot_e["pair_events"]) / (ms_e / 1e3),
+            "host": host_side(tot_e, ms_e)}
+        ms_w, _, tot_w, _ = gpu_run(args, w, args.precision, 0, 0, n_total, caps=caps)
+        other_windows["whole_run"] = {
+            "value": tot_w["particle_steps"] / (ms_w / 1e3), "ms_per_step": ms_w / n_total,
+            "steps": tot_w["window"], "events_per_s": (tot_w["emit_events"] + tot_w["pair_events"]) / (ms_w / 1e3),
+            "host": host_side(tot_w, ms_w)}
+
     fp64 = None
     if args.compare_fp64 and args.precision == "fp32" and world == 1:
-        ms64, wall64, tot64, _ = gpu_run(args, w, "fp64", warm, steps, caps=caps, profile=False)
+        ms64, wall64, tot64, _ = gpu_run(args, w, "fp64", start, warm, steps, caps=caps)
         fp64 = {"value": tot64["particle_steps"] / (ms64 / 1e3), "events_per_s":
                 (tot64["emit_events"] + tot64["pair_events"]) / (ms64 / 1e3), "ms_per_step": ms64 / steps}
 
@@ -582,7 +666,7 @@ def main():
         train_s = time.perf_counter() - t0
         P = q.qed_mlp_get_params(tg.ctx)
         tg.close()
-        ms_m, _, tot_m, _ = gpu_run(args, w, args.precision, warm, steps, mlp_params=P, caps=caps, profile=False)
+        ms_m, _, tot_m, _ = gpu_run(args, w, args.precision, start, warm, steps, mlp_params=P, caps=caps)
         mlp = {"value": tot_m["particle_steps"] / (ms_m / 1e3),
                "events_per_s": (tot_m["emit_events"] + tot_m["pair_events"]) / (ms_m / 1e3),
                "ms_per_step": ms_m / steps,
@@ -593,10 +677,9 @@ def main():
     if args.compare_od and world == 1 and args.workload != "batched_uniform_b":
         import paper_2409_17299_gb300 as q
         M = q.QED_METHOD_OPTICAL_DEPTH
-        caps_od = size_cascade(w, warm + steps, args.precision, M) if w.push_photons else None
-        ms_o, _, tot_op, counts_o = gpu_run(args, w, args.precision, warm, steps, caps=caps_od, method=M,
-                                            profile=False)
-        _, _, tot_o, _ = gpu_run(args, w, args.precision, warm, steps, caps=caps_od, method=M, profile=True)
+        caps_od = size_cascade(w, n_total, args.precision, M) if w.push_photons else None
+        ms_o, _, tot_op, counts_o = gpu_run(args, w, args.precision, start, warm, steps, caps=caps_od, method=M)
+        _, _, tot_o, _ = gpu_run(args, w, args.precision, start, warm, steps, caps=caps_od, method=M, profile=True)
         prec = args.precision
         lep_b = OD_LEPTON_BYTES[prec] * tot_o["lepton_steps"] + EMIT_BYTES[prec] * tot_o["emit_events"]
         ph_b = OD_PHOTON_BYTES[prec] * tot_o["photon_steps"] + PAIR_BYTES[prec] * tot_o["pair_events"]
@@ -614,8 +697,8 @@ def main():
 
     e2e = None
     if args.e2e:
-        ps_e, ms_e, wall_e, nb = e2e_run(w, args.precision, warm, steps, caps=caps)
-        e2e = {"value": ps_e / (ms_e / 1e3) * world, "unit": "particle-steps/s",
+        ps_e, ms_e2, wall_e, nb = e2e_run(w, args.precision, start, warm, steps, caps=caps)
+        e2e = {"value": ps_e / (ms_e2 / 1e3) * world, "unit": "particle-steps/s",
                "h2d_bytes_per_step": nb[0] // max(1, steps), "d2h_bytes_per_step": nb[1] // max(1, steps)}
 
     if rank != 0:
@@ -633,12 +716,13 @@ def main():
                           "bytes_per_particle_step": LEPTON_BYTES[prec], "bytes_per_emission": EMIT_BYTES[prec],
                           "units": "lepton particle-steps %d, emissions %d" % (tot["lepton_steps"],
                                                                              tot["emit_events"]),
-                          "traffic": None},
+                          "traffic": (NCU_LEPTON_BYTES_PER_STEP[prec] * tot["lepton_steps"] / steps
+                                      if NCU_LEPTON_BYTES_PER_STEP[prec] else None)},
         "k_photon_pass": {"achieved": ph_bytes / (ph_ms / 1e3) / 1e9 if ph_ms > 0 else None,
                           "kernel_ms": ph_ms, "launches": launches if w.push_photons else 0,
                           "bytes_per_photon_step": PHOTON_BYTES[prec], "bytes_per_pair": PAIR_BYTES[prec],
                           "units": "photon-steps %d, pairs %d" % (tot["photon_steps"], tot["pair_events"]),
-                          "traffic": (NCU_PHOTON_BYTES_PER_STEP[prec] * tot["photon_steps"] / launches
+                          "traffic": (NCU_PHOTON_BYTES_PER_STEP[prec] * tot["photon_steps"] / steps
                                       if NCU_PHOTON_BYTES_PER_STEP[prec] and w.push_photons else None)},
     }
     for k in kernels.values():
@@ -653,7 +737,12 @@ def main():
         "config": {"workload": args.workload, "precision": prec + (" (fp64 sub-step clock, fp64 chi fallback)" if prec == "fp32" else ""),
                    "seed_electrons": len(w.species[0]["id"]), "thin_cap": w.thin_cap,
                    "steps_total": w.nsteps, "dt": "T/%d" % round(2 * math.pi / w.dt),
+                   "step_range": tot_plain["window"], "warmup_range": [start, start + warm - 1] if warm else None,
+                   "counts_at_window_start": tot_plain["counts_start"],
+                   "window": ("the last %d steps of the run: the photons are leveled at the cap every step "
+                              "(steps before it run untimed)" % (warm + steps)) if start > 0 else "the run's start",
                    "l2": "flushed between timed steps (256 MB write)",
+                   "launch": "one CUDA graph per step (qed_push_async); one wait after the timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "events_per_s": ev_total / tmax,
         "final_counts": counts,
@@ -664,19 +753,21 @@ def main():
                      "kernel": "%s<%s>" % (dom, "float" if prec == "fp32" else "double"),
                      "peak_source": peak_src + " hbm_gbs",
                      "achieved_is": "algorithmic bytes of all launches / summed CUDA-event time of the launches",
-                     "traffic_is": "ncu DRAM bytes per unit x units per launch (average launch)",
+                     "traffic_is": "ncu DRAM bytes per unit x units per step-start launch",
                      "kernels": kernels},
         "breakdown_ms": {"lepton": tot["kernel_ms"][0], "photon": tot["kernel_ms"][1],
                          "compaction": tot["kernel_ms"][2], "leveling": tot["kernel_ms"][3],
-                         "host_sync_wait": tot["sync_ms"], "host_call_wall": tot["call_ms"],
                          "device_total": ms_prof, "device_total_uninstrumented": ms,
-                         "note": "kernel times from a second pass over the same steps with per-kernel events"},
+                         "note": "kernel times from a second pass over the same steps with per-kernel events "
+                                 "(host-driven launches)"},
+        "host": host_side(tot_plain, ms),
         "chi_fp64_fallbacks": tot["chi_fp64"],
         "paper_context": ("context only: the paper's QED module takes 2.19 s for 2.5e5 particles x 100 steps "
                           "on 2x Xeon Silver 4310T (20 cores, AVX-512), i.e. >= 1.1e7 particle-steps/s "
                           "(a lower bound derived here; the paper quotes no particle-steps/s)"),
         "clocks": clk.summary(),
     }
+    line.update(other_windows)
     if fp64:
         line["fp64"] = fp64
         line["fp32_speedup_over_fp64"] = line["value"] / fp64["value"]

@@ -145,7 +145,8 @@ typedef struct {
                                  context's stream) of the lepton push kernels, the photon
                                  push kernels, the dead-photon compaction, and leveling */
     double sync_ms;           /* host time spent waiting in stream synchronisation */
-    double call_ms;           /* host wall time of the call */
+    double call_ms;           /* host wall time of the call (of a batch: from its opening
+                                 qed_push_async to the end of qed_push_wait) */
 } qed_stats;
 
 /* Create a context and build its rate approximant and inverse-CDF tables on
@@ -172,6 +173,42 @@ qed_status qed_init_tables(qed_ctx **ctx, const qed_config *cfg, void *cuda_stre
  *  out may be NULL. */
 qed_status qed_push_and_generate(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field,
                                  double dt, int nsteps, int64_t step0, qed_stats *out);
+
+/* The same steps without waiting for the GPU: qed_push_async enqueues them
+ * and returns; qed_push_wait waits for everything enqueued since the batch
+ * opened and reports it.  qed_push_and_generate is qed_push_async followed
+ * by qed_push_wait.
+ *
+ * A batch opens with the first qed_push_async after a wait (or after the
+ * context was created): the counts and capacities of *p go to the device,
+ * and with restore_on_overflow the particle state is copied aside.  Later
+ * calls of the batch must pass the same arrays and capacities (else
+ * QED_ERR_STATE); their counts are not read, because the device holds the
+ * current counts until qed_push_wait writes them into *p.  step0 may jump
+ * (the steps run in call order with the indices given).
+ *
+ * Each step runs as one CUDA graph launch (Sec. 3, Algorithms 1-2): the
+ * step-start passes, a device-side loop over newborn passes (bounded by
+ * 100000 passes per step, QED_ERR_TIMEOUT beyond), and per species the merge
+ * step -- leveling when the count exceeds thin_cap, converted photons removed
+ * -- decided by the device.  The host never waits inside a batch.  With
+ * cfg.profile (per-kernel events) or without conditional graph nodes, the
+ * steps are driven from the host instead (the same kernels; the host reads
+ * the control block between passes).
+ *
+ * After a species runs out of capacity, every later step of the batch does
+ * nothing; qed_push_wait returns QED_ERR_CAPACITY with the demand in
+ * out->needed_capacity and, with restore_on_overflow, *p back at its state
+ * when the batch opened (grow and replay the whole batch).
+ * While a batch is open, qed_compact, qed_level_eval, qed_level_apply,
+ * qed_batch_push, qed_autotune_batch, qed_eval_chi and qed_set_optical_depth
+ * return QED_ERR_STATE.
+ *  qed_push_async: QED_OK, or an argument / state error (nothing enqueued).
+ *  qed_push_wait: the status of the batch; QED_ERR_STATE when none is open
+ *                 or *p holds other arrays.  out may be NULL. */
+qed_status qed_push_async(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
+                          int64_t step0);
+qed_status qed_push_wait(qed_ctx *ctx, qed_particles *p, qed_stats *out);
 
 /* Remove dead particles (weight 0) from every species, then, with thin_cap > 0,
  * apply global leveling at step index `step` (Sec. 4.2 merge step, Sec. 5.1).
@@ -362,11 +399,16 @@ qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const 
  * device-wide synchronisation cudaMalloc / cudaFree may cause.
  *  sp           in/out: caller-owned device arrays (16-byte aligned); count is
  *               read and updated (alive entries end up in [0, count))
+ *  od_dev       the species' optical-depth array (QED_METHOD_OPTICAL_DEPTH: one
+ *               value of the precision's type per particle, caller-owned,
+ *               aligned to the element size), moved with the particles like
+ *               the arrays of *sp; NULL when there is none (the sub-step method)
  *  precision    QED_FP64 (double arrays) or QED_FP32 (float arrays)
  *  cuda_stream  stream for the work (NULL = default stream); synchronised
  *               before returning
- * Same result as the compaction inside qed_compact(): the r-th dead slot
- * below the new count receives the r-th alive entry at or above it.
+ * Same result as the compaction inside qed_compact() with the same
+ * optical-depth array bound: the r-th dead slot below the new count receives
+ * the r-th alive entry at or above it.
  * Scratch: one file-scope device array of about 8 MB holding control words,
  * per-block counts and hole ranks, kept by every GPU that loads the library
  * until the process exits.  No context is needed and nothing is allocated:
@@ -379,7 +421,7 @@ qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const 
  * Errors: QED_ERR_INVALID for a null or misaligned array, an unknown
  * precision, count < 0 or > capacity, or count > QED_NOALLOC_MAX_ENTRIES;
  * QED_ERR_STATE if a bounds check inside the kernels failed; QED_ERR_CUDA. */
-qed_status qed_compact_species_noalloc(qed_species *sp, int precision, void *cuda_stream);
+qed_status qed_compact_species_noalloc(qed_species *sp, void *od_dev, int precision, void *cuda_stream);
 
 #ifdef __cplusplus
 }

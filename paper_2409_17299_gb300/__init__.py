@@ -21,7 +21,7 @@ QED_METHOD_SUBSTEP, QED_METHOD_OPTICAL_DEPTH = 0, 1
 QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
 QED_FIELD_UNIFORM, QED_FIELD_ROTATING_E, QED_FIELD_STANDING_CP, QED_FIELD_GRID = 0, 1, 2, 3
 
-EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_batch_push", "qed_autotune_batch", "qed_compact", "qed_get_stats", "qed_strerror",
+EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_push_async", "qed_push_wait", "qed_batch_push", "qed_autotune_batch", "qed_compact", "qed_get_stats", "qed_strerror",
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
             "qed_compact_species_noalloc", "qed_train_surrogate", "qed_mlp_set_params", "qed_mlp_get_params",
             "qed_mlp_forward", "qed_mlp_grad", "qed_level_begin", "qed_level_advance", "qed_level_eval",
@@ -96,6 +96,8 @@ def lib():
         "qed_init_tables": (i32, [C.POINTER(p), C.POINTER(QedConfig), p]),
         "qed_push_and_generate": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedFieldDesc), C.c_double, i32, i64,
                                         C.POINTER(QedStats)]),
+        "qed_push_async": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedFieldDesc), C.c_double, i32, i64]),
+        "qed_push_wait": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedStats)]),
         "qed_compact": (i32, [p, C.POINTER(QedParticles), i64]),
         "qed_batch_push": (i32, [p, C.POINTER(QedParticles), C.POINTER(QedFieldDesc), i32, C.c_double, i32, i64,
                                  C.POINTER(QedStats)]),
@@ -108,7 +110,7 @@ def lib():
         "qed_get_tables": (i32, [p, p, p, p, p]),
         "qed_eval_rate": (i32, [p, i32, p, i64, p]),
         "qed_sample": (i32, [p, i32, p, p, i64, p, p]),
-        "qed_compact_species_noalloc": (i32, [C.POINTER(QedSpecies), i32, p]),
+        "qed_compact_species_noalloc": (i32, [C.POINTER(QedSpecies), p, i32, p]),
         "qed_eval_chi": (i32, [p, i32, p, p, p, i64, p, C.POINTER(i64)]),
         "qed_train_surrogate": (i32, [p, i64, i32, C.c_double, C.c_uint64, C.POINTER(C.c_double)]),
         "qed_mlp_set_params": (i32, [p, p]),
@@ -155,6 +157,25 @@ def qed_push_and_generate(ctx, particles: QedParticles, field: QedFieldDesc, dt:
                                      int(step0), C.byref(st))
     if rc not in (QED_OK, QED_ERR_CAPACITY):
         raise QedError(rc, "qed_push_and_generate")
+    return rc, st.as_dict()
+
+
+def qed_push_async(ctx, particles: QedParticles, field: QedFieldDesc, dt: float, nsteps: int,
+                   step0: int = 0) -> None:
+    """Enqueue nsteps steps without waiting for the GPU (the counts stay on
+    the device until qed_push_wait)."""
+    rc = lib().qed_push_async(ctx, C.byref(particles), C.byref(field), float(dt), int(nsteps), int(step0))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_push_async")
+
+
+def qed_push_wait(ctx, particles: QedParticles):
+    """Wait for the enqueued steps; returns (status, stats dict) and updates
+    the counts in particles.  QED_ERR_CAPACITY is returned, not raised."""
+    st = QedStats()
+    rc = lib().qed_push_wait(ctx, C.byref(particles), C.byref(st))
+    if rc not in (QED_OK, QED_ERR_CAPACITY):
+        raise QedError(rc, "qed_push_wait", st.as_dict())
     return rc, st.as_dict()
 
 
@@ -365,11 +386,14 @@ def qed_mlp_grad(ctx, feat_dev_ptr: int, target_dev_ptr: int, n: int):
     return g, loss.value
 
 
-def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream: int | None = None) -> int:
+def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream: int | None = None,
+                                od_dev_ptr: int | None = None) -> int:
     """Compaction of one species that allocates no device memory (for callers
     whose device memory is owned by another allocator); species.count is
-    updated in place.  Overlapping calls on the GPU race (shared scratch)."""
-    rc = lib().qed_compact_species_noalloc(C.byref(species), int(precision), C.c_void_p(cuda_stream or 0))
+    updated in place and the optical-depth array, if given, moves with the
+    particles.  Overlapping calls on the GPU race (shared scratch)."""
+    rc = lib().qed_compact_species_noalloc(C.byref(species), C.c_void_p(od_dev_ptr or 0), int(precision),
+                                           C.c_void_p(cuda_stream or 0))
     if rc != QED_OK:
         raise QedError(rc, "qed_compact_species_noalloc")
     return rc
@@ -530,6 +554,24 @@ class Generator:
                 raise QedError(rc, "qed_push_and_generate", st)
             need = [max(2 * ens.capacity[s], 2 * st["needed_capacity"][s]) for s in range(3)]
             ens.grow(need)
+
+    def push_async(self, ens: DeviceEnsemble, field: QedFieldDesc, dt: float, nsteps: int, step0: int = 0):
+        """Enqueue steps and return at once; ens.count is stale until wait()."""
+        if not getattr(self, "_open", False):
+            self._bind(ens)
+            self._open = True
+        qed_push_async(self.ctx, ens.struct(), field, dt, nsteps, step0)
+
+    def wait(self, ens: DeviceEnsemble):
+        """Finish the enqueued steps: counts of ens updated; stats returned.
+        A capacity overflow raises (grow the ensemble and replay the batch)."""
+        P = ens.struct()
+        self._open = False
+        rc, st = qed_push_wait(self.ctx, P)
+        ens.pull_counts(P)
+        if rc != QED_OK:
+            raise QedError(rc, "qed_push_wait", st)
+        return st
 
     def _bind(self, ens):
         """The ensemble's optical-depth arrays (bound on every call: buffers

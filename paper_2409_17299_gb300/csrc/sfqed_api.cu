@@ -11,12 +11,14 @@ static void free_ctx(qed_ctx *c) {
     cudaStreamSynchronize(c->stream);
     sfq_batch_free(c);
     sfq_level_graphs_free(c);
+    sfq_step_graph_free(c);
     void *dev[] = {c->coef64, c->coef32, c->icdf_em64, c->icdf_pair64, c->icdf_em32, c->icdf_pair32, c->gl,
                    c->ctl, c->tau[0], c->tau[1], c->tau[2], c->blk, c->slots, c->snap, c->lev,
                    c->mlp_p, c->mlp_w16, c->mlp_loss};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    if (c->ctl_up) cudaFreeHost(c->ctl_up);
     if (c->pin) cudaFreeHost(c->pin);
     if (c->grid_il) cudaFree(c->grid_il);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -54,6 +56,7 @@ extern "C" qed_status qed_init_tables(qed_ctx **out, const qed_config *cfg, void
               cudaMalloc(&c->ctl, sizeof(DevCtl)) == cudaSuccess &&
               cudaMalloc(&c->lev, sizeof(LevelWork)) == cudaSuccess &&
               cudaHostAlloc(&c->ctl_host, sizeof(DevCtl), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(&c->ctl_up, sizeof(DevCtl), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(&c->pin, 64, cudaHostAllocDefault) == cudaSuccess &&
               cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
@@ -80,13 +83,24 @@ extern "C" qed_status qed_push_and_generate(qed_ctx *ctx, qed_particles *p, cons
     return sfq_push(ctx, p, field, dt, nsteps, step0, out);
 }
 
+extern "C" qed_status qed_push_async(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt,
+                                     int nsteps, int64_t step0) {
+    return sfq_push_async(ctx, p, field, dt, nsteps, step0);
+}
+
+extern "C" qed_status qed_push_wait(qed_ctx *ctx, qed_particles *p, qed_stats *out) {
+    return sfq_push_wait(ctx, p, out);
+}
+
 extern "C" qed_status qed_batch_push(qed_ctx *ctx, qed_particles *ens, const qed_field_desc *fields, int n_ens,
                                      double dt, int nsteps, int64_t step0, qed_stats *out) {
+    if (ctx && ctx->async_open) return QED_ERR_STATE;
     return sfq_batch_push(ctx, ens, fields, n_ens, dt, nsteps, step0, out, 0, 0);
 }
 
 extern "C" qed_status qed_set_optical_depth(qed_ctx *ctx, void *const od_dev[3]) {
     if (!ctx || !od_dev) return QED_ERR_INVALID;
+    if (ctx->async_open) return QED_ERR_STATE;
     const uintptr_t align = ctx->cfg.precision == QED_FP32 ? 4u : 8u;
     for (int s = 0; s < 3; ++s) {
         if (od_dev[s] && (reinterpret_cast<uintptr_t>(od_dev[s]) % align)) return QED_ERR_INVALID;
@@ -109,11 +123,13 @@ extern "C" qed_status qed_batch_shape(qed_ctx *ctx, int *threads, int *step_budg
 
 extern "C" qed_status qed_autotune_batch(qed_ctx *ctx, const qed_particles *ens, const qed_field_desc *fields,
                                          int n_ens, double dt, int nsteps, int *chosen_threads, double *ms3) {
+    if (ctx && ctx->async_open) return QED_ERR_STATE;
     return sfq_batch_autotune(ctx, ens, fields, n_ens, dt, nsteps, chosen_threads, ms3);
 }
 
 extern "C" qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step) {
     if (!ctx || !p || step < 0 || step > 0xFFFFFFFFll) return QED_ERR_INVALID;
+    if (ctx->async_open) return QED_ERR_STATE;
     for (int s = 0; s < 3; ++s)
         if (p->s[s].count < 0 || p->s[s].count > p->s[s].capacity) return QED_ERR_INVALID;
     SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -157,6 +173,7 @@ extern "C" qed_status qed_level_eval(qed_ctx *ctx, const qed_species *sp, int sp
                                      int64_t *C, int64_t *N, double *max_w) {
     if (!ctx || !sp || !A || !C || !N || !max_w || species < 0 || species > 2 || !(w > 0.0)) return QED_ERR_INVALID;
     if (sp->count < 0 || sp->count > sp->capacity || (sp->count > 0 && !sp->w)) return QED_ERR_INVALID;
+    if (ctx->async_open) return QED_ERR_STATE;
     SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
     qed_species copy = *sp;
     return sfq_level_eval(ctx, &copy, species, w, A, C, N, max_w);
@@ -165,6 +182,7 @@ extern "C" qed_status qed_level_eval(qed_ctx *ctx, const qed_species *sp, int sp
 extern "C" qed_status qed_level_apply(qed_ctx *ctx, qed_particles *p, int species, double wstar, int64_t step) {
     if (!ctx || !p || species < 0 || species > 2 || !(wstar >= 0.0) || step < 0 || step > 0xFFFFFFFFll)
         return QED_ERR_INVALID;
+    if (ctx->async_open) return QED_ERR_STATE;
     for (int s = 0; s < 3; ++s)
         if (p->s[s].count < 0 || p->s[s].count > p->s[s].capacity) return QED_ERR_INVALID;
     SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -231,6 +249,7 @@ extern "C" qed_status qed_eval_rate(qed_ctx *ctx, int is_photon, const double *c
 
 extern "C" qed_status qed_eval_chi(qed_ctx *ctx, int is_photon, const double *p_dev, const double *E_dev,
                                    const double *B_dev, int64_t n, double *chi_dev, int64_t *n_fp64) {
+    if (ctx && ctx->async_open) return QED_ERR_STATE;
     return sfq_eval_chi(ctx, is_photon, p_dev, E_dev, B_dev, n, chi_dev, n_fp64);
 }
 

@@ -222,7 +222,7 @@ __host__ __device__ __forceinline__ double double_of_bits(unsigned long long b) 
 // (after a leveling most weights equal it, and the next root usually lies
 // in the piece just above it), else at +inf.  The start changes only the
 // path: the root of its own piece is the same from any start.
-__global__ void k_lev_begin(LevelWork *lw, int s) {
+__device__ __forceinline__ void lev_start(LevelWork *lw, int s) {
     LevelIter &it = lw->it[s];
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     const double w0 = lw->prev[s] > 0.0 && lw->prev[s] < inf ? lw->prev[s] : inf;
@@ -239,6 +239,8 @@ __global__ void k_lev_begin(LevelWork *lw, int s) {
     lw->arrive[s] = 0;
     lw->passes[s] = 0;
 }
+
+__global__ void k_lev_begin(LevelWork *lw, int s) { lev_start(lw, s); }
 
 // error-free float-float accumulation (TwoSum), accurate to ~2^-48 relative
 struct FF {
@@ -482,23 +484,26 @@ constexpr int LROUNDS = 16;
 constexpr int LTILE = LT * LROUNDS;       // entries per tile (offsets fit 16 bits)
 constexpr int LSPAN = 32 * LROUNDS;       // contiguous entries per warp
 
+// Tiles holding entries of a species of n entries, and the tile grid: a
+// kernel loops over tiles (grid stride), so its grid can be fixed by the
+// species' capacity (a captured step graph) while the device count decides
+// the work.
+__device__ __forceinline__ long long tiles_of(unsigned long long n) { return (long long)((n + LTILE - 1) / LTILE); }
+
 // Pass 1.  LEVEL: first keep particle i (0 < w_i < w*) with probability
 // w_i / w*: the comparison u < w_i / w* is made in FP32 with a relative
 // margin, and in FP64 (the oracle's test) only for draws within that margin
-// of the boundary; kept particles get weight w*.
+// of the boundary; kept particles get weight w*.  The step index keying the
+// draws is `step`, or the control block's current step when step_from_ctl.
 template <class T, bool LEVEL>
 __global__ void __launch_bounds__(LT, 4) k_tile_dead(SpeciesDev S, DevCtl *ctl, int s, const LevelWork *lw,
-                                                  const PhiloxKeys keys, unsigned step, unsigned long long *blk,
-                                                  unsigned short *dl) {
+                                                  const PhiloxKeys keys, unsigned step, int step_from_ctl,
+                                                  unsigned long long *blk, unsigned short *dl) {
     __shared__ unsigned wdead[LT / 32];
     const unsigned long long n = ctl->count[s];
-    const unsigned long long base = (unsigned long long)blockIdx.x * LTILE;
-    if (base >= n) {
-        if (threadIdx.x == 0) blk[blockIdx.x] = 0;
-        return;
-    }
+    const long long nbe = tiles_of(n);
+    if (step_from_ctl) step = ctl->sv_step;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned long long wbase = base + (unsigned long long)wid * LSPAN;
     bool thin = false;
     double wstar = 0.0;
     float inv_f = 0.f, wup = 0.f, wnew = 0.f;
@@ -510,75 +515,81 @@ __global__ void __launch_bounds__(LT, 4) k_tile_dead(SpeciesDev S, DevCtl *ctl, 
         wup = it.wstar_up;
         wnew = it.wstar_f;
     }
-    unsigned mask[LROUNDS];
-    unsigned cnt = 0, removed = 0;
+    unsigned removed = 0;
+    for (long long tile = blockIdx.x; tile < nbe; tile += gridDim.x) {
+        const unsigned long long base = (unsigned long long)tile * LTILE;
+        const unsigned long long wbase = base + (unsigned long long)wid * LSPAN;
+        unsigned mask[LROUNDS];
+        unsigned cnt = 0;
 #pragma unroll
-    for (int c0 = 0; c0 < LROUNDS; c0 += 8) {
-        // weights and (leveling) ids of eight entries issued together: at
-        // the cap nearly every entry is below w* and needs its id
-        T v[8];
-        unsigned long long idv[8];
+        for (int c0 = 0; c0 < LROUNDS; c0 += 8) {
+            // weights and (leveling) ids of eight entries issued together: at
+            // the cap nearly every entry is below w* and needs its id
+            T v[8];
+            unsigned long long idv[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const unsigned long long i = wbase + (c0 + r) * 32 + lane;
-            v[r] = i < n ? ld<T>(S.w, i) : (T)0;
-            idv[r] = (LEVEL && thin && i < n) ? S.id[i] : 0ull;
-        }
-        bool below[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            if constexpr (sizeof(T) == 4) below[r] = LEVEL && thin && v[r] > (T)0 && (float)v[r] < wup;
-            else below[r] = LEVEL && thin && v[r] > (T)0 && (double)v[r] < wstar;
-        }
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const unsigned long long i = wbase + (c0 + r) * 32 + lane;
-            bool dead = i < n && !(v[r] > (T)0);
-            if (LEVEL && below[r]) {
-                const uint4 q = event_draw(keys, idv[r], step, 0xFFFFFFFFu);
-                const float uf = __uint2float_rn(q.x) * 0x1p-32f;     // u to within 2^-32 + FP32 rounding
-                const float pf = (float)v[r] * inv_f;
-                bool keep;
-                if (uf < pf * (1.0f - 1e-6f) - 0x1p-31f) keep = true;
-                else if (uf > pf * (1.0f + 1e-6f) + 0x1p-31f) keep = false;
-                else {
-                    double u, vv;
-                    Uniform<double>::draw(q.x, q.y, u, vv);
-                    keep = u < (double)v[r] / wstar;
-                }
-                if (keep) {
-                    if constexpr (sizeof(T) == 4) st<T>(S.w, i, wnew);
-                    else st<T>(S.w, i, wstar);
-                } else {
-                    st<T>(S.w, i, (T)0);
-                    dead = true;
-                    ++removed;
-                }
+            for (int r = 0; r < 8; ++r) {
+                const unsigned long long i = wbase + (c0 + r) * 32 + lane;
+                v[r] = i < n ? ld<T>(S.w, i) : (T)0;
+                idv[r] = (LEVEL && thin && i < n) ? S.id[i] : 0ull;
             }
-            mask[c0 + r] = __ballot_sync(0xffffffffu, dead);
-            cnt += __popc(mask[c0 + r]);
+            bool below[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                if constexpr (sizeof(T) == 4) below[r] = LEVEL && thin && v[r] > (T)0 && (float)v[r] < wup;
+                else below[r] = LEVEL && thin && v[r] > (T)0 && (double)v[r] < wstar;
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const unsigned long long i = wbase + (c0 + r) * 32 + lane;
+                bool dead = i < n && !(v[r] > (T)0);
+                if (LEVEL && below[r]) {
+                    const uint4 q = event_draw(keys, idv[r], step, 0xFFFFFFFFu);
+                    const float uf = __uint2float_rn(q.x) * 0x1p-32f;     // u to within 2^-32 + FP32 rounding
+                    const float pf = (float)v[r] * inv_f;
+                    bool keep;
+                    if (uf < pf * (1.0f - 1e-6f) - 0x1p-31f) keep = true;
+                    else if (uf > pf * (1.0f + 1e-6f) + 0x1p-31f) keep = false;
+                    else {
+                        double u, vv;
+                        Uniform<double>::draw(q.x, q.y, u, vv);
+                        keep = u < (double)v[r] / wstar;
+                    }
+                    if (keep) {
+                        if constexpr (sizeof(T) == 4) st<T>(S.w, i, wnew);
+                        else st<T>(S.w, i, wstar);
+                    } else {
+                        st<T>(S.w, i, (T)0);
+                        dead = true;
+                        ++removed;
+                    }
+                }
+                mask[c0 + r] = __ballot_sync(0xffffffffu, dead);
+                cnt += __popc(mask[c0 + r]);
+            }
         }
-    }
-    if (lane == 0) wdead[wid] = cnt;
-    __syncthreads();
-    unsigned before = 0, total = 0;
+        if (lane == 0) wdead[wid] = cnt;
+        __syncthreads();
+        unsigned before = 0, total = 0;
 #pragma unroll
-    for (int k = 0; k < LT / 32; ++k) {
-        const unsigned c = wdead[k];
-        before += k < wid ? c : 0u;
-        total += c;
-    }
-    unsigned short *tdl = dl + base;
-    const unsigned lt = (1u << lane) - 1u;
-    unsigned run = before;
+        for (int k = 0; k < LT / 32; ++k) {
+            const unsigned c = wdead[k];
+            before += k < wid ? c : 0u;
+            total += c;
+        }
+        unsigned short *tdl = dl + base;
+        const unsigned lt = (1u << lane) - 1u;
+        unsigned run = before;
 #pragma unroll
-    for (int r = 0; r < LROUNDS; ++r) {
-        if ((mask[r] >> lane) & 1u) tdl[run + __popc(mask[r] & lt)] = (unsigned short)(wid * LSPAN + r * 32 + lane);
-        run += __popc(mask[r]);
-    }
-    if (threadIdx.x == 0) {
-        const unsigned long long tn = n - base < (unsigned long long)LTILE ? n - base : (unsigned long long)LTILE;
-        blk[blockIdx.x] = tn - total;
+        for (int r = 0; r < LROUNDS; ++r) {
+            if ((mask[r] >> lane) & 1u) tdl[run + __popc(mask[r] & lt)] = (unsigned short)(wid * LSPAN + r * 32 + lane);
+            run += __popc(mask[r]);
+        }
+        if (threadIdx.x == 0) {
+            const unsigned long long tn = n - base < (unsigned long long)LTILE ? n - base : (unsigned long long)LTILE;
+            blk[tile] = tn - total;
+        }
+        __syncthreads();                       // wdead is rewritten by the next tile
     }
     if constexpr (LEVEL) {
         for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
@@ -586,18 +597,20 @@ __global__ void __launch_bounds__(LT, 4) k_tile_dead(SpeciesDev S, DevCtl *ctl, 
     }
 }
 
-// single block: exclusive scan of the tile counts (blk[nb] = A), then H from
-// the alive entries of the tile that holds A
+// single block: exclusive scan of the counts of the tiles holding entries
+// (blk[nbe] = A), then H from the alive entries of the tile that holds A
 template <class T>
 __global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long nb, DevCtl *ctl, int s) {
     __shared__ unsigned long long sw[32];
     __shared__ unsigned long long carry;
+    const long long nbe_all = tiles_of(ctl->count[s]);
+    const long long nbe = nbe_all < nb ? nbe_all : nb;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (long long b0 = 0; b0 < nb; b0 += blockDim.x) {
+    for (long long b0 = 0; b0 < nbe; b0 += blockDim.x) {
         const long long i = b0 + threadIdx.x;
-        const unsigned long long v = i < nb ? blk[i] : 0ull;
+        const unsigned long long v = i < nbe ? blk[i] : 0ull;
         unsigned long long x = v;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -615,7 +628,7 @@ __global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long n
         }
         __syncthreads();
         const unsigned long long before = carry + (wid > 0 ? sw[wid - 1] : 0ull) + x - v;
-        if (i < nb) blk[i] = before;
+        if (i < nbe) blk[i] = before;
         __syncthreads();
         if (threadIdx.x == 0) carry += sw[nw - 1];
         __syncthreads();
@@ -623,7 +636,7 @@ __global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long n
     const unsigned long long A = carry;
     const unsigned long long a = A / LTILE;
     unsigned long long below = A;                   // A on a tile boundary past the data: no holes
-    if ((long long)a < nb) {
+    if ((long long)a < nbe) {
         unsigned c = 0;
         for (unsigned long long i = a * LTILE + threadIdx.x; i < A; i += blockDim.x) c += alive_at<T>(w, i) ? 1u : 0u;
         for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -635,47 +648,52 @@ __global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long n
         below = blk[a] + tc;
     }
     if (threadIdx.x == 0) {
-        blk[nb] = A;
+        blk[nbe] = A;
         ctl->alive[s] = A;
         ctl->holes[s] = A - below;
     }
 }
 
-// pass 2: movers (alive entries at or above A) by rank
+// pass 2: movers (alive entries at or above A) by rank, over the tiles that
+// reach past A
 template <class T>
 __global__ void __launch_bounds__(LT) k_tile_movers(const void *w, DevCtl *ctl, int s, const unsigned long long *blk,
                                                     unsigned long long *movers) {
     __shared__ unsigned walive[LT / 32];
     const unsigned long long n = ctl->count[s], A = ctl->alive[s], H = ctl->holes[s];
-    const unsigned long long base = (unsigned long long)blockIdx.x * LTILE;
-    if (H == 0 || base + LTILE <= A || base >= n) return;
+    if (H == 0) return;
     const unsigned long long below_A = A - H;      // alive entries below A
+    const long long nbe = tiles_of(n);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned long long wbase = base + (unsigned long long)wid * LSPAN;
-    unsigned amask[LROUNDS];
-    unsigned cnt = 0;
+    for (long long tile = (long long)(A / LTILE) + blockIdx.x; tile < nbe; tile += gridDim.x) {
+        const unsigned long long base = (unsigned long long)tile * LTILE;
+        const unsigned long long wbase = base + (unsigned long long)wid * LSPAN;
+        unsigned amask[LROUNDS];
+        unsigned cnt = 0;
 #pragma unroll
-    for (int r = 0; r < LROUNDS; ++r) {
-        const unsigned long long i = wbase + r * 32 + lane;
-        amask[r] = __ballot_sync(0xffffffffu, i < n && alive_at<T>(w, i));
-        cnt += __popc(amask[r]);
-    }
-    if (lane == 0) walive[wid] = cnt;
-    __syncthreads();
-    unsigned before = 0;
-    for (int k = 0; k < wid; ++k) before += walive[k];
-    const unsigned lt = (1u << lane) - 1u;
-    unsigned long long run = blk[blockIdx.x] + before;   // alive entries before this warp's span
-#pragma unroll
-    for (int r = 0; r < LROUNDS; ++r) {
-        const unsigned long long i = wbase + r * 32 + lane;
-        if (((amask[r] >> lane) & 1u) && i >= A) {
-            const unsigned long long ab = run + __popc(amask[r] & lt);
-            const unsigned long long rank = ab - below_A;
-            if (ab >= below_A && rank < H) movers[rank] = i;
-            else atomicExch(&ctl->bad_index, i + 1);
+        for (int r = 0; r < LROUNDS; ++r) {
+            const unsigned long long i = wbase + r * 32 + lane;
+            amask[r] = __ballot_sync(0xffffffffu, i < n && alive_at<T>(w, i));
+            cnt += __popc(amask[r]);
         }
-        run += __popc(amask[r]);
+        if (lane == 0) walive[wid] = cnt;
+        __syncthreads();
+        unsigned before = 0;
+        for (int k = 0; k < wid; ++k) before += walive[k];
+        const unsigned lt = (1u << lane) - 1u;
+        unsigned long long run = blk[tile] + before;   // alive entries before this warp's span
+#pragma unroll
+        for (int r = 0; r < LROUNDS; ++r) {
+            const unsigned long long i = wbase + r * 32 + lane;
+            if (((amask[r] >> lane) & 1u) && i >= A) {
+                const unsigned long long ab = run + __popc(amask[r] & lt);
+                const unsigned long long rank = ab - below_A;
+                if (ab >= below_A && rank < H) movers[rank] = i;
+                else atomicExch(&ctl->bad_index, i + 1);
+            }
+            run += __popc(amask[r]);
+        }
+        __syncthreads();                       // walive is rewritten by the next tile
     }
 }
 
@@ -685,49 +703,74 @@ template <class T>
 __global__ void __launch_bounds__(LT) k_tile_fill(SpeciesDev S, DevCtl *ctl, int s, const unsigned long long *blk,
                                                   const unsigned short *dl, const unsigned long long *movers) {
     const unsigned long long n = ctl->count[s], A = ctl->alive[s], H = ctl->holes[s];
-    const unsigned long long base = (unsigned long long)blockIdx.x * LTILE;
-    if (H == 0 || base >= A) return;
-    const unsigned long long tn = n - base < (unsigned long long)LTILE ? n - base : (unsigned long long)LTILE;
-    const unsigned long long alive_t = blk[blockIdx.x + 1] - blk[blockIdx.x];
-    const unsigned dead_t = (unsigned)(tn - alive_t);
-    const unsigned long long dead_before = base - blk[blockIdx.x];
-    const unsigned short *tdl = dl + base;
-    for (unsigned k = threadIdx.x; k < dead_t; k += LT) {
-        const unsigned long long i = base + tdl[k];
-        if (i >= A) break;                      // offsets ascend: the rest lie at or above A too
-        const unsigned long long r = dead_before + k;
-        if (r < H) {
-            const unsigned long long src = movers[r];
-            if (src >= A && src < n) move_entry<T>(S, i, src);
-            else atomicExch(&ctl->bad_index, i + 1);
-        } else {
-            atomicExch(&ctl->bad_index, i + 1);
+    if (H == 0) return;
+    const long long nfill = tiles_of(A);
+    for (long long tile = blockIdx.x; tile < nfill; tile += gridDim.x) {
+        const unsigned long long base = (unsigned long long)tile * LTILE;
+        const unsigned long long tn = n - base < (unsigned long long)LTILE ? n - base : (unsigned long long)LTILE;
+        const unsigned long long alive_t = blk[tile + 1] - blk[tile];
+        const unsigned dead_t = (unsigned)(tn - alive_t);
+        const unsigned long long dead_before = base - blk[tile];
+        const unsigned short *tdl = dl + base;
+        for (unsigned k = threadIdx.x; k < dead_t; k += LT) {
+            const unsigned long long i = base + tdl[k];
+            if (i >= A) break;                      // offsets ascend: the rest lie at or above A too
+            const unsigned long long r = dead_before + k;
+            if (r < H) {
+                const unsigned long long src = movers[r];
+                if (src >= A && src < n) move_entry<T>(S, i, src);
+                else atomicExch(&ctl->bad_index, i + 1);
+            } else {
+                atomicExch(&ctl->bad_index, i + 1);
+            }
         }
     }
+}
+
+// Resident blocks of a tile kernel (its grid loops over tiles), at most one
+// block per tile.
+template <class K> static unsigned tile_grid(const qed_ctx *ctx, K kernel, long long nb) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LT, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const long long g = (long long)ctx->sm_count * per_sm;
+    return (unsigned)(nb < g ? (nb > 0 ? nb : 1) : g);
+}
+
+// The four passes and the count update.  bound: an upper bound of the device
+// count (the host count, or the capacity when the count is only known on the
+// device); step_from_ctl: the leveling draws take the step index from the
+// control block (a captured step graph).  The work buffers must hold
+// bound / 1024 + 2 block words and bound hole words (sfq_ensure_work).
+template <class T, bool LEVEL>
+qed_status compact_tiles_bounded(qed_ctx *ctx, qed_species *sp, int s, int64_t step, int64_t bound,
+                                 bool step_from_ctl) {
+    if (bound <= 0) return QED_OK;
+    const int64_t nb = (bound + LTILE - 1) / LTILE;
+    if (ctx->blk_cap < nb + 1 || ctx->slots_cap < bound) return QED_ERR_STATE;
+    SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
+                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr, ctx->od[s]};
+    // slots: bound 16-bit dead-list entries, then at most bound/2 mover indices
+    unsigned short *dl = reinterpret_cast<unsigned short *>(ctx->slots);
+    unsigned long long *movers = ctx->slots + (bound + 3) / 4;
+    cudaStream_t st = ctx->stream;
+    k_tile_dead<T, LEVEL><<<tile_grid(ctx, k_tile_dead<T, LEVEL>, nb), LT, 0, st>>>(
+        S, ctx->ctl, s, ctx->lev, philox_keys(ctx->cfg.seed), (unsigned)step, step_from_ctl ? 1 : 0, ctx->blk, dl);
+    k_scan_tiles<T><<<1, 1024, 0, st>>>(sp->w, ctx->blk, nb, ctx->ctl, s);
+    k_tile_movers<T><<<tile_grid(ctx, k_tile_movers<T>, nb), LT, 0, st>>>(sp->w, ctx->ctl, s, ctx->blk, movers);
+    k_tile_fill<T><<<tile_grid(ctx, k_tile_fill<T>, nb), LT, 0, st>>>(S, ctx->ctl, s, ctx->blk, dl, movers);
+    k_set_count<<<1, 1, 0, st>>>(ctx->ctl, s);
+    SFQ_LAUNCHED(ctx, 5);
+    SFQ_CUDA(cudaGetLastError());
+    return QED_OK;
 }
 
 template <class T, bool LEVEL>
 qed_status compact_tiles(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     const int64_t n = sp->count;   // upper bound; kernels read the device count
     if (n <= 0) return QED_OK;
-    const int64_t nb = (n + LTILE - 1) / LTILE;
-    qed_status e = sfq_ensure_work(ctx, nb + 1, n);
+    qed_status e = sfq_ensure_work(ctx, (n + LTILE - 1) / LTILE + 1, n);
     if (e != QED_OK) return e;
-    SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
-                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr, ctx->od[s]};
-    // slots: n 16-bit dead-list entries, then at most n/2 mover indices
-    unsigned short *dl = reinterpret_cast<unsigned short *>(ctx->slots);
-    unsigned long long *movers = ctx->slots + (n + 3) / 4;
-    cudaStream_t st = ctx->stream;
-    k_tile_dead<T, LEVEL><<<(unsigned)nb, LT, 0, st>>>(S, ctx->ctl, s, ctx->lev, philox_keys(ctx->cfg.seed),
-                                                       (unsigned)step, ctx->blk, dl);
-    k_scan_tiles<T><<<1, 1024, 0, st>>>(sp->w, ctx->blk, nb, ctx->ctl, s);
-    k_tile_movers<T><<<(unsigned)nb, LT, 0, st>>>(sp->w, ctx->ctl, s, ctx->blk, movers);
-    k_tile_fill<T><<<(unsigned)nb, LT, 0, st>>>(S, ctx->ctl, s, ctx->blk, dl, movers);
-    k_set_count<<<1, 1, 0, st>>>(ctx->ctl, s);
-    SFQ_LAUNCHED(ctx, 5);
-    SFQ_CUDA(cudaGetLastError());
-    return QED_OK;
+    return compact_tiles_bounded<T, LEVEL>(ctx, sp, s, step, n, false);
 }
 
 template <class T>
@@ -876,6 +919,70 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     return compact_tiles<T, true>(ctx, sp, s, step);
 }
 
+// ---- the merge step of a captured step graph ----
+// One thread decides on the device what a species' merge step does (no host
+// round trip): leveling when its count exceeds the cap (the iteration is
+// started as by k_lev_begin), dead entries removed when it was leveled or
+// may hold converted photons (otherwise the iteration is finished with w* = 0,
+// so the compaction only removes dead entries).  Nothing runs once a step
+// ran out of capacity or a device check failed.
+__global__ void k_merge_begin(DevCtl *ctl, LevelWork *lw, int s, long long cap, int always_compact,
+                              cudaGraphConditionalHandle h_lev, cudaGraphConditionalHandle h_cmp) {
+    const bool stop = ctl->overflow || ctl->timeout || ctl->bad_index;
+    const unsigned long long c = ctl->count[s], cp = ctl->capacity[s];
+    const unsigned long long n = c < cp ? c : cp;
+    const bool level = !stop && cap > 0 && n > (unsigned long long)cap;
+    lev_start(lw, s);
+    if (!level) lev_finish(lw->it[s], 0.0);
+    const bool compact = !stop && n > 0 && (level || always_compact);
+    if (cap > 0) cudaGraphSetConditional(h_lev, level ? 1u : 0u);
+    cudaGraphSetConditional(h_cmp, compact ? 1u : 0u);
+    if (compact) ctl->graph_kernels += 5;          // the compaction passes below
+}
+
+// Appends species s's merge step to a step graph under capture (ctx->stream
+// is the capture stream): the decision kernel, a while node running the
+// leveling passes, and an if node holding the compaction passes sized by the
+// capacity (their loops follow the device count).
+template <class T>
+qed_status capture_merge(qed_ctx *ctx, GraphBuild &gb, qed_species *sp, int s, bool always_compact) {
+    const long long cap = ctx->cfg.thin_cap;
+    if (sp->capacity <= 0 || (cap <= 0 && !always_compact)) return QED_OK;
+    cudaGraphConditionalHandle h_lev = 0, h_cmp = 0;
+    if (cap > 0 && cudaGraphConditionalHandleCreate(&h_lev, gb.g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+        return QED_ERR_CUDA;
+    if (cudaGraphConditionalHandleCreate(&h_cmp, gb.g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+        return QED_ERR_CUDA;
+    LevelWork *lw = ctx->lev;
+    DevCtl *ctl = ctx->ctl;
+    const int ac = always_compact ? 1 : 0;
+    if (gb.capture(gb.g, [&] {
+            k_merge_begin<<<1, 1, 0, ctx->stream>>>(ctl, lw, s, cap, ac, h_lev, h_cmp);
+            return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+        }) != cudaSuccess)
+        return QED_ERR_CUDA;
+    gb.top_kernels += 1;
+    if (cap > 0) {
+        cudaGraph_t body;
+        if (gb.conditional(h_lev, cudaGraphCondTypeWhile, &body) != cudaSuccess) return QED_ERR_CUDA;
+        int blocks = ctx->sm_count * 4;
+        blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
+        const void *w = sp->w;
+        if (gb.capture(body, [&] {
+                k_lev_step<T><<<blocks, LEV_T, 0, ctx->stream>>>(w, ctl, s, lw, cap);
+                k_lev_cond<<<1, 1, 0, ctx->stream>>>(lw, s, ctl, h_lev);
+                return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+            }) != cudaSuccess)
+            return QED_ERR_CUDA;
+    }
+    cudaGraph_t cbody;
+    if (gb.conditional(h_cmp, cudaGraphCondTypeIf, &cbody) != cudaSuccess) return QED_ERR_CUDA;
+    if (gb.capture(cbody, [&] { return compact_tiles_bounded<T, true>(ctx, sp, s, 0, sp->capacity, true); }) !=
+        cudaSuccess)
+        return QED_ERR_CUDA;
+    return QED_OK;
+}
+
 // ---- leveling over shards (one species split across processes) ----
 // The threshold is a property of all shards together: each shard evaluates
 // its sums at the current point (level_eval), the caller adds them over the
@@ -942,6 +1049,11 @@ qed_status sfq_ensure_work(qed_ctx *ctx, int64_t n_blocks, int64_t n_slots) {
         ctx->slots_cap = n_slots;
     }
     return QED_OK;
+}
+
+qed_status sfq_capture_merge(qed_ctx *ctx, GraphBuild &gb, qed_species *sp, int s, bool always_compact) {
+    if (ctx->cfg.precision == QED_FP32) return capture_merge<float>(ctx, gb, sp, s, always_compact);
+    return capture_merge<double>(ctx, gb, sp, s, always_compact);
 }
 
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s) {
@@ -1029,7 +1141,7 @@ unsigned long long *g_noalloc_addr[NA_MAX_DEVICES];   // device address of the a
 }
 
 template <class T>
-static qed_status noalloc_compact(qed_species *sp, cudaStream_t st, unsigned long long *base) {
+static qed_status noalloc_compact(qed_species *sp, void *od, cudaStream_t st, unsigned long long *base) {
     using namespace sfq;
     DevCtl *ctl = reinterpret_cast<DevCtl *>(base);
     unsigned long long *blk = base + NA_CTL_WORDS;
@@ -1037,7 +1149,7 @@ static qed_status noalloc_compact(qed_species *sp, cudaStream_t st, unsigned lon
     const long long n = sp->count;
     const long long nb = (n + CTILE - 1) / CTILE;
     SpeciesDev S{sp->x, sp->y, sp->z, sp->px, sp->py, sp->pz, sp->w,
-                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr, nullptr};
+                 reinterpret_cast<unsigned long long *>(sp->id), sp->nevents, nullptr, od};
     k_noalloc_begin<<<1, 1, 0, st>>>(ctl, (unsigned long long)n);
     k_count_alive<T><<<(unsigned)nb, CT, 0, st>>>(sp->w, ctl, 0, blk);
     k_scan_blocks<<<1, 1024, 0, st>>>(blk, nb, ctl, 0);
@@ -1053,9 +1165,11 @@ static qed_status noalloc_compact(qed_species *sp, cudaStream_t st, unsigned lon
     return QED_OK;
 }
 
-extern "C" qed_status qed_compact_species_noalloc(qed_species *sp, int precision, void *cuda_stream) {
+extern "C" qed_status qed_compact_species_noalloc(qed_species *sp, void *od_dev, int precision, void *cuda_stream) {
     using namespace sfq;
     if (!sp || (precision != QED_FP64 && precision != QED_FP32)) return QED_ERR_INVALID;
+    // the optical-depth array moves with the particles; element alignment as in qed_set_optical_depth
+    if (od_dev && (reinterpret_cast<uintptr_t>(od_dev) % (precision == QED_FP32 ? 4u : 8u))) return QED_ERR_INVALID;
     if (sp->count < 0 || sp->count > sp->capacity) return QED_ERR_INVALID;
     if (sp->count > NA_MAX_ENTRIES) return QED_ERR_INVALID;
     if (sp->count == 0) return QED_OK;
@@ -1073,6 +1187,6 @@ extern "C" qed_status qed_compact_species_noalloc(qed_species *sp, int precision
         g_noalloc_addr[dev] = static_cast<unsigned long long *>(p);
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (precision == QED_FP32) return noalloc_compact<float>(sp, st, g_noalloc_addr[dev]);
-    return noalloc_compact<double>(sp, st, g_noalloc_addr[dev]);
+    if (precision == QED_FP32) return noalloc_compact<float>(sp, od_dev, st, g_noalloc_addr[dev]);
+    return noalloc_compact<double>(sp, od_dev, st, g_noalloc_addr[dev]);
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "sfqed.h"
 
 namespace sfq {
@@ -52,7 +54,23 @@ struct DevCtl {
     unsigned long long bad_index;       // a bounds check failed (index recorded, access skipped)
     unsigned long long chi_fp64;        // FP32 mode: chi evaluations that fell back to FP64
     unsigned long long graph_kernels;   // kernels run inside graphs (their launches are on the device)
-    unsigned long long pad[6];
+    unsigned long long step_next;       // index of the step the next step-begin kernel opens
+    unsigned long long step_passes;     // newborn passes of the current step
+    unsigned long long timeout;         // a bounded device-side loop gave up (QED_ERR_TIMEOUT)
+    double sv_t_n;                      // current step: t_n = step * dt
+    float sv_t_red_f;                   // current step: (t_n mod 2 pi) rounded to float
+    unsigned sv_step;                   // current step index (Philox counter word 2)
+    unsigned long long pad[1];
+};
+
+// The current step's time as the pass kernels read it from the control
+// block (written by the step-begin kernel, so a captured step graph needs no
+// per-step kernel arguments); time_phase() takes it like an argument block.
+struct StepTime {
+    int field_kind;
+    double t_n;
+    float t_n_red_f;
+    unsigned step;
 };
 
 // Leveling: iteration state per species and per-block partial sums.
@@ -126,10 +144,6 @@ struct PassArgs {
     double lam_skip;        // 2^-54 / dt: below this rate no event can happen in a step (see the passes)
     float lam_skip_f;
     float dt_f_gt;          // smallest float above dt (FP32 first-iteration event test)
-    double t_n;             // step * dt
-    double t_n_red;         // (step * dt) reduced modulo 2 pi
-    float t_n_red_f;        // the same rounded to float (FP32 phase)
-    unsigned step;
     unsigned long long seed;
     PhiloxKeys keys;        // round keys of seed (event draws)
     int pass;               // 0: particles present at the step start (tau = 0)
@@ -152,7 +166,8 @@ struct qed_ctx {
     double *gl;              // Gauss-Legendre nodes and weights (work)
     // control
     sfq::DevCtl *ctl;
-    sfq::DevCtl *ctl_host;   // pinned mirror
+    sfq::DevCtl *ctl_host;   // pinned mirror (read back at the end of a batch of steps)
+    sfq::DevCtl *ctl_up;     // pinned staging of the upload when a batch of steps opens
     // newborn birth clocks
     double *tau[3];
     int64_t tau_cap[3];
@@ -187,6 +202,15 @@ struct qed_ctx {
     int tuned_budget;            // step budget picked by the autotuner (0: none yet)
     int spec_passes;             // newborn passes enqueued per host check (from the last step)
     int lev_chunk[3];            // leveling passes enqueued per host check (from the last leveling)
+    // steps enqueued without waiting (qed_push_async) until qed_push_wait:
+    // the device control block holds the counts meanwhile
+    int async_open;
+    qed_particles async_p;       // the arrays bound by the open batch (pointers and capacities)
+    int64_t async_count0[3];     // counts when the batch opened (restored on overflow)
+    int64_t async_next_step;     // step index following the last enqueued step
+    double async_t0_ms;          // host clock when the batch opened
+    void *step_graph;            // the captured PIC step (StepGraph, sfqed_push.cu) or null
+    int step_graph_failed;       // conditional graph nodes unavailable: host-driven steps
     // surrogate network: FP32 master parameters, Adam moments and gradient
     // (4 x 8577 floats), BF16 copy used by the kernels, loss accumulator
     float *mlp_p;
@@ -200,6 +224,10 @@ qed_status sfq_build_tables(qed_ctx *ctx);
 // Implemented in sfqed_push.cu
 qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt,
                     int nsteps, int64_t step0, qed_stats *out);
+qed_status sfq_push_async(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
+                          int64_t step0);
+qed_status sfq_push_wait(qed_ctx *ctx, qed_particles *p, qed_stats *out);
+void sfq_step_graph_free(qed_ctx *ctx);
 qed_status sfq_eval_rate(qed_ctx *ctx, int is_photon, const double *chi, int64_t n, double *F);
 qed_status sfq_sample(qed_ctx *ctx, int is_photon, const double *chi, const double *u, int64_t n,
                       double *delta, double *one_minus);
@@ -221,7 +249,54 @@ qed_status sfq_mlp_eval(qed_ctx *ctx, const float *feat, int64_t n, float *y);
 qed_status sfq_mlp_grad(qed_ctx *ctx, const float *feat, const float *target, int64_t n, float *grad_host,
                         double *loss);
 qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed, double *final_loss);
+// Building a CUDA graph from captured launches: each capture appends the
+// launches a function issues on `st` after the current tail of the top-level
+// graph (or into a conditional node's body graph, which starts empty).
+struct GraphBuild {
+    cudaGraph_t g = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<cudaGraphNode_t> tail;   // nodes the next top-level node depends on
+    int top_kernels = 0;                 // kernel nodes of the top level (run once per launch)
+
+    template <class F> cudaError_t capture(cudaGraph_t into, F issue) {
+        const bool top = into == g;
+        cudaError_t e = cudaStreamBeginCaptureToGraph(st, into, top && !tail.empty() ? tail.data() : nullptr, nullptr,
+                                                      top ? tail.size() : 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return e;
+        const qed_status q = issue();
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        cudaError_t e2 = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+        std::vector<cudaGraphNode_t> next(deps, deps + (e2 == cudaSuccess ? nd : 0));
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(st, &out);
+        if (e2 != cudaSuccess) return e2;
+        if (e != cudaSuccess) return e;
+        if (q != QED_OK) return cudaErrorUnknown;
+        if (top) tail.swap(next);
+        return cudaSuccess;
+    }
+    // a conditional node after the tail; *body receives its (first) body graph
+    cudaError_t conditional(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, cudaGraph_t *body) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = type;
+        cp.conditional.size = 1;
+        cudaGraphNode_t n;
+        cudaError_t e = cudaGraphAddNode(&n, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(), &cp);
+        if (e != cudaSuccess) return e;
+        *body = cp.conditional.phGraph_out[0];
+        tail.assign(1, n);
+        return cudaSuccess;
+    }
+};
+
 // Implemented in sfqed_compact.cu
+// the merge step of species s (leveling when its count exceeds the cap, dead
+// entries removed) appended to a step graph; decided on the device
+qed_status sfq_capture_merge(qed_ctx *ctx, GraphBuild &gb, qed_species *sp, int s, bool always_compact);
 qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);
 void sfq_level_graphs_free(qed_ctx *ctx);
 qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step);

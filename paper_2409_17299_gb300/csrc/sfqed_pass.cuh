@@ -39,13 +39,28 @@ __device__ __forceinline__ void field_at(const PassArgs &a, const T x[3], const 
 }
 
 template <class T>
-__device__ __forceinline__ void field_tau(const PassArgs &a, const T x[3], double tau, T E[3], T B[3]) {
+__device__ __forceinline__ void field_tau(const PassArgs &a, const StepTime &tm, const T x[3], double tau, T E[3],
+                                          T B[3]) {
 #if SFQ_GRID
     (void)tau;
+    (void)tm;
     eval_grid<T, PassArgs>(a, x, E, B);
 #else
-    eval_field<T, PassArgs>(a, x, tau, E, B);
+    eval_field_at<T, PassArgs>(a, x, time_phase<T, StepTime>(tm, tau), E, B);
 #endif
+}
+
+// The current step's time and index, written into the control block by the
+// step-begin kernel (so a step captured in a CUDA graph takes no per-step
+// kernel arguments)
+__device__ __forceinline__ StepTime load_step_time(const PassArgs &a) {
+    const DevCtl *c = a.ctl;
+    StepTime t;
+    t.field_kind = a.field_kind;
+    t.t_n = c->sv_t_n;
+    t.t_n_red_f = c->sv_t_red_f;
+    t.step = c->sv_step;
+    return t;
 }
 
 template <class T> __device__ __forceinline__ T t_inf();
@@ -110,6 +125,7 @@ template <class T> struct LeptonCtx {
     const T *icdf;
     unsigned long long cap_ph;
     T alpha_r;
+    const StepTime &tm;     // the step's time and index (block's shared copy)
     Phase<T> ph0;           // time phase at the step start (tau = 0)
 };
 
@@ -134,13 +150,13 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
     const PassArgs &a = c.a;
     T E[3], B[3];
     if constexpr (FRESH) field_at<T>(a, x, c.ph0, E, B);
-    else field_tau<T>(a, x, tau, E, B);
+    else field_tau<T>(a, c.tm, x, tau, E, B);
     T gam, chi, p2;
     lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
     const T lam = p2 > (T)0 ? f_div(c.alpha_r, gam) * rate_em<T>(c.coef, chi) : (T)0;
     T dth = t_inf<T>();
     if (lam > lam_skip<T>(a)) {
-        const uint4 r = event_draw(a.keys, id, a.step, k);
+        const uint4 r = event_draw(a.keys, id, c.tm.step, k);
         T uw, vw;
         Uniform<T>::draw(r.x, r.y, uw, vw);
         dth = f_div(Uniform<T>::neglog(uw, vw), lam);
@@ -175,7 +191,7 @@ __device__ __forceinline__ void emit_with(const LeptonCtx<T> &c, const T x[3], T
     const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
     const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
     if (!(a.soft_filter && k0 < (T)2)) {
-        const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, k);
+        const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, c.tm.step, k);
         const unsigned long long slot = warp_append(&c.ctl->count[2], 1);
         if (slot < c.cap_ph) {
             const SpeciesDev &P = a.sp[2];
@@ -199,7 +215,7 @@ template <class T>
 __device__ __forceinline__ void emit(const LeptonCtx<T> &c, const T x[3], T p[3], double tau, T w,
                                      unsigned long long id, unsigned k, uint2 rz, unsigned &n64) {
     T E[3], B[3];
-    field_tau<T>(c.a, x, tau, E, B);
+    field_tau<T>(c.a, c.tm, x, tau, E, B);
     T gam, chi, p2;
     lepton_chi<T>(p, E, B, gam, chi, p2, n64, c.a.field_zero);
     T om, ue, ve;
@@ -260,7 +276,7 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
         bool use_net = false;
         if (mine) {
             T E[3], B[3];
-            field_tau<T>(c.a, x, tau, E, B);
+            field_tau<T>(c.a, c.tm, x, tau, E, B);
             lepton_chi<T>(p, E, B, gam, chi, p2, n64, c.a.field_zero);
             Uniform<T>::draw(rz.x, rz.y, ue, ve);
             const float sl = (float)logit(ue, ve);
@@ -301,18 +317,22 @@ template <class T, bool FRESH, bool MLP>
 __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_lepton_pass(PassArgs a) {
     __shared__ __align__(16) T s_coef[RateWords<T>::N];
     __shared__ LeptonStack<T> q;
+    __shared__ StepTime s_tm;
     extern __shared__ __align__(16) unsigned char dyn[];
     MlpInf ms{nullptr, nullptr, nullptr};
     if constexpr (MLP) ms = mlp_stage(dyn, a.mlp_w16);
     for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
-    if (threadIdx.x == 0) q.n = 0;
+    if (threadIdx.x == 0) {
+        q.n = 0;
+        s_tm = load_step_time(a);
+    }
     __syncthreads();
     DevCtl *ctl = a.ctl;
     const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
     const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
     const unsigned long long n = n0 + n1;
     const LeptonCtx<T> c{a, ctl, s_coef, reinterpret_cast<const T *>(a.icdf_em), ctl->capacity[2], (T)(ALPHA * RS),
-                         time_phase<T>(a, 0.0)};
+                         s_tm, time_phase<T, StepTime>(s_tm, 0.0)};
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
 
@@ -413,8 +433,11 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
 template <class T, bool FRESH>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(PassArgs a) {
     __shared__ __align__(16) T s_coef[RateWords<T>::N];
+    __shared__ StepTime s_tm;
     for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    if (threadIdx.x == 0) s_tm = load_step_time(a);
     __syncthreads();
+    const StepTime &tm = s_tm;
     DevCtl *ctl = a.ctl;
     const unsigned long long b = ctl->begin[2], n = ctl->end[2] - b;
     const unsigned long long cap_e = ctl->capacity[0], cap_p = ctl->capacity[1];
@@ -423,7 +446,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     const SpeciesDev &S = a.sp[2];
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
-    const Phase<T> ph0 = time_phase<T>(a, 0.0);
+    const Phase<T> ph0 = time_phase<T, StepTime>(tm, 0.0);
     // FP32 step-start pass: each thread stages its next photon in shared
     // memory (two buffers) while it works on the current one
     constexpr bool STAGE = FRESH && sizeof(T) == 4;
@@ -485,7 +508,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
             if (FRESH || tau < a.dt) {
                 T E[3], B[3];
                 if constexpr (FRESH) field_at<T>(a, x, ph0, E, B);
-                else field_tau<T>(a, x, tau, E, B);
+                else field_tau<T>(a, tm, x, tau, E, B);
                 T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
                 T lam;
                 if constexpr (sizeof(T) == 4) lam = alpha_r * inv * rate_pair<T>(s_coef, chi);
@@ -493,7 +516,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 uint4 r = make_uint4(0, 0, 0, 0);
                 T dth = t_inf<T>();
                 if (lam > lam_skip<T>(a)) {
-                    r = event_draw(a.keys, id, a.step, k);
+                    r = event_draw(a.keys, id, tm.step, k);
                     T uw, vw;
                     Uniform<T>::draw(r.x, r.y, uw, vw);
                     dth = f_div(Uniform<T>::neglog(uw, vw), lam);
@@ -510,7 +533,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
                 if constexpr (FRESH) tau = (double)dth;
                 else tau += (double)dth;
-                field_tau<T>(a, x, tau, E, B);
+                field_tau<T>(a, tm, x, tau, E, B);
                 chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
                 T om, ue, ve;
                 Uniform<T>::draw(r.z, r.w, ue, ve);
@@ -519,7 +542,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 em = em < (T)1 ? (T)1 : em;
                 ep = ep < (T)1 ? (T)1 : ep;
                 const T pm = m_sqrt((em - (T)1) * (em + (T)1)), pp = m_sqrt((ep - (T)1) * (ep + (T)1));
-                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, k);
+                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, tm.step, k);
                 const unsigned long long se = warp_append(&ctl->count[0], 1);
                 const unsigned long long sp = warp_append(&ctl->count[1], 1);
                 if (se < cap_e) {
@@ -588,22 +611,26 @@ template <> __device__ __forceinline__ double dt_of<double>(const PassArgs &a) {
 
 // od after this step's decrement, drawn first when not drawn yet.  The
 // product is rounded on its own (no contraction), as in the oracle.
-template <class T> __device__ __forceinline__ T od_advance(const PassArgs &a, unsigned long long id, T od, T lam) {
-    if (!(od > (T)0)) od = od_exp1<T>(event_draw(a.keys, id, a.step, OD_DRAW));
+template <class T>
+__device__ __forceinline__ T od_advance(const PassArgs &a, unsigned step, unsigned long long id, T od, T lam) {
+    if (!(od > (T)0)) od = od_exp1<T>(event_draw(a.keys, id, step, OD_DRAW));
     return od - mul_rn<T>(lam, dt_of<T>(a));
 }
 
 template <class T>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(PassArgs a) {
     __shared__ __align__(16) T s_coef[RateWords<T>::N];
+    __shared__ StepTime s_tm;
     for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    if (threadIdx.x == 0) s_tm = load_step_time(a);
     __syncthreads();
+    const StepTime &tm = s_tm;
     DevCtl *ctl = a.ctl;
     const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
     const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
     const unsigned long long n = n0 + n1;
     const LeptonCtx<T> c{a, ctl, s_coef, reinterpret_cast<const T *>(a.icdf_em), ctl->capacity[2], (T)(ALPHA * RS),
-                         time_phase<T>(a, 0.0)};
+                         tm, time_phase<T, StepTime>(tm, 0.0)};
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
     for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -623,15 +650,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(Pas
         T gam, chi, p2;
         lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
         const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
-        od = od_advance<T>(a, id, od, lam);
+        od = od_advance<T>(a, tm.step, id, od, lam);
         const T qch = s == 0 ? (T)-1 : (T)1;
         boris<T>(x, p, qch, E, B, dt_of<T>(a));
         unsigned k = 0;
         if (od <= (T)0) {
             // the event at the end of the step
-            field_tau<T>(a, x, a.dt, E, B);
+            field_tau<T>(a, tm, x, a.dt, E, B);
             lepton_chi<T>(p, E, B, gam, chi, p2, n64, a.field_zero);
-            const uint4 r = event_draw(a.keys, id, a.step, 0u);
+            const uint4 r = event_draw(a.keys, id, tm.step, 0u);
             T om, ue, ve;
             Uniform<T>::draw(r.z, r.w, ue, ve);
             const T delta = sample_emission<T>(c.icdf, chi, ue, ve, &om);
@@ -653,8 +680,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(Pas
 template <class T>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(PassArgs a) {
     __shared__ __align__(16) T s_coef[RateWords<T>::N];
+    __shared__ StepTime s_tm;
     for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
+    if (threadIdx.x == 0) s_tm = load_step_time(a);
     __syncthreads();
+    const StepTime &tm = s_tm;
     DevCtl *ctl = a.ctl;
     const unsigned long long b = ctl->begin[2], n = ctl->end[2] - b;
     const unsigned long long cap_e = ctl->capacity[0], cap_p = ctl->capacity[1];
@@ -663,7 +693,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(Pas
     const SpeciesDev &S = a.sp[2];
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
-    const Phase<T> ph0 = time_phase<T>(a, 0.0);
+    const Phase<T> ph0 = time_phase<T, StepTime>(tm, 0.0);
     // FP32: each thread stages its next photon in shared memory (two
     // buffers) while it works on the current one, as in the step-start pass
     constexpr bool STAGE = sizeof(T) == 4;
@@ -725,14 +755,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(Pas
             field_at<T>(a, x, ph0, E, B);
             T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
             const T lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);
-            od = od_advance<T>(a, id, od, lam);
+            od = od_advance<T>(a, tm.step, id, od, lam);
             const T h = dt_of<T>(a);
             x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
             if (od <= (T)0) {
                 // pair creation at the end of the step
-                field_tau<T>(a, x, a.dt, E, B);
+                field_tau<T>(a, tm, x, a.dt, E, B);
                 chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
-                const uint4 r = event_draw(a.keys, id, a.step, 0u);
+                const uint4 r = event_draw(a.keys, id, tm.step, 0u);
                 T om, ue, ve;
                 Uniform<T>::draw(r.z, r.w, ue, ve);
                 const T delta = sample_pair<T>(icdf, chi, ue, ve, &om);
@@ -740,7 +770,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(Pas
                 em = em < (T)1 ? (T)1 : em;
                 ep = ep < (T)1 ? (T)1 : ep;
                 const T pm = m_sqrt((em - (T)1) * (em + (T)1)), pp = m_sqrt((ep - (T)1) * (ep + (T)1));
-                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, a.step, 0u);
+                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, tm.step, 0u);
                 const unsigned long long se = warp_append(&ctl->count[0], 1);
                 const unsigned long long sp = warp_append(&ctl->count[1], 1);
                 if (se < cap_e) {

@@ -28,16 +28,42 @@ __global__ void k_grid_interleave(const T *src, T *dst, long long nodes) {
     dst[8 * n + 7] = (T)0;
 }
 
-// Pass ranges: at the step start every particle present; afterwards the
-// particles appended since the previous pass.
-__global__ void k_step_begin(DevCtl *ctl) {
+// Newborn passes of one step after which the step gives up (QED_ERR_TIMEOUT).
+constexpr unsigned long long PASS_LIMIT = 100000;
+
+__device__ __forceinline__ bool ctl_stopped(const DevCtl *ctl) {
+    return ctl->overflow || ctl->timeout || ctl->bad_index;
+}
+
+// Opens the next step (index ctl->step_next): its time t_n = step dt and the
+// phase reduced mod 2 pi (the pass kernels read both from the control block),
+// and the pass ranges: every particle present.  After an overflow or a failed
+// device check the ranges are empty, so the rest of the enqueued work does
+// nothing.
+__global__ void k_step_begin(DevCtl *ctl, double dt) {
+    const unsigned long long step = ctl->step_next;
+    ctl->step_next = step + 1;
+    const double t_n = (double)step * dt;
+    ctl->sv_t_n = t_n;
+    ctl->sv_t_red_f = (float)fmod(t_n, 2.0 * 3.14159265358979323846);
+    ctl->sv_step = (unsigned)step;
+    ctl->step_passes = 0;
+    const bool stop = ctl_stopped(ctl);
     for (int s = 0; s < 3; ++s) {
         ctl->begin[s] = 0;
-        ctl->end[s] = min(ctl->count[s], ctl->capacity[s]);
+        ctl->end[s] = stop ? 0 : min(ctl->count[s], ctl->capacity[s]);
     }
 }
 
-__global__ void k_pass_setup(DevCtl *ctl) {
+__global__ void k_set_step(DevCtl *ctl, unsigned long long step) { ctl->step_next = step; }
+
+__global__ void k_set_timeout(DevCtl *ctl) { ctl->timeout = 1; }
+
+// Pass ranges of the next newborn pass: the particles appended since the
+// previous pass.  In a step graph it also sets the condition of the loop
+// over passes (the only setter): another pass while one found work, at most
+// PASS_LIMIT per step (then the step is marked as timed out).
+__device__ __forceinline__ unsigned long long pass_setup(DevCtl *ctl) {
     unsigned long long more = 0;
     for (int s = 0; s < 3; ++s) {
         const unsigned long long e = min(ctl->count[s], ctl->capacity[s]);
@@ -45,8 +71,27 @@ __global__ void k_pass_setup(DevCtl *ctl) {
         ctl->end[s] = e;
         if (e > ctl->begin[s]) more = 1;
     }
+    if (ctl_stopped(ctl)) {
+        more = 0;
+        for (int s = 0; s < 3; ++s) ctl->begin[s] = ctl->end[s];
+    }
     ctl->more = more;
     ctl->passes += more;
+    ctl->step_passes += more;
+    return more;
+}
+
+__global__ void k_pass_setup(DevCtl *ctl) { pass_setup(ctl); }
+
+__global__ void k_pass_setup_cond(DevCtl *ctl, cudaGraphConditionalHandle h, int in_body) {
+    unsigned long long more = pass_setup(ctl);
+    if (more && ctl->step_passes > PASS_LIMIT) {
+        ctl->timeout = 1;
+        more = 0;
+        for (int s = 0; s < 3; ++s) ctl->begin[s] = ctl->end[s];
+    }
+    if (in_body) ctl->graph_kernels += 3;       // the loop body: two passes and this kernel
+    cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---- component kernels for the parity tests ----
@@ -222,28 +267,217 @@ static qed_status launch_od(qed_ctx *ctx, PassArgs &a, bool photons) {
     return pass_analytic::launch_od<T>(ctx, a, photons);
 }
 
+// ---- the captured PIC step ----
+// One step as a CUDA graph: the step-begin kernel, the step-start passes,
+// then (a cascade) a while node sweeping the newborns until a pass creates
+// nothing (Algorithm 2), then each species' merge step (leveling and removal
+// of dead entries) decided on the device.  Every kernel reads its ranges and
+// the step's time from the control block, so one graph serves every step and
+// no step needs the host: a batch of steps is a run of graph launches.  The
+// graph is rebuilt when the bound arrays, capacities, field or step change.
+struct StepGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    PassArgs args;           // the kernel arguments captured (compared byte-wise)
+    int64_t cap[3];
+    double dt;
+    int top_kernels;         // kernel nodes outside the conditional bodies
+};
+
+void sfq_step_graph_free(qed_ctx *ctx) {
+    StepGraph *G = static_cast<StepGraph *>(ctx->step_graph);
+    if (!G) return;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->g) cudaGraphDestroy(G->g);
+    delete G;
+    ctx->step_graph = nullptr;
+}
+
 template <class T>
-static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
-                            int64_t step0, qed_stats *out) {
+static qed_status build_step_graph(qed_ctx *ctx, const PassArgs &args, qed_particles *p, double dt, StepGraph *G) {
     const bool cascade = ctx->cfg.push_photons != 0;
-    const auto call_t0 = std::chrono::steady_clock::now();
+    const bool od_method = ctx->cfg.event_method == QED_METHOD_OPTICAL_DEPTH;
+    const bool loop = cascade && !od_method;
+    GraphBuild gb;
+    if (cudaGraphCreate(&gb.g, 0) != cudaSuccess) return QED_ERR_CUDA;
+    gb.st = ctx->cap_stream;
+    const cudaStream_t saved = ctx->stream;
+    const int64_t launches = ctx->launches;
+    ctx->stream = gb.st;                   // the launchers issue on ctx->stream
+    PassArgs a = args;
+    qed_status rc = QED_OK;
+    cudaGraphConditionalHandle h_pass = 0;
+    do {
+        if (loop && cudaGraphConditionalHandleCreate(&h_pass, gb.g, 0, cudaGraphCondAssignDefault) != cudaSuccess) {
+            rc = QED_ERR_CUDA;
+            break;
+        }
+        cudaError_t e = gb.capture(gb.g, [&] {
+            k_step_begin<<<1, 1, 0, ctx->stream>>>(ctx->ctl, dt);
+            a.pass = 0;
+            const qed_status q = od_method ? launch_od<T>(ctx, a, cascade) : launch_pass<T>(ctx, a, cascade);
+            if (q != QED_OK) return q;
+            if (loop) k_pass_setup_cond<<<1, 1, 0, ctx->stream>>>(ctx->ctl, h_pass, 0);
+            return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+        });
+        if (e != cudaSuccess) {
+            rc = QED_ERR_CUDA;
+            break;
+        }
+        gb.top_kernels = 2 + (cascade ? 1 : 0) + (loop ? 1 : 0);
+        if (loop) {
+            cudaGraph_t body;
+            if (gb.conditional(h_pass, cudaGraphCondTypeWhile, &body) != cudaSuccess) {
+                rc = QED_ERR_CUDA;
+                break;
+            }
+            e = gb.capture(body, [&] {
+                a.pass = 1;
+                const qed_status q = launch_pass<T>(ctx, a, true);
+                if (q != QED_OK) return q;
+                k_pass_setup_cond<<<1, 1, 0, ctx->stream>>>(ctx->ctl, h_pass, 1);
+                return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+            });
+            if (e != cudaSuccess) {
+                rc = QED_ERR_CUDA;
+                break;
+            }
+        }
+        // merge step (Sec. 4.2): converted photons removed, each species
+        // leveled when its count exceeds the cap
+        if (cascade || ctx->cfg.thin_cap > 0)
+            for (int s = 0; s < 3 && rc == QED_OK; ++s) rc = sfq_capture_merge(ctx, gb, &p->s[s], s, cascade && s == 2);
+    } while (0);
+    ctx->stream = saved;
+    ctx->launches = launches;
+    if (rc == QED_OK && cudaGraphInstantiate(&G->exec, gb.g, 0) != cudaSuccess) rc = QED_ERR_CUDA;
+    if (rc != QED_OK) {
+        cudaGraphDestroy(gb.g);
+        cudaGetLastError();                        // clear a failed call's error
+        return rc;
+    }
+    G->g = gb.g;
+    G->args = args;
+    for (int s = 0; s < 3; ++s) G->cap[s] = p->s[s].capacity;
+    G->dt = dt;
+    G->top_kernels = gb.top_kernels;
+    return QED_OK;
+}
+
+// The step graph for these arguments (built or rebuilt when needed), or null
+// when graphs with conditional nodes are not available (host-driven steps).
+template <class T>
+static StepGraph *step_graph_for(qed_ctx *ctx, const PassArgs &a, qed_particles *p, double dt) {
+    if (ctx->step_graph_failed) return nullptr;
+    StepGraph *G = static_cast<StepGraph *>(ctx->step_graph);
+    bool same = G && G->dt == dt && memcmp(&G->args, &a, sizeof(PassArgs)) == 0;
+    for (int s = 0; same && s < 3; ++s) same = G->cap[s] == p->s[s].capacity;
+    if (same) return G;
+    sfq_step_graph_free(ctx);
+    G = new StepGraph;
+    if (build_step_graph<T>(ctx, a, p, dt, G) != QED_OK) {
+        delete G;
+        ctx->step_graph_failed = 1;
+        return nullptr;
+    }
+    ctx->step_graph = G;
+    return G;
+}
+
+// Host-driven steps: the same kernels launched one by one, the host reading
+// the control block between newborn-pass groups and before the merge step.
+// Used to time the kernels individually (cfg.profile: CUDA events around
+// each launch) and where graphs with conditional nodes are unavailable.
+template <class T>
+static qed_status host_steps(qed_ctx *ctx, qed_particles *pw, PassArgs &a, double dt, int nsteps) {
+    const bool cascade = ctx->cfg.push_photons != 0;
+    const bool od_method = ctx->cfg.event_method == QED_METHOD_OPTICAL_DEPTH;
+    qed_particles P = *pw;                         // counts below: bounds read back from the device
+    int spec_passes = ctx->spec_passes > 0 ? ctx->spec_passes : 2;
+    for (int it = 0; it < nsteps; ++it) {
+        a.pass = 0;
+        k_step_begin<<<1, 1, 0, ctx->stream>>>(ctx->ctl, dt);
+        SFQ_LAUNCHED(ctx, 1);
+        qed_status e = od_method ? launch_od<T>(ctx, a, cascade) : launch_pass<T>(ctx, a, cascade);
+        if (e != QED_OK) return e;
+        if (cascade && !od_method) {
+            // Algorithm 2: sweep the newborns until a pass creates nothing.
+            // Passes are enqueued in groups (a pass over an empty range
+            // returns at once), so the host reads the control block once per
+            // group; the group size follows the previous step's pass count.
+            int pass = 1;
+            k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
+            SFQ_LAUNCHED(ctx, 1);
+            for (;;) {
+                for (int g = 0; g < spec_passes; ++g, ++pass) {
+                    a.pass = pass;
+                    e = launch_pass<T>(ctx, a, true);
+                    if (e != QED_OK) return e;
+                    k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
+                    SFQ_LAUNCHED(ctx, 1);
+                }
+                e = read_ctl(ctx);
+                if (e != QED_OK) return e;
+                if (ctx->ctl_host->overflow || !ctx->ctl_host->more) break;
+                if (pass >= (int)PASS_LIMIT) {
+                    // give up like the graph's loop does (the wait reports it)
+                    k_set_timeout<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
+                    SFQ_LAUNCHED(ctx, 1);
+                    break;
+                }
+            }
+            // passes with work in this step (the control block counts them)
+            const long long used = (long long)ctx->ctl_host->step_passes;
+            spec_passes = used < 1 ? 1 : (used > 8 ? 8 : (int)used);
+        }
+        if (cascade || ctx->cfg.thin_cap > 0) {
+            // merge step (Sec. 4.2): drop dead photons, then level
+            if (!cascade || od_method) {
+                e = read_ctl(ctx);
+                if (e != QED_OK) return e;
+            }
+            const DevCtl &c = *ctx->ctl_host;
+            if (c.overflow || c.timeout || c.bad_index) break;
+            for (int s = 0; s < 3; ++s) P.s[s].count = (int64_t)c.count[s];
+            // per species: leveling (it skips dead entries and compacts), else
+            // removal of the photons that converted
+            for (int s = 0; s < 3; ++s) {
+                const bool level = ctx->cfg.thin_cap > 0 && P.s[s].count > ctx->cfg.thin_cap;
+                const int64_t step = (int64_t)c.step_next - 1;
+                if (level) {
+                    e = timed_block(ctx, 3, [&] { return sfq_level_species(ctx, &P.s[s], s, step); });
+                } else if (cascade && s == 2) {
+                    e = timed_block(ctx, 2, [&] { return sfq_compact_species(ctx, &P.s[2], 2); });
+                }
+                if (e != QED_OK) return e;
+            }
+        }
+    }
+    ctx->spec_passes = spec_passes;
+    return QED_OK;
+}
+
+// Opens a batch of steps: the counts and capacities of *p go to the device
+// control block (staged in pinned memory), the context's per-particle work
+// buffers grow to the capacities, and with restore_on_overflow the particle
+// state is copied aside.
+static qed_status open_batch(qed_ctx *ctx, qed_particles *p, int64_t step0) {
     ctx->launches = 0;
     ctx->sync_ms = 0.0;
     for (int k = 0; k < 4; ++k) ctx->kernel_ms[k] = 0.0;
+    ctx->async_t0_ms = std::chrono::duration<double, std::milli>(
+        std::chrono::steady_clock::now().time_since_epoch()).count();
     if (ctx->cfg.profile) {
         qed_status e = ensure_events(ctx);
         if (e != QED_OK) return e;
     }
-    int64_t count0[3];
-    for (int s = 0; s < 3; ++s) count0[s] = p->s[s].count;
-    // the pinned mirror stages the upload (a pageable source would block the host)
-    SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
-    DevCtl &h = *ctx->ctl_host;
+    DevCtl &h = *ctx->ctl_up;
     memset(&h, 0, sizeof(DevCtl));
     for (int s = 0; s < 3; ++s) {
         h.count[s] = (unsigned long long)p->s[s].count;
         h.capacity[s] = (unsigned long long)p->s[s].capacity;
     }
+    h.step_next = (unsigned long long)step0;
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl, &h, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
     int64_t cap_max = 0;
     for (int s = 0; s < 3; ++s) {
@@ -252,15 +486,42 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
         cap_max = p->s[s].capacity > cap_max ? p->s[s].capacity : cap_max;
     }
     // compaction work buffers sized once for the largest species
-    {
-        qed_status e = sfq_ensure_work(ctx, (cap_max + 1023) / 1024 + 2, cap_max);
-        if (e != QED_OK) return e;
-    }
+    qed_status e = sfq_ensure_work(ctx, (cap_max + 1023) / 1024 + 2, cap_max);
+    if (e != QED_OK) return e;
     if (ctx->cfg.restore_on_overflow) {
-        qed_status e = snapshot(ctx, p, false);
+        e = snapshot(ctx, p, false);
         if (e != QED_OK) return e;
     }
-    PassArgs a{};
+    ctx->async_p = *p;
+    for (int s = 0; s < 3; ++s) ctx->async_count0[s] = p->s[s].count;
+    ctx->async_next_step = step0;
+    ctx->async_open = 1;
+    return QED_OK;
+}
+
+static bool same_binding(const qed_particles &a, const qed_particles &b) {
+    for (int s = 0; s < 3; ++s) {
+        const qed_species &x = a.s[s], &y = b.s[s];
+        if (x.x != y.x || x.y != y.y || x.z != y.z || x.px != y.px || x.py != y.py || x.pz != y.pz || x.w != y.w ||
+            x.id != y.id || x.nevents != y.nevents || x.capacity != y.capacity)
+            return false;
+    }
+    return true;
+}
+
+// Enqueue nsteps steps of the open batch (no host wait on the graph path).
+template <class T>
+static qed_status enqueue_steps(qed_ctx *ctx, const qed_field_desc *field, double dt, int nsteps, int64_t step0) {
+    qed_particles *p = &ctx->async_p;
+    const bool cascade = ctx->cfg.push_photons != 0;
+    if (step0 != ctx->async_next_step) {
+        k_set_step<<<1, 1, 0, ctx->stream>>>(ctx->ctl, (unsigned long long)step0);
+        SFQ_LAUNCHED(ctx, 1);
+    }
+    ctx->async_next_step = step0 + nsteps;
+    if (nsteps == 0) return QED_OK;
+    PassArgs a;
+    memset(&a, 0, sizeof a);                       // padding included: the graph key compares bytes
     for (int s = 0; s < 3; ++s) {
         const qed_species &S = p->s[s];
         a.sp[s] = SpeciesDev{S.x, S.y, S.z, S.px, S.py, S.pz, S.w,
@@ -312,82 +573,25 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     a.soft_filter = ctx->cfg.soft_photon_filter;
     a.record_newborn_tau = cascade ? 1 : 0;
 
-    qed_status rc = QED_OK;
-    int spec_passes = ctx->spec_passes > 0 ? ctx->spec_passes : 2;
-    long long passes_before = 0;
-    for (int it = 0; it < nsteps; ++it) {
-        const int64_t step = step0 + it;
-        a.step = (unsigned)step;
-        a.t_n = (double)step * dt;
-        a.t_n_red = fmod(a.t_n, 2.0 * 3.14159265358979323846);
-        a.t_n_red_f = (float)a.t_n_red;
-        a.pass = 0;
-        k_step_begin<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
-        SFQ_LAUNCHED(ctx, 1);
-        const bool od_method = ctx->cfg.event_method == QED_METHOD_OPTICAL_DEPTH;
-        qed_status e = od_method ? launch_od<T>(ctx, a, cascade) : launch_pass<T>(ctx, a, cascade);
-        if (e != QED_OK) return e;
-        if (cascade && od_method) {
-            // one event at most per step: the children start at the next step
-            e = read_ctl(ctx);
-            if (e != QED_OK) return e;
-        } else if (cascade) {
-            // Algorithm 2: sweep the newborns until a pass creates nothing.
-            // Passes are enqueued in groups without waiting for the host: a
-            // pass whose range is empty (set up after a pass that created
-            // nothing) returns at once, so the host reads the control block
-            // once per group, not once per pass.  The group size follows the
-            // number of passes the previous step needed.
-            // Every pass follows a setup of its range; the host looks at the
-            // last setup of a group.
-            int pass = 1;
-            k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
-            SFQ_LAUNCHED(ctx, 1);
-            for (;;) {
-                const int group = spec_passes;
-                for (int g = 0; g < group; ++g, ++pass) {
-                    a.pass = pass;
-                    e = launch_pass<T>(ctx, a, true);
-                    if (e != QED_OK) return e;
-                    k_pass_setup<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
-                    SFQ_LAUNCHED(ctx, 1);
-                }
-                e = read_ctl(ctx);
-                if (e != QED_OK) return e;
-                if (ctx->ctl_host->overflow || !ctx->ctl_host->more || pass >= 100000) break;
-            }
-            // passes with work in this step (the control block counts them)
-            const long long used = (long long)ctx->ctl_host->passes - passes_before;
-            passes_before = (long long)ctx->ctl_host->passes;
-            spec_passes = used < 1 ? 1 : (used > 8 ? 8 : (int)used);
-        }
-        if (cascade || ctx->cfg.thin_cap > 0) {
-            // merge step (Sec. 4.2): drop dead photons, then level
-            if (!cascade) {
-                e = read_ctl(ctx);
-                if (e != QED_OK) return e;
-            }
-            if (ctx->ctl_host->overflow) { rc = QED_ERR_CAPACITY; break; }
-            for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)ctx->ctl_host->count[s];
-            // per species: leveling (it skips dead entries and compacts), else
-            // removal of the photons that converted
-            for (int s = 0; s < 3; ++s) {
-                const bool level = ctx->cfg.thin_cap > 0 && p->s[s].count > ctx->cfg.thin_cap;
-                if (level) {
-                    e = timed_block(ctx, 3, [&] { return sfq_level_species(ctx, &p->s[s], s, step); });
-                } else if (cascade && s == 2) {
-                    e = timed_block(ctx, 2, [&] { return sfq_compact_species(ctx, &p->s[2], 2); });
-                }
-                if (e != QED_OK) return e;
-            }
-        }
-    }
-    ctx->spec_passes = spec_passes;
+    StepGraph *G = ctx->cfg.profile ? nullptr : step_graph_for<T>(ctx, a, p, dt);
+    if (!G) return host_steps<T>(ctx, p, a, dt, nsteps);
+    for (int it = 0; it < nsteps; ++it) SFQ_CUDA(cudaGraphLaunch(G->exec, ctx->stream));
+    SFQ_LAUNCHED(ctx, (int64_t)nsteps * G->top_kernels);
+    return QED_OK;
+}
+
+// Ends the open batch: reads the control block back (the one wait), fills the
+// statistics, updates the counts of *p (or restores the state at the batch's
+// start after an overflow, with restore_on_overflow).
+static qed_status wait_batch(qed_ctx *ctx, qed_particles *p, qed_stats *out) {
     qed_status e = read_ctl(ctx);
+    ctx->async_open = 0;
     if (e != QED_OK) return e;
     DevCtl &c = *ctx->ctl_host;
+    qed_status rc = QED_OK;
     if (c.overflow) rc = QED_ERR_CAPACITY;
-    if (c.bad_index) return QED_ERR_STATE;
+    if (c.timeout) rc = QED_ERR_TIMEOUT;
+    if (c.bad_index) rc = QED_ERR_STATE;
     qed_stats st{};
     st.particle_steps = (int64_t)c.particle_steps;
     st.emit_events = (int64_t)c.emit_events;
@@ -407,15 +611,18 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     for (int k = 0; k < 4; ++k) st.kernel_ms[k] = ctx->kernel_ms[k];
     st.launches = ctx->launches + (int64_t)c.graph_kernels;
     st.sync_ms = ctx->sync_ms;
-    st.call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - call_t0).count();
+    st.call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch())
+                     .count() - ctx->async_t0_ms;
+    qed_particles &B = ctx->async_p;
     if (rc == QED_ERR_CAPACITY && ctx->cfg.restore_on_overflow) {
-        for (int s = 0; s < 3; ++s) p->s[s].count = count0[s];
-        e = snapshot(ctx, p, true);
+        for (int s = 0; s < 3; ++s) B.s[s].count = ctx->async_count0[s];
+        e = snapshot(ctx, &B, true);
         if (e != QED_OK) return e;
         SFQ_CUDA(cudaStreamSynchronize(ctx->stream));
     } else {
-        for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)min(c.count[s], c.capacity[s]);
+        for (int s = 0; s < 3; ++s) B.s[s].count = (int64_t)min(c.count[s], c.capacity[s]);
     }
+    for (int s = 0; s < 3; ++s) p->s[s].count = B.s[s].count;
     if (out) *out = st;
     ctx->acc.particle_steps += st.particle_steps;
     ctx->acc.emit_events += st.emit_events;
@@ -433,11 +640,11 @@ static qed_status push_impl(qed_ctx *ctx, qed_particles *p, const qed_field_desc
     return rc;
 }
 
-qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
-                    int64_t step0, qed_stats *out) {
-    if (ctx && ctx->cfg.sampler == QED_SAMPLER_MLP && !ctx->mlp_ready) return QED_ERR_STATE;
+static qed_status check_push_args(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
+                                  int64_t step0) {
     if (!ctx || !p || !field || nsteps < 0 || !(dt > 0.0) || step0 < 0 || step0 + nsteps > 0xFFFFFFFFll)
         return QED_ERR_INVALID;
+    if (ctx->cfg.sampler == QED_SAMPLER_MLP && !ctx->mlp_ready) return QED_ERR_STATE;
     if (field->kind < QED_FIELD_UNIFORM || field->kind > QED_FIELD_GRID) return QED_ERR_INVALID;
     if (ctx->cfg.event_method == QED_METHOD_OPTICAL_DEPTH) {
         for (int s = 0; s < 3; ++s)
@@ -453,12 +660,46 @@ qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field,
             if (!(n >= 1.0 && n <= 65536.0 && n == floor(n)) || !(len > 0.0)) return QED_ERR_INVALID;
         }
     }
+    if (ctx->async_open) return same_binding(ctx->async_p, *p) ? QED_OK : QED_ERR_STATE;
     for (int s = 0; s < 3; ++s) {
         qed_status e = check_species(p->s[s]);
         if (e != QED_OK) return e;
     }
-    if (ctx->cfg.precision == QED_FP32) return push_impl<float>(ctx, p, field, dt, nsteps, step0, out);
-    return push_impl<double>(ctx, p, field, dt, nsteps, step0, out);
+    return QED_OK;
+}
+
+qed_status sfq_push_async(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
+                          int64_t step0) {
+    qed_status e = check_push_args(ctx, p, field, dt, nsteps, step0);
+    if (e != QED_OK) return e;
+    if (!ctx->async_open) {
+        e = open_batch(ctx, p, step0);
+        if (e != QED_OK) return e;
+    }
+    if (ctx->cfg.precision == QED_FP32) return enqueue_steps<float>(ctx, field, dt, nsteps, step0);
+    return enqueue_steps<double>(ctx, field, dt, nsteps, step0);
+}
+
+qed_status sfq_push_wait(qed_ctx *ctx, qed_particles *p, qed_stats *out) {
+    if (!ctx || !p) return QED_ERR_INVALID;
+    if (!ctx->async_open) return QED_ERR_STATE;
+    if (!same_binding(ctx->async_p, *p)) return QED_ERR_STATE;
+    return wait_batch(ctx, p, out);
+}
+
+qed_status sfq_push(qed_ctx *ctx, qed_particles *p, const qed_field_desc *field, double dt, int nsteps,
+                    int64_t step0, qed_stats *out) {
+    const bool opened = ctx && !ctx->async_open;
+    qed_status e = sfq_push_async(ctx, p, field, dt, nsteps, step0);
+    if (e != QED_OK) {
+        // a batch this call opened is closed again (its work is drained)
+        if (opened && ctx->async_open) {
+            qed_stats tmp;
+            wait_batch(ctx, p, &tmp);
+        }
+        return e;
+    }
+    return wait_batch(ctx, p, out);
 }
 
 qed_status sfq_philox(const uint32_t *ctr, int64_t n, uint64_t key, uint32_t *out, cudaStream_t s) {
