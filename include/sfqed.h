@@ -387,6 +387,17 @@ qed_status qed_eval_chi(qed_ctx *ctx, int is_photon, const double *p_dev, const 
 qed_status qed_sample(qed_ctx *ctx, int is_photon, const double *chi_dev, const double *u_dev,
                       int64_t n, double *delta_dev, double *one_minus_dev);
 
+/* ---- measurement ------------------------------------------------------
+ * FP64 arithmetic rate of the current device, the roofline denominator of the
+ * FP64 mode (every step of Algorithm 1 in FP64): one wave of resident blocks,
+ * each thread running eight independent FP64 fused multiply-add chains of
+ * `iters` steps (2 FLOPs each), timed with CUDA events on cuda_stream (NULL =
+ * default stream); best of three launches after a warm-up.  *flops_per_s
+ * receives the rate, *ms (may be NULL) the best launch's duration.
+ * QED_ERR_INVALID for iters <= 0 or a null flops_per_s; synchronises the
+ * stream. */
+qed_status qed_measure_fp64_peak(int iters, double *flops_per_s, double *ms, void *cuda_stream);
+
 /* ---- compaction for callers that cannot allocate --------------------- */
 
 /* Largest species count qed_compact_species_noalloc() accepts. */

@@ -25,7 +25,8 @@ EXPORTED = ("qed_init_tables", "qed_push_and_generate", "qed_push_async", "qed_p
             "qed_destroy", "qed_philox", "qed_get_tables", "qed_eval_rate", "qed_sample", "qed_eval_chi",
             "qed_compact_species_noalloc", "qed_train_surrogate", "qed_mlp_set_params", "qed_mlp_get_params",
             "qed_mlp_forward", "qed_mlp_grad", "qed_level_begin", "qed_level_advance", "qed_level_eval",
-            "qed_level_apply", "qed_batch_shape", "qed_set_field_grid", "qed_set_optical_depth")
+            "qed_level_apply", "qed_batch_shape", "qed_set_field_grid", "qed_set_optical_depth",
+            "qed_measure_fp64_peak")
 QED_NOALLOC_MAX_ENTRIES = 1 << 20
 
 
@@ -125,6 +126,7 @@ def lib():
         "qed_batch_shape": (i32, [p, C.POINTER(i32), C.POINTER(i32)]),
         "qed_set_field_grid": (i32, [p, p]),
         "qed_set_optical_depth": (i32, [p, C.POINTER(C.c_void_p)]),
+        "qed_measure_fp64_peak": (i32, [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -384,6 +386,15 @@ def qed_mlp_grad(ctx, feat_dev_ptr: int, target_dev_ptr: int, n: int):
     if rc != QED_OK:
         raise QedError(rc, "qed_mlp_grad")
     return g, loss.value
+
+
+def qed_measure_fp64_peak(iters: int = 1 << 16, cuda_stream: int | None = None):
+    """(FP64 FLOP/s, ms of the timed launch) of the current device."""
+    f, ms = C.c_double(), C.c_double()
+    rc = lib().qed_measure_fp64_peak(int(iters), C.byref(f), C.byref(ms), C.c_void_p(cuda_stream or 0))
+    if rc != QED_OK:
+        raise QedError(rc, "qed_measure_fp64_peak")
+    return f.value, ms.value
 
 
 def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream: int | None = None,

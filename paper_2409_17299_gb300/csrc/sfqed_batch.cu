@@ -212,9 +212,9 @@ __device__ __forceinline__ void fused_emit(const FusedCtx &c, const EnsDev &e, u
     const T delta = sample_emission<T>(reinterpret_cast<const T *>(b.icdf), chi, ue, ve, &om);
     T g_after = om * gam, k0 = delta * gam;
     if (g_after < (T)1) { g_after = (T)1; k0 = gam - (T)1; }
-    const T inv = (T)1 / m_sqrt(p2);
+    const T inv = f_rsqrt(p2);
     const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
-    const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
+    const T pa = f_sqrt((g_after - (T)1) * (g_after + (T)1));
     if (!(b.soft_filter && k0 < (T)2)) {
         const uint4 rid = event_draw(b.seed ^ CHILD_KEY_XOR, id, step, k);
         const unsigned long long slot = warp_append(&b.ph_count[ens], 1);

@@ -43,6 +43,12 @@ __device__ __forceinline__ double f_exp(double a) { return exp(a); }
 __device__ __forceinline__ float f_exp(float a) { return __expf(a); }
 __device__ __forceinline__ double f_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float f_div(float a, float b) { return __fdividef(a, b); }
+// 1 / sqrt and sqrt: IEEE in FP64 mode; in FP32 mode from the hardware
+// reciprocal square root (2 ulp), sqrt(v) = v / sqrt(v) with 0 kept exact
+__device__ __forceinline__ double f_rsqrt(double a) { return 1.0 / sqrt(a); }
+__device__ __forceinline__ float f_rsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double f_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float f_sqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
 
 // Per-thread asynchronous copies global -> shared (cp.async): a thread
 // stages the next particle while it computes on the current one; the
@@ -173,10 +179,14 @@ template <class T> struct Phase { T s, c; };
 template <class T, class A> __device__ __forceinline__ Phase<T> time_phase(const A &a, double tau) {
     Phase<T> q{(T)0, (T)1};
     if (a.field_kind == QED_FIELD_UNIFORM) return q;
-    T ph;
-    if constexpr (sizeof(T) == 8) ph = a.t_n + tau;
-    else ph = a.t_n_red_f + (float)tau;
-    m_sincos(ph, &q.s, &q.c);
+    if constexpr (sizeof(T) == 8) {
+        m_sincos(a.t_n + tau, &q.s, &q.c);
+    } else {
+        // the phase reduced mod 2 pi plus the clock inside the step: an
+        // argument in [0, 2 pi + dt], where the hardware sine and cosine are
+        // within 1e-6 absolute
+        __sincosf(a.t_n_red_f + (float)tau, &q.s, &q.c);
+    }
     return q;
 }
 
@@ -335,7 +345,7 @@ __device__ __forceinline__ float chi_guarded(float e0, const float p[3], const f
         const float bz = diff_of_products(p[0], B[1], p[1], B[0]);
         float S = ax * ax + ay * ay + az * az + bx * bx + by * by + bz * bz;
         if (LEPTON) S += E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
-        return sqrtf(S) * (float)(1.0 / RS);
+        return f_sqrt(S) * (float)(1.0 / RS);
     }
     if (zero == 1) {
         const float ax = diff_of_products(p[1], E[2], p[2], E[1]);
@@ -343,13 +353,13 @@ __device__ __forceinline__ float chi_guarded(float e0, const float p[3], const f
         const float az = diff_of_products(p[0], E[1], p[1], E[0]);
         float S = ax * ax + ay * ay + az * az;
         if (LEPTON) S += E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
-        return sqrtf(S) * (float)(1.0 / RS);
+        return f_sqrt(S) * (float)(1.0 / RS);
     }
     if (zero == 2) {
         const float bx = diff_of_products(p[1], B[2], p[2], B[1]);
         const float by = diff_of_products(p[2], B[0], p[0], B[2]);
         const float bz = diff_of_products(p[0], B[1], p[1], B[0]);
-        return sqrtf(bx * bx + by * by + bz * bz) * (float)(1.0 / RS);
+        return f_sqrt(bx * bx + by * by + bz * bz) * (float)(1.0 / RS);
     }
     const float ax = diff_of_products(p[1], E[2], p[2], E[1]);
     const float ay = diff_of_products(p[2], E[0], p[0], E[2]);
@@ -363,7 +373,7 @@ __device__ __forceinline__ float chi_guarded(float e0, const float p[3], const f
     const float T = te * (E[0] * bx + E[1] * by + E[2] * bz);
     const float M = S + te * (fabsf(E[0] * bx) + fabsf(E[1] * by) + fabsf(E[2] * bz));
     const float r = S + T;
-    if (M <= 4.0f * r) return sqrtf(r) * (float)(1.0 / RS);
+    if (M <= 4.0f * r) return f_sqrt(r) * (float)(1.0 / RS);
     ++*fp64_used;
     const double pd0 = p[0], pd1 = p[1], pd2 = p[2];
     const double e0d = LEPTON ? sqrt(1.0 + (pd0 * pd0 + pd1 * pd1 + pd2 * pd2)) : sqrt(pd0 * pd0 + pd1 * pd1 + pd2 * pd2);
@@ -380,7 +390,7 @@ __device__ __forceinline__ void lepton_chi(const T p[3], const T E[3], const T B
         chi = chi_fp64(gam, p[0], p[1], p[2], E[0], E[1], E[2], B[0], B[1], B[2]);
     } else {
         p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
-        gam = sqrtf(1.0f + p2);
+        gam = f_sqrt(1.0f + p2);
         chi = chi_guarded<true>(gam, p, E, B, &n64, zero);
     }
 }
@@ -393,26 +403,33 @@ __device__ __forceinline__ T photon_chi(T k0, const T k[3], const T E[3], const 
 
 // ---------------------------------------------------------------------------
 // Boris push: half electric kick, magnetic rotation, half kick, then
-// x += p/gamma h with the new momentum.  q = -1 (e-) or +1 (e+).
+// x += p/gamma h with the new momentum.  q = -1 (e-) or +1 (e+).  no_b: B = 0
+// wherever the field is evaluated (the rotation is the identity and is
+// skipped).  FP32 mode takes 1/gamma from the hardware reciprocal square root
+// and the rotation factor from the fast division.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ void boris(T x[3], T p[3], T q, const T E[3], const T B[3], T h) {
+__device__ __forceinline__ void boris(T x[3], T p[3], T q, const T E[3], const T B[3], T h, bool no_b = false) {
     const T qh2 = (T)0.5 * q * h;
     T m0 = p[0] + qh2 * E[0], m1 = p[1] + qh2 * E[1], m2 = p[2] + qh2 * E[2];
-    const T ig = (T)1 / m_sqrt((T)1 + m0 * m0 + m1 * m1 + m2 * m2);
-    const T t0 = qh2 * B[0] * ig, t1 = qh2 * B[1] * ig, t2 = qh2 * B[2] * ig;
-    const T f = (T)2 / ((T)1 + t0 * t0 + t1 * t1 + t2 * t2);
-    const T s0 = f * t0, s1 = f * t1, s2 = f * t2;
-    const T a0 = m0 + (m1 * t2 - m2 * t1);
-    const T a1 = m1 + (m2 * t0 - m0 * t2);
-    const T a2 = m2 + (m0 * t1 - m1 * t0);
-    m0 += a1 * s2 - a2 * s1;
-    m1 += a2 * s0 - a0 * s2;
-    m2 += a0 * s1 - a1 * s0;
+    if (!no_b) {
+        const T ig = f_rsqrt((T)1 + m0 * m0 + m1 * m1 + m2 * m2);
+        const T t0 = qh2 * B[0] * ig, t1 = qh2 * B[1] * ig, t2 = qh2 * B[2] * ig;
+        const T f = f_div((T)2, (T)1 + t0 * t0 + t1 * t1 + t2 * t2);
+        const T s0 = f * t0, s1 = f * t1, s2 = f * t2;
+        const T a0 = m0 + (m1 * t2 - m2 * t1);
+        const T a1 = m1 + (m2 * t0 - m0 * t2);
+        const T a2 = m2 + (m0 * t1 - m1 * t0);
+        m0 += a1 * s2 - a2 * s1;
+        m1 += a2 * s0 - a0 * s2;
+        m2 += a0 * s1 - a1 * s0;
+    }
     p[0] = m0 + qh2 * E[0];
     p[1] = m1 + qh2 * E[1];
     p[2] = m2 + qh2 * E[2];
-    const T vh = h / m_sqrt((T)1 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    T vh;
+    if constexpr (sizeof(T) == 8) vh = h / sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    else vh = h * rsqrtf(1.0f + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
     x[0] += p[0] * vh;
     x[1] += p[1] * vh;
     x[2] += p[2] * vh;
@@ -515,20 +532,33 @@ __device__ __forceinline__ T bilinear(const T *tab, int nchi, int ns, T c, T t) 
     return lo + fc * (hi - lo);
 }
 
-// logit u = ln u - ln(1 - u) from (u, v = 1 - u)
+// logit u = ln u - ln(1 - u) from (u, v = 1 - u); FP32: hardware logarithms
+// (u and v each hold full relative precision, and the table coordinate needs
+// about 1e-5 absolute)
 __device__ __forceinline__ double logit(double u, double) { return log(u) - log1p(-u); }
-__device__ __forceinline__ float logit(float u, float v) { return logf(u) - logf(v); }
+__device__ __forceinline__ float logit(float u, float v) { return __logf(u) - __logf(v); }
+// log10 chi and exp of the table value: IEEE in FP64 mode, hardware in FP32
+__device__ __forceinline__ double s_log10(double a) { return log10(a); }
+__device__ __forceinline__ float s_log10(float a) { return __log10f(a); }
+__device__ __forceinline__ double s_exp(double a) { return exp(a); }
+__device__ __forceinline__ float s_exp(float a) { return __expf(a); }
 
 // photon energy fraction delta (returned) and 1 - delta
 template <class T>
 __device__ __forceinline__ T sample_emission(const T *tab, T chi, T u, T v, T *one_minus) {
     const T s = logit(u, v);
-    const T c = (m_log10(chi) + (T)3) * (T)20;
+    const T c = (s_log10(chi) + (T)3) * (T)20;
     const T t = (s + (T)16) * (T)8;
     const T zeta = bilinear(tab, EM_NCHI, EM_NS, c, t);
-    const T a = (T)3 * chi * m_exp(zeta);
-    *one_minus = (T)2 / ((T)2 + a);
-    return a / ((T)2 + a);
+    const T a = (T)3 * chi * s_exp(zeta);
+    if constexpr (sizeof(T) == 8) {
+        *one_minus = 2.0 / (2.0 + a);
+        return a / (2.0 + a);
+    } else {
+        const float inv = __fdividef(1.0f, 2.0f + a);
+        *one_minus = 2.0f * inv;
+        return a * inv;
+    }
 }
 
 // electron energy fraction delta (returned) and 1 - delta (positron fraction)
@@ -536,9 +566,9 @@ template <class T>
 __device__ __forceinline__ T sample_pair(const T *tab, T chi, T u, T v, T *one_minus) {
     const bool flip = u > (T)0.5;
     const T s = flip ? logit(v, u) : logit(u, v);   // logit of min(u, 1 - u)
-    const T c = (m_log10(chi) + (T)2) * (T)20;
+    const T c = (s_log10(chi) + (T)2) * (T)20;
     const T t = (s + (T)16) * (T)8;
-    const T d = m_exp(bilinear(tab, PAIR_NCHI, PAIR_NS, c, t));
+    const T d = s_exp(bilinear(tab, PAIR_NCHI, PAIR_NS, c, t));
     if (flip) { *one_minus = d; return (T)1 - d; }
     *one_minus = (T)1 - d;
     return d;

@@ -63,6 +63,12 @@ __device__ __forceinline__ StepTime load_step_time(const PassArgs &a) {
     return t;
 }
 
+// tau < dt for the clock's non-negative doubles, as an integer comparison of
+// their bit patterns (which order like the values): no FP64 instruction
+__device__ __forceinline__ bool before_step_end(double tau, double dt) {
+    return __double_as_longlong(tau) < __double_as_longlong(dt);
+}
+
 template <class T> __device__ __forceinline__ T t_inf();
 template <> __device__ __forceinline__ double t_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
 template <> __device__ __forceinline__ float t_inf<float>() { return __int_as_float(0x7f800000); }
@@ -166,13 +172,25 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
     T h;
     if constexpr (FRESH && sizeof(T) == 4) { no_event = dth >= a.dt_f_gt; h = a.dt_f; }
     else if constexpr (FRESH) { no_event = dth > a.dt; h = a.dt; }
-    else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
+    else if constexpr (sizeof(T) == 4) {
+        // FP32 mode after a particle's first event: the FP64 test
+        // tau + dth > dt decided in FP32 wherever dth lies outside a margin
+        // around the remaining time rem = dt - tau (rounded once to float);
+        // the margin (2^-20 rem + 2^-40 dt) exceeds every rounding involved,
+        // so the decision is the FP64 one, and within it the FP64 test runs
+        const float rf = __double2float_rn(a.dt - tau);
+        const float marg = fmaf(rf, 0x1p-20f, a.dt_f * 0x1p-40f);
+        if (dth > rf + marg) no_event = true;
+        else if (dth < rf - marg) no_event = false;
+        else no_event = tau + (double)dth > a.dt;
+        h = rf;
+    } else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
     if (no_event) {
-        boris<T>(x, p, q, E, B, h);
+        boris<T>(x, p, q, E, B, h, a.field_zero == 1);
         tau = a.dt;
         return false;
     }
-    boris<T>(x, p, q, E, B, dth);
+    boris<T>(x, p, q, E, B, dth, a.field_zero == 1);
     if constexpr (FRESH) tau = (double)dth;
     else tau += (double)dth;
     return true;
@@ -187,9 +205,9 @@ __device__ __forceinline__ void emit_with(const LeptonCtx<T> &c, const T x[3], T
     const PassArgs &a = c.a;
     T g_after = om * gam, k0 = delta * gam;
     if (g_after < (T)1) { g_after = (T)1; k0 = gam - (T)1; }
-    const T inv = (T)1 / m_sqrt(p2);
+    const T inv = f_rsqrt(p2);
     const T nx = p[0] * inv, ny = p[1] * inv, nz = p[2] * inv;
-    const T pa = m_sqrt((g_after - (T)1) * (g_after + (T)1));
+    const T pa = f_sqrt((g_after - (T)1) * (g_after + (T)1));
     if (!(a.soft_filter && k0 < (T)2)) {
         const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, c.tm.step, k);
         const unsigned long long slot = warp_append(&c.ctl->count[2], 1);
@@ -303,7 +321,7 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
         ++k;
         ++ev;
         const T qch = (idx >> 31) ? (T)1 : (T)-1;
-        if (tau < c.a.dt && advance<T, false>(c, x, p, qch, tau, id, k, rz, n64)) {
+        if (before_step_end(tau, c.a.dt) && advance<T, false>(c, x, p, qch, tau, id, k, rz, n64)) {
             stack_push<T>(q, x, p, tau, id, w, idx, k, rz);
         } else {
             finish<T>(c.a, idx, x, p, k);
@@ -409,7 +427,7 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
                     const T qch = s == 0 ? (T)-1 : (T)1;
                     bool event;
                     if constexpr (FRESH) event = advance<T, true>(c, x, p, qch, tau, id, 0u, rz, n64);
-                    else event = tau < a.dt && advance<T, false>(c, x, p, qch, tau, id, 0u, rz, n64);
+                    else event = before_step_end(tau, a.dt) && advance<T, false>(c, x, p, qch, tau, id, 0u, rz, n64);
                     if (event) {
                         stack_push<T>(q, x, p, tau, id, w, idx, 0u, rz);
                     } else {
@@ -499,13 +517,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
         if (!(w > (T)0)) continue;
         double tau = FRESH ? 0.0 : S.tau[i];
         const T kv[3] = {kx, ky, kz};
-        const T k0 = m_sqrt(kx * kx + ky * ky + kz * kz);
+        const T k0 = f_sqrt(kx * kx + ky * ky + kz * kz);
         unsigned k = 0;
         if (k0 > (T)0) {
             const T inv = f_div((T)1, k0);
             const T nx = kx * inv, ny = ky * inv, nz = kz * inv;
             // one waiting time: the photon either reaches the step end or converts
-            if (FRESH || tau < a.dt) {
+            if (FRESH || before_step_end(tau, a.dt)) {
                 T E[3], B[3];
                 if constexpr (FRESH) field_at<T>(a, x, ph0, E, B);
                 else field_tau<T>(a, tm, x, tau, E, B);
@@ -525,7 +543,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 T h;
                 if constexpr (FRESH && sizeof(T) == 4) { no_event = dth >= a.dt_f_gt; h = a.dt_f; }
                 else if constexpr (FRESH) { no_event = dth > a.dt; h = a.dt; }
-                else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
+                else if constexpr (sizeof(T) == 4) {
+                    // as in the lepton pass: the FP64 test decided in FP32 outside a margin
+                    const float rf = __double2float_rn(a.dt - tau);
+                    const float marg = fmaf(rf, 0x1p-20f, a.dt_f * 0x1p-40f);
+                    if (dth > rf + marg) no_event = true;
+                    else if (dth < rf - marg) no_event = false;
+                    else no_event = tau + (double)dth > a.dt;
+                    h = rf;
+                } else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
                 if (no_event) {
                     x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
                     tau = a.dt;
@@ -541,7 +567,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 T em = delta * k0, ep = om * k0;
                 em = em < (T)1 ? (T)1 : em;
                 ep = ep < (T)1 ? (T)1 : ep;
-                const T pm = m_sqrt((em - (T)1) * (em + (T)1)), pp = m_sqrt((ep - (T)1) * (ep + (T)1));
+                const T pm = f_sqrt((em - (T)1) * (em + (T)1)), pp = f_sqrt((ep - (T)1) * (ep + (T)1));
                 const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, tm.step, k);
                 const unsigned long long se = warp_append(&ctl->count[0], 1);
                 const unsigned long long sp = warp_append(&ctl->count[1], 1);
@@ -652,7 +678,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(Pas
         const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
         od = od_advance<T>(a, tm.step, id, od, lam);
         const T qch = s == 0 ? (T)-1 : (T)1;
-        boris<T>(x, p, qch, E, B, dt_of<T>(a));
+        boris<T>(x, p, qch, E, B, dt_of<T>(a), a.field_zero == 1);
         unsigned k = 0;
         if (od <= (T)0) {
             // the event at the end of the step
@@ -746,10 +772,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(Pas
         }
         if (!(w > (T)0)) continue;
         ++my_steps;
-        const T k0 = m_sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+        const T k0 = f_sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
         unsigned k = 0;
         if (k0 > (T)0) {
-            const T inv = (T)1 / k0;
+            const T inv = f_div((T)1, k0);
             const T nx = kv[0] * inv, ny = kv[1] * inv, nz = kv[2] * inv;
             T E[3], B[3];
             field_at<T>(a, x, ph0, E, B);
@@ -769,7 +795,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_od(Pas
                 T em = delta * k0, ep = om * k0;
                 em = em < (T)1 ? (T)1 : em;
                 ep = ep < (T)1 ? (T)1 : ep;
-                const T pm = m_sqrt((em - (T)1) * (em + (T)1)), pp = m_sqrt((ep - (T)1) * (ep + (T)1));
+                const T pm = f_sqrt((em - (T)1) * (em + (T)1)), pp = f_sqrt((ep - (T)1) * (ep + (T)1));
                 const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, tm.step, 0u);
                 const unsigned long long se = warp_append(&ctl->count[0], 1);
                 const unsigned long long sp = warp_append(&ctl->count[1], 1);
