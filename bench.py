@@ -57,6 +57,11 @@ OD_PHOTON_BYTES = {"fp32": PHOTON_BYTES["fp32"] + 8, "fp64": PHOTON_BYTES["fp64"
 # None when the kernel changed since its capture
 NCU_PHOTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
 NCU_LEPTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
+# FP64 FLOPs (2 DFMA + DADD + DMUL thread instructions) per particle-step of
+# the FP64 step-start passes at the rotating-E cascade's cap (0.3 emissions
+# per lepton-step), from one ncu capture of the current kernels
+# (profiles/fp64_passes_rotating_e_cascade.md)
+NCU_FP64_FLOP_PER_STEP = {"k_lepton_pass": 478.0, "k_photon_pass": 193.0}
 
 
 def parse():
@@ -76,10 +81,19 @@ def parse():
     ap.add_argument("--compare-od", type=int, default=1,
                     help="also time the accumulated optical-depth scheme on the same workload (extra key)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--growth", type=int, default=1,
+                    help="also run the paper's test problem (Sec. 5.1, 5 seeds x FP64, FP32, network sampler) "
+                         "and report the growth rate and density profile (extra key)")
     ap.add_argument("--e2e", type=int, default=1)
     ap.add_argument("--scale", type=float, default=1.0, help="scale the seed count (tests only)")
     ap.add_argument("--batch-threads", type=int, default=0, choices=[0, 128, 256, 512],
                     help="batched workload: fixed block shape instead of the autotuner's (0)")
+    ap.add_argument("--ncu-window", action="store_true",
+                    help="profiling run for ncu --profile-from-start off: only the host-driven pass over the timed "
+                         "window, its K steps inside cudaProfilerStart/Stop; prints the window's statistics")
+    ap.add_argument("--profile-step", type=int, default=None,
+                    help="profiling run for ncu --profile-from-start off: drive the workload (--scale) to this "
+                         "step, then one host-driven step inside cudaProfilerStart/Stop")
     return ap.parse_args()
 
 
@@ -320,7 +334,8 @@ def size_cascade(w, nsteps, precision, method=0):
     return caps
 
 
-def gpu_run(args, w, precision, start, warm, steps, profile=False, mlp_params=None, caps=None, method=0):
+def gpu_run(args, w, precision, start, warm, steps, profile=False, mlp_params=None, caps=None, method=0,
+            profiler_range=False):
     """Steps 0..start+warm-1 untimed (one batch, one wait), then `steps`
     timed steps: per step an L2 flush, then the step enqueued between two
     CUDA events (qed_push_async; no host wait inside the loop); one
@@ -356,6 +371,8 @@ def gpu_run(args, w, precision, start, warm, steps, profile=False, mlp_params=No
     torch.cuda.synchronize()
     counts0 = list(ens.count)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    if profiler_range:
+        torch.cuda.profiler.start()
     t0 = time.perf_counter()
     host_in_loop = 0.0
     for k, s in enumerate(range(s0, s0 + steps)):
@@ -368,10 +385,18 @@ def gpu_run(args, w, precision, start, warm, steps, profile=False, mlp_params=No
         gen.push_async(ens, field, w.dt, 1, s)
         host_in_loop += time.perf_counter() - th
         b.record(stream)
+    # qed_push_wait removes the dead entries the steps left in place (moves are
+    # deferred while few): timed apart, between an event before the call and
+    # one after it (an upper bound: it includes the call's return)
+    c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c.record(stream)
     tw = time.perf_counter()
     st = gen.wait(ens)
     drain = time.perf_counter() - tw
+    d.record(stream)
     torch.cuda.synchronize()
+    if profiler_range:
+        torch.cuda.profiler.stop()
     wall = time.perf_counter() - t0
     ms = sum(a.elapsed_time(b) for _, a, b in ev)
     # device time between the end of a step and the next flush: the GPU
@@ -387,6 +412,7 @@ def gpu_run(args, w, precision, start, warm, steps, profile=False, mlp_params=No
     st["host_enqueue_ms"] = host_in_loop * 1e3
     st["drain_wait_ms"] = drain * 1e3
     st["window"] = [s0, s0 + steps - 1]
+    st["final_compaction_ms"] = c.elapsed_time(d)
     return ms, wall, st, counts
 
 
@@ -554,6 +580,8 @@ def reduce_over_ranks(particle_steps, events, secs, world):
 
 def main():
     args = parse()
+    if args.ncu_window or args.profile_step is not None:
+        args.cpu_baseline = 0                     # a profiling run times nothing on the host
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     w0 = make_workload(args.workload, args.scale)
@@ -606,7 +634,17 @@ def main():
     hbm_peak = hbm_peak or 6800.0
 
     n_total = start + warm + steps
+    if args.profile_step is not None:
+        return profile_step(w, args.precision, args.profile_step)
     caps = size_cascade(w, n_total, args.precision) if w.push_photons else None
+    if args.ncu_window:
+        _, _, t, _ = gpu_run(args, w, args.precision, start, warm, steps, caps=caps, profile=True,
+                             profiler_range=True)
+        print(json.dumps({"ncu_window": t["window"], "particle_steps": t["particle_steps"],
+                          "lepton_steps": t["lepton_steps"], "photon_steps": t["photon_steps"],
+                          "emit_events": t["emit_events"], "pair_events": t["pair_events"],
+                          "counts_at_start": t["counts_start"], "kernel_ms": t["kernel_ms"]}), flush=True)
+        return
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -630,6 +668,7 @@ def main():
         # one wait after the loop (the graph path issues no other)
         inside = max(0.0, t["sync_ms"] - t["drain_wait_ms"])
         return {"host_sync_wait_in_loop_ms": inside, "drain_wait_after_loop_ms": t["drain_wait_ms"],
+                "final_compaction_ms": t["final_compaction_ms"],
                 "host_enqueue_ms": t["host_enqueue_ms"], "gpu_idle_between_steps_ms": t["gpu_idle_ms"],
                 "device_ms": dev_ms, "host_sync_wait_frac_of_device": inside / dev_ms if dev_ms > 0 else None}
 
@@ -652,8 +691,10 @@ def main():
     fp64 = None
     if args.compare_fp64 and args.precision == "fp32" and world == 1:
         ms64, wall64, tot64, _ = gpu_run(args, w, "fp64", start, warm, steps, caps=caps)
+        _, _, tot64p, _ = gpu_run(args, w, "fp64", start, warm, steps, caps=caps, profile=True)
         fp64 = {"value": tot64["particle_steps"] / (ms64 / 1e3), "events_per_s":
-                (tot64["emit_events"] + tot64["pair_events"]) / (ms64 / 1e3), "ms_per_step": ms64 / steps}
+                (tot64["emit_events"] + tot64["pair_events"]) / (ms64 / 1e3), "ms_per_step": ms64 / steps,
+                "roofline": fp64_roofline(tot64p, hbm_peak)}
 
     mlp = None
     if args.compare_mlp and world == 1 and args.workload == "rotating_e_cascade":
@@ -672,6 +713,23 @@ def main():
                "ms_per_step": ms_m / steps,
                "train_samples": int(args.mlp_samples), "train_seconds": train_s, "train_final_mse": loss,
                "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation (mma.sync)"}
+
+    growth = None
+    if args.growth and world == 1 and args.workload == "rotating_e_cascade":
+        import numpy as np
+        modes = {"fp64": [growth_run("fp64", sd) for sd in GROWTH_SEEDS],
+                 "fp32": [growth_run("fp32", sd) for sd in GROWTH_SEEDS]}
+        if mlp:
+            modes["surrogate_fp32"] = [growth_run("fp32", sd, mlp_params=P) for sd in GROWTH_SEEDS]
+        growth = {k: growth_summary(v) for k, v in modes.items()}
+        ref = growth["fp64"]
+        for k, v in growth.items():
+            v["eta_gamma_vs_fp64"] = v["gamma_mean"] / ref["gamma_mean"] - 1
+            v["profile_l1_vs_fp64"] = float(np.abs(np.array(v["profile_mean"]) - np.array(ref["profile_mean"])).sum())
+        growth["setup"] = ("paper test problem: 2.5e5 e-/e+ at rest filling the 1-wavelength box, standing CP wave "
+                           "a0 = 1557, dt = T/200, 5 T, leveling cap %d per species; Gamma fitted over steps %d-%d "
+                           "from the leptons' total weight; density profile of lepton weight along x, %d bins; "
+                           "seeds %s" % (GROWTH_CAP, GROWTH_FIT[0], GROWTH_FIT[1], GROWTH_BINS, list(GROWTH_SEEDS)))
 
     od = None
     if args.compare_od and world == 1 and args.workload != "batched_uniform_b":
@@ -778,6 +836,8 @@ def main():
             line["surrogate_speedup_over_fp64_table"] = mlp["value"] / fp64["value"]
     if od:
         line["optical_depth_method"] = od
+    if growth:
+        line["test_problem_growth"] = growth
     if e2e:
         line["e2e"] = e2e
     if cpu:
@@ -795,6 +855,125 @@ ISSUE_PEAK_WARP_INSTR = 152 * 4 * 2.07e9
 # threads, budget 4) from one ncu capture of the current kernel
 # (profiles/k_emission_fused_batched_uniform_b.md); None when not captured
 NCU_FUSED_WARP_INSTR_PER_STEP = {"fp32": 47.9, "fp64": None}
+
+
+# The paper's test problem (Sec. 5.1-5.2): growth rate of the cascade in its
+# exponential stage and the lepton density profile, per mode and seed
+GROWTH_SEEDS = (11, 12, 13, 14, 15)
+GROWTH_CAP = 2_000_000          # leveling cap per species (the paper does not print its own)
+GROWTH_FIT = (700, 1000)        # steps fitted: 3.5 T to 5 T (the paper: exponential after ~3.5 T)
+GROWTH_BINS = 64
+
+
+def growth_run(precision, seed, mlp_params=None, n=250_000, cap=GROWTH_CAP, hook=None):
+    """One 5 T run of the test problem (one step per call): Gamma (per
+    period) from the slope of ln W, W the leptons' total weight (leveling keeps
+    its expectation), over GROWTH_FIT; the weighted lepton density along x
+    (wrapped to the box) at the end, normalised.  hook(step, gen, ens) runs
+    before each step."""
+    import numpy as np
+    import torch
+    import paper_2409_17299_gb300 as q
+    w = W.paper_test_problem(n=n, seed=seed, thin_cap=cap)
+    prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
+    gen = q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=1, thin_cap=cap,
+                                    sampler=q.QED_SAMPLER_MLP if mlp_params is not None else q.QED_SAMPLER_TABLE))
+    if mlp_params is not None:
+        q.qed_mlp_set_params(gen.ctx, mlp_params)
+    ens = q.DeviceEnsemble.from_host(w.species, [int(1.3 * cap) + n, int(1.3 * cap) + n, int(1.8 * cap) + n], prec)
+    field = q.make_field(w.field_kind, w.field_prm)
+    lnw = []
+    t0 = time.perf_counter()
+    for s in range(w.nsteps):
+        if hook is not None:
+            hook(s, gen, ens, w, field)
+        gen.push(ens, field, w.dt, 1, s)
+        tot = sum(ens.arr[k]["w"][:ens.count[k]].double().sum() for k in (0, 1))
+        lnw.append(math.log(float(tot)))
+    secs = time.perf_counter() - t0
+    t = (np.arange(w.nsteps) + 1) * w.dt
+    a, b = GROWTH_FIT
+    gamma = float(np.polyfit(t[a:b], np.array(lnw[a:b]), 1)[0] * 2 * math.pi)
+    xs, ws = [], []
+    for k in (0, 1):
+        m = ens.count[k]
+        xs.append(ens.arr[k]["x"][:m].double().cpu().numpy())
+        ws.append(ens.arr[k]["w"][:m].double().cpu().numpy())
+    x = (np.concatenate(xs) + math.pi) % (2 * math.pi) - math.pi
+    h, _ = np.histogram(x, bins=GROWTH_BINS, range=(-math.pi, math.pi), weights=np.concatenate(ws))
+    counts = list(ens.count)
+    gen.close()
+    del ens
+    torch.cuda.empty_cache()
+    return {"gamma": gamma, "profile": (h / h.sum()).tolist(), "counts": counts, "seconds": secs}
+
+
+def growth_summary(runs):
+    """Gamma mean, standard deviation, 3-sigma envelope of the mean and the
+    mean profile of a mode's runs."""
+    import numpy as np
+    g = np.array([r["gamma"] for r in runs])
+    sd = float(g.std(ddof=1)) if len(g) > 1 else 0.0
+    m = float(g.mean())
+    env = 3 * sd / math.sqrt(len(g))
+    return {"gamma_per_period": g.tolist(), "gamma_mean": m, "gamma_std": sd, "gamma_mean_3sigma": [m - env, m + env],
+            "profile_mean": np.mean([r["profile"] for r in runs], axis=0).tolist(),
+            "seconds": float(sum(r["seconds"] for r in runs))}
+
+
+def profile_step(w, precision, step):
+    """Drive the workload to `step` (captured steps), then run one step
+    through the host-driven launches inside cudaProfilerStart/Stop: the small
+    case an ncu capture of single kernels is taken on."""
+    import torch
+    import paper_2409_17299_gb300 as q
+    prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
+    caps = [int(c * 1.1) for c in capacities(w, w.nsteps)]
+    gen = q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap))
+    ens = q.DeviceEnsemble.from_host(w.species, caps, prec)
+    field = q.make_field(w.field_kind, w.field_prm)
+    for s in range(0, step, 10):
+        gen.push(ens, field, w.dt, min(10, step - s), s)
+    genp = q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons,
+                                     thin_cap=w.thin_cap, profile=1))
+    counts0 = list(ens.count)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    st = genp.push(ens, field, w.dt, 1, step)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profiled_step": step, "counts_at_start": counts0, "counts_after": list(ens.count),
+                      **{k: st[k] for k in ("particle_steps", "lepton_steps", "photon_steps", "emit_events",
+                                            "pair_events", "passes", "thinned")}}), flush=True)
+    gen.close()
+    genp.close()
+
+
+def fp64_roofline(tot, hbm_peak):
+    """The FP64 mode's pass kernels against the measured FP64 arithmetic peak
+    (qed_measure_fp64_peak, timed live) and against HBM."""
+    import paper_2409_17299_gb300 as q
+    peak, _ = q.qed_measure_fp64_peak(1 << 16)
+    out = {"bound": "fp64", "unit": "FLOP/s", "peak": peak,
+           "peak_source": "measured: qed_measure_fp64_peak (FP64 FMA chains, one wave of resident blocks)",
+           "flop_is": "2 DFMA + DADD + DMUL thread instructions per particle-step (ncu) x particle-steps / "
+                      "summed CUDA-event time of the launches", "kernels": {}}
+    for k, ms, units, nbytes in (("k_lepton_pass", tot["kernel_ms"][0], tot["lepton_steps"],
+                                  LEPTON_BYTES["fp64"] * tot["lepton_steps"] + EMIT_BYTES["fp64"] * tot["emit_events"]),
+                                 ("k_photon_pass", tot["kernel_ms"][1], tot["photon_steps"],
+                                  PHOTON_BYTES["fp64"] * tot["photon_steps"] + PAIR_BYTES["fp64"] * tot["pair_events"])):
+        if ms <= 0:
+            continue
+        fl = NCU_FP64_FLOP_PER_STEP[k] * units / (ms / 1e3)
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out["kernels"][k] = {"kernel_ms": ms, "achieved": fl, "frac": fl / peak,
+                             "flop_per_particle_step": NCU_FP64_FLOP_PER_STEP[k],
+                             "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+    dom = max(out["kernels"], key=lambda k: out["kernels"][k]["kernel_ms"]) if out["kernels"] else None
+    if dom:
+        out.update({"kernel": dom + "<double>", "achieved": out["kernels"][dom]["achieved"],
+                    "frac": out["kernels"][dom]["frac"], "hbm_frac": out["kernels"][dom]["hbm_frac"]})
+    return out
 
 
 def batch_roofline(st, precision):

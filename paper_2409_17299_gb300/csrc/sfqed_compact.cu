@@ -180,7 +180,17 @@ __global__ void __launch_bounds__(CT) k_fill_holes(SpeciesDev S, DevCtl *ctl, in
     }
 }
 
+// Entries a tile pass covers: the count (at most the capacity), none once a
+// step ran out of capacity or a device check failed (the state is then left
+// as it is for the caller's replay).
+__device__ __forceinline__ unsigned long long tile_count(const DevCtl *ctl, int s) {
+    if (ctl->overflow || ctl->timeout || ctl->bad_index) return 0;
+    const unsigned long long c = ctl->count[s], cp = ctl->capacity[s];
+    return c < cp ? c : cp;
+}
+
 __global__ void k_set_count(DevCtl *ctl, int s) {
+    if (ctl->overflow || ctl->timeout || ctl->bad_index) return;
     ctl->count[s] = ctl->alive[s];
     ctl->end[s] = ctl->alive[s];
     ctl->begin[s] = ctl->alive[s];
@@ -339,13 +349,16 @@ __device__ __forceinline__ void lev_accumulate(const void *w, unsigned long long
             const float4 *w4 = reinterpret_cast<const float4 *>(wf);
             const unsigned long long n4 = n / 4;
             unsigned long long j = t0;
-            for (; j + stride < n4; j += 2 * stride) {          // two 16-byte loads in flight
-                const float4 a = w4[j], b = w4[j + stride];
+            for (; j + 3 * stride < n4; j += 4 * stride) {      // four 16-byte loads in flight
+                const float4 a = __ldg(w4 + j), b = __ldg(w4 + j + stride);
+                const float4 c4 = __ldg(w4 + j + 2 * stride), d = __ldg(w4 + j + 3 * stride);
                 one(a.x); one(a.y); one(a.z); one(a.w);
                 one(b.x); one(b.y); one(b.z); one(b.w);
+                one(c4.x); one(c4.y); one(c4.z); one(c4.w);
+                one(d.x); one(d.y); one(d.z); one(d.w);
             }
-            if (j < n4) {
-                const float4 a = w4[j];
+            for (; j < n4; j += stride) {
+                const float4 a = __ldg(w4 + j);
                 one(a.x); one(a.y); one(a.z); one(a.w);
             }
             i0 = n4 * 4;
@@ -385,7 +398,7 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
                                                     long long cap) {
     LevelIter &it = lw->it[s];
     if (*reinterpret_cast<volatile unsigned long long *>(&it.done)) return;
-    const unsigned long long n = ctl->count[s];
+    const unsigned long long n = min(ctl->count[s], ctl->capacity[s]);
     const unsigned long long t0 = (unsigned long long)blockIdx.x * LEV_T + threadIdx.x;
     const unsigned long long stride = (unsigned long long)gridDim.x * LEV_T;
     double A;
@@ -500,7 +513,7 @@ __global__ void __launch_bounds__(LT, 4) k_tile_dead(SpeciesDev S, DevCtl *ctl, 
                                                   const PhiloxKeys keys, unsigned step, int step_from_ctl,
                                                   unsigned long long *blk, unsigned short *dl) {
     __shared__ unsigned wdead[LT / 32];
-    const unsigned long long n = ctl->count[s];
+    const unsigned long long n = tile_count(ctl, s);
     const long long nbe = tiles_of(n);
     if (step_from_ctl) step = ctl->sv_step;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -598,12 +611,19 @@ __global__ void __launch_bounds__(LT, 4) k_tile_dead(SpeciesDev S, DevCtl *ctl, 
 }
 
 // single block: exclusive scan of the counts of the tiles holding entries
-// (blk[nbe] = A), then H from the alive entries of the tile that holds A
+// (blk[nbe] = A), then H from the alive entries of the tile that holds A.
+// may_defer: while dead entries are at most DEFER_DEN-th of the species and
+// the count leaves a fifth of the capacity free, the move is deferred (H = 0,
+// the count stays): the dead entries (weight 0) are skipped by every pass
+// until a later step compacts, with holes denser and fewer moves per step.
+constexpr unsigned long long DEFER_DEN = 4;
+
 template <class T>
-__global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long nb, DevCtl *ctl, int s) {
+__global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long nb, DevCtl *ctl, int s,
+                             int may_defer) {
     __shared__ unsigned long long sw[32];
     __shared__ unsigned long long carry;
-    const long long nbe_all = tiles_of(ctl->count[s]);
+    const long long nbe_all = tiles_of(tile_count(ctl, s));
     const long long nbe = nbe_all < nb ? nbe_all : nb;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -648,9 +668,17 @@ __global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long n
         below = blk[a] + tc;
     }
     if (threadIdx.x == 0) {
+        const unsigned long long n = tile_count(ctl, s);
         blk[nbe] = A;
-        ctl->alive[s] = A;
-        ctl->holes[s] = A - below;
+        if (may_defer && (n - A) * DEFER_DEN <= n && 5 * n <= 4 * ctl->capacity[s]) {
+            ctl->alive[s] = n;                      // nothing moves; count unchanged
+            ctl->holes[s] = 0;
+            ctl->deferred[s] = n - A;
+        } else {
+            ctl->alive[s] = A;
+            ctl->holes[s] = A - below;
+            ctl->deferred[s] = 0;
+        }
     }
 }
 
@@ -660,7 +688,7 @@ template <class T>
 __global__ void __launch_bounds__(LT) k_tile_movers(const void *w, DevCtl *ctl, int s, const unsigned long long *blk,
                                                     unsigned long long *movers) {
     __shared__ unsigned walive[LT / 32];
-    const unsigned long long n = ctl->count[s], A = ctl->alive[s], H = ctl->holes[s];
+    const unsigned long long n = tile_count(ctl, s), A = ctl->alive[s], H = ctl->holes[s];
     if (H == 0) return;
     const unsigned long long below_A = A - H;      // alive entries below A
     const long long nbe = tiles_of(n);
@@ -698,11 +726,14 @@ __global__ void __launch_bounds__(LT) k_tile_movers(const void *w, DevCtl *ctl, 
 }
 
 // pass 3: the k-th dead entry of tile b has rank (dead entries before the
-// tile) + k; dead entries below A receive the mover of their rank
+// tile) + k; dead entries below A receive the mover of their rank.  (One
+// warp per tile with four moves in flight per lane was measured slower: the
+// moves are bound by the scattered 32-byte sectors they write, not by the
+// latency of their loads.)
 template <class T>
 __global__ void __launch_bounds__(LT) k_tile_fill(SpeciesDev S, DevCtl *ctl, int s, const unsigned long long *blk,
                                                   const unsigned short *dl, const unsigned long long *movers) {
-    const unsigned long long n = ctl->count[s], A = ctl->alive[s], H = ctl->holes[s];
+    const unsigned long long n = tile_count(ctl, s), A = ctl->alive[s], H = ctl->holes[s];
     if (H == 0) return;
     const long long nfill = tiles_of(A);
     for (long long tile = blockIdx.x; tile < nfill; tile += gridDim.x) {
@@ -743,7 +774,7 @@ template <class K> static unsigned tile_grid(const qed_ctx *ctx, K kernel, long 
 // bound / 1024 + 2 block words and bound hole words (sfq_ensure_work).
 template <class T, bool LEVEL>
 qed_status compact_tiles_bounded(qed_ctx *ctx, qed_species *sp, int s, int64_t step, int64_t bound,
-                                 bool step_from_ctl) {
+                                 bool step_from_ctl, bool may_defer = false) {
     if (bound <= 0) return QED_OK;
     const int64_t nb = (bound + LTILE - 1) / LTILE;
     if (ctx->blk_cap < nb + 1 || ctx->slots_cap < bound) return QED_ERR_STATE;
@@ -755,7 +786,7 @@ qed_status compact_tiles_bounded(qed_ctx *ctx, qed_species *sp, int s, int64_t s
     cudaStream_t st = ctx->stream;
     k_tile_dead<T, LEVEL><<<tile_grid(ctx, k_tile_dead<T, LEVEL>, nb), LT, 0, st>>>(
         S, ctx->ctl, s, ctx->lev, philox_keys(ctx->cfg.seed), (unsigned)step, step_from_ctl ? 1 : 0, ctx->blk, dl);
-    k_scan_tiles<T><<<1, 1024, 0, st>>>(sp->w, ctx->blk, nb, ctx->ctl, s);
+    k_scan_tiles<T><<<1, 1024, 0, st>>>(sp->w, ctx->blk, nb, ctx->ctl, s, may_defer ? 1 : 0);
     k_tile_movers<T><<<tile_grid(ctx, k_tile_movers<T>, nb), LT, 0, st>>>(sp->w, ctx->ctl, s, ctx->blk, movers);
     k_tile_fill<T><<<tile_grid(ctx, k_tile_fill<T>, nb), LT, 0, st>>>(S, ctx->ctl, s, ctx->blk, dl, movers);
     k_set_count<<<1, 1, 0, st>>>(ctx->ctl, s);
@@ -765,17 +796,17 @@ qed_status compact_tiles_bounded(qed_ctx *ctx, qed_species *sp, int s, int64_t s
 }
 
 template <class T, bool LEVEL>
-qed_status compact_tiles(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
+qed_status compact_tiles(qed_ctx *ctx, qed_species *sp, int s, int64_t step, bool may_defer = false) {
     const int64_t n = sp->count;   // upper bound; kernels read the device count
     if (n <= 0) return QED_OK;
     qed_status e = sfq_ensure_work(ctx, (n + LTILE - 1) / LTILE + 1, n);
     if (e != QED_OK) return e;
-    return compact_tiles_bounded<T, LEVEL>(ctx, sp, s, step, n, false);
+    return compact_tiles_bounded<T, LEVEL>(ctx, sp, s, step, n, false, may_defer);
 }
 
 template <class T>
-qed_status compact_impl(qed_ctx *ctx, qed_species *sp, int s) {
-    return compact_tiles<T, false>(ctx, sp, s, 0);
+qed_status compact_impl(qed_ctx *ctx, qed_species *sp, int s, bool may_defer) {
+    return compact_tiles<T, false>(ctx, sp, s, 0, may_defer);
 }
 
 // The leveling iteration of one species as a CUDA graph: k_lev_begin, then
@@ -883,16 +914,16 @@ static bool lev_graph_launch(qed_ctx *ctx, const void *w, int s, long long cap, 
 // keep/drop fused with the first compaction pass.  sp->count must bound the
 // device count.
 template <class T>
-qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
+qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step, bool may_defer) {
     const int64_t cap = ctx->cfg.thin_cap;
     cudaStream_t st = ctx->stream;
     if (cap <= 0 || sp->count <= cap) return QED_OK;
     int blocks = ctx->sm_count * 4;
     blocks = blocks > LEVEL_MAX_BLOCKS ? LEVEL_MAX_BLOCKS : blocks;
-    if (lev_graph_launch<T>(ctx, sp->w, s, (long long)cap, blocks)) {
+    if (!ctx->cfg.profile && lev_graph_launch<T>(ctx, sp->w, s, (long long)cap, blocks)) {
         SFQ_LAUNCHED(ctx, 1);                    // k_lev_begin; the passes are counted on the device
         SFQ_CUDA(cudaGetLastError());
-        return compact_tiles<T, true>(ctx, sp, s, step);
+        return compact_tiles<T, true>(ctx, sp, s, step, may_defer);
     }
     k_lev_begin<<<1, 1, 0, st>>>(ctx->lev, s);
     SFQ_LAUNCHED(ctx, 1);
@@ -916,7 +947,7 @@ qed_status level_impl(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
     const int used = (int)ctx->pin[1];
     ctx->lev_chunk[s] = used < 2 ? 2 : (used > 12 ? 12 : used);
     SFQ_CUDA(cudaGetLastError());
-    return compact_tiles<T, true>(ctx, sp, s, step);
+    return compact_tiles<T, true>(ctx, sp, s, step, may_defer);
 }
 
 // ---- the merge step of a captured step graph ----
@@ -977,7 +1008,7 @@ qed_status capture_merge(qed_ctx *ctx, GraphBuild &gb, qed_species *sp, int s, b
     }
     cudaGraph_t cbody;
     if (gb.conditional(h_cmp, cudaGraphCondTypeIf, &cbody) != cudaSuccess) return QED_ERR_CUDA;
-    if (gb.capture(cbody, [&] { return compact_tiles_bounded<T, true>(ctx, sp, s, 0, sp->capacity, true); }) !=
+    if (gb.capture(cbody, [&] { return compact_tiles_bounded<T, true>(ctx, sp, s, 0, sp->capacity, true, true); }) !=
         cudaSuccess)
         return QED_ERR_CUDA;
     return QED_OK;
@@ -1002,6 +1033,7 @@ qed_status level_eval_impl(qed_ctx *ctx, qed_species *sp, int s, double w, doubl
     const unsigned long long n = (unsigned long long)sp->count;
     const unsigned zero = 0;
     SFQ_CUDA(cudaMemcpyAsync(&ctx->ctl->count[s], &n, sizeof n, cudaMemcpyHostToDevice, st));
+    SFQ_CUDA(cudaMemcpyAsync(&ctx->ctl->capacity[s], &n, sizeof n, cudaMemcpyHostToDevice, st));
     SFQ_CUDA(cudaMemcpyAsync(&ctx->lev->it[s], &h, sizeof h, cudaMemcpyHostToDevice, st));
     SFQ_CUDA(cudaMemcpyAsync(&ctx->lev->arrive[s], &zero, sizeof zero, cudaMemcpyHostToDevice, st));
     if (n > 0) {
@@ -1056,9 +1088,17 @@ qed_status sfq_capture_merge(qed_ctx *ctx, GraphBuild &gb, qed_species *sp, int 
     return capture_merge<double>(ctx, gb, sp, s, always_compact);
 }
 
-qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s) {
-    if (ctx->cfg.precision == QED_FP32) return compact_impl<float>(ctx, sp, s);
-    return compact_impl<double>(ctx, sp, s);
+// Removes every dead entry of the species, its count known only on the device
+// (bounded by the capacity): the end of a batch whose steps deferred moves.
+qed_status sfq_compact_pending(qed_ctx *ctx, qed_species *sp, int s) {
+    if (sp->capacity <= 0) return QED_OK;
+    if (ctx->cfg.precision == QED_FP32) return compact_tiles_bounded<float, false>(ctx, sp, s, 0, sp->capacity, false);
+    return compact_tiles_bounded<double, false>(ctx, sp, s, 0, sp->capacity, false);
+}
+
+qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s, bool may_defer) {
+    if (ctx->cfg.precision == QED_FP32) return compact_impl<float>(ctx, sp, s, may_defer);
+    return compact_impl<double>(ctx, sp, s, may_defer);
 }
 
 void sfq_level_graphs_free(qed_ctx *ctx) {
@@ -1068,9 +1108,9 @@ void sfq_level_graphs_free(qed_ctx *ctx) {
     }
 }
 
-qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step) {
-    if (ctx->cfg.precision == QED_FP32) return level_impl<float>(ctx, sp, s, step);
-    return level_impl<double>(ctx, sp, s, step);
+qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step, bool may_defer) {
+    if (ctx->cfg.precision == QED_FP32) return level_impl<float>(ctx, sp, s, step, may_defer);
+    return level_impl<double>(ctx, sp, s, step, may_defer);
 }
 
 qed_status sfq_level_eval(qed_ctx *ctx, qed_species *sp, int s, double w, double *A, int64_t *C, int64_t *N,

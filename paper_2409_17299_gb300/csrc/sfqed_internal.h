@@ -60,7 +60,8 @@ struct DevCtl {
     double sv_t_n;                      // current step: t_n = step * dt
     float sv_t_red_f;                   // current step: (t_n mod 2 pi) rounded to float
     unsigned sv_step;                   // current step index (Philox counter word 2)
-    unsigned long long pad[1];
+    unsigned long long deferred[3];     // dead entries left in place by the last merge step
+    unsigned long long pad[6];
 };
 
 // The current step's time as the pass kernels read it from the control
@@ -210,6 +211,7 @@ struct qed_ctx {
     int64_t async_next_step;     // step index following the last enqueued step
     double async_t0_ms;          // host clock when the batch opened
     void *step_graph;            // the captured PIC step (StepGraph, sfqed_push.cu) or null
+    int async_deferred;          // the open batch's steps may have left dead entries in place
     int step_graph_failed;       // conditional graph nodes unavailable: host-driven steps
     // surrogate network: FP32 master parameters, Adam moments and gradient
     // (4 x 8577 floats), BF16 copy used by the kernels, loss accumulator
@@ -297,9 +299,12 @@ struct GraphBuild {
 // the merge step of species s (leveling when its count exceeds the cap, dead
 // entries removed) appended to a step graph; decided on the device
 qed_status sfq_capture_merge(qed_ctx *ctx, GraphBuild &gb, qed_species *sp, int s, bool always_compact);
-qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s);
+// may_defer: the moves may be left for a later step (dead entries stay in
+// place while they are few; see k_scan_tiles)
+qed_status sfq_compact_species(qed_ctx *ctx, qed_species *sp, int s, bool may_defer = false);
+qed_status sfq_compact_pending(qed_ctx *ctx, qed_species *sp, int s);
 void sfq_level_graphs_free(qed_ctx *ctx);
-qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step);
+qed_status sfq_level_species(qed_ctx *ctx, qed_species *sp, int s, int64_t step, bool may_defer = false);
 qed_status sfq_level_eval(qed_ctx *ctx, qed_species *sp, int s, double w, double *A, int64_t *C, int64_t *N,
                           double *M);
 qed_status sfq_level_apply_species(qed_ctx *ctx, qed_species *sp, int s, double wstar, int64_t step);

@@ -445,9 +445,9 @@ static qed_status host_steps(qed_ctx *ctx, qed_particles *pw, PassArgs &a, doubl
                 const bool level = ctx->cfg.thin_cap > 0 && P.s[s].count > ctx->cfg.thin_cap;
                 const int64_t step = (int64_t)c.step_next - 1;
                 if (level) {
-                    e = timed_block(ctx, 3, [&] { return sfq_level_species(ctx, &P.s[s], s, step); });
+                    e = timed_block(ctx, 3, [&] { return sfq_level_species(ctx, &P.s[s], s, step, true); });
                 } else if (cascade && s == 2) {
-                    e = timed_block(ctx, 2, [&] { return sfq_compact_species(ctx, &P.s[2], 2); });
+                    e = timed_block(ctx, 2, [&] { return sfq_compact_species(ctx, &P.s[2], 2, true); });
                 }
                 if (e != QED_OK) return e;
             }
@@ -493,6 +493,7 @@ static qed_status open_batch(qed_ctx *ctx, qed_particles *p, int64_t step0) {
         if (e != QED_OK) return e;
     }
     ctx->async_p = *p;
+    ctx->async_deferred = 0;
     for (int s = 0; s < 3; ++s) ctx->async_count0[s] = p->s[s].count;
     ctx->async_next_step = step0;
     ctx->async_open = 1;
@@ -573,6 +574,7 @@ static qed_status enqueue_steps(qed_ctx *ctx, const qed_field_desc *field, doubl
     a.soft_filter = ctx->cfg.soft_photon_filter;
     a.record_newborn_tau = cascade ? 1 : 0;
 
+    ctx->async_deferred = 1;
     StepGraph *G = ctx->cfg.profile ? nullptr : step_graph_for<T>(ctx, a, p, dt);
     if (!G) return host_steps<T>(ctx, p, a, dt, nsteps);
     for (int it = 0; it < nsteps; ++it) SFQ_CUDA(cudaGraphLaunch(G->exec, ctx->stream));
@@ -584,6 +586,19 @@ static qed_status enqueue_steps(qed_ctx *ctx, const qed_field_desc *field, doubl
 // statistics, updates the counts of *p (or restores the state at the batch's
 // start after an overflow, with restore_on_overflow).
 static qed_status wait_batch(qed_ctx *ctx, qed_particles *p, qed_stats *out) {
+    if (ctx->async_deferred) {
+        // the steps may have left dead entries in place: remove them, so the
+        // counts returned hold live particles only (after a step that ran out
+        // of capacity nothing is moved)
+        ctx->async_deferred = 0;
+        for (int s = 0; s < 3; ++s) {
+            qed_status e = sfq_compact_pending(ctx, &ctx->async_p.s[s], s);
+            if (e != QED_OK) {
+                ctx->async_open = 0;
+                return e;
+            }
+        }
+    }
     qed_status e = read_ctl(ctx);
     ctx->async_open = 0;
     if (e != QED_OK) return e;

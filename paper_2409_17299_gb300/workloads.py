@@ -101,6 +101,24 @@ def standing_wave_cascade(n=1_000_000, seed=4, a0=2000.0, steps_per_period=100, 
                     thin_cap=thin_cap, seed=seed, notes={"n": n, "a0": a0})
 
 
+def paper_test_problem(n=250_000, seed=11, a0=1557.0, steps_per_period=200, periods=5, thin_cap=2_000_000):
+    """The paper's test problem (Sec. 5.1): seed electrons and positrons
+    (n / 2 each) at rest, uniformly filling the one-wavelength periodic box,
+    in the standing circularly polarised wave at the printed amplitude
+    6.25e15 V/m (a0 = 1557 in these units), dt = T/200, 5 periods, global
+    leveling at thin_cap per species (the paper does not print its cap)."""
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3)) * TWO_PI
+    pos[:, 0] -= math.pi                       # x in [-pi, pi): the electric antinode at the box centre
+    half = n // 2
+    z = np.zeros(n - half)
+    e = _ensemble(pos[:half, 0], pos[:half, 1], pos[:half, 2], np.zeros(half), np.zeros(half), np.zeros(half))
+    p = _ensemble(pos[half:, 0], pos[half:, 1], pos[half:, 2], z, z, z, id0=half)
+    return Workload("paper_test_problem", [e, p, _empty()], FIELD_STANDING_CP, [a0],
+                    TWO_PI / steps_per_period, steps_per_period * periods, push_photons=1,
+                    thin_cap=thin_cap, seed=seed, notes={"n": n, "a0": a0})
+
+
 GRID_SHAPE = (128, 4, 4)          # the paper's box: one wavelength, 128 x 4 x 4 cells (Sec. 5.1)
 
 
