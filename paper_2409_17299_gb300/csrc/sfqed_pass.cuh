@@ -248,7 +248,7 @@ constexpr int MLP_SMEM_BYTES = MLP_INF_BYTES;
 template <class T>
 __device__ __forceinline__ void finish(const PassArgs &a, unsigned idx, const T x[3], const T p[3], unsigned k) {
     const SpeciesDev &S = a.sp[idx >> 31];
-    const unsigned long long i = idx & 0x7FFFFFFFu;
+    const unsigned i = idx & 0x7FFFFFFFu;
     st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
     st<T>(S.px, i, p[0]); st<T>(S.py, i, p[1]); st<T>(S.pz, i, p[2]);
     if (k) S.nev[i] += k;
@@ -346,9 +346,10 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
     }
     __syncthreads();
     DevCtl *ctl = a.ctl;
-    const unsigned long long b0 = ctl->begin[0], n0 = ctl->end[0] - b0;
-    const unsigned long long b1 = ctl->begin[1], n1 = ctl->end[1] - b1;
-    const unsigned long long n = n0 + n1;
+    // 32-bit indices (a species holds fewer than 2^31 entries: bit 31 of idx names the species)
+    const unsigned b0 = (unsigned)ctl->begin[0], n0 = (unsigned)(ctl->end[0] - ctl->begin[0]);
+    const unsigned b1 = (unsigned)ctl->begin[1], n1 = (unsigned)(ctl->end[1] - ctl->begin[1]);
+    const unsigned n = n0 + n1;
     const LeptonCtx<T> c{a, ctl, s_coef, reinterpret_cast<const T *>(a.icdf_em), ctl->capacity[2], (T)(ALPHA * RS),
                          s_tm, time_phase<T, StepTime>(s_tm, 0.0)};
     unsigned long long my_steps = 0, my_ev = 0;
@@ -359,11 +360,11 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
     constexpr bool STAGE = FRESH && sizeof(T) == 4;
     constexpr int NF = STAGE ? 9 : 1, NT = STAGE ? LB : 1;
     __shared__ __align__(16) float stg[NF][NT];            // w x y z px py pz id(2 words)
-    const unsigned long long stride = (unsigned long long)gridDim.x * LB;
-    auto stage = [&](unsigned long long jj) {
+    const unsigned stride = gridDim.x * LB;
+    auto stage = [&](unsigned jj) {
         if constexpr (STAGE) {
             const int sp = jj < n0 ? 0 : 1;
-            const unsigned long long ii = sp == 0 ? b0 + jj : b1 + (jj - n0);
+            const unsigned ii = sp == 0 ? b0 + jj : b1 + (jj - n0);
             const SpeciesDev &P = a.sp[sp];
             const int t = threadIdx.x;
             cp_async4(&stg[0][t], reinterpret_cast<const float *>(P.w) + ii);
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
         }
     };
     if constexpr (STAGE) {
-        const unsigned long long j0 = (unsigned long long)blockIdx.x * LB + threadIdx.x;
+        const unsigned j0 = blockIdx.x * LB + threadIdx.x;
         if (j0 < n) stage(j0);
         cp_async_commit();
     }
@@ -388,10 +389,10 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
     // round (and the event arithmetic in it) then has a single inlined copy,
     // so which round processes a particle, which depends on the order of the
     // arrays, cannot change how its results are rounded.
-    unsigned long long base = (unsigned long long)blockIdx.x * LB;
+    unsigned base = blockIdx.x * LB;
     for (;;) {
         if (base < n && q.n < LB) {
-            const unsigned long long j = base + threadIdx.x;
+            const unsigned j = base + threadIdx.x;
             T w = (T)0, x[3], p[3];
             unsigned long long id = 0;
             if constexpr (STAGE) {
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
             }
             if (j < n) {
                 const int s = j < n0 ? 0 : 1;
-                const unsigned long long i = s == 0 ? b0 + j : b1 + (j - n0);
+                const unsigned i = s == 0 ? b0 + j : b1 + (j - n0);
                 const SpeciesDev &S = a.sp[s];
                 if constexpr (!STAGE) {
                     w = ld<T>(S.w, i);
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
                 }
                 if (w > (T)0) {
                     double tau = FRESH ? 0.0 : S.tau[i];
-                    const unsigned idx = (unsigned)i | ((unsigned)s << 31);
+                    const unsigned idx = i | ((unsigned)s << 31);
                     ++my_steps;
                     uint2 rz = make_uint2(0, 0);
                     const T qch = s == 0 ? (T)-1 : (T)1;
@@ -446,6 +447,54 @@ __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_le
     flush_stats(ctl, my_steps, my_ev, my_max, false, n64);
 }
 
+// Pair creation at a photon's event point x at clock tau (Sec. 3): chi there,
+// electron fraction from the inverse CDF with the draw words rz, both leptons
+// along the photon's direction with energy-conserving momenta, appended with
+// their ids and birth clock.  The caller removes the photon.
+template <class T>
+__device__ __forceinline__ void pair_create(const PassArgs &a, const StepTime &tm, const T *icdf, const T x[3],
+                                            const T kv[3], T k0, T nx, T ny, T nz, double tau, T w,
+                                            unsigned long long id, unsigned k, uint2 rz, unsigned &n64) {
+    DevCtl *ctl = a.ctl;
+    T E[3], B[3];
+    field_tau<T>(a, tm, x, tau, E, B);
+    const T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
+    T om, ue, ve;
+    Uniform<T>::draw(rz.x, rz.y, ue, ve);
+    const T delta = sample_pair<T>(icdf, chi, ue, ve, &om);
+    T em = delta * k0, ep = om * k0;
+    em = em < (T)1 ? (T)1 : em;
+    ep = ep < (T)1 ? (T)1 : ep;
+    const T pm = f_sqrt((em - (T)1) * (em + (T)1)), pp = f_sqrt((ep - (T)1) * (ep + (T)1));
+    const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, tm.step, k);
+    const unsigned long long se = warp_append(&ctl->count[0], 1);
+    const unsigned long long sp = warp_append(&ctl->count[1], 1);
+    if (se < ctl->capacity[0]) {
+        const SpeciesDev &P = a.sp[0];
+        st<T>(P.x, se, x[0]); st<T>(P.y, se, x[1]); st<T>(P.z, se, x[2]);
+        st<T>(P.px, se, pm * nx); st<T>(P.py, se, pm * ny); st<T>(P.pz, se, pm * nz);
+        st<T>(P.w, se, w);
+        P.id[se] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
+        P.nev[se] = 0u;
+        P.tau[se] = tau;
+        if (P.od) st<T>(P.od, se, (T)0);
+    } else {
+        note_overflow(ctl, 0, se);
+    }
+    if (sp < ctl->capacity[1]) {
+        const SpeciesDev &P = a.sp[1];
+        st<T>(P.x, sp, x[0]); st<T>(P.y, sp, x[1]); st<T>(P.z, sp, x[2]);
+        st<T>(P.px, sp, pp * nx); st<T>(P.py, sp, pp * ny); st<T>(P.pz, sp, pp * nz);
+        st<T>(P.w, sp, w);
+        P.id[sp] = (unsigned long long)rid.z | ((unsigned long long)rid.w << 32);
+        P.nev[sp] = 0u;
+        P.tau[sp] = tau;
+        if (P.od) st<T>(P.od, sp, (T)0);
+    } else {
+        note_overflow(ctl, 1, sp);
+    }
+}
+
 // Photon push: straight flight, pair creation at the event, the photon is
 // removed (weight 0) and the pair appended.
 template <class T, bool FRESH>
@@ -457,8 +506,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     __syncthreads();
     const StepTime &tm = s_tm;
     DevCtl *ctl = a.ctl;
-    const unsigned long long b = ctl->begin[2], n = ctl->end[2] - b;
-    const unsigned long long cap_e = ctl->capacity[0], cap_p = ctl->capacity[1];
+    // 32-bit indices (a species holds fewer than 2^31 entries)
+    const unsigned b = (unsigned)ctl->begin[2], n = (unsigned)(ctl->end[2] - ctl->begin[2]);
     const T *icdf = reinterpret_cast<const T *>(a.icdf_pair);
     const T alpha_r = (T)(ALPHA * RS);
     const SpeciesDev &S = a.sp[2];
@@ -470,10 +519,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     constexpr bool STAGE = FRESH && sizeof(T) == 4;
     constexpr int NB = STAGE ? 2 : 1, NF = STAGE ? 9 : 1, NT = STAGE ? LB : 1;
     __shared__ __align__(16) float stg[NB][NF][NT];       // w x y z kx ky kz id(2 words)
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    auto stage = [&](unsigned long long jj, int buf) {
+    const unsigned stride = gridDim.x * blockDim.x;
+    auto stage = [&](unsigned jj, int buf) {
         if constexpr (STAGE) {
-            const unsigned long long ii = b + jj;
+            const unsigned ii = b + jj;
             const int t = threadIdx.x;
             cp_async4(&stg[buf][0][t], reinterpret_cast<const float *>(S.w) + ii);
             cp_async4(&stg[buf][1][t], reinterpret_cast<const float *>(S.x) + ii);
@@ -486,14 +535,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
             cp_async4(&stg[buf][8][t], reinterpret_cast<const unsigned *>(S.id + ii) + 1);
         }
     };
-    const unsigned long long j0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned j0 = blockIdx.x * blockDim.x + threadIdx.x;
     if constexpr (STAGE) {
         if (j0 < n) stage(j0, 0);
         cp_async_commit();
     }
     int buf = 0;
-    for (unsigned long long j = j0; j < n; j += stride, buf ^= 1) {
-        const unsigned long long i = b + j;
+    for (unsigned j = j0; j < n; j += stride, buf ^= 1) {
+        const unsigned i = b + j;
         T w, x[3], kx, ky, kz;
         unsigned long long id;
         if constexpr (STAGE) {
@@ -559,42 +608,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
                 x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
                 if constexpr (FRESH) tau = (double)dth;
                 else tau += (double)dth;
-                field_tau<T>(a, tm, x, tau, E, B);
-                chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
-                T om, ue, ve;
-                Uniform<T>::draw(r.z, r.w, ue, ve);
-                const T delta = sample_pair<T>(icdf, chi, ue, ve, &om);
-                T em = delta * k0, ep = om * k0;
-                em = em < (T)1 ? (T)1 : em;
-                ep = ep < (T)1 ? (T)1 : ep;
-                const T pm = f_sqrt((em - (T)1) * (em + (T)1)), pp = f_sqrt((ep - (T)1) * (ep + (T)1));
-                const uint4 rid = event_draw(a.seed ^ CHILD_KEY_XOR, id, tm.step, k);
-                const unsigned long long se = warp_append(&ctl->count[0], 1);
-                const unsigned long long sp = warp_append(&ctl->count[1], 1);
-                if (se < cap_e) {
-                    const SpeciesDev &P = a.sp[0];
-                    st<T>(P.x, se, x[0]); st<T>(P.y, se, x[1]); st<T>(P.z, se, x[2]);
-                    st<T>(P.px, se, pm * nx); st<T>(P.py, se, pm * ny); st<T>(P.pz, se, pm * nz);
-                    st<T>(P.w, se, w);
-                    P.id[se] = (unsigned long long)rid.x | ((unsigned long long)rid.y << 32);
-                    P.nev[se] = 0u;
-                    P.tau[se] = tau;
-                    if (P.od) st<T>(P.od, se, (T)0);
-                } else {
-                    note_overflow(ctl, 0, se);
-                }
-                if (sp < cap_p) {
-                    const SpeciesDev &P = a.sp[1];
-                    st<T>(P.x, sp, x[0]); st<T>(P.y, sp, x[1]); st<T>(P.z, sp, x[2]);
-                    st<T>(P.px, sp, pp * nx); st<T>(P.py, sp, pp * ny); st<T>(P.pz, sp, pp * nz);
-                    st<T>(P.w, sp, w);
-                    P.id[sp] = (unsigned long long)rid.z | ((unsigned long long)rid.w << 32);
-                    P.nev[sp] = 0u;
-                    P.tau[sp] = tau;
-                    if (P.od) st<T>(P.od, sp, (T)0);
-                } else {
-                    note_overflow(ctl, 1, sp);
-                }
+                pair_create<T>(a, tm, icdf, x, kv, k0, nx, ny, nz, tau, w, id, k, make_uint2(r.z, r.w), n64);
                 w = (T)0;       // the photon is eliminated
                 k = 1;
                 }

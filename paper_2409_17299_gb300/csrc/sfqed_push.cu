@@ -152,6 +152,7 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 static qed_status check_species(const qed_species &s) {
     const void *ptrs[] = {s.x, s.y, s.z, s.px, s.py, s.pz, s.w, s.id, s.nevents};
     if (s.capacity < 0 || s.count < 0 || s.count > s.capacity) return QED_ERR_INVALID;
+    if (s.capacity >= (int64_t)1 << 31) return QED_ERR_INVALID;   // the pass kernels index in 31 bits
     if (s.capacity == 0) return QED_OK;
     for (const void *q : ptrs)
         if (!q || !aligned16(q)) return QED_ERR_INVALID;
