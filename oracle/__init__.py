@@ -109,6 +109,8 @@ def lib():
                 "or_mlp_nparams": (i32, []),
                 "or_mlp_forward": (None, [p, i64, p, p]),
                 "or_mlp_loss_grad": (d, [p, i64, p, p, p]),
+                "or_mlp_forward_q": (None, [p, i64, p, p]),
+                "or_mlp_loss_grad_q": (d, [p, i64, p, p, p]),
                 "or_mlp_features": (None, [d, d, p]),
                 "or_mlp_delta": (d, [d, d, p]),
             }
@@ -443,20 +445,25 @@ def mlp_nparams() -> int:
     return lib().or_mlp_nparams()
 
 
-def mlp_forward(params, feat) -> np.ndarray:
+def mlp_forward(params, feat, bf16_storage=False) -> np.ndarray:
+    """Network output; bf16_storage: hidden activations stored as bfloat16."""
     P = np.ascontiguousarray(params, dtype=np.float64)
     F = np.ascontiguousarray(feat, dtype=np.float64).reshape(-1, 2)
     y = np.zeros(F.shape[0])
-    lib().or_mlp_forward(_ptr(P), F.shape[0], _ptr(F), _ptr(y))
+    f = lib().or_mlp_forward_q if bf16_storage else lib().or_mlp_forward
+    f(_ptr(P), F.shape[0], _ptr(F), _ptr(y))
     return y
 
 
-def mlp_loss_grad(params, feat, target):
+def mlp_loss_grad(params, feat, target, bf16_storage=False):
+    """Mean squared error and its gradient; bf16_storage: activations and
+    back-propagated deltas stored as bfloat16."""
     P = np.ascontiguousarray(params, dtype=np.float64)
     F = np.ascontiguousarray(feat, dtype=np.float64).reshape(-1, 2)
     T = np.ascontiguousarray(target, dtype=np.float64)
     g = np.zeros_like(P)
-    loss = lib().or_mlp_loss_grad(_ptr(P), F.shape[0], _ptr(F), _ptr(T), _ptr(g))
+    f = lib().or_mlp_loss_grad_q if bf16_storage else lib().or_mlp_loss_grad
+    loss = f(_ptr(P), F.shape[0], _ptr(F), _ptr(T), _ptr(g))
     return loss, g
 
 

@@ -1261,8 +1261,26 @@ static double or_dsilu(double z) { double s = 1.0 / (1.0 + exp(-z)); return s * 
 
 int or_mlp_nparams(void) { return OR_MLP_NP; }
 
-/* one sample: pre-activations z1..z3 and activations h1..h3 */
-static double mlp_one(const double *P, const double f[2], double z[3][OR_MLP_H], double h[3][OR_MLP_H])
+/* The storage rounding of a network that keeps its hidden activations and
+   back-propagated deltas as bfloat16: the value rounded to single precision,
+   then to bfloat16 (8 significand bits, nearest, ties to even).  qz = 0 is
+   the exact network (no rounding). */
+static double or_q(double v, int qz)
+{
+    if (!qz) return v;
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+        memcpy(&f, &u, sizeof f);
+    }
+    return (double)f;
+}
+
+/* one sample: pre-activations z1..z3 and activations h1..h3 (activations
+   stored with the rounding qz) */
+static double mlp_one_r(const double *P, const double f[2], double z[3][OR_MLP_H], double h[3][OR_MLP_H], int qz)
 {
     const double *W1 = P, *b1 = W1 + 2 * OR_MLP_H;
     const double *W2 = b1 + OR_MLP_H, *b2 = W2 + OR_MLP_H * OR_MLP_H;
@@ -1270,33 +1288,64 @@ static double mlp_one(const double *P, const double f[2], double z[3][OR_MLP_H],
     const double *W4 = b3 + OR_MLP_H, *b4 = W4 + OR_MLP_H;
     for (int o = 0; o < OR_MLP_H; ++o) {
         z[0][o] = W1[2 * o] * f[0] + W1[2 * o + 1] * f[1] + b1[o];
-        h[0][o] = or_silu(z[0][o]);
+        h[0][o] = or_q(or_silu(z[0][o]), qz);
     }
     for (int o = 0; o < OR_MLP_H; ++o) {
         double s = b2[o];
         for (int i = 0; i < OR_MLP_H; ++i) s += W2[o * OR_MLP_H + i] * h[0][i];
         z[1][o] = s;
-        h[1][o] = or_silu(s);
+        h[1][o] = or_q(or_silu(s), qz);
     }
     for (int o = 0; o < OR_MLP_H; ++o) {
         double s = b3[o];
         for (int i = 0; i < OR_MLP_H; ++i) s += W3[o * OR_MLP_H + i] * h[1][i];
         z[2][o] = s;
-        h[2][o] = or_silu(s);
+        h[2][o] = or_q(or_silu(s), qz);
     }
     double y = b4[0];
     for (int i = 0; i < OR_MLP_H; ++i) y += W4[i] * h[2][i];
     return y;
 }
 
-void or_mlp_forward(const double *P, int64_t n, const double *feat /* n x 2 */, double *y)
+static double mlp_one(const double *P, const double f[2], double z[3][OR_MLP_H], double h[3][OR_MLP_H])
+{
+    return mlp_one_r(P, f, z, h, 0);
+}
+
+static void mlp_forward_r(const double *P, int64_t n, const double *feat, double *y, int qz)
 {
     double z[3][OR_MLP_H], h[3][OR_MLP_H];
-    for (int64_t k = 0; k < n; ++k) y[k] = mlp_one(P, feat + 2 * k, z, h);
+    for (int64_t k = 0; k < n; ++k) y[k] = mlp_one_r(P, feat + 2 * k, z, h, qz);
 }
+
+void or_mlp_forward(const double *P, int64_t n, const double *feat /* n x 2 */, double *y)
+{
+    mlp_forward_r(P, n, feat, y, 0);
+}
+
+/* The network with bfloat16 storage of its activations (as a kernel that
+   stores them in that format computes it). */
+void or_mlp_forward_q(const double *P, int64_t n, const double *feat, double *y)
+{
+    mlp_forward_r(P, n, feat, y, 1);
+}
+
+static double mlp_loss_grad_r(const double *P, int64_t n, const double *feat, const double *t, double *g, int qz);
 
 /* loss = mean_k (y_k - t_k)^2; g = d loss / d P */
 double or_mlp_loss_grad(const double *P, int64_t n, const double *feat, const double *t, double *g)
+{
+    return mlp_loss_grad_r(P, n, feat, t, g, 0);
+}
+
+/* The same with bfloat16 storage of the activations h1..h3 and of the
+   back-propagated deltas d3, d2, d1 (the products and sums stay exact). */
+double or_mlp_loss_grad_q(const double *P, int64_t n, const double *feat, const double *t, double *g)
+{
+    return mlp_loss_grad_r(P, n, feat, t, g, 1);
+}
+
+static double mlp_loss_grad_r(const double *P, int64_t n, const double *feat, const double *t, double *g, int qz)
 {
     const double *W1 = P, *b1 = W1 + 2 * OR_MLP_H;
     const double *W2 = b1 + OR_MLP_H, *b2 = W2 + OR_MLP_H * OR_MLP_H;
@@ -1312,14 +1361,14 @@ double or_mlp_loss_grad(const double *P, int64_t n, const double *feat, const do
     double z[3][OR_MLP_H], h[3][OR_MLP_H], d3[OR_MLP_H], d2[OR_MLP_H], d1[OR_MLP_H];
     for (int64_t k = 0; k < n; ++k) {
         const double *f = feat + 2 * k;
-        double y = mlp_one(P, f, z, h);
+        double y = mlp_one_r(P, f, z, h, qz);
         double r = y - t[k];
         loss += r * r;
         double dy = 2.0 * r / (double)n;
         gb4[0] += dy;
         for (int i = 0; i < OR_MLP_H; ++i) {
             gW4[i] += dy * h[2][i];
-            d3[i] = dy * W4[i] * or_dsilu(z[2][i]);
+            d3[i] = or_q(dy * W4[i] * or_dsilu(z[2][i]), qz);
         }
         for (int o = 0; o < OR_MLP_H; ++o) {
             gb3[o] += d3[o];
@@ -1328,7 +1377,7 @@ double or_mlp_loss_grad(const double *P, int64_t n, const double *feat, const do
         for (int i = 0; i < OR_MLP_H; ++i) {
             double s = 0.0;
             for (int o = 0; o < OR_MLP_H; ++o) s += W3[o * OR_MLP_H + i] * d3[o];
-            d2[i] = s * or_dsilu(z[1][i]);
+            d2[i] = or_q(s * or_dsilu(z[1][i]), qz);
         }
         for (int o = 0; o < OR_MLP_H; ++o) {
             gb2[o] += d2[o];
@@ -1337,7 +1386,7 @@ double or_mlp_loss_grad(const double *P, int64_t n, const double *feat, const do
         for (int i = 0; i < OR_MLP_H; ++i) {
             double s = 0.0;
             for (int o = 0; o < OR_MLP_H; ++o) s += W2[o * OR_MLP_H + i] * d2[o];
-            d1[i] = s * or_dsilu(z[0][i]);
+            d1[i] = or_q(s * or_dsilu(z[0][i]), qz);
         }
         for (int o = 0; o < OR_MLP_H; ++o) {
             gb1[o] += d1[o];

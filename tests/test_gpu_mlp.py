@@ -75,6 +75,93 @@ def test_gradient_matches_oracle():
     g.close()
 
 
+def _exact_case(seed, n):
+    """Weights and features exactly representable in bfloat16."""
+    P = bf16_round(_params(seed))
+    rng = np.random.default_rng(seed + 100)
+    feat = bf16_round(rng.uniform(-1, 1, size=(n, 2)).astype(np.float32))
+    tgt = rng.normal(size=n).astype(np.float32)
+    return P, feat, tgt
+
+
+def test_forward_bf16_storage_matches_oracle():
+    """Weights and inputs exact in bfloat16: the kernels' forward pass against
+    the oracle's network with the same bfloat16 storage of the activations.
+    What remains is FP32 accumulation and the hardware exponential, which
+    move an activation across a bfloat16 rounding boundary only rarely."""
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    P, feat, _ = _exact_case(10, 4096)
+    q.qed_mlp_set_params(g.ctx, P)
+    df = torch.from_numpy(feat).cuda()
+    y = torch.empty(len(feat), dtype=torch.float32, device="cuda")
+    q.qed_mlp_forward(g.ctx, df.data_ptr(), len(feat), y.data_ptr())
+    got = y.cpu().numpy().astype(np.float64)
+    want = oracle.mlp_forward(P.astype(np.float64), feat.astype(np.float64), bf16_storage=True)
+    err = np.abs(got - want) / max(1.0, np.abs(want).max())
+    assert np.median(err) < 1e-5 and np.quantile(err, 0.99) < 1e-3 and err.max() < 1e-2, \
+        (np.median(err), np.quantile(err, 0.99), err.max())
+    g.close()
+
+
+def test_gradient_bf16_storage_matches_oracle():
+    """Weights and inputs exact in bfloat16: every parameter block of the
+    gradient within 1e-3 (relative norm) of the oracle's gradient of the
+    network with the same bfloat16 storage of activations and deltas, the
+    loss within 1e-4.  A wrong term in any layer's backward pass (say a
+    SiLU derivative) is far outside this bound."""
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    P, feat, tgt = _exact_case(11, 4096)
+    q.qed_mlp_set_params(g.ctx, P)
+    dfeat, dtgt = torch.from_numpy(feat).cuda(), torch.from_numpy(tgt).cuda()
+    grad, loss = q.qed_mlp_grad(g.ctx, dfeat.data_ptr(), dtgt.data_ptr(), len(feat))
+    oloss, ograd = oracle.mlp_loss_grad(P.astype(np.float64), feat.astype(np.float64), tgt.astype(np.float64),
+                                        bf16_storage=True)
+    assert loss == pytest.approx(oloss, rel=1e-4)
+    blocks = [(0, 128), (128, 192), (192, 4288), (4288, 4352), (4352, 8448), (8448, 8512), (8512, 8576), (8576, 8577)]
+    rel = {}
+    for a, b in blocks:
+        rel[(a, b)] = np.linalg.norm(grad[a:b] - ograd[a:b]) / max(np.linalg.norm(ograd[a:b]), 1e-30)
+    assert max(rel.values()) < 1e-3, rel
+    g.close()
+
+
+def test_gradient_against_gpu_finite_differences():
+    """The kernels' gradient against central differences of the kernels'
+    own forward pass: moving a few parameters of every layer at once (four
+    draws), (L(P+) - L(P-)) equals the gradient dotted with the difference
+    of the bfloat16 weights actually applied (P+ and P- rounded as the
+    kernels round them), within 3%."""
+    g = q.Generator(q.make_config(precision=q.QED_FP32))
+    P, feat, tgt = _exact_case(12, 2048)
+    dfeat, dtgt = torch.from_numpy(feat).cuda(), torch.from_numpy(tgt).cuda()
+    q.qed_mlp_set_params(g.ctx, P)
+    grad, _ = q.qed_mlp_grad(g.ctx, dfeat.data_ptr(), dtgt.data_ptr(), len(feat))
+    y = torch.empty(len(feat), dtype=torch.float32, device="cuda")
+
+    def loss(params):
+        q.qed_mlp_set_params(g.ctx, params)
+        q.qed_mlp_forward(g.ctx, dfeat.data_ptr(), len(feat), y.data_ptr())
+        return float(np.mean((y.cpu().numpy().astype(np.float64) - tgt) ** 2))
+    rng = np.random.default_rng(13)
+    blocks = [(0, 128), (128, 192), (192, 4288), (4288, 4352), (4352, 8448), (8448, 8512), (8512, 8576)]
+    for trial in range(4):
+        # a few parameters of every block (drawn among those with a sizeable
+        # gradient), each moved by 2% along its gradient's sign: large enough
+        # that bfloat16 rounding of the activations stays small against the
+        # first-order change, small enough that higher orders do too (the
+        # oracle's network with the same storage: within 1.2% at this step)
+        v = np.zeros_like(P)
+        for a, b in blocks:
+            cand = a + np.argsort(-np.abs(grad[a:b]))[: max(4, (b - a) // 8)]
+            pick = rng.choice(cand, size=min(6, len(cand)), replace=False)
+            v[pick] = 0.02 * np.sign(grad[pick]) * np.maximum(np.abs(P[pick]), 0.05)
+        Pp, Pm = bf16_round(P + v), bf16_round(P - v)
+        fd = loss(Pp) - loss(Pm)
+        lin = float(grad.astype(np.float64) @ (Pp.astype(np.float64) - Pm.astype(np.float64)))
+        assert abs(fd - lin) < 0.03 * abs(lin), (fd, lin)
+    g.close()
+
+
 @pytest.fixture(scope="module")
 def trained_params():
     g = q.Generator(q.make_config(precision=q.QED_FP32))
