@@ -333,6 +333,10 @@ __device__ __forceinline__ void stack_round(const LeptonCtx<T> &c, LeptonStack<T
 
 template <class T, bool FRESH, bool MLP>
 __global__ void __launch_bounds__(LB, (sizeof(T) == 4 ? (MLP ? 2 : 4) : 1)) k_lepton_pass(PassArgs a) {
+    // blocks past the pass's range leave before staging anything (a newborn
+    // pass is often far smaller than the resident grid)
+    if ((unsigned long long)blockIdx.x * LB >= (a.ctl->end[0] - a.ctl->begin[0]) + (a.ctl->end[1] - a.ctl->begin[1]))
+        return;
     __shared__ __align__(16) T s_coef[RateWords<T>::N];
     __shared__ LeptonStack<T> q;
     __shared__ StepTime s_tm;
@@ -499,6 +503,7 @@ __device__ __forceinline__ void pair_create(const PassArgs &a, const StepTime &t
 // removed (weight 0) and the pair appended.
 template <class T, bool FRESH>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(PassArgs a) {
+    if ((unsigned long long)blockIdx.x * blockDim.x >= a.ctl->end[2] - a.ctl->begin[2]) return;   // no photon here
     __shared__ __align__(16) T s_coef[RateWords<T>::N];
     __shared__ StepTime s_tm;
     for (int i = threadIdx.x; i < RateWords<T>::N; i += blockDim.x) s_coef[i] = reinterpret_cast<const T *>(a.coef)[i];
