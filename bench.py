@@ -62,6 +62,10 @@ NCU_LEPTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
 # per lepton-step), from one ncu capture of the current kernels
 # (profiles/fp64_passes_rotating_e_cascade.md)
 NCU_FP64_FLOP_PER_STEP = {"k_lepton_pass": 478.0, "k_photon_pass": 193.0}
+# algorithmic FLOPs per training sample of the 2-64-64-64-1 network: forward
+# 2 x (2*64 + 64*64 + 64*64 + 64) multiply-adds, backward the two 64x64 input
+# gradients, the two 64x64 weight gradients, W1's and W4's gradients
+MLP_TRAIN_FLOP_PER_SAMPLE = 2 * (2 * 64 + 64 * 64 + 64 * 64 + 64) + 2 * (4 * 64 * 64 + 2 * 64 + 64)
 
 
 def parse():
@@ -712,7 +716,17 @@ def main():
                "events_per_s": (tot_m["emit_events"] + tot_m["pair_events"]) / (ms_m / 1e3),
                "ms_per_step": ms_m / steps,
                "train_samples": int(args.mlp_samples), "train_seconds": train_s, "train_final_mse": loss,
-               "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation (mma.sync)"}
+               "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation; training on tcgen05.mma with "
+                          "tensor-memory accumulators (one cooperative launch), inference inside the lepton "
+                          "pass on mma.sync"}
+        bf16_peak = peaks.get("bf16_tflops")
+        ach = MLP_TRAIN_FLOP_PER_SAMPLE * int(args.mlp_samples) / train_s / 1e12
+        mlp["train_roofline"] = {
+            "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": ach / bf16_peak if bf16_peak else None,
+            "peak_source": "measured bf16_tflops (burst)" if bf16_peak else None,
+            "flop_per_sample": MLP_TRAIN_FLOP_PER_SAMPLE,
+            "achieved_is": "algorithmic FLOPs of the matrix products x samples / wall time of the training call"}
 
     growth = None
     if args.growth and world == 1 and args.workload == "rotating_e_cascade":

@@ -260,9 +260,15 @@ qed_status qed_batch_shape(qed_ctx *ctx, int *threads, int *step_budget);
 
 /* Train on n_samples draws (log10 chi uniform on [-3, 3], u uniform) labelled
  * by the emission table, in batches of `batch` (a multiple of 128): forward
- * and backward passes on the tensor cores, Adam, learning rate decaying from
- * lr to lr/100 (cosine).  *final_loss (may be NULL): mean squared error over
- * the last 16 batches. */
+ * and backward passes on the tensor cores (tcgen05, accumulators in tensor
+ * memory), Adam, learning rate decaying from lr to lr/100 (cosine).  Every
+ * step runs inside one cooperative launch (one CTA per SM at most, a grid
+ * barrier per step); the call allocates its scratch, blocks until the
+ * launch ends and frees it.  *final_loss (may be NULL): mean squared error
+ * over the last 16 batches.  QED_ERR_TIMEOUT if a grid barrier or a
+ * tensor-core wait inside the launch ran out (bounded waits); the
+ * parameters are then left as they were before the call's first step
+ * (the freshly initialised network). */
 qed_status qed_train_surrogate(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed,
                                double *final_loss);
 
@@ -276,7 +282,9 @@ qed_status qed_mlp_forward(qed_ctx *ctx, const float *feat_dev, int64_t n, float
 
 /* Gradient of the mean squared error (1/n) sum (y - target)^2 over n given
  * samples, without updating anything (grad: host array of 8577 floats;
- * *loss may be NULL). */
+ * *loss may be NULL).  Same kernel as the training, one pass over the
+ * samples; activations and deltas are rounded to BF16 where the products
+ * read them, as in the training. */
 qed_status qed_mlp_grad(qed_ctx *ctx, const float *feat_dev, const float *target_dev, int64_t n,
                         float *grad, double *loss);
 

@@ -4,34 +4,83 @@
 // FP32 accumulation) maps (log10(chi)/3, logit(u)/16) to zeta/16 + 1/2, where
 // zeta = ln y is what the emission table stores (y = 2 d / (3 chi (1-d))).
 // It is trained on samples drawn from the table method itself; the table is
-// kept as the fallback outside the trained range.  Training: one block per
-// 128 samples, forward and backward through the 64 x 64 layers on the
-// tensor cores (mma.sync BF16), gradients accumulated in FP32, then Adam.
+// kept as the fallback outside the trained range.  Training (k_mlp_train
+// below): forward and backward products of 128-sample tiles on the tcgen05
+// tensor cores with accumulators in tensor memory, gradients summed in FP32,
+// Adam, all steps in one cooperative launch.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "sfqed_device.cuh"
 #include "sfqed_internal.h"
 #include "sfqed_mma.cuh"
+#include "sfqed_tc.cuh"
 
 namespace sfq {
 namespace {
 
-constexpr int TB = 128;                   // samples (threads) per training block
-constexpr int TR_SMEM = 3 * TB * MLP_H * 4 + 4 * TB * MLP_H * 2 + MLP_NP * 2 + TB * 3 * 4 + 64;
+// ---- training on the tensor cores (tcgen05, accumulators in tensor memory)
+//
+// One persistent cooperative kernel runs every optimizer step.  A CTA holds
+// 128 samples at a time (one per thread and tensor-memory lane) and keeps,
+// in shared memory, its own copy of the FP32 parameters and Adam moments:
+// every CTA applies the same Adam update to the same summed gradient, so
+// the copies stay identical and one grid barrier per step suffices.
+//
+// Per tile of 128 samples (B = BF16 storage, as in the network the oracle
+// defines; Z and dy stay FP32):
+//   Z2 = H1 W2^T, Z3 = H2 W3^T           M=128 N=64 K=64   (tensor memory)
+//   P3 = D3 W3,   P2 = D2 W2             M=128 N=64 K=64
+//   G1 = [D3;D2]^T-stacked x [H2;H1;1]   M=128 N=144 K=128: dW3, dW2, db3, db2
+//   G2 = [D1;H3]   x [f0 hi/lo, f1 hi/lo, 1, dy hi/lo]
+//                                        M=128 N=16 K=128: dW1, db1, dW4
+// Layer 1 (2 -> 64) and layer 4 (64 -> 1) run on the CUDA cores; Z1 is
+// recomputed from the features rather than stored, Z2 stays in tensor
+// memory until the backward pass needs it.  G1 and G2 accumulate over the
+// CTA's tiles of a step and are added to the step's gradient sum with
+// vector atomics.  Features and dy enter G2 as BF16 hi + lo pairs, so the
+// BF16 operand rounding leaves them exact to about 2^-17.
+constexpr int TT = 128;                       // samples per tile = threads = tensor-memory lanes
+constexpr int GSTRIDE = 8580;                 // MLP_NP rounded up to whole float4s
+// shared memory (bytes).  Activation / delta tiles: 128 samples x 64 units
+// in core matrices of 8 samples x 8 units; unit block j at j x 2048, sample
+// r at r x 16.  Weight tiles W[o][i]: (o/8) x 1024 + (i/8) x 128.
+constexpr int SM_W2 = 0, SM_W3 = 8192;
+constexpr int SM_D3 = 16384, SM_D2 = SM_D3 + 16384;                       // [D3; D2]
+constexpr int SM_H2 = SM_D2 + 16384, SM_H1 = SM_H2 + 16384;               // [H2; H1; ones; zero]
+constexpr int SM_ONES = SM_H1 + 16384, SM_ZERO = SM_ONES + 2048;
+constexpr int SM_FB = SM_ZERO + 2048, SM_D1 = SM_FB + 2048, SM_H3 = SM_D1 + 16384;   // [FB; D1], [D1; H3]
+constexpr int SM_P = SM_H3 + 16384, SM_M = SM_P + GSTRIDE * 4, SM_V = SM_M + GSTRIDE * 4;
+constexpr int SM_WQ = SM_V + GSTRIDE * 4;                                 // BF16-rounded W1, biases, W4 (MLP_F_*)
+constexpr int SM_MISC = SM_WQ + 388 * 4;
+constexpr int TR_SMEM = SM_MISC + 64;
+static_assert(SM_MISC % 8 == 0, "mbarrier alignment");
+static_assert(TR_SMEM <= 227 * 1024, "shared memory");
+// tensor-memory columns
+constexpr uint32_t TM_COLS = 512, TZ2 = 0, TZ3 = 64, TG1 = 128, TG2 = 288;
+constexpr uint32_t WAIT_POLLS = 1u << 22, BAR_POLLS = 1u << 22;
+// instruction descriptors: forward (A, B K-major), backward (B MN-major), gradients
+constexpr uint32_t ID_FWD = tc::idesc_bf16(128, 64, 0, 0), ID_BWD = tc::idesc_bf16(128, 64, 0, 1);
+constexpr uint32_t ID_G1 = tc::idesc_bf16(128, 144, 1, 1), ID_G2 = tc::idesc_bf16(128, 16, 1, 1);
 
 struct TrainArgs {
-    const __nv_bfloat16 *W16;
-    float *grad;
-    float *loss;                          // accumulated sum of squared errors
-    const float *icdf_em32;               // target generator (the table method)
-    const float *feat;                    // given features (n x 2), or null: draw them
-    const float *target;                  // given targets, or null: from the table
+    float *P, *M, *V;                         // parameters and moments (read at start, written back at the end)
+    float *gbuf;                              // three gradient sums of GSTRIDE floats (zero at launch); the gradient
+    __nv_bfloat16 *W16;
+    float *loss;                              // sum of squared errors of the counted steps
+    const float *icdf_em32;                   // target generator (the table method)
+    const float *feat, *target;               // given samples, or null: draw them
+    const float *sched;                       // per step: learning rate, bias corrections 1 and 2
     unsigned long long seed;
-    unsigned long long sample0;
-    long long n;                          // samples in this launch
-    float inv_total;                      // 1 / samples per optimizer step
+    long long per_step;                       // samples per step (the batch), or the given samples
+    long long steps;                          // optimizer steps; 0: one gradient, no update
+    long long tail_from;                      // steps from here on add to *loss
+    float inv_total;                          // 1 / per_step
+    unsigned *bar;                            // grid-barrier arrivals (zero at launch)
+    int *status;                              // 0 ok, 1 a barrier wait ran out, 2 an MMA wait ran out
 };
 
 // table target for (log10 chi, logit u) in the FP32 table's own arithmetic
@@ -41,161 +90,325 @@ __device__ __forceinline__ float table_zeta(const float *tab, float lc, float s)
     return bilinear(tab, EM_NCHI, EM_NS, c, t);
 }
 
-__global__ void __launch_bounds__(TB) k_mlp_train(TrainArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    float *Z1 = reinterpret_cast<float *>(sm);
-    float *Z2 = Z1 + TB * MLP_H;
-    float *Z3 = Z2 + TB * MLP_H;
-    __nv_bfloat16 *H1 = reinterpret_cast<__nv_bfloat16 *>(Z3 + TB * MLP_H);
-    __nv_bfloat16 *H2 = H1 + TB * MLP_H;
-    __nv_bfloat16 *H3 = H2 + TB * MLP_H;
-    __nv_bfloat16 *D = H3 + TB * MLP_H;
-    __nv_bfloat16 *W = D + TB * MLP_H;
-    float *F = reinterpret_cast<float *>(W + MLP_NP + (MLP_NP & 1));
-    float *DY = F + 2 * TB;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    for (int i = tid; i < MLP_NP; i += TB) W[i] = a.W16[i];
-    const long long idx = (long long)blockIdx.x * TB + tid;
-    const bool live = idx < a.n;
-    float f0 = 0.f, f1 = 0.f, ty = 0.f;
-    if (live) {
-        if (a.feat) {
-            f0 = a.feat[2 * idx];
-            f1 = a.feat[2 * idx + 1];
-            ty = a.target[idx];
-        } else {
-            const unsigned long long g = a.sample0 + (unsigned long long)idx;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), 0u, 0x4D4C5000u),
-                                          make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32)));
-            float u1, v1, u2, v2;
-            Uniform<float>::draw(r.x, r.y, u1, v1);
-            Uniform<float>::draw(r.z, r.w, u2, v2);
-            const float lc = -3.0f + 6.0f * u1;
-            float s = logit(u2, v2);
-            s = fminf(fmaxf(s, -16.0f), 16.0f);
-            f0 = lc / 3.0f;
-            f1 = s / 16.0f;
-            ty = table_zeta(a.icdf_em32, lc, s) / 16.0f + 0.5f;
+__device__ __forceinline__ uint32_t wtile_off(int o, int i) {
+    return (uint32_t)((o >> 3) * 1024 + (i >> 3) * 128 + (o & 7) * 16 + (i & 7) * 2);
+}
+
+// parameter p's BF16 value where the forward and backward passes read it
+__device__ __forceinline__ void put_weight(unsigned char *sm, float *wq, int p, float v) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    if (p >= MLP_W2 && p < MLP_B2) {
+        const int q = p - MLP_W2;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + SM_W2 + wtile_off(q >> 6, q & 63)) = b;
+    } else if (p >= MLP_W3 && p < MLP_B3) {
+        const int q = p - MLP_W3;
+        *reinterpret_cast<__nv_bfloat16 *>(sm + SM_W3 + wtile_off(q >> 6, q & 63)) = b;
+    } else {
+        int d;
+        if (p < MLP_B1) d = MLP_F_W1 + p;
+        else if (p < MLP_W2) d = MLP_F_B1 + (p - MLP_B1);
+        else if (p < MLP_W3) d = MLP_F_B2 + (p - MLP_B2);
+        else if (p < MLP_W4) d = MLP_F_B3 + (p - MLP_B3);
+        else if (p < MLP_B4) d = MLP_F_W4 + (p - MLP_W4);
+        else d = MLP_F_B4;
+        wq[d] = __bfloat162float(b);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    return pack_bf16(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+}
+
+// all CTAs arrive; false when a wait ran out (the status word says which)
+__device__ bool grid_sync(unsigned *bar, unsigned target, int *status, int *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        unsigned v = 0;
+        for (uint32_t it = 0; it < BAR_POLLS; ++it) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target || *reinterpret_cast<volatile int *>(status)) break;
+            __nanosleep(64);
         }
-    }
-    F[2 * tid] = f0;
-    F[2 * tid + 1] = f1;
-    __syncthreads();
-    // layer 1 (FP32)
-    for (int o = 0; o < MLP_H; ++o) {
-        const float z = __bfloat162float(W[MLP_W1 + 2 * o]) * f0 + __bfloat162float(W[MLP_W1 + 2 * o + 1]) * f1 +
-                        __bfloat162float(W[MLP_B1 + o]);
-        Z1[tid * MLP_H + o] = z;
-        H1[tid * MLP_H + o] = __float2bfloat16_rn(silu_f(z));
+        if (v < target) {
+            atomicCAS(status, 0, 1);
+            *s_flag = 1;
+        }
+        __threadfence();
     }
     __syncthreads();
-    // layers 2 and 3 on the tensor cores: Z = H W^T + b, each warp its 32 rows
-    for (int layer = 0; layer < 2; ++layer) {
-        const __nv_bfloat16 *Hin = layer == 0 ? H1 : H2;
-        __nv_bfloat16 *Hout = layer == 0 ? H2 : H3;
-        float *Zout = layer == 0 ? Z2 : Z3;
-        const __nv_bfloat16 *Wl = W + (layer == 0 ? MLP_W2 : MLP_W3);
-        const __nv_bfloat16 *bl = W + (layer == 0 ? MLP_B2 : MLP_B3);
-        auto A = [&](int i, int k) { return Hin[i * MLP_H + k]; };
-        auto B = [&](int k, int j) { return Wl[j * MLP_H + k]; };
-        for (int mt = 0; mt < 2; ++mt)
-            for (int nt = 0; nt < 8; ++nt) {
-                float c[4] = {0.f, 0.f, 0.f, 0.f};
-                const int r0 = warp * 32 + mt * 16;
-                mma_tile(r0, nt * 8, MLP_H, A, B, c);
-                for (int q = 0; q < 4; ++q) {
-                    int r, col;
-                    tile_coords(r0, nt * 8, q, r, col);
-                    const float z = c[q] + __bfloat162float(bl[col]);
-                    Zout[r * MLP_H + col] = z;
-                    Hout[r * MLP_H + col] = __float2bfloat16_rn(silu_f(z));
+    return *reinterpret_cast<volatile int *>(s_flag) == 0;
+}
+
+__global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *sP = reinterpret_cast<float *>(sm + SM_P), *sM = reinterpret_cast<float *>(sm + SM_M);
+    float *sV = reinterpret_cast<float *>(sm + SM_V), *wq = reinterpret_cast<float *>(sm + SM_WQ);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + SM_MISC);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + SM_MISC + 8);
+    int *s_flag = reinterpret_cast<int *>(sm + SM_MISC + 12);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool train = a.steps > 0;
+    const uint32_t base = tc::smem_u32(sm);
+
+    for (int p = tid; p < MLP_NP; p += TT) {
+        sP[p] = a.P[p];
+        sM[p] = train ? a.M[p] : 0.f;
+        sV[p] = train ? a.V[p] : 0.f;
+        put_weight(sm, wq, p, sP[p]);
+    }
+    // constant blocks: a BF16 one in unit 0 of every sample row; zeros
+    *reinterpret_cast<uint4 *>(sm + SM_ONES + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(sm + SM_ZERO + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
+    if (warp == 0) tc::alloc(tslot, TM_COLS);
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        *s_flag = 0;
+    }
+    tc::fence_proxy_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot, tl = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    // shared-memory writes done: hand the tiles to the tensor cores, one
+    // thread issues `fn`, everyone waits for its completion
+    auto run_mma = [&](auto fn) -> bool {
+        tc::fence_proxy_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            fn();
+            tc::commit(mbar);
+        }
+        bool done = tc::mbar_wait(mbar, phase, WAIT_POLLS);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        done = __syncthreads_and(done);
+        if (!done && tid == 0) atomicCAS(a.status, 0, 2);
+        return done;
+    };
+    auto k_steps = [&](uint32_t d, uint32_t aa, uint32_t alb, uint32_t asb, uint32_t ast, uint32_t bb,
+                       uint32_t blb, uint32_t bsb, uint32_t bst, uint32_t id, int n, bool acc) {
+        for (int kk = 0; kk < n; ++kk)
+            tc::mma(d, tc::sdesc(aa + kk * ast, alb, asb), tc::sdesc(bb + kk * bst, blb, bsb), id, acc || kk > 0);
+    };
+
+    const long long tiles = (a.per_step + TT - 1) / TT;
+    const long long nsteps = train ? a.steps : 1;
+    for (long long s = 0; s < nsteps && ok; ++s) {
+        float *g = a.gbuf + (train ? (s % 3) * GSTRIDE : 0);
+        float dysum = 0.f, sq = 0.f;
+        bool first = true;
+        for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            const long long idx = t * TT + tid;
+            const bool live = idx < a.per_step;
+            float f0 = 0.f, f1 = 0.f, ty = 0.f;
+            if (live) {
+                if (a.feat) {
+                    f0 = a.feat[2 * idx];
+                    f1 = a.feat[2 * idx + 1];
+                    ty = a.target[idx];
+                } else {
+                    const unsigned long long gi = (unsigned long long)s * a.per_step + (unsigned long long)idx;
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)gi, (uint32_t)(gi >> 32), 0u, 0x4D4C5000u),
+                                                  make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32)));
+                    float u1, v1, u2, v2;
+                    Uniform<float>::draw(r.x, r.y, u1, v1);
+                    Uniform<float>::draw(r.z, r.w, u2, v2);
+                    const float lc = -3.0f + 6.0f * u1;
+                    float sv = logit(u2, v2);
+                    sv = fminf(fmaxf(sv, -16.0f), 16.0f);
+                    f0 = lc / 3.0f;
+                    f1 = sv / 16.0f;
+                    ty = table_zeta(a.icdf_em32, lc, sv) / 16.0f + 0.5f;
                 }
             }
-        __syncthreads();
-    }
-    // layer 4 and the loss
-    float y = __bfloat162float(W[MLP_B4]);
-    for (int i = 0; i < MLP_H; ++i) y += __bfloat162float(W[MLP_W4 + i]) * __bfloat162float(H3[tid * MLP_H + i]);
-    const float res = live ? y - ty : 0.f;
-    DY[tid] = 2.0f * res * a.inv_total;
-    __syncthreads();
-    // gradients of layer 4
-    if (tid < MLP_H) {
-        float g = 0.f;
-        for (int k = 0; k < TB; ++k) g += DY[k] * __bfloat162float(H3[k * MLP_H + tid]);
-        atomicAdd(&a.grad[MLP_W4 + tid], g);
-    } else if (tid == MLP_H) {
-        float g = 0.f;
-        for (int k = 0; k < TB; ++k) g += DY[k];
-        atomicAdd(&a.grad[MLP_B4], g);
-    }
-    // D3 = dy W4 * silu'(Z3)
-    for (int o = 0; o < MLP_H; ++o)
-        D[tid * MLP_H + o] = __float2bfloat16_rn(DY[tid] * __bfloat162float(W[MLP_W4 + o]) * dsilu_f(Z3[tid * MLP_H + o]));
-    __syncthreads();
-    // layers 3 and 2 backward: dW = D^T H_in, db = sum D, D_in = (D W) * silu'(Z_in)
-    for (int layer = 1; layer >= 0; --layer) {
-        const __nv_bfloat16 *Hin = layer == 1 ? H2 : H1;
-        const float *Zin = layer == 1 ? Z2 : Z1;
-        const __nv_bfloat16 *Wl = W + (layer == 1 ? MLP_W3 : MLP_W2);
-        float *gW = a.grad + (layer == 1 ? MLP_W3 : MLP_W2);
-        float *gb = a.grad + (layer == 1 ? MLP_B3 : MLP_B2);
-        {   // dW (64 x 64) over the block's 128 samples: 32 tiles, 8 per warp
-            auto A = [&](int o, int k) { return D[k * MLP_H + o]; };
-            auto B = [&](int k, int i) { return Hin[k * MLP_H + i]; };
-            for (int tt = warp; tt < 32; tt += TB / 32) {
-                const int mt = tt >> 3, nt = tt & 7;
-                float c[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_tile(mt * 16, nt * 8, TB, A, B, c);
-                for (int q = 0; q < 4; ++q) {
-                    int r, col;
-                    tile_coords(mt * 16, nt * 8, q, r, col);
-                    atomicAdd(&gW[r * MLP_H + col], c[q]);
+            auto z1_of = [&](int o) {
+                return wq[MLP_F_W1 + 2 * o] * f0 + wq[MLP_F_W1 + 2 * o + 1] * f1 + wq[MLP_F_B1 + o];
+            };
+            // layer 1 on the CUDA cores: H1 row
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pk[q] = silu_pack(z1_of(8 * j + 2 * q), z1_of(8 * j + 2 * q + 1));
+                *reinterpret_cast<uint4 *>(sm + SM_H1 + j * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            // Z2 = H1 W2^T
+            ok = run_mma([&] { k_steps(tmem + TZ2, base + SM_H1, 2048, 128, 4096, base + SM_W2, 128, 1024, 256, ID_FWD, 4, false); });
+            if (!ok) break;
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float z[16];
+                tc::ld16(tl + TZ2 + c, z);
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    pk[q] = silu_pack(z[2 * q] + wq[MLP_F_B2 + c + 2 * q], z[2 * q + 1] + wq[MLP_F_B2 + c + 2 * q + 1]);
+                *reinterpret_cast<uint4 *>(sm + SM_H2 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(sm + SM_H2 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            // Z3 = H2 W3^T; H3 row and the output y (layer 4, in unit order)
+            ok = run_mma([&] { k_steps(tmem + TZ3, base + SM_H2, 2048, 128, 4096, base + SM_W3, 128, 1024, 256, ID_FWD, 4, false); });
+            if (!ok) break;
+            float y = wq[MLP_F_B4];
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float z[16];
+                tc::ld16(tl + TZ3 + c, z);
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    pk[q] = silu_pack(z[2 * q] + wq[MLP_F_B3 + c + 2 * q], z[2 * q + 1] + wq[MLP_F_B3 + c + 2 * q + 1]);
+                    y += wq[MLP_F_W4 + c + 2 * q] * bf16_lo(pk[q]);
+                    y += wq[MLP_F_W4 + c + 2 * q + 1] * bf16_hi(pk[q]);
                 }
+                *reinterpret_cast<uint4 *>(sm + SM_H3 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(sm + SM_H3 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            const float res = live ? y - ty : 0.f;
+            const float dy = 2.0f * res * a.inv_total;
+            dysum += dy;
+            sq += res * res;
+            {   // G2's B row: f0, f1 and dy as BF16 hi + lo, and a one
+                const __nv_bfloat16 f0h = __float2bfloat16_rn(f0), f1h = __float2bfloat16_rn(f1);
+                const __nv_bfloat16 dyh = __float2bfloat16_rn(dy);
+                const __nv_bfloat16 f0l = __float2bfloat16_rn(f0 - __bfloat162float(f0h));
+                const __nv_bfloat16 f1l = __float2bfloat16_rn(f1 - __bfloat162float(f1h));
+                const __nv_bfloat16 dyl = __float2bfloat16_rn(dy - __bfloat162float(dyh));
+                *reinterpret_cast<uint4 *>(sm + SM_FB + tid * 16) =
+                    make_uint4(pack_bf16(f0h, f0l), pack_bf16(f1h, f1l), pack_bf16(__float2bfloat16_rn(1.0f), dyh),
+                               pack_bf16(dyl, __float2bfloat16_rn(0.0f)));
+            }
+            // D3 = dy W4 silu'(Z3)
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float z[16];
+                tc::ld16(tl + TZ3 + c, z);
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int o = c + 2 * q;
+                    pk[q] = pack2(dy * wq[MLP_F_W4 + o] * dsilu_f(z[2 * q] + wq[MLP_F_B3 + o]),
+                                  dy * wq[MLP_F_W4 + o + 1] * dsilu_f(z[2 * q + 1] + wq[MLP_F_B3 + o + 1]));
+                }
+                *reinterpret_cast<uint4 *>(sm + SM_D3 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(sm + SM_D3 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            // P3 = D3 W3; D2 = P3 silu'(Z2)
+            ok = run_mma([&] { k_steps(tmem + TZ3, base + SM_D3, 2048, 128, 4096, base + SM_W3, 1024, 128, 2048, ID_BWD, 4, false); });
+            if (!ok) break;
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float pv[16], z[16];
+                tc::ld16(tl + TZ3 + c, pv);
+                tc::ld16(tl + TZ2 + c, z);
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int o = c + 2 * q;
+                    pk[q] = pack2(pv[2 * q] * dsilu_f(z[2 * q] + wq[MLP_F_B2 + o]),
+                                  pv[2 * q + 1] * dsilu_f(z[2 * q + 1] + wq[MLP_F_B2 + o + 1]));
+                }
+                *reinterpret_cast<uint4 *>(sm + SM_D2 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(sm + SM_D2 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            // P2 = D2 W2; D1 = P2 silu'(Z1)
+            ok = run_mma([&] { k_steps(tmem + TZ3, base + SM_D2, 2048, 128, 4096, base + SM_W2, 1024, 128, 2048, ID_BWD, 4, false); });
+            if (!ok) break;
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float pv[16];
+                tc::ld16(tl + TZ3 + c, pv);
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int o = c + 2 * q;
+                    pk[q] = pack2(pv[2 * q] * dsilu_f(z1_of(o)), pv[2 * q + 1] * dsilu_f(z1_of(o + 1)));
+                }
+                *reinterpret_cast<uint4 *>(sm + SM_D1 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(sm + SM_D1 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            // weight and bias gradients of the tile, accumulated over the CTA's tiles of the step
+            const bool acc = !first;
+            ok = run_mma([&] {
+                k_steps(tmem + TG1, base + SM_D3, 128, 2048, 256, base + SM_H2, 128, 2048, 256, ID_G1, 8, acc);
+                k_steps(tmem + TG2, base + SM_D1, 128, 2048, 256, base + SM_FB, 128, 2048, 256, ID_G2, 8, acc);
+            });
+            first = false;
+        }
+        if (!ok) break;
+        if (!first) {
+            // row tid of G1: dW3 row tid and db3 (tid < 64), or dW2 row tid - 64 and db2
+            const bool lo = tid < 64;
+            float *gw = g + (lo ? MLP_W3 + tid * 64 : MLP_W2 + (tid - 64) * 64);
+            const uint32_t c0 = TG1 + (lo ? 0u : 64u);
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                float v[16];
+                tc::ld16(tl + c0 + c, v);
+#pragma unroll
+                for (int q = 0; q < 16; q += 4)
+                    atomicAdd(reinterpret_cast<float4 *>(gw + c + q), make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
+            }
+            float v8[8];
+            tc::ld8(tl + TG1 + 128, v8);
+            atomicAdd(g + (lo ? MLP_B3 + tid : MLP_B2 + (tid - 64)), v8[0]);
+            tc::ld8(tl + TG2, v8);
+            if (lo) {
+                atomicAdd(reinterpret_cast<float2 *>(g + MLP_W1 + 2 * tid), make_float2(v8[0] + v8[1], v8[2] + v8[3]));
+                atomicAdd(g + MLP_B1 + tid, v8[4]);
+            } else {
+                atomicAdd(g + MLP_W4 + (tid - 64), v8[5] + v8[6]);
             }
         }
-        if (tid < MLP_H) {
-            float g = 0.f;
-            for (int k = 0; k < TB; ++k) g += __bfloat162float(D[k * MLP_H + tid]);
-            atomicAdd(&gb[tid], g);
+        for (int o = 16; o > 0; o >>= 1) {
+            dysum += __shfl_down_sync(0xffffffffu, dysum, o);
+            sq += __shfl_down_sync(0xffffffffu, sq, o);
         }
-        // D_in into H3's buffer (H3 is dead after layer 4's gradients), then back to D
-        __nv_bfloat16 *Dn = H3;
-        {
-            auto A = [&](int k, int o) { return D[k * MLP_H + o]; };
-            auto B = [&](int o, int i) { return Wl[o * MLP_H + i]; };
-            for (int mt = 0; mt < 2; ++mt)
-                for (int nt = 0; nt < 8; ++nt) {
-                    float c[4] = {0.f, 0.f, 0.f, 0.f};
-                    const int r0 = warp * 32 + mt * 16;
-                    mma_tile(r0, nt * 8, MLP_H, A, B, c);
-                    for (int q = 0; q < 4; ++q) {
-                        int r, col;
-                        tile_coords(r0, nt * 8, q, r, col);
-                        Dn[r * MLP_H + col] = __float2bfloat16_rn(c[q] * dsilu_f(Zin[r * MLP_H + col]));
-                    }
-                }
+        if (lane == 0) {
+            if (dysum != 0.f) atomicAdd(g + MLP_B4, dysum);
+            if (!train || s >= a.tail_from) atomicAdd(a.loss, sq);
         }
-        __syncthreads();
-        for (int o = 0; o < MLP_H; ++o) D[tid * MLP_H + o] = Dn[tid * MLP_H + o];
+        if (!train) break;
+        // every CTA's sums are in: the same Adam update in every CTA
+        if (!grid_sync(a.bar, (unsigned)(gridDim.x * (s + 1)), a.status, s_flag)) {
+            ok = false;
+            break;
+        }
+        const float lr = a.sched[3 * s], bc1 = a.sched[3 * s + 1], bc2 = a.sched[3 * s + 2];
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        for (int p = tid; p < MLP_NP; p += TT) {
+            const float gv = __ldcg(g + p);
+            const float m = b1 * sM[p] + (1.f - b1) * gv;
+            const float v = b2 * sV[p] + (1.f - b2) * gv * gv;
+            sM[p] = m;
+            sV[p] = v;
+            const float np = sP[p] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+            sP[p] = np;
+            put_weight(sm, wq, p, np);
+        }
+        // the sum two steps ahead was last read before this step's barrier
+        float *gz = a.gbuf + ((s + 2) % 3) * GSTRIDE;
+        for (int p = blockIdx.x * TT + tid; p < GSTRIDE; p += gridDim.x * TT) __stcg(gz + p, 0.f);
         __syncthreads();
     }
-    // layer 1 gradients
-    if (tid < MLP_H) {
-        float g0 = 0.f, g1 = 0.f, gbv = 0.f;
-        for (int k = 0; k < TB; ++k) {
-            const float d = __bfloat162float(D[k * MLP_H + tid]);
-            g0 += d * F[2 * k];
-            g1 += d * F[2 * k + 1];
-            gbv += d;
+    if (train && ok && blockIdx.x == 0) {
+        for (int p = tid; p < MLP_NP; p += TT) {
+            a.P[p] = sP[p];
+            a.M[p] = sM[p];
+            a.V[p] = sV[p];
+            a.W16[p] = __float2bfloat16_rn(sP[p]);
         }
-        atomicAdd(&a.grad[MLP_W1 + 2 * tid], g0);
-        atomicAdd(&a.grad[MLP_W1 + 2 * tid + 1], g1);
-        atomicAdd(&a.grad[MLP_B1 + tid], gbv);
     }
-    float l = res * res;
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if ((tid & 31) == 0) atomicAdd(a.loss, l);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tmem, TM_COLS);
 }
 
 __global__ void k_mlp_adam(float *P, float *M, float *V, float *G, __nv_bfloat16 *W16, float lr, float bc1, float bc2) {
@@ -302,60 +515,114 @@ qed_status sfq_mlp_eval(qed_ctx *ctx, const float *feat, int64_t n, float *y) {
     return QED_OK;
 }
 
+// scratch of one training or gradient call: three gradient sums (the
+// gradient call uses the context's gradient buffer instead), the step
+// schedule, the barrier counter and the status word
+struct TrainScratch {
+    void *mem = nullptr;
+    float *gbuf = nullptr, *sched = nullptr;
+    unsigned *bar = nullptr;
+    int *status = nullptr;
+    ~TrainScratch() {
+        if (mem) cudaFree(mem);
+    }
+};
+
+static qed_status train_scratch(TrainScratch &t, int64_t steps, cudaStream_t st) {
+    const size_t g = sizeof(float) * 3 * GSTRIDE, sc = sizeof(float) * 3 * (size_t)(steps > 0 ? steps : 1);
+    const size_t bytes = g + ((sc + 255) / 256) * 256 + 256;
+    if (cudaMalloc(&t.mem, bytes) != cudaSuccess) return QED_ERR_NOMEM;
+    t.gbuf = static_cast<float *>(t.mem);
+    t.sched = reinterpret_cast<float *>(static_cast<char *>(t.mem) + g);
+    t.bar = reinterpret_cast<unsigned *>(static_cast<char *>(t.mem) + g + ((sc + 255) / 256) * 256);
+    t.status = reinterpret_cast<int *>(t.bar + 1);
+    SFQ_CUDA(cudaMemsetAsync(t.gbuf, 0, g, st));
+    SFQ_CUDA(cudaMemsetAsync(t.bar, 0, 256, st));
+    return QED_OK;
+}
+
+// CTAs of the training kernel: one per SM at most (its shared memory and
+// tensor-memory columns take a whole SM), no more than there are tiles
+static qed_status train_grid(long long tiles, int *grid) {
+    int dev = 0, sms = 0, per_sm = 0;
+    SFQ_CUDA(cudaGetDevice(&dev));
+    SFQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SFQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_train, TT, TR_SMEM));
+    if (per_sm < 1) return QED_ERR_CUDA;
+    const long long cap = (long long)sms * per_sm;
+    *grid = (int)(tiles < cap ? tiles : cap);
+    return QED_OK;
+}
+
 // one gradient of the mean squared error over n given samples (no update)
 qed_status sfq_mlp_grad(qed_ctx *ctx, const float *feat, const float *target, int64_t n, float *grad_host,
                         double *loss) {
     if (!ctx || n <= 0 || !feat || !target || !grad_host) return QED_ERR_INVALID;
     if (!ctx->mlp_p) return QED_ERR_STATE;
     cudaStream_t st = ctx->stream;
-    float *G = ctx->mlp_p + 3 * MLP_NP;
-    SFQ_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * MLP_NP, st));
+    float *P = ctx->mlp_p;
+    TrainScratch t;
+    qed_status e = train_scratch(t, 0, st);
+    if (e != QED_OK) return e;
     SFQ_CUDA(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(float), st));
-    TrainArgs a{ctx->mlp_w16, G, ctx->mlp_loss, ctx->icdf_em32, feat, target, 0ull, 0ull, (long long)n,
-                1.0f / (float)n};
-    k_mlp_train<<<(unsigned)((n + TB - 1) / TB), TB, TR_SMEM, st>>>(a);
+    int grid = 0;
+    if ((e = train_grid((n + TT - 1) / TT, &grid)) != QED_OK) return e;
+    TrainArgs a{P, P + MLP_NP, P + 2 * MLP_NP, t.gbuf, ctx->mlp_w16, ctx->mlp_loss, ctx->icdf_em32, feat, target,
+                t.sched, 0ull, (long long)n, 0ll, 0ll, 1.0f / (float)n, t.bar, t.status};
+    k_mlp_train<<<grid, TT, TR_SMEM, st>>>(a);
     SFQ_CUDA(cudaGetLastError());
+    SFQ_LAUNCHED(ctx, 1);
     float l = 0.f;
-    SFQ_CUDA(cudaMemcpyAsync(grad_host, G, sizeof(float) * MLP_NP, cudaMemcpyDeviceToHost, st));
+    int status = 0;
+    SFQ_CUDA(cudaMemcpyAsync(grad_host, t.gbuf, sizeof(float) * MLP_NP, cudaMemcpyDeviceToHost, st));
     SFQ_CUDA(cudaMemcpyAsync(&l, ctx->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    SFQ_CUDA(cudaMemcpyAsync(&status, t.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     SFQ_CUDA(cudaStreamSynchronize(st));
-    SFQ_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * MLP_NP, st));
+    if (status) return QED_ERR_TIMEOUT;
     if (loss) *loss = l / (double)n;
     return QED_OK;
 }
 
 // Train on n_samples table draws: batches of `batch`, Adam with a cosine
-// learning-rate decay from lr to lr/100.
+// learning-rate decay from lr to lr/100.  All steps run in one cooperative
+// launch of k_mlp_train; the step schedule is computed here in FP64 and
+// rounded to FP32 once.
 qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed, double *final_loss) {
-    if (!ctx || n_samples <= 0 || batch <= 0 || batch % TB || !(lr > 0.0)) return QED_ERR_INVALID;
+    if (!ctx || n_samples <= 0 || batch <= 0 || batch % TT || !(lr > 0.0)) return QED_ERR_INVALID;
     qed_status e = mlp_alloc(ctx);
     if (e != QED_OK) return e;
     cudaStream_t st = ctx->stream;
     float *P = ctx->mlp_p, *M = P + MLP_NP, *V = P + 2 * MLP_NP, *G = P + 3 * MLP_NP;
     k_mlp_init<<<(MLP_NP + 255) / 256, 256, 0, st>>>(P, M, V, G, ctx->mlp_w16, seed);
-    const int64_t steps = (n_samples + batch - 1) / batch;
-    double last = 0.0;
-    int64_t last_n = 0;
-    for (int64_t s = 0; s < steps; ++s) {
-        const bool tail = s >= steps - 16;        // loss of the last steps
-        if (tail && s == steps - 16) SFQ_CUDA(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(float), st));
-        TrainArgs a{ctx->mlp_w16, G, ctx->mlp_loss, ctx->icdf_em32, nullptr, nullptr, seed,
-                    (unsigned long long)(s * batch), (long long)batch, 1.0f / (float)batch};
-        k_mlp_train<<<(unsigned)(batch / TB), TB, TR_SMEM, st>>>(a);
-        const double frac = (double)s / (double)(steps > 1 ? steps - 1 : 1);
-        const double lr_t = lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(3.14159265358979323846 * frac)));
-        const double bc1 = 1.0 - pow(0.9, (double)(s + 1)), bc2 = 1.0 - pow(0.999, (double)(s + 1));
-        k_mlp_adam<<<(MLP_NP + 255) / 256, 256, 0, st>>>(P, M, V, G, ctx->mlp_w16, (float)lr_t, (float)bc1,
-                                                          (float)bc2);
-        SFQ_LAUNCHED(ctx, 2);
-        if (tail) last_n += batch;
-    }
     SFQ_CUDA(cudaGetLastError());
+    const int64_t steps = (n_samples + batch - 1) / batch;
+    std::vector<float> sched((size_t)steps * 3);
+    for (int64_t s = 0; s < steps; ++s) {
+        const double frac = (double)s / (double)(steps > 1 ? steps - 1 : 1);
+        sched[3 * s] = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(3.14159265358979323846 * frac))));
+        sched[3 * s + 1] = (float)(1.0 - pow(0.9, (double)(s + 1)));
+        sched[3 * s + 2] = (float)(1.0 - pow(0.999, (double)(s + 1)));
+    }
+    TrainScratch t;
+    if ((e = train_scratch(t, steps, st)) != QED_OK) return e;
+    SFQ_CUDA(cudaMemcpyAsync(t.sched, sched.data(), sizeof(float) * sched.size(), cudaMemcpyHostToDevice, st));
+    SFQ_CUDA(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(float), st));
+    int grid = 0;
+    if ((e = train_grid(batch / TT, &grid)) != QED_OK) return e;
+    const int64_t tail = steps < 16 ? steps : 16;     // the loss is averaged over the last 16 steps
+    TrainArgs a{P, M, V, t.gbuf, ctx->mlp_w16, ctx->mlp_loss, ctx->icdf_em32, nullptr, nullptr, t.sched, seed,
+                (long long)batch, (long long)steps, (long long)(steps - tail), 1.0f / (float)batch, t.bar, t.status};
+    void *args[] = {&a};
+    SFQ_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_mlp_train), dim3(grid), dim3(TT), args,
+                                         (size_t)TR_SMEM, st));
+    SFQ_LAUNCHED(ctx, 2);
     float l = 0.f;
+    int status = 0;
     SFQ_CUDA(cudaMemcpyAsync(&l, ctx->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    SFQ_CUDA(cudaMemcpyAsync(&status, t.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     SFQ_CUDA(cudaStreamSynchronize(st));
-    last = last_n ? (double)l / (double)last_n : 0.0;
-    if (final_loss) *final_loss = last;
+    if (status) return QED_ERR_TIMEOUT;
+    if (final_loss) *final_loss = (double)l / (double)(tail * batch);
     ctx->mlp_ready = 1;
     return QED_OK;
 }

@@ -1,7 +1,7 @@
 // Warp-level BF16 tensor-core tiles (mma.sync m16n8k16, FP32 accumulation)
-// for the 2 -> 64 -> 64 -> 64 -> 1 surrogate network.  Operands are read
-// through index functors so one routine serves the forward product H W^T,
-// the input-gradient product D W and the weight-gradient product D^T H.
+// for inference of the 2 -> 64 -> 64 -> 64 -> 1 surrogate network inside the
+// lepton pass, where each warp evaluates its own 32 samples; the parameter
+// layout and the activation functions are shared with the training kernel.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,33 +25,6 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], 
         "{%0,%1,%2,%3};\n"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// One 16 x 8 tile of C = A B (rows row0.., columns col0..) accumulated over
-// K (a multiple of 16).  a(i, k) and b(k, j) return bf16 elements.  The
-// fragment layout is that of mma.m16n8k16: lane = 4 g + t holds
-// A rows g, g+8 / columns 2t, 2t+1, 2t+8, 2t+9; B rows 2t, 2t+1, 2t+8, 2t+9 /
-// column g; C rows g, g+8 / columns 2t, 2t+1.
-template <class FA, class FB>
-__device__ __forceinline__ void mma_tile(int row0, int col0, int K, FA a, FB b, float c[4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t af[4], bf[2];
-        af[0] = pack_bf16(a(row0 + g, k0 + 2 * t), a(row0 + g, k0 + 2 * t + 1));
-        af[1] = pack_bf16(a(row0 + g + 8, k0 + 2 * t), a(row0 + g + 8, k0 + 2 * t + 1));
-        af[2] = pack_bf16(a(row0 + g, k0 + 2 * t + 8), a(row0 + g, k0 + 2 * t + 9));
-        af[3] = pack_bf16(a(row0 + g + 8, k0 + 2 * t + 8), a(row0 + g + 8, k0 + 2 * t + 9));
-        bf[0] = pack_bf16(b(k0 + 2 * t, col0 + g), b(k0 + 2 * t + 1, col0 + g));
-        bf[1] = pack_bf16(b(k0 + 2 * t + 8, col0 + g), b(k0 + 2 * t + 9, col0 + g));
-        mma_bf16_16816(c, af, bf);
-    }
-}
-
-// where the four accumulators of a tile live in C
-__device__ __forceinline__ void tile_coords(int row0, int col0, int q, int &r, int &col) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    r = row0 + g + ((q & 2) ? 8 : 0);
-    col = col0 + 2 * t + (q & 1);
 }
 
 // SiLU z * sigmoid(z) with the fast exponential and division (the exponent
