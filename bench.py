@@ -53,10 +53,15 @@ PAIR_BYTES = {"fp32": 4 + 2 * (7 * 4 + 8 + 4 + 8), "fp64": 8 + 2 * (7 * 8 + 8 + 
 OD_LEPTON_BYTES = {"fp32": LEPTON_BYTES["fp32"] + 8, "fp64": LEPTON_BYTES["fp64"] + 16}
 OD_PHOTON_BYTES = {"fp32": PHOTON_BYTES["fp32"] + 8, "fp64": PHOTON_BYTES["fp64"] + 16}
 # DRAM bytes (read + write) per particle-step of the step-start passes, from
-# one ncu capture of the current kernels in the timed window (profiles/);
-# None when the kernel changed since its capture
-NCU_PHOTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
-NCU_LEPTON_BYTES_PER_STEP = {"fp32": None, "fp64": None}
+# one ncu capture of the current kernels at the first step of the timed
+# window of the default workload (dram__bytes_read.sum + dram__bytes_write.sum
+# over the particles at the step start; the lepton figure includes the
+# photon records of its 0.3 emissions per lepton-step):
+# profiles/k_photon_pass_fp32_rotating_e_cascade.md and
+# profiles/k_lepton_pass_fp32_rotating_e_cascade.md.  None when the kernel
+# changed since its capture.
+NCU_PHOTON_BYTES_PER_STEP = {"fp32": 47.6, "fp64": None}
+NCU_LEPTON_BYTES_PER_STEP = {"fp32": 80.1, "fp64": None}
 # FP64 FLOPs (2 DFMA + DADD + DMUL thread instructions) per particle-step of
 # the FP64 step-start passes at the rotating-E cascade's cap (0.3 emissions
 # per lepton-step), from one ncu capture of the current kernels
@@ -82,6 +87,8 @@ def parse():
     ap.add_argument("--compare-mlp", type=int, default=1,
                     help="also train the surrogate sampler (1e8 table draws) and time the cascade with it")
     ap.add_argument("--mlp-samples", type=float, default=1e8)
+    ap.add_argument("--train-only", action="store_true",
+                    help="only train the surrogate on --mlp-samples draws and print the training line")
     ap.add_argument("--compare-od", type=int, default=1,
                     help="also time the accumulated optical-depth scheme on the same workload (extra key)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
@@ -584,7 +591,7 @@ def reduce_over_ranks(particle_steps, events, secs, world):
 
 def main():
     args = parse()
-    if args.ncu_window or args.profile_step is not None:
+    if args.ncu_window or args.profile_step is not None or args.train_only:
         args.cpu_baseline = 0                     # a profiling run times nothing on the host
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -638,6 +645,10 @@ def main():
     hbm_peak = hbm_peak or 6800.0
 
     n_total = start + warm + steps
+    if args.train_only:
+        _, train = train_surrogate_timed(int(args.mlp_samples), peaks)
+        print(json.dumps(train), flush=True)
+        return
     if args.profile_step is not None:
         return profile_step(w, args.precision, args.profile_step)
     caps = size_cascade(w, n_total, args.precision) if w.push_photons else None
@@ -647,7 +658,8 @@ def main():
         print(json.dumps({"ncu_window": t["window"], "particle_steps": t["particle_steps"],
                           "lepton_steps": t["lepton_steps"], "photon_steps": t["photon_steps"],
                           "emit_events": t["emit_events"], "pair_events": t["pair_events"],
-                          "counts_at_start": t["counts_start"], "kernel_ms": t["kernel_ms"]}), flush=True)
+                          "counts_at_start": t["counts_start"], "kernel_ms": t["kernel_ms"],
+                          "thinned": t["thinned"], "moved": t["moved"]}), flush=True)
         return
     if world > 1:
         dist.barrier()
@@ -703,30 +715,11 @@ def main():
     mlp = None
     if args.compare_mlp and world == 1 and args.workload == "rotating_e_cascade":
         import paper_2409_17299_gb300 as q
-        tg = q.Generator(q.make_config(precision=q.QED_FP32))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        loss = q.qed_train_surrogate(tg.ctx, int(args.mlp_samples), 8192, 4e-3, 7)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t0
-        P = q.qed_mlp_get_params(tg.ctx)
-        tg.close()
+        P, train = train_surrogate_timed(int(args.mlp_samples), peaks)
         ms_m, _, tot_m, _ = gpu_run(args, w, args.precision, start, warm, steps, mlp_params=P, caps=caps)
         mlp = {"value": tot_m["particle_steps"] / (ms_m / 1e3),
                "events_per_s": (tot_m["emit_events"] + tot_m["pair_events"]) / (ms_m / 1e3),
-               "ms_per_step": ms_m / steps,
-               "train_samples": int(args.mlp_samples), "train_seconds": train_s, "train_final_mse": loss,
-               "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation; training on tcgen05.mma with "
-                          "tensor-memory accumulators (one cooperative launch), inference inside the lepton "
-                          "pass on mma.sync"}
-        bf16_peak = peaks.get("bf16_tflops")
-        ach = MLP_TRAIN_FLOP_PER_SAMPLE * int(args.mlp_samples) / train_s / 1e12
-        mlp["train_roofline"] = {
-            "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
-            "frac": ach / bf16_peak if bf16_peak else None,
-            "peak_source": "measured bf16_tflops (burst)" if bf16_peak else None,
-            "flop_per_sample": MLP_TRAIN_FLOP_PER_SAMPLE,
-            "achieved_is": "algorithmic FLOPs of the matrix products x samples / wall time of the training call"}
+               "ms_per_step": ms_m / steps, **train}
 
     growth = None
     if args.growth and world == 1 and args.workload == "rotating_e_cascade":
@@ -788,12 +781,14 @@ def main():
                           "bytes_per_particle_step": LEPTON_BYTES[prec], "bytes_per_emission": EMIT_BYTES[prec],
                           "units": "lepton particle-steps %d, emissions %d" % (tot["lepton_steps"],
                                                                              tot["emit_events"]),
+                          "algorithmic_bytes_per_step": lep_bytes / steps,
                           "traffic": (NCU_LEPTON_BYTES_PER_STEP[prec] * tot["lepton_steps"] / steps
                                       if NCU_LEPTON_BYTES_PER_STEP[prec] else None)},
         "k_photon_pass": {"achieved": ph_bytes / (ph_ms / 1e3) / 1e9 if ph_ms > 0 else None,
                           "kernel_ms": ph_ms, "launches": launches if w.push_photons else 0,
                           "bytes_per_photon_step": PHOTON_BYTES[prec], "bytes_per_pair": PAIR_BYTES[prec],
                           "units": "photon-steps %d, pairs %d" % (tot["photon_steps"], tot["pair_events"]),
+                          "algorithmic_bytes_per_step": ph_bytes / steps,
                           "traffic": (NCU_PHOTON_BYTES_PER_STEP[prec] * tot["photon_steps"] / steps
                                       if NCU_PHOTON_BYTES_PER_STEP[prec] and w.push_photons else None)},
     }
@@ -825,7 +820,8 @@ def main():
                      "kernel": "%s<%s>" % (dom, "float" if prec == "fp32" else "double"),
                      "peak_source": peak_src + " hbm_gbs",
                      "achieved_is": "algorithmic bytes of all launches / summed CUDA-event time of the launches",
-                     "traffic_is": "ncu DRAM bytes per unit x units per step-start launch",
+                     "traffic_is": "ncu DRAM bytes per particle-step (step-start launch at the cap) x the "
+                                   "kernel's particle-steps per step: bytes per step, all launches",
                      "kernels": kernels},
         "breakdown_ms": {"lepton": tot["kernel_ms"][0], "photon": tot["kernel_ms"][1],
                          "compaction": tot["kernel_ms"][2], "leveling": tot["kernel_ms"][3],
@@ -958,9 +954,39 @@ def profile_step(w, precision, step):
     torch.cuda.profiler.stop()
     print(json.dumps({"profiled_step": step, "counts_at_start": counts0, "counts_after": list(ens.count),
                       **{k: st[k] for k in ("particle_steps", "lepton_steps", "photon_steps", "emit_events",
-                                            "pair_events", "passes", "thinned")}}), flush=True)
+                                            "pair_events", "passes", "thinned", "moved")}}), flush=True)
     gen.close()
     genp.close()
+
+
+def train_surrogate_timed(samples, peaks):
+    """Train the surrogate on `samples` table draws (batch 8192, the settings
+    the tests use) after a short warm-up training; wall time of the call and
+    the training roofline against the measured BF16 peak."""
+    import torch
+    import paper_2409_17299_gb300 as q
+    tg = q.Generator(q.make_config(precision=q.QED_FP32))
+    q.qed_train_surrogate(tg.ctx, 8192 * 16, 8192, 4e-3, 7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = q.qed_train_surrogate(tg.ctx, samples, 8192, 4e-3, 7)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    P = q.qed_mlp_get_params(tg.ctx)
+    tg.close()
+    bf16_peak = peaks.get("bf16_tflops")
+    ach = MLP_TRAIN_FLOP_PER_SAMPLE * samples / train_s / 1e12
+    return P, {
+        "train_samples": samples, "train_seconds": train_s, "train_final_mse": loss,
+        "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation; training on tcgen05.mma with "
+                   "tensor-memory accumulators (one cooperative launch), inference inside the lepton "
+                   "pass on mma.sync",
+        "train_roofline": {
+            "bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": ach / bf16_peak if bf16_peak else None,
+            "peak_source": "measured bf16_tflops (burst)" if bf16_peak else None,
+            "flop_per_sample": MLP_TRAIN_FLOP_PER_SAMPLE,
+            "achieved_is": "algorithmic FLOPs of the matrix products x samples / wall time of the training call"}}
 
 
 def fp64_roofline(tot, hbm_peak):

@@ -25,25 +25,29 @@ namespace {
 // ---- training on the tensor cores (tcgen05, accumulators in tensor memory)
 //
 // One persistent cooperative kernel runs every optimizer step.  A CTA holds
-// 128 samples at a time (one per thread and tensor-memory lane) and keeps,
-// in shared memory, its own copy of the FP32 parameters and Adam moments:
-// every CTA applies the same Adam update to the same summed gradient, so
-// the copies stay identical and one grid barrier per step suffices.
+// 128 samples at a time (one per tensor-memory lane) and keeps, in shared
+// memory, its own copy of the FP32 parameters and Adam moments: every CTA
+// applies the same Adam update to the same summed gradient, so the copies
+// stay identical and one grid barrier per step suffices.  512 threads: the
+// four warps that share a lane quadrant split the 64 columns of their 32
+// samples, 16 each.
 //
 // Per tile of 128 samples (B = BF16 storage, as in the network the oracle
 // defines; Z and dy stay FP32):
 //   Z2 = H1 W2^T, Z3 = H2 W3^T           M=128 N=64 K=64   (tensor memory)
 //   P3 = D3 W3,   P2 = D2 W2             M=128 N=64 K=64
-//   G1 = [D3;D2]^T-stacked x [H2;H1;1]   M=128 N=144 K=128: dW3, dW2, db3, db2
-//   G2 = [D1;H3]   x [f0 hi/lo, f1 hi/lo, 1, dy hi/lo]
+//   G1 = [D3;D2] x [H2;H1;1]             M=128 N=144 K=128: dW3, dW2, db3, db2
+//   G2 = [D1;H3] x [f0 hi/lo, f1 hi/lo, 1, dy hi/lo]
 //                                        M=128 N=16 K=128: dW1, db1, dW4
-// Layer 1 (2 -> 64) and layer 4 (64 -> 1) run on the CUDA cores; Z1 is
-// recomputed from the features rather than stored, Z2 stays in tensor
-// memory until the backward pass needs it.  G1 and G2 accumulate over the
-// CTA's tiles of a step and are added to the step's gradient sum with
+// (the first factor MN-major: rows are units, K runs over the samples).
+// Layer 1 (2 -> 64) and layer 4 (64 -> 1) run on the CUDA cores.  The SiLU
+// derivatives are computed in the forward pass and kept in tensor memory
+// until the backward pass multiplies them in.  G1 and G2 accumulate over
+// the CTA's tiles of a step and are added to the step's gradient sum with
 // vector atomics.  Features and dy enter G2 as BF16 hi + lo pairs, so the
 // BF16 operand rounding leaves them exact to about 2^-17.
-constexpr int TT = 128;                       // samples per tile = threads = tensor-memory lanes
+constexpr int TT = 512;                       // threads
+constexpr int TS = 128;                       // samples per tile = tensor-memory lanes
 constexpr int GSTRIDE = 8580;                 // MLP_NP rounded up to whole float4s
 // shared memory (bytes).  Activation / delta tiles: 128 samples x 64 units
 // in core matrices of 8 samples x 8 units; unit block j at j x 2048, sample
@@ -55,13 +59,15 @@ constexpr int SM_ONES = SM_H1 + 16384, SM_ZERO = SM_ONES + 2048;
 constexpr int SM_FB = SM_ZERO + 2048, SM_D1 = SM_FB + 2048, SM_H3 = SM_D1 + 16384;   // [FB; D1], [D1; H3]
 constexpr int SM_P = SM_H3 + 16384, SM_M = SM_P + GSTRIDE * 4, SM_V = SM_M + GSTRIDE * 4;
 constexpr int SM_WQ = SM_V + GSTRIDE * 4;                                 // BF16-rounded W1, biases, W4 (MLP_F_*)
-constexpr int SM_MISC = SM_WQ + 388 * 4;
+constexpr int SM_YP = SM_WQ + 388 * 4;                                    // partial outputs [4][128]
+constexpr int SM_SF = SM_YP + 4 * TS * 4;                                 // sample: f0, f1, target, live [128]
+constexpr int SM_MISC = SM_SF + TS * 16;
 constexpr int TR_SMEM = SM_MISC + 64;
-static_assert(SM_MISC % 8 == 0, "mbarrier alignment");
+static_assert(SM_WQ % 16 == 0 && SM_MISC % 8 == 0, "alignment");
 static_assert(TR_SMEM <= 227 * 1024, "shared memory");
-// tensor-memory columns
-constexpr uint32_t TM_COLS = 512, TZ2 = 0, TZ3 = 64, TG1 = 128, TG2 = 288;
-constexpr uint32_t WAIT_POLLS = 1u << 22, BAR_POLLS = 1u << 22;
+// tensor-memory columns: products, SiLU derivatives of layers 1 and 2, gradients
+constexpr uint32_t TM_COLS = 512, TZ = 0, TD1 = 64, TD2 = 128, TG1 = 256, TG2 = 416;
+constexpr uint32_t WAIT_POLLS = 1u << 22, BAR_POLLS = 1u << 24;
 // instruction descriptors: forward (A, B K-major), backward (B MN-major), gradients
 constexpr uint32_t ID_FWD = tc::idesc_bf16(128, 64, 0, 0), ID_BWD = tc::idesc_bf16(128, 64, 0, 1);
 constexpr uint32_t ID_G1 = tc::idesc_bf16(128, 144, 1, 1), ID_G2 = tc::idesc_bf16(128, 16, 1, 1);
@@ -73,7 +79,7 @@ struct TrainArgs {
     float *loss;                              // sum of squared errors of the counted steps
     const float *icdf_em32;                   // target generator (the table method)
     const float *feat, *target;               // given samples, or null: draw them
-    const float *sched;                       // per step: learning rate, bias corrections 1 and 2
+    const float *sched;                       // per step: lr / bias correction 1, 1 / bias correction 2
     unsigned long long seed;
     long long per_step;                       // samples per step (the batch), or the given samples
     long long steps;                          // optimizer steps; 0: one gradient, no update
@@ -116,7 +122,14 @@ __device__ __forceinline__ void put_weight(unsigned char *sm, float *wq, int p, 
 }
 
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
-    return pack_bf16(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);     // a in the low half
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // all CTAs arrive; false when a wait ran out (the status word says which)
@@ -129,7 +142,6 @@ __device__ bool grid_sync(unsigned *bar, unsigned target, int *status, int *s_fl
         for (uint32_t it = 0; it < BAR_POLLS; ++it) {
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
             if (v >= target || *reinterpret_cast<volatile int *>(status)) break;
-            __nanosleep(64);
         }
         if (v < target) {
             atomicCAS(status, 0, 1);
@@ -141,14 +153,44 @@ __device__ bool grid_sync(unsigned *bar, unsigned target, int *status, int *s_fl
     return *reinterpret_cast<volatile int *>(s_flag) == 0;
 }
 
+// 16 activations of one sample row (units u0..u0+15): pre-activation z (with
+// bias) -> BF16 SiLU into two unit blocks of `tile`, SiLU derivative into d
+__device__ __forceinline__ void silu_row(unsigned char *tile, int u0, int r, const float z[16], float d[16],
+                                         float h[16]) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float s0 = sigmoid_f(z[2 * q]), s1 = sigmoid_f(z[2 * q + 1]);
+        pk[q] = pack2(z[2 * q] * s0, z[2 * q + 1] * s1);
+        d[2 * q] = s0 * (1.0f + z[2 * q] * (1.0f - s0));
+        d[2 * q + 1] = s1 * (1.0f + z[2 * q + 1] * (1.0f - s1));
+        h[2 * q] = bf16_lo(pk[q]);
+        h[2 * q + 1] = bf16_hi(pk[q]);
+    }
+    *reinterpret_cast<uint4 *>(tile + (u0 / 8) * 2048 + r * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4 *>(tile + (u0 / 8 + 1) * 2048 + r * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+__device__ __forceinline__ void store_row(unsigned char *tile, int u0, int r, const float v[16]) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pk[q] = pack2(v[2 * q], v[2 * q + 1]);
+    *reinterpret_cast<uint4 *>(tile + (u0 / 8) * 2048 + r * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4 *>(tile + (u0 / 8 + 1) * 2048 + r * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
 __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float *sP = reinterpret_cast<float *>(sm + SM_P), *sM = reinterpret_cast<float *>(sm + SM_M);
     float *sV = reinterpret_cast<float *>(sm + SM_V), *wq = reinterpret_cast<float *>(sm + SM_WQ);
+    float *yp = reinterpret_cast<float *>(sm + SM_YP);
+    float4 *sf = reinterpret_cast<float4 *>(sm + SM_SF);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + SM_MISC);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + SM_MISC + 8);
     int *s_flag = reinterpret_cast<int *>(sm + SM_MISC + 12);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, cq = warp >> 2;       // lane quadrant; column quarter
+    const int r = quad * 32 + lane, u0 = cq * 16;    // sample row; first unit of this thread
     const bool train = a.steps > 0;
     const uint32_t base = tc::smem_u32(sm);
 
@@ -159,8 +201,10 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
         put_weight(sm, wq, p, sP[p]);
     }
     // constant blocks: a BF16 one in unit 0 of every sample row; zeros
-    *reinterpret_cast<uint4 *>(sm + SM_ONES + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4 *>(sm + SM_ZERO + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
+    if (tid < TS) {
+        *reinterpret_cast<uint4 *>(sm + SM_ONES + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(sm + SM_ZERO + tid * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (warp == 0) tc::alloc(tslot, TM_COLS);
     if (tid == 0) {
         tc::mbar_init(mbar, 1);
@@ -170,7 +214,7 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tslot, tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tmem = *tslot, tl = tmem + ((uint32_t)(quad * 32) << 16);
     uint32_t phase = 0;
     bool ok = true;
 
@@ -197,142 +241,132 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
         for (int kk = 0; kk < n; ++kk)
             tc::mma(d, tc::sdesc(aa + kk * ast, alb, asb), tc::sdesc(bb + kk * bst, blb, bsb), id, acc || kk > 0);
     };
+    auto bias16 = [&](int off, float z[16]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 b = *reinterpret_cast<const float4 *>(wq + off + u0 + 4 * q);
+            z[4 * q] += b.x;
+            z[4 * q + 1] += b.y;
+            z[4 * q + 2] += b.z;
+            z[4 * q + 3] += b.w;
+        }
+    };
 
-    const long long tiles = (a.per_step + TT - 1) / TT;
+    const long long tiles = (a.per_step + TS - 1) / TS;
     const long long nsteps = train ? a.steps : 1;
     for (long long s = 0; s < nsteps && ok; ++s) {
         float *g = a.gbuf + (train ? (s % 3) * GSTRIDE : 0);
         float dysum = 0.f, sq = 0.f;
         bool first = true;
         for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-            const long long idx = t * TT + tid;
-            const bool live = idx < a.per_step;
-            float f0 = 0.f, f1 = 0.f, ty = 0.f;
-            if (live) {
-                if (a.feat) {
-                    f0 = a.feat[2 * idx];
-                    f1 = a.feat[2 * idx + 1];
-                    ty = a.target[idx];
-                } else {
-                    const unsigned long long gi = (unsigned long long)s * a.per_step + (unsigned long long)idx;
-                    const uint4 r = philox4x32_10(make_uint4((uint32_t)gi, (uint32_t)(gi >> 32), 0u, 0x4D4C5000u),
-                                                  make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32)));
-                    float u1, v1, u2, v2;
-                    Uniform<float>::draw(r.x, r.y, u1, v1);
-                    Uniform<float>::draw(r.z, r.w, u2, v2);
-                    const float lc = -3.0f + 6.0f * u1;
-                    float sv = logit(u2, v2);
-                    sv = fminf(fmaxf(sv, -16.0f), 16.0f);
-                    f0 = lc / 3.0f;
-                    f1 = sv / 16.0f;
-                    ty = table_zeta(a.icdf_em32, lc, sv) / 16.0f + 0.5f;
+            // the tile's samples: drawn (or read) by the first 128 threads
+            if (tid < TS) {
+                const long long idx = t * TS + tid;
+                float f0 = 0.f, f1 = 0.f, ty = 0.f;
+                const bool live = idx < a.per_step;
+                if (live) {
+                    if (a.feat) {
+                        f0 = a.feat[2 * idx];
+                        f1 = a.feat[2 * idx + 1];
+                        ty = a.target[idx];
+                    } else {
+                        const unsigned long long gi = (unsigned long long)s * a.per_step + (unsigned long long)idx;
+                        const uint4 q = philox4x32_10(make_uint4((uint32_t)gi, (uint32_t)(gi >> 32), 0u, 0x4D4C5000u),
+                                                      make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32)));
+                        float u1, v1, u2, v2;
+                        Uniform<float>::draw(q.x, q.y, u1, v1);
+                        Uniform<float>::draw(q.z, q.w, u2, v2);
+                        const float lc = -3.0f + 6.0f * u1;
+                        float sv = logit(u2, v2);
+                        sv = fminf(fmaxf(sv, -16.0f), 16.0f);
+                        f0 = lc / 3.0f;
+                        f1 = sv / 16.0f;
+                        ty = table_zeta(a.icdf_em32, lc, sv) / 16.0f + 0.5f;
+                    }
                 }
+                sf[tid] = make_float4(f0, f1, ty, live ? 1.f : 0.f);
             }
-            auto z1_of = [&](int o) {
-                return wq[MLP_F_W1 + 2 * o] * f0 + wq[MLP_F_W1 + 2 * o + 1] * f1 + wq[MLP_F_B1 + o];
-            };
-            // layer 1 on the CUDA cores: H1 row
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                uint32_t pk[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) pk[q] = silu_pack(z1_of(8 * j + 2 * q), z1_of(8 * j + 2 * q + 1));
-                *reinterpret_cast<uint4 *>(sm + SM_H1 + j * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            }
-            // Z2 = H1 W2^T
-            ok = run_mma([&] { k_steps(tmem + TZ2, base + SM_H1, 2048, 128, 4096, base + SM_W2, 128, 1024, 256, ID_FWD, 4, false); });
-            if (!ok) break;
-#pragma unroll
-            for (int c = 0; c < 64; c += 16) {
-                float z[16];
-                tc::ld16(tl + TZ2 + c, z);
-                uint32_t pk[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    pk[q] = silu_pack(z[2 * q] + wq[MLP_F_B2 + c + 2 * q], z[2 * q + 1] + wq[MLP_F_B2 + c + 2 * q + 1]);
-                *reinterpret_cast<uint4 *>(sm + SM_H2 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4 *>(sm + SM_H2 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-            // Z3 = H2 W3^T; H3 row and the output y (layer 4, in unit order)
-            ok = run_mma([&] { k_steps(tmem + TZ3, base + SM_H2, 2048, 128, 4096, base + SM_W3, 128, 1024, 256, ID_FWD, 4, false); });
-            if (!ok) break;
-            float y = wq[MLP_F_B4];
-#pragma unroll
-            for (int c = 0; c < 64; c += 16) {
-                float z[16];
-                tc::ld16(tl + TZ3 + c, z);
-                uint32_t pk[8];
+            __syncthreads();
+            const float4 smp = sf[r];
+            const float f0 = smp.x, f1 = smp.y;
+            // layer 1 on the CUDA cores: H1, SiLU' into tensor memory
+            {
+                float z[16], d[16], h[16];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    pk[q] = silu_pack(z[2 * q] + wq[MLP_F_B3 + c + 2 * q], z[2 * q + 1] + wq[MLP_F_B3 + c + 2 * q + 1]);
-                    y += wq[MLP_F_W4 + c + 2 * q] * bf16_lo(pk[q]);
-                    y += wq[MLP_F_W4 + c + 2 * q + 1] * bf16_hi(pk[q]);
+                    const float4 w = *reinterpret_cast<const float4 *>(wq + MLP_F_W1 + 2 * (u0 + 2 * q));
+                    z[2 * q] = w.x * f0 + w.y * f1;
+                    z[2 * q + 1] = w.z * f0 + w.w * f1;
                 }
-                *reinterpret_cast<uint4 *>(sm + SM_H3 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4 *>(sm + SM_H3 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                bias16(MLP_F_B1, z);
+                silu_row(sm + SM_H1, u0, r, z, d, h);
+                tc::st16(tl + TD1 + u0, d);
             }
-            const float res = live ? y - ty : 0.f;
-            const float dy = 2.0f * res * a.inv_total;
-            dysum += dy;
-            sq += res * res;
-            {   // G2's B row: f0, f1 and dy as BF16 hi + lo, and a one
-                const __nv_bfloat16 f0h = __float2bfloat16_rn(f0), f1h = __float2bfloat16_rn(f1);
-                const __nv_bfloat16 dyh = __float2bfloat16_rn(dy);
-                const __nv_bfloat16 f0l = __float2bfloat16_rn(f0 - __bfloat162float(f0h));
-                const __nv_bfloat16 f1l = __float2bfloat16_rn(f1 - __bfloat162float(f1h));
-                const __nv_bfloat16 dyl = __float2bfloat16_rn(dy - __bfloat162float(dyh));
-                *reinterpret_cast<uint4 *>(sm + SM_FB + tid * 16) =
-                    make_uint4(pack_bf16(f0h, f0l), pack_bf16(f1h, f1l), pack_bf16(__float2bfloat16_rn(1.0f), dyh),
-                               pack_bf16(dyl, __float2bfloat16_rn(0.0f)));
-            }
-            // D3 = dy W4 silu'(Z3)
-#pragma unroll
-            for (int c = 0; c < 64; c += 16) {
-                float z[16];
-                tc::ld16(tl + TZ3 + c, z);
-                uint32_t pk[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int o = c + 2 * q;
-                    pk[q] = pack2(dy * wq[MLP_F_W4 + o] * dsilu_f(z[2 * q] + wq[MLP_F_B3 + o]),
-                                  dy * wq[MLP_F_W4 + o + 1] * dsilu_f(z[2 * q + 1] + wq[MLP_F_B3 + o + 1]));
-                }
-                *reinterpret_cast<uint4 *>(sm + SM_D3 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4 *>(sm + SM_D3 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-            // P3 = D3 W3; D2 = P3 silu'(Z2)
-            ok = run_mma([&] { k_steps(tmem + TZ3, base + SM_D3, 2048, 128, 4096, base + SM_W3, 1024, 128, 2048, ID_BWD, 4, false); });
+            // Z2 = H1 W2^T -> H2, SiLU'
+            ok = run_mma([&] { k_steps(tmem + TZ, base + SM_H1, 2048, 128, 4096, base + SM_W2, 128, 1024, 256, ID_FWD, 4, false); });
             if (!ok) break;
-#pragma unroll
-            for (int c = 0; c < 64; c += 16) {
-                float pv[16], z[16];
-                tc::ld16(tl + TZ3 + c, pv);
-                tc::ld16(tl + TZ2 + c, z);
-                uint32_t pk[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int o = c + 2 * q;
-                    pk[q] = pack2(pv[2 * q] * dsilu_f(z[2 * q] + wq[MLP_F_B2 + o]),
-                                  pv[2 * q + 1] * dsilu_f(z[2 * q + 1] + wq[MLP_F_B2 + o + 1]));
-                }
-                *reinterpret_cast<uint4 *>(sm + SM_D2 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4 *>(sm + SM_D2 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            {
+                float z[16], d[16], h[16];
+                tc::ld16(tl + TZ + u0, z);
+                bias16(MLP_F_B2, z);
+                silu_row(sm + SM_H2, u0, r, z, d, h);
+                tc::st16(tl + TD2 + u0, d);
             }
-            // P2 = D2 W2; D1 = P2 silu'(Z1)
-            ok = run_mma([&] { k_steps(tmem + TZ3, base + SM_D2, 2048, 128, 4096, base + SM_W2, 1024, 128, 2048, ID_BWD, 4, false); });
+            // Z3 = H2 W3^T -> H3, the output y (layer 4), D3 = dy W4 SiLU'(Z3)
+            ok = run_mma([&] { k_steps(tmem + TZ, base + SM_H2, 2048, 128, 4096, base + SM_W3, 128, 1024, 256, ID_FWD, 4, false); });
             if (!ok) break;
+            {
+                float z[16], d[16], h[16];
+                tc::ld16(tl + TZ + u0, z);
+                bias16(MLP_F_B3, z);
+                silu_row(sm + SM_H3, u0, r, z, d, h);
+                float yq = 0.f;
 #pragma unroll
-            for (int c = 0; c < 64; c += 16) {
-                float pv[16];
-                tc::ld16(tl + TZ3 + c, pv);
-                uint32_t pk[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int o = c + 2 * q;
-                    pk[q] = pack2(pv[2 * q] * dsilu_f(z1_of(o)), pv[2 * q + 1] * dsilu_f(z1_of(o + 1)));
+                for (int q = 0; q < 16; ++q) yq += wq[MLP_F_W4 + u0 + q] * h[q];
+                yp[cq * TS + r] = yq;
+                __syncthreads();
+                const float y = wq[MLP_F_B4] + ((yp[r] + yp[TS + r]) + yp[2 * TS + r]) + yp[3 * TS + r];
+                const float res = smp.w != 0.f ? y - smp.z : 0.f;
+                const float dy = 2.0f * res * a.inv_total;
+                if (cq == 0) {
+                    dysum += dy;
+                    sq += res * res;
+                    // G2's B row: f0, f1 and dy as BF16 hi + lo, and a one
+                    const __nv_bfloat16 f0h = __float2bfloat16_rn(f0), f1h = __float2bfloat16_rn(f1);
+                    const __nv_bfloat16 dyh = __float2bfloat16_rn(dy);
+                    const __nv_bfloat16 f0l = __float2bfloat16_rn(f0 - __bfloat162float(f0h));
+                    const __nv_bfloat16 f1l = __float2bfloat16_rn(f1 - __bfloat162float(f1h));
+                    const __nv_bfloat16 dyl = __float2bfloat16_rn(dy - __bfloat162float(dyh));
+                    *reinterpret_cast<uint4 *>(sm + SM_FB + r * 16) =
+                        make_uint4(pack_bf16(f0h, f0l), pack_bf16(f1h, f1l), pack_bf16(__float2bfloat16_rn(1.0f), dyh),
+                                   pack_bf16(dyl, __float2bfloat16_rn(0.0f)));
                 }
-                *reinterpret_cast<uint4 *>(sm + SM_D1 + (c / 8) * 2048 + tid * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4 *>(sm + SM_D1 + (c / 8 + 1) * 2048 + tid * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = dy * wq[MLP_F_W4 + u0 + q] * d[q];
+                store_row(sm + SM_D3, u0, r, v);
+            }
+            // P3 = D3 W3; D2 = P3 SiLU'(Z2)
+            ok = run_mma([&] { k_steps(tmem + TZ, base + SM_D3, 2048, 128, 4096, base + SM_W3, 1024, 128, 2048, ID_BWD, 4, false); });
+            if (!ok) break;
+            {
+                float pv[16], d[16];
+                tc::ld16(tl + TZ + u0, pv);
+                tc::ld16(tl + TD2 + u0, d);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) pv[q] *= d[q];
+                store_row(sm + SM_D2, u0, r, pv);
+            }
+            // P2 = D2 W2; D1 = P2 SiLU'(Z1)
+            ok = run_mma([&] { k_steps(tmem + TZ, base + SM_D2, 2048, 128, 4096, base + SM_W2, 1024, 128, 2048, ID_BWD, 4, false); });
+            if (!ok) break;
+            {
+                float pv[16], d[16];
+                tc::ld16(tl + TZ + u0, pv);
+                tc::ld16(tl + TD1 + u0, d);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) pv[q] *= d[q];
+                store_row(sm + SM_D1, u0, r, pv);
             }
             // weight and bias gradients of the tile, accumulated over the CTA's tiles of the step
             const bool acc = !first;
@@ -344,36 +378,37 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
         }
         if (!ok) break;
         if (!first) {
-            // row tid of G1: dW3 row tid and db3 (tid < 64), or dW2 row tid - 64 and db2
-            const bool lo = tid < 64;
-            float *gw = g + (lo ? MLP_W3 + tid * 64 : MLP_W2 + (tid - 64) * 64);
-            const uint32_t c0 = TG1 + (lo ? 0u : 64u);
+            // row r of G1: dW3 row r and db3 (r < 64), or dW2 row r - 64 and db2;
+            // this thread's 16 columns of it
+            const bool lo = r < 64;
+            float *gw = g + (lo ? MLP_W3 + r * 64 : MLP_W2 + (r - 64) * 64) + u0;
+            float v[16];
+            tc::ld16(tl + TG1 + (lo ? 0u : 64u) + u0, v);
 #pragma unroll
-            for (int c = 0; c < 64; c += 16) {
-                float v[16];
-                tc::ld16(tl + c0 + c, v);
-#pragma unroll
-                for (int q = 0; q < 16; q += 4)
-                    atomicAdd(reinterpret_cast<float4 *>(gw + c + q), make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
-            }
-            float v8[8];
-            tc::ld8(tl + TG1 + 128, v8);
-            atomicAdd(g + (lo ? MLP_B3 + tid : MLP_B2 + (tid - 64)), v8[0]);
-            tc::ld8(tl + TG2, v8);
-            if (lo) {
-                atomicAdd(reinterpret_cast<float2 *>(g + MLP_W1 + 2 * tid), make_float2(v8[0] + v8[1], v8[2] + v8[3]));
-                atomicAdd(g + MLP_B1 + tid, v8[4]);
-            } else {
-                atomicAdd(g + MLP_W4 + (tid - 64), v8[5] + v8[6]);
+            for (int q = 0; q < 16; q += 4)
+                atomicAdd(reinterpret_cast<float4 *>(gw + q), make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
+            if (cq == 0) {
+                float v8[8];
+                tc::ld8(tl + TG1 + 128, v8);
+                atomicAdd(g + (lo ? MLP_B3 + r : MLP_B2 + (r - 64)), v8[0]);
+                tc::ld8(tl + TG2, v8);
+                if (lo) {
+                    atomicAdd(reinterpret_cast<float2 *>(g + MLP_W1 + 2 * r), make_float2(v8[0] + v8[1], v8[2] + v8[3]));
+                    atomicAdd(g + MLP_B1 + r, v8[4]);
+                } else {
+                    atomicAdd(g + MLP_W4 + (r - 64), v8[5] + v8[6]);
+                }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            dysum += __shfl_down_sync(0xffffffffu, dysum, o);
-            sq += __shfl_down_sync(0xffffffffu, sq, o);
-        }
-        if (lane == 0) {
-            if (dysum != 0.f) atomicAdd(g + MLP_B4, dysum);
-            if (!train || s >= a.tail_from) atomicAdd(a.loss, sq);
+        if (cq == 0) {
+            for (int o = 16; o > 0; o >>= 1) {
+                dysum += __shfl_down_sync(0xffffffffu, dysum, o);
+                sq += __shfl_down_sync(0xffffffffu, sq, o);
+            }
+            if (lane == 0) {
+                if (dysum != 0.f) atomicAdd(g + MLP_B4, dysum);
+                if (!train || s >= a.tail_from) atomicAdd(a.loss, sq);
+            }
         }
         if (!train) break;
         // every CTA's sums are in: the same Adam update in every CTA
@@ -381,7 +416,7 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
             ok = false;
             break;
         }
-        const float lr = a.sched[3 * s], bc1 = a.sched[3 * s + 1], bc2 = a.sched[3 * s + 2];
+        const float lr_c = a.sched[2 * s], ibc2 = a.sched[2 * s + 1];
         const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
         for (int p = tid; p < MLP_NP; p += TT) {
             const float gv = __ldcg(g + p);
@@ -389,7 +424,7 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
             const float v = b2 * sV[p] + (1.f - b2) * gv * gv;
             sM[p] = m;
             sV[p] = v;
-            const float np = sP[p] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+            const float np = sP[p] - __fdividef(lr_c * m, sqrt_approx(v * ibc2) + eps);
             sP[p] = np;
             put_weight(sm, wq, p, np);
         }
@@ -529,7 +564,7 @@ struct TrainScratch {
 };
 
 static qed_status train_scratch(TrainScratch &t, int64_t steps, cudaStream_t st) {
-    const size_t g = sizeof(float) * 3 * GSTRIDE, sc = sizeof(float) * 3 * (size_t)(steps > 0 ? steps : 1);
+    const size_t g = sizeof(float) * 3 * GSTRIDE, sc = sizeof(float) * 2 * (size_t)(steps > 0 ? steps : 1);
     const size_t bytes = g + ((sc + 255) / 256) * 256 + 256;
     if (cudaMalloc(&t.mem, bytes) != cudaSuccess) return QED_ERR_NOMEM;
     t.gbuf = static_cast<float *>(t.mem);
@@ -566,7 +601,7 @@ qed_status sfq_mlp_grad(qed_ctx *ctx, const float *feat, const float *target, in
     if (e != QED_OK) return e;
     SFQ_CUDA(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(float), st));
     int grid = 0;
-    if ((e = train_grid((n + TT - 1) / TT, &grid)) != QED_OK) return e;
+    if ((e = train_grid((n + TS - 1) / TS, &grid)) != QED_OK) return e;
     TrainArgs a{P, P + MLP_NP, P + 2 * MLP_NP, t.gbuf, ctx->mlp_w16, ctx->mlp_loss, ctx->icdf_em32, feat, target,
                 t.sched, 0ull, (long long)n, 0ll, 0ll, 1.0f / (float)n, t.bar, t.status};
     k_mlp_train<<<grid, TT, TR_SMEM, st>>>(a);
@@ -588,7 +623,7 @@ qed_status sfq_mlp_grad(qed_ctx *ctx, const float *feat, const float *target, in
 // launch of k_mlp_train; the step schedule is computed here in FP64 and
 // rounded to FP32 once.
 qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, uint64_t seed, double *final_loss) {
-    if (!ctx || n_samples <= 0 || batch <= 0 || batch % TT || !(lr > 0.0)) return QED_ERR_INVALID;
+    if (!ctx || n_samples <= 0 || batch <= 0 || batch % TS || !(lr > 0.0)) return QED_ERR_INVALID;
     qed_status e = mlp_alloc(ctx);
     if (e != QED_OK) return e;
     cudaStream_t st = ctx->stream;
@@ -596,19 +631,20 @@ qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, 
     k_mlp_init<<<(MLP_NP + 255) / 256, 256, 0, st>>>(P, M, V, G, ctx->mlp_w16, seed);
     SFQ_CUDA(cudaGetLastError());
     const int64_t steps = (n_samples + batch - 1) / batch;
-    std::vector<float> sched((size_t)steps * 3);
+    std::vector<float> sched((size_t)steps * 2);
     for (int64_t s = 0; s < steps; ++s) {
         const double frac = (double)s / (double)(steps > 1 ? steps - 1 : 1);
-        sched[3 * s] = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(3.14159265358979323846 * frac))));
-        sched[3 * s + 1] = (float)(1.0 - pow(0.9, (double)(s + 1)));
-        sched[3 * s + 2] = (float)(1.0 - pow(0.999, (double)(s + 1)));
+        const double lr_t = lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(3.14159265358979323846 * frac)));
+        const double bc1 = 1.0 - pow(0.9, (double)(s + 1)), bc2 = 1.0 - pow(0.999, (double)(s + 1));
+        sched[2 * s] = (float)(lr_t / bc1);
+        sched[2 * s + 1] = (float)(1.0 / bc2);
     }
     TrainScratch t;
     if ((e = train_scratch(t, steps, st)) != QED_OK) return e;
     SFQ_CUDA(cudaMemcpyAsync(t.sched, sched.data(), sizeof(float) * sched.size(), cudaMemcpyHostToDevice, st));
     SFQ_CUDA(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(float), st));
     int grid = 0;
-    if ((e = train_grid(batch / TT, &grid)) != QED_OK) return e;
+    if ((e = train_grid(batch / TS, &grid)) != QED_OK) return e;
     const int64_t tail = steps < 16 ? steps : 16;     // the loss is averaged over the last 16 steps
     TrainArgs a{P, M, V, t.gbuf, ctx->mlp_w16, ctx->mlp_loss, ctx->icdf_em32, nullptr, nullptr, t.sched, seed,
                 (long long)batch, (long long)steps, (long long)(steps - tail), 1.0f / (float)batch, t.bar, t.status};

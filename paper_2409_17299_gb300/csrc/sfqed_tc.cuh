@@ -1,7 +1,7 @@
 // Blackwell tensor-core primitives (tcgen05) for one CTA (cta_group::1):
 // tensor-memory allocation, shared-memory matrix descriptors, the BF16 MMA
 // with FP32 accumulation in tensor memory, completion through an mbarrier,
-// and tensor-memory loads.
+// and tensor-memory loads and stores.
 //
 // Operand layout (no swizzle): a matrix is a grid of 8 x 8 "core matrices",
 // each 8 rows of 16 contiguous bytes (128 contiguous bytes).  For an operand
@@ -104,6 +104,18 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// store 16 FP32 columns of this thread's lane (shape 32x32b, as ld16) and
+// wait until the store has completed
+__device__ __forceinline__ void st16(uint32_t taddr, const float v[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])));
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void ld8(uint32_t taddr, float v[8]) {
