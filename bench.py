@@ -64,9 +64,9 @@ NCU_PHOTON_BYTES_PER_STEP = {"fp32": 47.6, "fp64": None}
 NCU_LEPTON_BYTES_PER_STEP = {"fp32": 80.1, "fp64": None}
 # FP64 FLOPs (2 DFMA + DADD + DMUL thread instructions) per particle-step of
 # the FP64 step-start passes at the rotating-E cascade's cap (0.3 emissions
-# per lepton-step), from one ncu capture of the current kernels
-# (profiles/fp64_passes_rotating_e_cascade.md)
-NCU_FP64_FLOP_PER_STEP = {"k_lepton_pass": 478.0, "k_photon_pass": 193.0}
+# per lepton-step): the launch's count over the particles it pushed, from one
+# ncu capture of the current kernels (profiles/fp64_passes_rotating_e_cascade.md)
+NCU_FP64_FLOP_PER_STEP = {"k_lepton_pass": 481.7, "k_photon_pass": 206.0}
 # algorithmic FLOPs per training sample of the 2-64-64-64-1 network: forward
 # 2 x (2*64 + 64*64 + 64*64 + 64) multiply-adds, backward the two 64x64 input
 # gradients, the two 64x64 weight gradients, W1's and W4's gradients
@@ -105,6 +105,10 @@ def parse():
     ap.add_argument("--profile-step", type=int, default=None,
                     help="profiling run for ncu --profile-from-start off: drive the workload (--scale) to this "
                          "step, then one host-driven step inside cudaProfilerStart/Stop")
+    ap.add_argument("--profile-sampler", default="table", choices=["table", "mlp"],
+                    help="--profile-step: emission sampler (mlp: a network trained on --mlp-samples draws first)")
+    ap.add_argument("--profile-method", default="waiting-time", choices=["waiting-time", "optical-depth"],
+                    help="--profile-step: event method")
     return ap.parse_args()
 
 
@@ -650,7 +654,11 @@ def main():
         print(json.dumps(train), flush=True)
         return
     if args.profile_step is not None:
-        return profile_step(w, args.precision, args.profile_step)
+        mlp_params = None
+        if args.profile_sampler == "mlp":
+            mlp_params, _ = train_surrogate_timed(int(args.mlp_samples), peaks)
+        return profile_step(w, args.precision, args.profile_step, mlp_params,
+                            1 if args.profile_method == "optical-depth" else 0)
     caps = size_cascade(w, n_total, args.precision) if w.push_photons else None
     if args.ncu_window:
         _, _, t, _ = gpu_run(args, w, args.precision, start, warm, steps, caps=caps, profile=True,
@@ -931,21 +939,29 @@ def growth_summary(runs):
             "seconds": float(sum(r["seconds"] for r in runs))}
 
 
-def profile_step(w, precision, step):
+def profile_step(w, precision, step, mlp_params=None, method=0):
     """Drive the workload to `step` (captured steps), then run one step
     through the host-driven launches inside cudaProfilerStart/Stop: the small
-    case an ncu capture of single kernels is taken on."""
+    case an ncu capture of single kernels is taken on.  mlp_params: network
+    sampler with these parameters; method: event method."""
     import torch
     import paper_2409_17299_gb300 as q
     prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
     caps = [int(c * 1.1) for c in capacities(w, w.nsteps)]
-    gen = q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons, thin_cap=w.thin_cap))
-    ens = q.DeviceEnsemble.from_host(w.species, caps, prec)
+    sampler = q.QED_SAMPLER_MLP if mlp_params is not None else q.QED_SAMPLER_TABLE
+
+    def generator(profile):
+        g = q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons,
+                                      thin_cap=w.thin_cap, profile=profile, sampler=sampler, event_method=method))
+        if mlp_params is not None:
+            q.qed_mlp_set_params(g.ctx, mlp_params)
+        return g
+    gen = generator(0)
+    ens = q.DeviceEnsemble.from_host(w.species, caps, prec, optical_depth=method != 0)
     field = q.make_field(w.field_kind, w.field_prm)
     for s in range(0, step, 10):
         gen.push(ens, field, w.dt, min(10, step - s), s)
-    genp = q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=w.push_photons,
-                                     thin_cap=w.thin_cap, profile=1))
+    genp = generator(1)
     counts0 = list(ens.count)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()

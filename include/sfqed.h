@@ -147,6 +147,8 @@ typedef struct {
     double sync_ms;           /* host time spent waiting in stream synchronisation */
     double call_ms;           /* host wall time of the call (of a batch: from its opening
                                  qed_push_async to the end of qed_push_wait) */
+    int64_t moved;            /* entries moved into holes by the merge step (Sec. 4.2);
+                                 holes left in place (deferred) are counted when filled */
 } qed_stats;
 
 /* Create a context and build its rate approximant and inverse-CDF tables on

@@ -62,7 +62,8 @@ class QedStats(C.Structure):
                 ("needed_capacity", C.c_int64 * 3), ("max_subevents", C.c_int64), ("overflow", C.c_int64),
                 ("passes", C.c_int64), ("thinned", C.c_int64), ("lepton_steps", C.c_int64),
                 ("photon_steps", C.c_int64), ("launches", C.c_int64), ("chi_fp64", C.c_int64),
-                ("kernel_ms", C.c_double * 4), ("sync_ms", C.c_double), ("call_ms", C.c_double)]
+                ("kernel_ms", C.c_double * 4), ("sync_ms", C.c_double), ("call_ms", C.c_double),
+                ("moved", C.c_int64)]
 
     def as_dict(self):
         return {"particle_steps": self.particle_steps, "emit_events": self.emit_events,
@@ -70,7 +71,8 @@ class QedStats(C.Structure):
                 "max_subevents": self.max_subevents, "overflow": self.overflow,
                 "passes": self.passes, "thinned": self.thinned, "lepton_steps": self.lepton_steps,
                 "photon_steps": self.photon_steps, "launches": self.launches, "chi_fp64": self.chi_fp64,
-                "kernel_ms": list(self.kernel_ms), "sync_ms": self.sync_ms, "call_ms": self.call_ms}
+                "kernel_ms": list(self.kernel_ms), "sync_ms": self.sync_ms, "call_ms": self.call_ms,
+                "moved": self.moved}
 
 
 class QedError(RuntimeError):

@@ -151,6 +151,7 @@ extern "C" qed_status qed_compact(qed_ctx *ctx, qed_particles *p, int64_t step) 
     if (ctx->ctl_host->bad_index) return QED_ERR_STATE;
     for (int s = 0; s < 3; ++s) p->s[s].count = (int64_t)ctx->ctl_host->count[s];
     ctx->acc.thinned += (int64_t)ctx->ctl_host->thinned;
+    ctx->acc.moved += (int64_t)ctx->ctl_host->moved;
     return QED_OK;
 }
 
@@ -200,6 +201,7 @@ extern "C" qed_status qed_level_apply(qed_ctx *ctx, qed_particles *p, int specie
     if (ctx->ctl_host->bad_index) return QED_ERR_STATE;
     p->s[species].count = (int64_t)ctx->ctl_host->count[species];
     ctx->acc.thinned += (int64_t)ctx->ctl_host->thinned;
+    ctx->acc.moved += (int64_t)ctx->ctl_host->moved;
     return QED_OK;
 }
 

@@ -677,6 +677,7 @@ __global__ void k_scan_tiles(const void *w, unsigned long long *blk, long long n
         } else {
             ctl->alive[s] = A;
             ctl->holes[s] = A - below;
+            ctl->moved += A - below;
             ctl->deferred[s] = 0;
         }
     }

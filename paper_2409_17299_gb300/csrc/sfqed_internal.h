@@ -61,7 +61,8 @@ struct DevCtl {
     float sv_t_red_f;                   // current step: (t_n mod 2 pi) rounded to float
     unsigned sv_step;                   // current step index (Philox counter word 2)
     unsigned long long deferred[3];     // dead entries left in place by the last merge step
-    unsigned long long pad[6];
+    unsigned long long moved;           // compaction: entries moved into holes
+    unsigned long long pad[5];
 };
 
 // The current step's time as the pass kernels read it from the control

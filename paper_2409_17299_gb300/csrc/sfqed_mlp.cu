@@ -63,7 +63,10 @@ constexpr int SM_YP = SM_WQ + 388 * 4;                                    // par
 constexpr int SM_SF = SM_YP + 4 * TS * 4;                                 // sample: f0, f1, target, live [128]
 constexpr int SM_MISC = SM_SF + TS * 16;
 constexpr int TR_SMEM = SM_MISC + 64;
-static_assert(SM_WQ % 16 == 0 && SM_MISC % 8 == 0, "alignment");
+static_assert(SM_P % 16 == 0 && SM_WQ % 16 == 0 && SM_MISC % 8 == 0 && GSTRIDE % 4 == 0, "alignment");
+static_assert(MLP_B1 % 4 == 0 && MLP_W2 % 4 == 0 && MLP_B2 % 4 == 0 && MLP_W3 % 4 == 0 && MLP_B3 % 4 == 0 &&
+                  MLP_W4 % 4 == 0 && MLP_B4 % 4 == 0 && GSTRIDE - MLP_B4 <= 4,
+              "the Adam update takes the parameters in groups of four that never straddle two regions");
 static_assert(TR_SMEM <= 227 * 1024, "shared memory");
 // tensor-memory columns: products, SiLU derivatives of layers 1 and 2, gradients
 constexpr uint32_t TM_COLS = 512, TZ = 0, TD1 = 64, TD2 = 128, TG1 = 256, TG2 = 416;
@@ -124,6 +127,18 @@ __device__ __forceinline__ void put_weight(unsigned char *sm, float *wq, int p, 
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);     // a in the low half
     return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// fire-and-forget additions to global memory (no value returned)
+__device__ __forceinline__ void red_add(float *p, float a) {
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
+}
+__device__ __forceinline__ void red_add2(float *p, float a, float b) {
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
 }
 
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -194,11 +209,12 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
     const bool train = a.steps > 0;
     const uint32_t base = tc::smem_u32(sm);
 
-    for (int p = tid; p < MLP_NP; p += TT) {
-        sP[p] = a.P[p];
-        sM[p] = train ? a.M[p] : 0.f;
-        sV[p] = train ? a.V[p] : 0.f;
-        put_weight(sm, wq, p, sP[p]);
+    for (int p = tid; p < GSTRIDE; p += TT) {
+        const bool in = p < MLP_NP;                  // the last three entries pad to a whole float4
+        sP[p] = in ? a.P[p] : 0.f;
+        sM[p] = in && train ? a.M[p] : 0.f;
+        sV[p] = in && train ? a.V[p] : 0.f;
+        if (in) put_weight(sm, wq, p, sP[p]);
     }
     // constant blocks: a BF16 one in unit 0 of every sample row; zeros
     if (tid < TS) {
@@ -252,40 +268,47 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
         }
     };
 
+    // the samples of tile t of step s: drawn (or read) by the first 128
+    // threads into sf; the caller synchronises the block before use
+    auto draw = [&](long long s_, long long t) {
+        if (tid < TS) {
+            const long long idx = t * TS + tid;
+            float f0 = 0.f, f1 = 0.f, ty = 0.f;
+            const bool live = idx < a.per_step;
+            if (live) {
+                if (a.feat) {
+                    f0 = a.feat[2 * idx];
+                    f1 = a.feat[2 * idx + 1];
+                    ty = a.target[idx];
+                } else {
+                    const unsigned long long gi = (unsigned long long)s_ * a.per_step + (unsigned long long)idx;
+                    const uint4 q = philox4x32_10(make_uint4((uint32_t)gi, (uint32_t)(gi >> 32), 0u, 0x4D4C5000u),
+                                                  make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32)));
+                    float u1, v1, u2, v2;
+                    Uniform<float>::draw(q.x, q.y, u1, v1);
+                    Uniform<float>::draw(q.z, q.w, u2, v2);
+                    const float lc = -3.0f + 6.0f * u1;
+                    float sv = logit(u2, v2);
+                    sv = fminf(fmaxf(sv, -16.0f), 16.0f);
+                    f0 = lc / 3.0f;
+                    f1 = sv / 16.0f;
+                    ty = table_zeta(a.icdf_em32, lc, sv) / 16.0f + 0.5f;
+                }
+            }
+            sf[tid] = make_float4(f0, f1, ty, live ? 1.f : 0.f);
+        }
+    };
+
     const long long tiles = (a.per_step + TS - 1) / TS;
     const long long nsteps = train ? a.steps : 1;
+    bool drawn = false;                              // sf already holds the next tile's samples
     for (long long s = 0; s < nsteps && ok; ++s) {
         float *g = a.gbuf + (train ? (s % 3) * GSTRIDE : 0);
         float dysum = 0.f, sq = 0.f;
         bool first = true;
         for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-            // the tile's samples: drawn (or read) by the first 128 threads
-            if (tid < TS) {
-                const long long idx = t * TS + tid;
-                float f0 = 0.f, f1 = 0.f, ty = 0.f;
-                const bool live = idx < a.per_step;
-                if (live) {
-                    if (a.feat) {
-                        f0 = a.feat[2 * idx];
-                        f1 = a.feat[2 * idx + 1];
-                        ty = a.target[idx];
-                    } else {
-                        const unsigned long long gi = (unsigned long long)s * a.per_step + (unsigned long long)idx;
-                        const uint4 q = philox4x32_10(make_uint4((uint32_t)gi, (uint32_t)(gi >> 32), 0u, 0x4D4C5000u),
-                                                      make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32)));
-                        float u1, v1, u2, v2;
-                        Uniform<float>::draw(q.x, q.y, u1, v1);
-                        Uniform<float>::draw(q.z, q.w, u2, v2);
-                        const float lc = -3.0f + 6.0f * u1;
-                        float sv = logit(u2, v2);
-                        sv = fminf(fmaxf(sv, -16.0f), 16.0f);
-                        f0 = lc / 3.0f;
-                        f1 = sv / 16.0f;
-                        ty = table_zeta(a.icdf_em32, lc, sv) / 16.0f + 0.5f;
-                    }
-                }
-                sf[tid] = make_float4(f0, f1, ty, live ? 1.f : 0.f);
-            }
+            if (!drawn) draw(s, t);
+            drawn = false;
             __syncthreads();
             const float4 smp = sf[r];
             const float f0 = smp.x, f1 = smp.y;
@@ -386,17 +409,17 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
             tc::ld16(tl + TG1 + (lo ? 0u : 64u) + u0, v);
 #pragma unroll
             for (int q = 0; q < 16; q += 4)
-                atomicAdd(reinterpret_cast<float4 *>(gw + q), make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
+                red_add4(gw + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
             if (cq == 0) {
                 float v8[8];
                 tc::ld8(tl + TG1 + 128, v8);
-                atomicAdd(g + (lo ? MLP_B3 + r : MLP_B2 + (r - 64)), v8[0]);
+                red_add(g + (lo ? MLP_B3 + r : MLP_B2 + (r - 64)), v8[0]);
                 tc::ld8(tl + TG2, v8);
                 if (lo) {
-                    atomicAdd(reinterpret_cast<float2 *>(g + MLP_W1 + 2 * r), make_float2(v8[0] + v8[1], v8[2] + v8[3]));
-                    atomicAdd(g + MLP_B1 + r, v8[4]);
+                    red_add2(g + MLP_W1 + 2 * r, v8[0] + v8[1], v8[2] + v8[3]);
+                    red_add(g + MLP_B1 + r, v8[4]);
                 } else {
-                    atomicAdd(g + MLP_W4 + (r - 64), v8[5] + v8[6]);
+                    red_add(g + MLP_W4 + (r - 64), v8[5] + v8[6]);
                 }
             }
         }
@@ -406,11 +429,17 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
                 sq += __shfl_down_sync(0xffffffffu, sq, o);
             }
             if (lane == 0) {
-                if (dysum != 0.f) atomicAdd(g + MLP_B4, dysum);
-                if (!train || s >= a.tail_from) atomicAdd(a.loss, sq);
+                if (dysum != 0.f) red_add(g + MLP_B4, dysum);
+                if (!train || s >= a.tail_from) red_add(a.loss, sq);
             }
         }
         if (!train) break;
+        // the next step's first samples do not depend on the update: drawn
+        // while the other CTAs arrive
+        if (s + 1 < nsteps && blockIdx.x < tiles) {
+            draw(s + 1, blockIdx.x);
+            drawn = true;
+        }
         // every CTA's sums are in: the same Adam update in every CTA
         if (!grid_sync(a.bar, (unsigned)(gridDim.x * (s + 1)), a.status, s_flag)) {
             ok = false;
@@ -418,15 +447,48 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
         }
         const float lr_c = a.sched[2 * s], ibc2 = a.sched[2 * s + 1];
         const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-        for (int p = tid; p < MLP_NP; p += TT) {
-            const float gv = __ldcg(g + p);
-            const float m = b1 * sM[p] + (1.f - b1) * gv;
-            const float v = b2 * sV[p] + (1.f - b2) * gv * gv;
-            sM[p] = m;
-            sV[p] = v;
-            const float np = sP[p] - __fdividef(lr_c * m, sqrt_approx(v * ibc2) + eps);
-            sP[p] = np;
-            put_weight(sm, wq, p, np);
+        // four consecutive parameters per thread and group (every region of
+        // the layout starts at a multiple of four, so a group never straddles
+        // two), all gradient loads in flight before the first use
+        constexpr int NG = GSTRIDE / 4, AG = (NG + TT - 1) / TT;
+        float4 gv[AG];
+#pragma unroll
+        for (int k = 0; k < AG; ++k) {
+            const int gi = tid + k * TT;
+            gv[k] = gi < NG ? __ldcg(reinterpret_cast<const float4 *>(g) + gi) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        auto adam = [&](float gr, float &m, float &v, float &pp) {
+            m = b1 * m + (1.f - b1) * gr;
+            v = b2 * v + (1.f - b2) * gr * gr;
+            pp = pp - __fdividef(lr_c * m, sqrt_approx(v * ibc2) + eps);
+        };
+#pragma unroll
+        for (int k = 0; k < AG; ++k) {
+            const int gi = tid + k * TT, p = 4 * gi;
+            if (gi >= NG) break;
+            float4 m4 = reinterpret_cast<float4 *>(sM)[gi], v4 = reinterpret_cast<float4 *>(sV)[gi];
+            float4 p4 = reinterpret_cast<float4 *>(sP)[gi];
+            adam(gv[k].x, m4.x, v4.x, p4.x);
+            adam(gv[k].y, m4.y, v4.y, p4.y);
+            adam(gv[k].z, m4.z, v4.z, p4.z);
+            adam(gv[k].w, m4.w, v4.w, p4.w);
+            reinterpret_cast<float4 *>(sM)[gi] = m4;
+            reinterpret_cast<float4 *>(sV)[gi] = v4;
+            reinterpret_cast<float4 *>(sP)[gi] = p4;
+            // the BF16 values where the passes read them
+            const uint2 b = make_uint2(pack2(p4.x, p4.y), pack2(p4.z, p4.w));
+            if (p >= MLP_W2 && p < MLP_B2) {
+                const int q = p - MLP_W2;
+                *reinterpret_cast<uint2 *>(sm + SM_W2 + wtile_off(q >> 6, q & 63)) = b;
+            } else if (p >= MLP_W3 && p < MLP_B3) {
+                const int q = p - MLP_W3;
+                *reinterpret_cast<uint2 *>(sm + SM_W3 + wtile_off(q >> 6, q & 63)) = b;
+            } else {
+                // W1, b1 at MLP_F_W1 = 0.., b2 at MLP_F_B2, b3, W4, b4 (and the
+                // group's padding) at MLP_F_B3..: offsets p, p - 4096, p - 8192
+                const int d = p < MLP_W2 ? p : (p < MLP_W3 ? p - (MLP_B2 - MLP_F_B2) : p - (MLP_B3 - MLP_F_B3));
+                *reinterpret_cast<float4 *>(wq + d) = make_float4(bf16_lo(b.x), bf16_hi(b.x), bf16_lo(b.y), bf16_hi(b.y));
+            }
         }
         // the sum two steps ahead was last read before this step's barrier
         float *gz = a.gbuf + ((s + 2) % 3) * GSTRIDE;

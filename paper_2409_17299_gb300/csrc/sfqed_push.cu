@@ -617,6 +617,7 @@ static qed_status wait_batch(qed_ctx *ctx, qed_particles *p, qed_stats *out) {
     st.overflow = (int64_t)c.overflow;
     st.passes = (int64_t)c.passes;
     st.thinned = (int64_t)c.thinned;
+    st.moved = (int64_t)c.moved;
     st.lepton_steps = (int64_t)c.lepton_steps;
     st.chi_fp64 = (int64_t)c.chi_fp64;
     st.photon_steps = (int64_t)c.photon_steps;
@@ -645,6 +646,7 @@ static qed_status wait_batch(qed_ctx *ctx, qed_particles *p, qed_stats *out) {
     ctx->acc.pair_events += st.pair_events;
     ctx->acc.passes += st.passes;
     ctx->acc.thinned += st.thinned;
+    ctx->acc.moved += st.moved;
     ctx->acc.lepton_steps += st.lepton_steps;
     ctx->acc.chi_fp64 += st.chi_fp64;
     ctx->acc.photon_steps += st.photon_steps;
