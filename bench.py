@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--compare-mlp", type=int, default=1,
                     help="also train the surrogate sampler (1e8 table draws) and time the cascade with it")
     ap.add_argument("--mlp-samples", type=float, default=1e8)
+    ap.add_argument("--mlp-batch", type=int, default=8192,
+                    help="--train-only: samples per optimizer step (a multiple of 128)")
     ap.add_argument("--train-only", action="store_true",
                     help="only train the surrogate on --mlp-samples draws and print the training line")
     ap.add_argument("--compare-od", type=int, default=1,
@@ -650,7 +652,7 @@ def main():
 
     n_total = start + warm + steps
     if args.train_only:
-        _, train = train_surrogate_timed(int(args.mlp_samples), peaks)
+        _, train = train_surrogate_timed(int(args.mlp_samples), peaks, args.mlp_batch)
         print(json.dumps(train), flush=True)
         return
     if args.profile_step is not None:
@@ -975,17 +977,17 @@ def profile_step(w, precision, step, mlp_params=None, method=0):
     genp.close()
 
 
-def train_surrogate_timed(samples, peaks):
-    """Train the surrogate on `samples` table draws (batch 8192, the settings
-    the tests use) after a short warm-up training; wall time of the call and
-    the training roofline against the measured BF16 peak."""
+def train_surrogate_timed(samples, peaks, batch=8192):
+    """Train the surrogate on `samples` table draws (batch 8192 and lr 4e-3
+    are the settings the tests use) after a short warm-up training; wall time
+    of the call and the training roofline against the measured BF16 peak."""
     import torch
     import paper_2409_17299_gb300 as q
     tg = q.Generator(q.make_config(precision=q.QED_FP32))
-    q.qed_train_surrogate(tg.ctx, 8192 * 16, 8192, 4e-3, 7)
+    q.qed_train_surrogate(tg.ctx, batch * 16, batch, 4e-3, 7)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    loss = q.qed_train_surrogate(tg.ctx, samples, 8192, 4e-3, 7)
+    loss = q.qed_train_surrogate(tg.ctx, samples, batch, 4e-3, 7)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     P = q.qed_mlp_get_params(tg.ctx)
@@ -993,7 +995,7 @@ def train_surrogate_timed(samples, peaks):
     bf16_peak = peaks.get("bf16_tflops")
     ach = MLP_TRAIN_FLOP_PER_SAMPLE * samples / train_s / 1e12
     return P, {
-        "train_samples": samples, "train_seconds": train_s, "train_final_mse": loss,
+        "train_samples": samples, "train_batch": batch, "train_seconds": train_s, "train_final_mse": loss,
         "network": "2-64-64-64-1 SiLU, BF16 weights, FP32 accumulation; training on tcgen05.mma with "
                    "tensor-memory accumulators (one cooperative launch), inference inside the lepton "
                    "pass on mma.sync",
