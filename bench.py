@@ -730,6 +730,17 @@ def main():
         mlp = {"value": tot_m["particle_steps"] / (ms_m / 1e3),
                "events_per_s": (tot_m["emit_events"] + tot_m["pair_events"]) / (ms_m / 1e3),
                "ms_per_step": ms_m / steps, **train}
+        # the same training at larger batches: more tiles per Adam step
+        # amortise the step's barriers, but fewer steps leave a higher loss
+        runs = []
+        for b in (19456, 38912, 77824):
+            _, tb = train_surrogate_timed(int(args.mlp_samples), peaks, b)
+            runs.append({"batch": b, "seconds": tb["train_seconds"], "final_mse": tb["train_final_mse"],
+                         "achieved_tflops": tb["train_roofline"]["achieved"], "frac": tb["train_roofline"]["frac"]})
+        mlp["train_batch_sweep"] = {
+            "note": "same samples and learning rate as the headline training (batch 8192, the setting the "
+                    "tests validate); a larger batch means fewer Adam steps and a higher final loss",
+            "runs": runs}
 
     growth = None
     if args.growth and world == 1 and args.workload == "rotating_e_cascade":
@@ -872,9 +883,10 @@ def main():
 # one warp instruction per scheduler per clock.
 ISSUE_PEAK_WARP_INSTR = 152 * 4 * 2.07e9
 # Warp instructions per lepton-step of the step-fused batch kernel (128
-# threads, budget 4) from one ncu capture of the current kernel
+# threads) from one ncu capture of the current kernel: the 10-step call's
+# count over its 4.02e7 lepton-steps
 # (profiles/k_emission_fused_batched_uniform_b.md); None when not captured
-NCU_FUSED_WARP_INSTR_PER_STEP = {"fp32": 47.9, "fp64": None}
+NCU_FUSED_WARP_INSTR_PER_STEP = {"fp32": 40.8, "fp64": None}
 
 
 # The paper's test problem (Sec. 5.1-5.2): growth rate of the cascade in its
