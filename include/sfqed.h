@@ -90,7 +90,12 @@ typedef struct {
                                  choice, else 4 */
     int event_method;         /* QED_METHOD_SUBSTEP (Algorithm 1, default) or
                                  QED_METHOD_OPTICAL_DEPTH (see below) */
-    int reserved[3];
+    int pass_limit;           /* newborn passes (Algorithm 2 sweeps) a step may run; a
+                                 step that needs more stops there and the call returns
+                                 QED_ERR_TIMEOUT; 0 = 100000 */
+    int wait_polls;           /* polls of each grid barrier inside qed_train_surrogate
+                                 before the launch gives up (QED_ERR_TIMEOUT); 0 = 2^24 */
+    int reserved[1];
 } qed_config;
 
 /* Event methods of qed_push_and_generate.

@@ -35,7 +35,7 @@ class QedConfig(C.Structure):
                 ("push_photons", C.c_int), ("soft_photon_filter", C.c_int), ("thin_cap", C.c_int64),
                 ("restore_on_overflow", C.c_int), ("block_threads", C.c_int), ("blocks_per_sm", C.c_int),
                 ("profile", C.c_int), ("batch_step_budget", C.c_int), ("event_method", C.c_int),
-                ("reserved", C.c_int * 3)]
+                ("pass_limit", C.c_int), ("wait_polls", C.c_int), ("reserved", C.c_int * 1)]
 
 
 class QedLevelState(C.Structure):
@@ -417,7 +417,8 @@ def qed_compact_species_noalloc(species: QedSpecies, precision: int, cuda_stream
 # --------------------------------------------------------------------------
 def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0, thin_cap=0,
                 restore_on_overflow=1, block_threads=0, blocks_per_sm=0, profile=0,
-                sampler=QED_SAMPLER_TABLE, batch_step_budget=0, event_method=QED_METHOD_SUBSTEP) -> QedConfig:
+                sampler=QED_SAMPLER_TABLE, batch_step_budget=0, event_method=QED_METHOD_SUBSTEP,
+                pass_limit=0, wait_polls=0) -> QedConfig:
     c = QedConfig()
     c.precision = int(precision)
     c.sampler = int(sampler)
@@ -431,6 +432,8 @@ def make_config(precision=QED_FP64, seed=0, push_photons=1, soft_photon_filter=0
     c.profile = int(profile)
     c.batch_step_budget = int(batch_step_budget)
     c.event_method = int(event_method)
+    c.pass_limit = int(pass_limit)
+    c.wait_polls = int(wait_polls)
     return c
 
 

@@ -62,7 +62,8 @@ struct DevCtl {
     unsigned sv_step;                   // current step index (Philox counter word 2)
     unsigned long long deferred[3];     // dead entries left in place by the last merge step
     unsigned long long moved;           // compaction: entries moved into holes
-    unsigned long long pad[5];
+    unsigned long long pass_limit;      // newborn passes a step may run (then timeout)
+    unsigned long long pad[4];
 };
 
 // The current step's time as the pass kernels read it from the control

@@ -70,7 +70,7 @@ static_assert(MLP_B1 % 4 == 0 && MLP_W2 % 4 == 0 && MLP_B2 % 4 == 0 && MLP_W3 % 
 static_assert(TR_SMEM <= 227 * 1024, "shared memory");
 // tensor-memory columns: products, SiLU derivatives of layers 1 and 2, gradients
 constexpr uint32_t TM_COLS = 512, TZ = 0, TD1 = 64, TD2 = 128, TG1 = 256, TG2 = 416;
-constexpr uint32_t WAIT_POLLS = 1u << 22, BAR_POLLS = 1u << 24;
+constexpr uint32_t WAIT_POLLS = 1u << 22, BAR_POLLS = 1u << 24;      // defaults of the bounded waits
 // instruction descriptors: forward (A, B K-major), backward (B MN-major), gradients
 constexpr uint32_t ID_FWD = tc::idesc_bf16(128, 64, 0, 0), ID_BWD = tc::idesc_bf16(128, 64, 0, 1);
 constexpr uint32_t ID_G1 = tc::idesc_bf16(128, 144, 1, 1), ID_G2 = tc::idesc_bf16(128, 16, 1, 1);
@@ -89,6 +89,7 @@ struct TrainArgs {
     long long tail_from;                      // steps from here on add to *loss
     float inv_total;                          // 1 / per_step
     unsigned *bar;                            // grid-barrier arrivals (zero at launch)
+    uint32_t bar_polls;                       // polls of a grid barrier before the launch gives up
     int *status;                              // 0 ok, 1 a barrier wait ran out, 2 an MMA wait ran out
 };
 
@@ -148,13 +149,13 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 // all CTAs arrive; false when a wait ran out (the status word says which)
-__device__ bool grid_sync(unsigned *bar, unsigned target, int *status, int *s_flag) {
+__device__ bool grid_sync(unsigned *bar, unsigned target, uint32_t polls, int *status, int *s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(bar, 1u);
         unsigned v = 0;
-        for (uint32_t it = 0; it < BAR_POLLS; ++it) {
+        for (uint32_t it = 0; it < polls; ++it) {
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
             if (v >= target || *reinterpret_cast<volatile int *>(status)) break;
         }
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(TT, 1) k_mlp_train(TrainArgs a) {
             drawn = true;
         }
         // every CTA's sums are in: the same Adam update in every CTA
-        if (!grid_sync(a.bar, (unsigned)(gridDim.x * (s + 1)), a.status, s_flag)) {
+        if (!grid_sync(a.bar, (unsigned)(gridDim.x * (s + 1)), a.bar_polls, a.status, s_flag)) {
             ok = false;
             break;
         }
@@ -665,7 +666,7 @@ qed_status sfq_mlp_grad(qed_ctx *ctx, const float *feat, const float *target, in
     int grid = 0;
     if ((e = train_grid((n + TS - 1) / TS, &grid)) != QED_OK) return e;
     TrainArgs a{P, P + MLP_NP, P + 2 * MLP_NP, t.gbuf, ctx->mlp_w16, ctx->mlp_loss, ctx->icdf_em32, feat, target,
-                t.sched, 0ull, (long long)n, 0ll, 0ll, 1.0f / (float)n, t.bar, t.status};
+                t.sched, 0ull, (long long)n, 0ll, 0ll, 1.0f / (float)n, t.bar, BAR_POLLS, t.status};
     k_mlp_train<<<grid, TT, TR_SMEM, st>>>(a);
     SFQ_CUDA(cudaGetLastError());
     SFQ_LAUNCHED(ctx, 1);
@@ -709,7 +710,8 @@ qed_status sfq_mlp_train(qed_ctx *ctx, int64_t n_samples, int batch, double lr, 
     if ((e = train_grid(batch / TS, &grid)) != QED_OK) return e;
     const int64_t tail = steps < 16 ? steps : 16;     // the loss is averaged over the last 16 steps
     TrainArgs a{P, M, V, t.gbuf, ctx->mlp_w16, ctx->mlp_loss, ctx->icdf_em32, nullptr, nullptr, t.sched, seed,
-                (long long)batch, (long long)steps, (long long)(steps - tail), 1.0f / (float)batch, t.bar, t.status};
+                (long long)batch, (long long)steps, (long long)(steps - tail), 1.0f / (float)batch, t.bar,
+                ctx->cfg.wait_polls > 0 ? (uint32_t)ctx->cfg.wait_polls : BAR_POLLS, t.status};
     void *args[] = {&a};
     SFQ_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_mlp_train), dim3(grid), dim3(TT), args,
                                          (size_t)TR_SMEM, st));

@@ -28,8 +28,12 @@ __global__ void k_grid_interleave(const T *src, T *dst, long long nodes) {
     dst[8 * n + 7] = (T)0;
 }
 
-// Newborn passes of one step after which the step gives up (QED_ERR_TIMEOUT).
+// Newborn passes of one step after which the step gives up (QED_ERR_TIMEOUT),
+// unless the configuration sets another limit.
 constexpr unsigned long long PASS_LIMIT = 100000;
+static unsigned long long pass_limit_of(const qed_ctx *ctx) {
+    return ctx->cfg.pass_limit > 0 ? (unsigned long long)ctx->cfg.pass_limit : PASS_LIMIT;
+}
 
 __device__ __forceinline__ bool ctl_stopped(const DevCtl *ctl) {
     return ctl->overflow || ctl->timeout || ctl->bad_index;
@@ -62,7 +66,7 @@ __global__ void k_set_timeout(DevCtl *ctl) { ctl->timeout = 1; }
 // Pass ranges of the next newborn pass: the particles appended since the
 // previous pass.  In a step graph it also sets the condition of the loop
 // over passes (the only setter): another pass while one found work, at most
-// PASS_LIMIT per step (then the step is marked as timed out).
+// ctl->pass_limit per step (then the step is marked as timed out).
 __device__ __forceinline__ unsigned long long pass_setup(DevCtl *ctl) {
     unsigned long long more = 0;
     for (int s = 0; s < 3; ++s) {
@@ -85,7 +89,8 @@ __global__ void k_pass_setup(DevCtl *ctl) { pass_setup(ctl); }
 
 __global__ void k_pass_setup_cond(DevCtl *ctl, cudaGraphConditionalHandle h, int in_body) {
     unsigned long long more = pass_setup(ctl);
-    if (more && ctl->step_passes > PASS_LIMIT) {
+    const unsigned long long limit = ctl->pass_limit ? ctl->pass_limit : PASS_LIMIT;
+    if (more && ctl->step_passes > limit) {
         ctl->timeout = 1;
         more = 0;
         for (int s = 0; s < 3; ++s) ctl->begin[s] = ctl->end[s];
@@ -420,7 +425,7 @@ static qed_status host_steps(qed_ctx *ctx, qed_particles *pw, PassArgs &a, doubl
                 e = read_ctl(ctx);
                 if (e != QED_OK) return e;
                 if (ctx->ctl_host->overflow || !ctx->ctl_host->more) break;
-                if (pass >= (int)PASS_LIMIT) {
+                if ((unsigned long long)pass >= pass_limit_of(ctx)) {
                     // give up like the graph's loop does (the wait reports it)
                     k_set_timeout<<<1, 1, 0, ctx->stream>>>(ctx->ctl);
                     SFQ_LAUNCHED(ctx, 1);
@@ -479,6 +484,7 @@ static qed_status open_batch(qed_ctx *ctx, qed_particles *p, int64_t step0) {
         h.capacity[s] = (unsigned long long)p->s[s].capacity;
     }
     h.step_next = (unsigned long long)step0;
+    h.pass_limit = pass_limit_of(ctx);
     SFQ_CUDA(cudaMemcpyAsync(ctx->ctl, &h, sizeof(DevCtl), cudaMemcpyHostToDevice, ctx->stream));
     int64_t cap_max = 0;
     for (int s = 0; s < 3; ++s) {
