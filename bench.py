@@ -730,6 +730,20 @@ def main():
         mlp = {"value": tot_m["particle_steps"] / (ms_m / 1e3),
                "events_per_s": (tot_m["emit_events"] + tot_m["pair_events"]) / (ms_m / 1e3),
                "ms_per_step": ms_m / steps, **train}
+        # the pass kernels' HBM fractions with the network sampler (a second,
+        # instrumented pass over the same steps)
+        _, _, tot_mp, _ = gpu_run(args, w, args.precision, start, warm, steps, mlp_params=P, caps=caps,
+                                  profile=True)
+        pr = args.precision
+        lb = LEPTON_BYTES[pr] * tot_mp["lepton_steps"] + EMIT_BYTES[pr] * tot_mp["emit_events"]
+        pb = PHOTON_BYTES[pr] * tot_mp["photon_steps"] + PAIR_BYTES[pr] * tot_mp["pair_events"]
+        lk, pk = tot_mp["kernel_ms"][0], tot_mp["kernel_ms"][1]
+        mlp["roofline"] = {
+            "k_lepton_pass (network sampler)": {"kernel_ms": lk, "achieved_gbs": lb / (lk / 1e3) / 1e9 if lk > 0 else None,
+                                                "frac": lb / (lk / 1e3) / 1e9 / hbm_peak if lk > 0 else None},
+            "k_photon_pass": {"kernel_ms": pk, "achieved_gbs": pb / (pk / 1e3) / 1e9 if pk > 0 else None,
+                              "frac": pb / (pk / 1e3) / 1e9 / hbm_peak if pk > 0 else None},
+            "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src + " hbm_gbs"}
         # the same training at larger batches: more tiles per Adam step
         # amortise the step's barriers, but fewer steps leave a higher loss
         runs = []
@@ -754,6 +768,20 @@ def main():
         for k, v in growth.items():
             v["eta_gamma_vs_fp64"] = v["gamma_mean"] / ref["gamma_mean"] - 1
             v["profile_l1_vs_fp64"] = float(np.abs(np.array(v["profile_mean"]) - np.array(ref["profile_mean"])).sum())
+        # one seed per mode over 20 T (the paper's long runs): Gamma fitted
+        # from 3.5 T to 20 T
+        s20 = GROWTH_SEEDS[:4]
+        t20 = {"fp64": [growth_run("fp64", sd, periods=20, fit=GROWTH_FIT_20T) for sd in s20],
+               "fp32": [growth_run("fp32", sd, periods=20, fit=GROWTH_FIT_20T) for sd in s20]}
+        if mlp:
+            t20["surrogate_fp32"] = [growth_run("fp32", sd, mlp_params=P, periods=20, fit=GROWTH_FIT_20T)
+                                     for sd in s20[:2]]
+        growth["t20"] = {k: growth_summary(v) for k, v in t20.items()}
+        for k, v in growth["t20"].items():
+            v["eta_gamma_vs_fp64"] = v["gamma_mean"] / growth["t20"]["fp64"]["gamma_mean"] - 1
+            v["profile_l1_vs_fp64"] = float(np.abs(np.array(v["profile_mean"]) -
+                                                   np.array(growth["t20"]["fp64"]["profile_mean"])).sum())
+            v["seeds"] = list(s20[:len(t20[k])])
         growth["setup"] = ("paper test problem: 2.5e5 e-/e+ at rest filling the 1-wavelength box, standing CP wave "
                            "a0 = 1557, dt = T/200, 5 T, leveling cap %d per species; Gamma fitted over steps %d-%d "
                            "from the leptons' total weight; density profile of lepton weight along x, %d bins; "
@@ -894,19 +922,20 @@ NCU_FUSED_WARP_INSTR_PER_STEP = {"fp32": 40.8, "fp64": None}
 GROWTH_SEEDS = (11, 12, 13, 14, 15)
 GROWTH_CAP = 2_000_000          # leveling cap per species (the paper does not print its own)
 GROWTH_FIT = (700, 1000)        # steps fitted: 3.5 T to 5 T (the paper: exponential after ~3.5 T)
+GROWTH_FIT_20T = (700, 4000)    # the 20 T runs: 3.5 T to 20 T
 GROWTH_BINS = 64
 
 
-def growth_run(precision, seed, mlp_params=None, n=250_000, cap=GROWTH_CAP, hook=None):
-    """One 5 T run of the test problem (one step per call): Gamma (per
-    period) from the slope of ln W, W the leptons' total weight (leveling keeps
-    its expectation), over GROWTH_FIT; the weighted lepton density along x
-    (wrapped to the box) at the end, normalised.  hook(step, gen, ens) runs
-    before each step."""
+def growth_run(precision, seed, mlp_params=None, n=250_000, cap=GROWTH_CAP, hook=None, periods=5, fit=GROWTH_FIT):
+    """One run of the test problem over `periods` periods (5 T by default;
+    one step per call): Gamma (per period) from the slope of ln W, W the
+    leptons' total weight (leveling keeps its expectation), over the steps
+    `fit`; the weighted lepton density along x (wrapped to the box) at the
+    end, normalised.  hook(step, gen, ens) runs before each step."""
     import numpy as np
     import torch
     import paper_2409_17299_gb300 as q
-    w = W.paper_test_problem(n=n, seed=seed, thin_cap=cap)
+    w = W.paper_test_problem(n=n, seed=seed, thin_cap=cap, periods=periods)
     prec = q.QED_FP32 if precision == "fp32" else q.QED_FP64
     gen = q.Generator(q.make_config(precision=prec, seed=w.seed, push_photons=1, thin_cap=cap,
                                     sampler=q.QED_SAMPLER_MLP if mlp_params is not None else q.QED_SAMPLER_TABLE))
@@ -924,7 +953,7 @@ def growth_run(precision, seed, mlp_params=None, n=250_000, cap=GROWTH_CAP, hook
         lnw.append(math.log(float(tot)))
     secs = time.perf_counter() - t0
     t = (np.arange(w.nsteps) + 1) * w.dt
-    a, b = GROWTH_FIT
+    a, b = fit
     gamma = float(np.polyfit(t[a:b], np.array(lnw[a:b]), 1)[0] * 2 * math.pi)
     xs, ws = [], []
     for k in (0, 1):

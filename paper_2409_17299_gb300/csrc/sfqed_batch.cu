@@ -149,11 +149,11 @@ __device__ __forceinline__ bool fused_advance(const FusedCtx &c, const FieldView
     else if constexpr (FRESH) { no_event = dth > b.dt; h = b.dt; }
     else { no_event = tau + (double)dth > b.dt; h = (T)(b.dt - tau); }
     if (no_event) {
-        boris<T>(x, p, q, E, B, h);
+        boris<T>(x, p, q, E, B, h, false, id, step, k);
         tau = b.dt;
         return false;
     }
-    boris<T>(x, p, q, E, B, dth);
+    boris<T>(x, p, q, E, B, dth, false, id, step, k);
     if constexpr (FRESH) tau = (double)dth;
     else tau += (double)dth;
     return true;

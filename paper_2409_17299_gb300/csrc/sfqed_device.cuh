@@ -402,14 +402,53 @@ __device__ __forceinline__ T photon_chi(T k0, const T k[3], const T E[3], const 
 }
 
 // ---------------------------------------------------------------------------
+// FP32 position update.  Rounding x + dx to the nearest float loses every
+// displacement below half an ulp of x (an ulp is 2.4e-7 at |x| ~ pi) and
+// biases those of a few ulp: a slow lepton at an electric antinode away from
+// the origin would stop moving in x, stay in the strongest field and radiate
+// there, which the FP64 arithmetic does not do (over 20 wave periods of the
+// standing-wave cascade such leptons piled up at x = +-pi and raised the
+// growth rate by ~3%).  Displacements of at least 2^-16 |x| take the plain
+// sum (rounding changes them by at most 2^-7 of themselves); smaller ones are
+// rounded stochastically to one of the two neighbouring floats, with the
+// probabilities that make the expected result x + dx exact (the rounding
+// error from TwoSum, written with explicitly rounded operations so that no
+// step is contracted).  The random bits come from (id, step, k, coordinate).
+__device__ __forceinline__ uint32_t round_bits(unsigned long long id, unsigned step, unsigned k) {
+    // a lowbias32-style integer finaliser (xor-shifts and odd multipliers)
+    uint32_t h = (uint32_t)id ^ ((uint32_t)(id >> 32) * 0x9E3779B1u) ^ (step * 0x85EBCA77u) ^ (k * 0xC2B2AE3Du);
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ float add_sr(float x, float dx, unsigned long long id, unsigned step, unsigned k) {
+    const float s = __fadd_rn(x, dx);
+    if (!(fabsf(dx) < __fmul_rn(fabsf(x), 0x1p-16f))) return s;
+    const float bp = __fsub_rn(s, x);
+    const float err = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bp)), __fsub_rn(dx, bp));   // x + dx - s exactly
+    if (err == 0.f || s == 0.f) return s;
+    const int bits = __float_as_int(s);
+    const float nb = __int_as_float(bits + (((err > 0.f) == (s > 0.f)) ? 1 : -1));   // neighbour on err's side
+    const float gap = fabsf(__fsub_rn(nb, s));
+    const uint32_t r = round_bits(id, step, k);
+    return __fmul_rn((float)(r >> 8) * 0x1p-24f, gap) < fabsf(err) ? nb : s;
+}
+
+// ---------------------------------------------------------------------------
 // Boris push: half electric kick, magnetic rotation, half kick, then
-// x += p/gamma h with the new momentum.  q = -1 (e-) or +1 (e+).  no_b: B = 0
+// x += p/gamma h with the new momentum (FP32: add_sr, keyed by the particle's
+// id, the step and its iteration k).  q = -1 (e-) or +1 (e+).  no_b: B = 0
 // wherever the field is evaluated (the rotation is the identity and is
 // skipped).  FP32 mode takes 1/gamma from the hardware reciprocal square root
 // and the rotation factor from the fast division.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ void boris(T x[3], T p[3], T q, const T E[3], const T B[3], T h, bool no_b = false) {
+__device__ __forceinline__ void boris(T x[3], T p[3], T q, const T E[3], const T B[3], T h, bool no_b,
+                                      unsigned long long id, unsigned step, unsigned k) {
     const T qh2 = (T)0.5 * q * h;
     T m0 = p[0] + qh2 * E[0], m1 = p[1] + qh2 * E[1], m2 = p[2] + qh2 * E[2];
     if (!no_b) {
@@ -427,12 +466,17 @@ __device__ __forceinline__ void boris(T x[3], T p[3], T q, const T E[3], const T
     p[0] = m0 + qh2 * E[0];
     p[1] = m1 + qh2 * E[1];
     p[2] = m2 + qh2 * E[2];
-    T vh;
-    if constexpr (sizeof(T) == 8) vh = h / sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    else vh = h * rsqrtf(1.0f + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    x[0] += p[0] * vh;
-    x[1] += p[1] * vh;
-    x[2] += p[2] * vh;
+    if constexpr (sizeof(T) == 8) {
+        const double vh = h / sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+        x[0] += p[0] * vh;
+        x[1] += p[1] * vh;
+        x[2] += p[2] * vh;
+    } else {
+        const float vh = h * rsqrtf(1.0f + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+        x[0] = add_sr(x[0], __fmul_rn(p[0], vh), id, step, 3u * k);
+        x[1] = add_sr(x[1], __fmul_rn(p[1], vh), id, step, 3u * k + 1u);
+        x[2] = add_sr(x[2], __fmul_rn(p[2], vh), id, step, 3u * k + 2u);
+    }
 }
 
 // ---------------------------------------------------------------------------

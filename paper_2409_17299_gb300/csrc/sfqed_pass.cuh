@@ -186,11 +186,11 @@ __device__ __forceinline__ bool advance(const LeptonCtx<T> &c, T x[3], T p[3], T
         h = rf;
     } else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
     if (no_event) {
-        boris<T>(x, p, q, E, B, h, a.field_zero == 1);
+        boris<T>(x, p, q, E, B, h, a.field_zero == 1, id, c.tm.step, k);
         tau = a.dt;
         return false;
     }
-    boris<T>(x, p, q, E, B, dth, a.field_zero == 1);
+    boris<T>(x, p, q, E, B, dth, a.field_zero == 1, id, c.tm.step, k);
     if constexpr (FRESH) tau = (double)dth;
     else tau += (double)dth;
     return true;
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_lepton_od(Pas
         const T lam = p2 > (T)0 ? c.alpha_r / gam * rate_em<T>(c.coef, chi) : (T)0;
         od = od_advance<T>(a, tm.step, id, od, lam);
         const T qch = s == 0 ? (T)-1 : (T)1;
-        boris<T>(x, p, qch, E, B, dt_of<T>(a), a.field_zero == 1);
+        boris<T>(x, p, qch, E, B, dt_of<T>(a), a.field_zero == 1, id, tm.step, 0u);
         unsigned k = 0;
         if (od <= (T)0) {
             // the event at the end of the step
