@@ -54,7 +54,9 @@ enum { QED_FP64 = 0,        /* all arithmetic and storage in FP64 */
        QED_FP32 = 1 };      /* FP32 storage, push, rates and sampling; chi in a
                                cancellation-free FP32 form with an FP64 fallback
                                where cancellation is detected; the event clock of
-                               the sub-steps after a particle's first in FP64 */
+                               the sub-steps after a particle's first in FP64;
+                               lepton displacements below 2^-16 |x| rounded
+                               stochastically (unbiased, keyed by id and step) */
 enum { QED_SAMPLER_TABLE = 0, QED_SAMPLER_MLP = 1 };
 enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 };
 
