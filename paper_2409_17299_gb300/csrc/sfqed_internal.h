@@ -65,6 +65,7 @@ struct DevCtl {
     unsigned long long pass_limit;      // newborn passes a step may run (then timeout)
     unsigned long long pad[4];
 };
+static_assert(sizeof(DevCtl) == 384, "control block layout");
 
 // The current step's time as the pass kernels read it from the control
 // block (written by the step-begin kernel, so a captured step graph needs no
