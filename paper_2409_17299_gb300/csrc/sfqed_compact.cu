@@ -197,6 +197,7 @@ __global__ void k_set_count(DevCtl *ctl, int s) {
 }
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+constexpr unsigned long long INF_BITS = 0x7ff0000000000000ull;    // +inf as double bits
 
 // ---- leveling: device-resident piecewise-exact Newton iteration ----
 // S(w) = sum_i min(1, w_i / w) = A(w) / w + C(w) with A = sum of weights below
@@ -284,9 +285,15 @@ __host__ __device__ __forceinline__ void lev_finish(LevelIter &it, double wstar)
 }
 
 // Newton step from the sums at it.w: A (weights below w), C (count at or
-// above w), N (alive count), M (largest weight, double bits)
+// above w), N (alive count), M (largest weight, double bits).  PL and PH
+// (double bits; PH = 0: not given) bound the piece of w: the largest weight
+// below w and the smallest at or above it.  A Newton point c with
+// PL < c <= PH lies on w's piece, where A and C are those just summed, so the
+// next pass would return c itself and finish there: the iteration finishes at
+// c now, with the same result and one pass fewer.
 __host__ __device__ void lev_advance(LevelIter &it, double A, unsigned long long C, unsigned long long N,
-                                     unsigned long long M, long long cap) {
+                                     unsigned long long M, long long cap, unsigned long long PL = 0,
+                                     unsigned long long PH = 0) {
     const double inf = double_of_bits(0x7ff0000000000000ull);
     const double w = it.w;
     if (it.iters == 0) {                           // first pass: at +inf or at a warm start w
@@ -306,10 +313,15 @@ __host__ __device__ void lev_advance(LevelIter &it, double A, unsigned long long
     ++it.iters;
     double c = (double)cap > (double)C ? A / ((double)cap - (double)C) : inf;
     if (c == w) { lev_finish(it, w); return; }     // root of its own piece
-    if (!(c > it.lo && c <= it.hi)) c = 0.5 * (it.lo + it.hi);
+    const bool newton = c > it.lo && c <= it.hi;
+    if (!newton) c = 0.5 * (it.lo + it.hi);
     // stop at double resolution of the bracket (hi, evaluated, is the answer)
     if (!(c > it.lo && c <= it.hi) || (c == it.hi && it.hi == w) || it.iters >= LEVEL_ITERS) {
         lev_finish(it, it.hi);
+        return;
+    }
+    if (newton && PH != 0 && c > double_of_bits(PL) && c <= double_of_bits(PH)) {
+        lev_finish(it, c);
         return;
     }
     it.w = c;
@@ -326,21 +338,29 @@ constexpr int LEV_T = 256;
 template <class T>
 __device__ __forceinline__ void lev_accumulate(const void *w, unsigned long long n, unsigned long long t0,
                                                unsigned long long stride, const LevelIter &it, double &A,
-                                               unsigned long long &C, unsigned long long &N, unsigned long long &M) {
+                                               unsigned long long &C, unsigned long long &N, unsigned long long &M,
+                                               unsigned long long &L, unsigned long long &H) {
     C = 0;
     N = 0;
     M = 0;
+    L = 0;
+    H = INF_BITS;
     if constexpr (sizeof(T) == 4) {
         // FP32 weights: exact float comparisons and float-float sums, no FP64 per element
         const float wc = it.w_up;
         FF acc;
-        unsigned mb = 0, c = 0, nn = 0;
+        unsigned mb = 0, c = 0, nn = 0, lb = 0, hb = 0x7f800000u;    // positive floats order like their bits
         auto one = [&](float v) {
             if (v > 0.f) {
                 ++nn;
                 mb = max(mb, __float_as_uint(v));
-                if (v < wc) acc.add(v);
-                else ++c;
+                if (v < wc) {
+                    acc.add(v);
+                    lb = max(lb, __float_as_uint(v));
+                } else {
+                    ++c;
+                    hb = min(hb, __float_as_uint(v));
+                }
             }
         };
         const float *wf = reinterpret_cast<const float *>(w);
@@ -368,6 +388,8 @@ __device__ __forceinline__ void lev_accumulate(const void *w, unsigned long long
         C = c;
         N = nn;
         M = nn ? dbits((double)__uint_as_float(mb)) : 0ull;
+        L = lb ? dbits((double)__uint_as_float(lb)) : 0ull;
+        H = hb < 0x7f800000u ? dbits((double)__uint_as_float(hb)) : INF_BITS;
     } else {
         const double wc = it.w;
         double comp = 0.0;           // Kahan
@@ -382,8 +404,10 @@ __device__ __forceinline__ void lev_accumulate(const void *w, unsigned long long
                 const double t = A + y;
                 comp = (t - A) - y;
                 A = t;
+                L = max(L, dbits(v));
             } else {
                 ++C;
+                H = min(H, dbits(v));
             }
         }
     }
@@ -402,28 +426,34 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
     const unsigned long long t0 = (unsigned long long)blockIdx.x * LEV_T + threadIdx.x;
     const unsigned long long stride = (unsigned long long)gridDim.x * LEV_T;
     double A;
-    unsigned long long C, N, M;
-    lev_accumulate<T>(w, n, t0, stride, it, A, C, N, M);
+    unsigned long long C, N, M, L, H;
+    lev_accumulate<T>(w, n, t0, stride, it, A, C, N, M, L, H);
     __shared__ double sA[LEV_T / 32];
-    __shared__ unsigned long long sC[LEV_T / 32], sN[LEV_T / 32], sM[LEV_T / 32];
+    __shared__ unsigned long long sC[LEV_T / 32], sN[LEV_T / 32], sM[LEV_T / 32], sL[LEV_T / 32], sH[LEV_T / 32];
     __shared__ int s_last;
     for (int o = 16; o > 0; o >>= 1) {
         A += __shfl_down_sync(0xffffffffu, A, o);
         C += __shfl_down_sync(0xffffffffu, C, o);
         N += __shfl_down_sync(0xffffffffu, N, o);
         M = max(M, __shfl_down_sync(0xffffffffu, M, o));
+        L = max(L, __shfl_down_sync(0xffffffffu, L, o));
+        H = min(H, __shfl_down_sync(0xffffffffu, H, o));
     }
     const int wid = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { sA[wid] = A; sC[wid] = C; sN[wid] = N; sM[wid] = M; }
+    if ((threadIdx.x & 31) == 0) { sA[wid] = A; sC[wid] = C; sN[wid] = N; sM[wid] = M; sL[wid] = L; sH[wid] = H; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0;
-        unsigned long long c = 0, nn = 0, m = 0;
-        for (int k = 0; k < LEV_T / 32; ++k) { a += sA[k]; c += sC[k]; nn += sN[k]; m = max(m, sM[k]); }
+        unsigned long long c = 0, nn = 0, m = 0, pl = 0, ph = INF_BITS;
+        for (int k = 0; k < LEV_T / 32; ++k) {
+            a += sA[k]; c += sC[k]; nn += sN[k]; m = max(m, sM[k]); pl = max(pl, sL[k]); ph = min(ph, sH[k]);
+        }
         lw->partA[blockIdx.x] = a;
         lw->partC[blockIdx.x] = c;
         lw->partN[blockIdx.x] = nn;
         lw->partM[blockIdx.x] = m;
+        lw->partL[blockIdx.x] = pl;
+        lw->partH[blockIdx.x] = ph;
         __threadfence();
         const unsigned prev = atomicAdd(&lw->arrive[s], 1u);
         s_last = prev == gridDim.x - 1;
@@ -433,17 +463,19 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
     __threadfence();
     // the last block: partials b = t, t + LEV_T, ... per thread, then a tree of fixed shape
     __shared__ double rh[LEV_T], rl[LEV_T];
-    __shared__ unsigned long long rc[LEV_T], rn[LEV_T], rm[LEV_T];
+    __shared__ unsigned long long rc[LEV_T], rn[LEV_T], rm[LEV_T], rpl[LEV_T], rph[LEV_T];
     const int t = threadIdx.x;
     DD acc;
-    unsigned long long c = 0, nn = 0, m = 0;
+    unsigned long long c = 0, nn = 0, m = 0, pl = 0, ph = INF_BITS;
     for (int b = t; b < (int)gridDim.x; b += LEV_T) {
         acc.add(__ldcg(&lw->partA[b]));
         c += __ldcg(&lw->partC[b]);
         nn += __ldcg(&lw->partN[b]);
         m = max(m, __ldcg(&lw->partM[b]));
+        pl = max(pl, __ldcg(&lw->partL[b]));
+        ph = min(ph, __ldcg(&lw->partH[b]));
     }
-    rh[t] = acc.hi; rl[t] = acc.lo; rc[t] = c; rn[t] = nn; rm[t] = m;
+    rh[t] = acc.hi; rl[t] = acc.lo; rc[t] = c; rn[t] = nn; rm[t] = m; rpl[t] = pl; rph[t] = ph;
     __syncthreads();
     for (int o = LEV_T / 2; o > 0; o >>= 1) {
         if (t < o) {
@@ -457,6 +489,8 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
             rc[t] += rc[t + o];
             rn[t] += rn[t + o];
             rm[t] = max(rm[t], rm[t + o]);
+            rpl[t] = max(rpl[t], rpl[t + o]);
+            rph[t] = min(rph[t], rph[t + o]);
         }
         __syncthreads();
     }
@@ -467,7 +501,7 @@ __global__ void __launch_bounds__(LEV_T) k_lev_step(const void *w, const DevCtl 
             it.sumN = rn[0];
             it.sumM = rm[0];
         } else {
-            lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap);
+            lev_advance(it, rh[0] + rl[0], rc[0], rn[0], rm[0], cap, rpl[0], rph[0]);
             if (it.done && it.wstar > 0.0) lw->prev[s] = it.wstar;
         }
         lw->arrive[s] = 0;
@@ -529,35 +563,50 @@ __global__ void __launch_bounds__(LT, 4) k_tile_dead(SpeciesDev S, DevCtl *ctl, 
         wnew = it.wstar_f;
     }
     unsigned removed = 0;
+    // FP32 leveling: groups of four entries whose draws are computed together
+    constexpr bool SPEC = LEVEL && sizeof(T) == 4;
+    constexpr int G = SPEC ? 4 : 8;           // entries per group of loads
+    static_assert(LROUNDS % G == 0, "groups tile the rounds");
     for (long long tile = blockIdx.x; tile < nbe; tile += gridDim.x) {
         const unsigned long long base = (unsigned long long)tile * LTILE;
         const unsigned long long wbase = base + (unsigned long long)wid * LSPAN;
         unsigned mask[LROUNDS];
         unsigned cnt = 0;
 #pragma unroll
-        for (int c0 = 0; c0 < LROUNDS; c0 += 8) {
-            // weights and (leveling) ids of eight entries issued together: at
+        for (int c0 = 0; c0 < LROUNDS; c0 += G) {
+            // weights and (leveling) ids of G entries issued together: at
             // the cap nearly every entry is below w* and needs its id
-            T v[8];
-            unsigned long long idv[8];
+            T v[G];
+            unsigned long long idv[G];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < G; ++r) {
                 const unsigned long long i = wbase + (c0 + r) * 32 + lane;
                 v[r] = i < n ? ld<T>(S.w, i) : (T)0;
                 idv[r] = (LEVEL && thin && i < n) ? S.id[i] : 0ull;
             }
-            bool below[8];
+            bool below[G];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < G; ++r) {
                 if constexpr (sizeof(T) == 4) below[r] = LEVEL && thin && v[r] > (T)0 && (float)v[r] < wup;
                 else below[r] = LEVEL && thin && v[r] > (T)0 && (double)v[r] < wstar;
             }
+            // FP32 leveling: the G draws are computed together, outside the
+            // per-entry branch, so their Philox rounds interleave (one draw
+            // per branch ran the ten dependent rounds back to back); only the
+            // entries below w* use theirs
+            uint4 qv[G];
+            if constexpr (SPEC) {
+                if (thin) {
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+                    for (int r = 0; r < G; ++r) qv[r] = event_draw(keys, idv[r], step, 0xFFFFFFFFu);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < G; ++r) {
                 const unsigned long long i = wbase + (c0 + r) * 32 + lane;
                 bool dead = i < n && !(v[r] > (T)0);
                 if (LEVEL && below[r]) {
-                    const uint4 q = event_draw(keys, idv[r], step, 0xFFFFFFFFu);
+                    const uint4 q = SPEC ? qv[r] : event_draw(keys, idv[r], step, 0xFFFFFFFFu);
                     const float uf = __uint2float_rn(q.x) * 0x1p-32f;     // u to within 2^-32 + FP32 rounding
                     const float pf = (float)v[r] * inv_f;
                     bool keep;

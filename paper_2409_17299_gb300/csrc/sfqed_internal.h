@@ -100,6 +100,8 @@ struct LevelWork {
     unsigned long long partC[LEVEL_MAX_BLOCKS]; // count at or above w
     unsigned long long partN[LEVEL_MAX_BLOCKS]; // alive count
     unsigned long long partM[LEVEL_MAX_BLOCKS]; // largest weight (double bits)
+    unsigned long long partL[LEVEL_MAX_BLOCKS]; // largest weight below w (double bits; 0: none)
+    unsigned long long partH[LEVEL_MAX_BLOCKS]; // smallest weight at or above w (double bits; +inf: none)
 };
 
 // Philox round keys of one seed: k[2 r], k[2 r + 1] are the key of round r

@@ -499,6 +499,70 @@ __device__ __forceinline__ void pair_create(const PassArgs &a, const StepTime &t
     }
 }
 
+// One photon of a pass from its loaded state (index i, weight w, position x,
+// momentum k, id): straight flight, pair creation at the event (the photon
+// is removed: weight 0 and its event count stored here).  Returns false for
+// a dead photon (weight 0: nothing to do and nothing to store); otherwise x
+// holds the new position, which the caller stores, and k the events.
+template <class T, bool FRESH>
+__device__ __forceinline__ bool photon_step(const PassArgs &a, const StepTime &tm, const T *s_coef, const T *icdf,
+                                            const Phase<T> &ph0, const SpeciesDev &S, unsigned i, T w, T x[3],
+                                            T kx, T ky, T kz, unsigned long long id, unsigned &k, unsigned &n64) {
+    k = 0;
+    if (!(w > (T)0)) return false;
+    const T alpha_r = (T)(ALPHA * RS);
+    double tau = FRESH ? 0.0 : S.tau[i];
+    const T kv[3] = {kx, ky, kz};
+    const T k0 = f_sqrt(kx * kx + ky * ky + kz * kz);
+    if (k0 > (T)0) {
+        const T inv = f_div((T)1, k0);
+        const T nx = kx * inv, ny = ky * inv, nz = kz * inv;
+        // one waiting time: the photon either reaches the step end or converts
+        if (FRESH || before_step_end(tau, a.dt)) {
+            T E[3], B[3];
+            if constexpr (FRESH) field_at<T>(a, x, ph0, E, B);
+            else field_tau<T>(a, tm, x, tau, E, B);
+            T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
+            T lam;
+            if constexpr (sizeof(T) == 4) lam = alpha_r * inv * rate_pair<T>(s_coef, chi);
+            else lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);     // the oracle's rounding
+            uint4 r = make_uint4(0, 0, 0, 0);
+            T dth = t_inf<T>();
+            if (lam > lam_skip<T>(a)) {
+                r = event_draw(a.keys, id, tm.step, k);
+                T uw, vw;
+                Uniform<T>::draw(r.x, r.y, uw, vw);
+                dth = f_div(Uniform<T>::neglog(uw, vw), lam);
+            }
+            bool no_event;
+            T h;
+            if constexpr (FRESH && sizeof(T) == 4) { no_event = dth >= a.dt_f_gt; h = a.dt_f; }
+            else if constexpr (FRESH) { no_event = dth > a.dt; h = a.dt; }
+            else if constexpr (sizeof(T) == 4) {
+                // as in the lepton pass: the FP64 test decided in FP32 outside a margin
+                const float rf = __double2float_rn(a.dt - tau);
+                const float marg = fmaf(rf, 0x1p-20f, a.dt_f * 0x1p-40f);
+                if (dth > rf + marg) no_event = true;
+                else if (dth < rf - marg) no_event = false;
+                else no_event = tau + (double)dth > a.dt;
+                h = rf;
+            } else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
+            if (no_event) {
+                x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
+            } else {
+                x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
+                if constexpr (FRESH) tau = (double)dth;
+                else tau += (double)dth;
+                pair_create<T>(a, tm, icdf, x, kv, k0, nx, ny, nz, tau, w, id, k, make_uint2(r.z, r.w), n64);
+                k = 1;
+                st<T>(S.w, i, (T)0);       // the photon is eliminated
+                S.nev[i] += k;
+            }
+        }
+    }
+    return true;
+}
+
 // Photon push: straight flight, pair creation at the event, the photon is
 // removed (weight 0) and the pair appended.
 template <class T, bool FRESH>
@@ -514,7 +578,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
     // 32-bit indices (a species holds fewer than 2^31 entries)
     const unsigned b = (unsigned)ctl->begin[2], n = (unsigned)(ctl->end[2] - ctl->begin[2]);
     const T *icdf = reinterpret_cast<const T *>(a.icdf_pair);
-    const T alpha_r = (T)(ALPHA * RS);
     const SpeciesDev &S = a.sp[2];
     unsigned long long my_steps = 0, my_ev = 0;
     unsigned my_max = 0, n64 = 0;
@@ -568,59 +631,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 4 : 1)) k_photon_pass(P
             kx = ld<T>(S.px, i); ky = ld<T>(S.py, i); kz = ld<T>(S.pz, i);
             id = __ldg(S.id + i);
         }
-        if (!(w > (T)0)) continue;
-        double tau = FRESH ? 0.0 : S.tau[i];
-        const T kv[3] = {kx, ky, kz};
-        const T k0 = f_sqrt(kx * kx + ky * ky + kz * kz);
-        unsigned k = 0;
-        if (k0 > (T)0) {
-            const T inv = f_div((T)1, k0);
-            const T nx = kx * inv, ny = ky * inv, nz = kz * inv;
-            // one waiting time: the photon either reaches the step end or converts
-            if (FRESH || before_step_end(tau, a.dt)) {
-                T E[3], B[3];
-                if constexpr (FRESH) field_at<T>(a, x, ph0, E, B);
-                else field_tau<T>(a, tm, x, tau, E, B);
-                T chi = photon_chi<T>(k0, kv, E, B, n64, a.field_zero);
-                T lam;
-                if constexpr (sizeof(T) == 4) lam = alpha_r * inv * rate_pair<T>(s_coef, chi);
-                else lam = alpha_r / k0 * rate_pair<T>(s_coef, chi);     // the oracle's rounding
-                uint4 r = make_uint4(0, 0, 0, 0);
-                T dth = t_inf<T>();
-                if (lam > lam_skip<T>(a)) {
-                    r = event_draw(a.keys, id, tm.step, k);
-                    T uw, vw;
-                    Uniform<T>::draw(r.x, r.y, uw, vw);
-                    dth = f_div(Uniform<T>::neglog(uw, vw), lam);
-                }
-                bool no_event;
-                T h;
-                if constexpr (FRESH && sizeof(T) == 4) { no_event = dth >= a.dt_f_gt; h = a.dt_f; }
-                else if constexpr (FRESH) { no_event = dth > a.dt; h = a.dt; }
-                else if constexpr (sizeof(T) == 4) {
-                    // as in the lepton pass: the FP64 test decided in FP32 outside a margin
-                    const float rf = __double2float_rn(a.dt - tau);
-                    const float marg = fmaf(rf, 0x1p-20f, a.dt_f * 0x1p-40f);
-                    if (dth > rf + marg) no_event = true;
-                    else if (dth < rf - marg) no_event = false;
-                    else no_event = tau + (double)dth > a.dt;
-                    h = rf;
-                } else { no_event = tau + (double)dth > a.dt; h = (T)(a.dt - tau); }
-                if (no_event) {
-                    x[0] += nx * h; x[1] += ny * h; x[2] += nz * h;
-                    tau = a.dt;
-                } else {
-                x[0] += nx * dth; x[1] += ny * dth; x[2] += nz * dth;
-                if constexpr (FRESH) tau = (double)dth;
-                else tau += (double)dth;
-                pair_create<T>(a, tm, icdf, x, kv, k0, nx, ny, nz, tau, w, id, k, make_uint2(r.z, r.w), n64);
-                w = (T)0;       // the photon is eliminated
-                k = 1;
-                }
-            }
-        }
+        unsigned k;
+        if (!photon_step<T, FRESH>(a, tm, s_coef, icdf, ph0, S, i, w, x, kx, ky, kz, id, k, n64)) continue;
         st<T>(S.x, i, x[0]); st<T>(S.y, i, x[1]); st<T>(S.z, i, x[2]);
-        if (k) { st<T>(S.w, i, w); S.nev[i] += k; }
         ++my_steps;
         my_ev += k;
         my_max = max(my_max, k);
