@@ -311,7 +311,9 @@ qed_status qed_mlp_grad(qed_ctx *ctx, const float *feat_dev, const float *target
  *     qed_level_apply(ctx, &my_particles, s, st.wstar, step);
  * The iteration is the one a single GPU runs on the device (piecewise-exact
  * Newton steps inside a bisection bracket), so every rank holds the same
- * state after each advance.  Keep/drop draws are keyed on particle id and
+ * state after each advance.  (The device iteration also reduces the bounds
+ * of the evaluated piece and stops one pass early when the Newton point
+ * lies between them; the threshold is the same.)  Keep/drop draws are keyed on particle id and
  * step, so the survivors do not depend on how the species is split. */
 typedef struct {
     double lo, hi;      /* bracket of w*: S(lo) > cap >= S(hi) */
